@@ -1,0 +1,148 @@
+"""Pins of the oracle's SSA (Sec. 2.2, Eq. 1-2) against closed forms and exact
+CME solutions.  Every check is statistical with a fixed seed; bounds are set
+at >= 4 sigma so a correct implementation passes and a dropped term, wrong
+sign, wrong propensity or wrong selection fails by a wide margin."""
+import math
+
+import numpy as np
+import pytest
+from scipy import stats
+
+import workloads
+from tests import _cme
+
+
+def _chi2_ok(obs, expected_p, alpha=1e-4):
+    """Pearson chi-square with bins of expected count < 5 merged."""
+    n = obs.sum()
+    e = expected_p * n
+    o_b, e_b = [], []
+    acc_o = acc_e = 0.0
+    for oi, ei in zip(obs, e):
+        acc_o += oi
+        acc_e += ei
+        if acc_e >= 5:
+            o_b.append(acc_o); e_b.append(acc_e)
+            acc_o = acc_e = 0.0
+    if acc_e > 0:
+        o_b[-1] += acc_o; e_b[-1] += acc_e
+    o_b, e_b = np.asarray(o_b), np.asarray(e_b)
+    chi2 = ((o_b - e_b) ** 2 / e_b).sum()
+    return chi2 < stats.chi2.ppf(1 - alpha, len(o_b) - 1), chi2
+
+
+def test_pure_decay_binomial(orc):
+    # A -> 0 at rate k A: A(T) ~ Binomial(A0, exp(-k T)).
+    A0, k, T = 1000, 1.0, 1.0
+    m, p = workloads.pure_decay(A0, k, T)
+    r = orc.run(m, p, seed=11, n_traj=4000, want_x=True)
+    assert (r['status'] == 0).all() and (r['verdict'] == 1).all()
+    a = r['x_final'][:, 0]
+    q = math.exp(-k * T)
+    mean, var = A0 * q, A0 * q * (1 - q)
+    assert abs(a.mean() - mean) < 4.5 * math.sqrt(var / a.size)
+    assert abs(a.var() / var - 1) < 0.12
+    ks = np.arange(A0 + 1)
+    hist = np.bincount(a, minlength=A0 + 1)
+    ok, chi2 = _chi2_ok(hist, stats.binom.pmf(ks, A0, q))
+    assert ok, chi2
+    # the final state is the state occupied at T: entered at or before T
+    assert (r['t_final'] <= T).all()
+
+
+def test_immigration_death_poisson(orc):
+    # 0 -> A (k1), A -> 0 (k2 A) from A0 = 0: A(T) ~ Poisson(k1/k2 (1 - e^{-k2 T})).
+    m, _ = workloads.immigration_death()
+    T = 60.0
+    p = workloads.Property([workloads.atom(['A'], 'A', '>=', 0)], ('G', 0.0, T, ('atom', 0)))
+    r = orc.run(m, p, seed=5, n_traj=3000, want_x=True)
+    a = r['x_final'][:, 0]
+    lam = 10.0 / 0.1 * (1 - math.exp(-0.1 * T))
+    assert abs(a.mean() - lam) < 4.5 * math.sqrt(lam / a.size)
+    assert abs(a.var() / lam - 1) < 0.12
+    ks = np.arange(a.max() + 40)
+    ok, chi2 = _chi2_ok(np.bincount(a, minlength=ks.size), stats.poisson.pmf(ks, lam))
+    assert ok, chi2
+
+
+def test_immigration_event_count_poisson(orc):
+    # 0 -> A at rate k: the number of events with entry time <= T is Poisson(kT).
+    k, T = 5.0, 10.0
+    m, p = workloads.immigration_only(k, T)
+    r = orc.run(m, p, seed=9, n_traj=4000)
+    ev = r['events'].astype(np.int64)
+    lam = k * T
+    assert abs(ev.mean() - lam) < 4.5 * math.sqrt(lam / ev.size)
+    ok, chi2 = _chi2_ok(np.bincount(ev, minlength=120), stats.poisson.pmf(np.arange(120), lam))
+    assert ok, chi2
+
+
+def test_homodimer_two_molecules(orc):
+    # 2A -> B from A0 = 2: exactly one pair, so h = 1 and the reaction
+    # happens by time t with probability 1 - exp(-c t).
+    sp = ['A', 'B']
+    c, t = 0.7, 1.3
+    m = workloads.Model('dimer2', sp, [[0, 0]], [[-2, 1]], [[c]], [[2, 0]])
+    p = workloads.Property([workloads.atom(sp, 'B', '>=', 1)], ('F', 0.0, t, ('atom', 0)))
+    r = orc.run(m, p, seed=3, n_traj=20000)
+    exact = 1 - math.exp(-c * t)
+    assert abs(r['verdict'].mean() - exact) < 4.5 * math.sqrt(exact * (1 - exact) / 20000)
+
+
+def test_heterodimer_and_selection_against_cme(orc):
+    # A + B -> C (c1) competing with A -> 0 (c2); P(F[0,T] C >= 2) by CME.
+    sp = ['A', 'B', 'C']
+    m = workloads.Model('hetero', sp, [[0, 1], [0, -1]], [[-1, -1, 1], [-1, 0, 0]],
+                        [[0.05, 0.4]], [[6, 4, 0]])
+    T = 1.5
+    p = workloads.Property([workloads.atom(sp, 'C', '>=', 2)], ('F', 0.0, T, ('atom', 0)))
+    exact = _cme.eventually_probability(m, lambda x: x[2] >= 2, T)
+    n = 20000
+    r = orc.run(m, p, seed=21, n_traj=n)
+    assert abs(r['verdict'].mean() - exact) < 4.5 * math.sqrt(exact * (1 - exact) / n)
+
+
+def test_c1_matches_exact_cme(orc):
+    # Immigration-death, F[0,100](A >= 130): exact value from the CME with
+    # A = 130 absorbing (a 131-state chain), compared with 10,000 oracle
+    # trajectories at Philox seed 0.
+    m, p = workloads.immigration_death()
+    exact = _cme.eventually_probability(m, lambda x: x[0] >= 130, 100.0)
+    assert abs(exact - 0.0912186) < 5e-7
+    r = orc.run(m, p, seed=0, n_traj=10000)
+    from oracle import wilson
+    _, lo, hi = wilson.wilson_interval(int(r['verdict'].sum()), 10000, 0.9999)
+    assert lo <= exact <= hi
+    # on-the-fly stopping: every true verdict stops at the first state with A = 130
+    # and every false one at the first draw past t = 100
+    assert (r['t_final'][r['verdict'] == 1] <= 100.0).all()
+
+
+def test_instances_and_trajectories_are_independent_streams(orc):
+    # different trajectory ids / instances give different paths; the same id
+    # gives the same path whatever range it is run in.
+    m, p = workloads.immigration_death(n_inst=2)
+    a = orc.run(m, p, seed=1, instance=0, traj_begin=0, n_traj=50)
+    b = orc.run(m, p, seed=1, instance=0, traj_begin=20, n_traj=10)
+    assert (a['events'][20:30] == b['events']).all()
+    assert (a['t_final'][20:30] == b['t_final']).all()
+    c = orc.run(m, p, seed=1, instance=1, traj_begin=0, n_traj=50)
+    assert (a['events'] != c['events']).sum() > 40
+    d = orc.run(m, p, seed=2, instance=0, traj_begin=0, n_traj=50)
+    assert (a['events'] != d['events']).sum() > 40
+
+
+def test_event_budget_is_reported(orc):
+    m, p = workloads.immigration_death()
+    r = orc.run(m, p, seed=0, n_traj=200, budget=100)
+    assert (r['status'] == 1).sum() > 150
+    assert (r['events'][r['status'] == 1] == 100).all()
+
+
+def test_absorbing_state_closes_the_path(orc):
+    # A -> 0 from A0 = 3 with F[0,100](A >= 5): the path absorbs at A = 0
+    # after exactly 3 events and the verdict is false.
+    m, _ = workloads.pure_decay(3, 1.0, 1.0)
+    p = workloads.Property([workloads.atom(['A'], 'A', '>=', 5)], ('F', 0.0, 100.0, ('atom', 0)))
+    r = orc.run(m, p, seed=0, n_traj=100)
+    assert (r['status'] == 0).all() and (r['verdict'] == 0).all() and (r['events'] == 3).all()
