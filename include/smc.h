@@ -1,0 +1,229 @@
+/*
+ * smc.h -- C ABI of the GB300 statistical model checking library.
+ *
+ * The library estimates P(phi) for a mass-action reaction network and a
+ * time-bounded BLTLc formula phi, as in Ballarini, Forlin, Mazza and Prandi,
+ * "Efficient Parallel Statistical Model Checking of Biochemical Networks"
+ * (PDMC 2009): it generates independent trajectories with Gillespie's direct
+ * method (Sec. 2.2, Eq. 1, 2a, 2b), checks each one on the fly against phi
+ * (Sec. 3.1 semantics, Sec. 3.2 on-the-fly verification) and stops it as soon
+ * as its verdict is fixed, and reduces the verdicts into the Wilson score
+ * interval (Eq. 4) with the iterative sample-size rule (Eq. 5, Fig. 2).
+ *
+ * Every step of that path runs in the library's own CUDA kernels on one GPU.
+ *
+ * Conventions for every entry point:
+ *  - Return value: SMC_OK (0) or a negative SMC_E_* code; no exceptions
+ *    cross the ABI.  smc_last_error() gives a message for the last failure
+ *    on a context.
+ *  - Host pointers are read during the call only; the library copies what
+ *    it keeps (the caller keeps ownership).  Pointers documented as device
+ *    pointers must be device memory of the context's GPU (for example from
+ *    torch), owned by the caller.
+ *  - A context is used by one host thread at a time; calls on one context do
+ *    not overlap.  Work is issued on the context's stream unless a stream is
+ *    passed; entry points that return host results synchronise with it.
+ *  - Trajectory indices are 32-bit per instance (fewer than 2^32
+ *    trajectories per instance per seed).
+ */
+#ifndef SMC_H
+#define SMC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- return codes ------------------------------------------------------ */
+#define SMC_OK 0
+#define SMC_E_INVALID_ARG (-1) /* bad shape, negative or non-finite rate, ... */
+#define SMC_E_OOM (-2)         /* device or host allocation failed             */
+#define SMC_E_CUDA (-3)        /* a CUDA call failed; see smc_last_error       */
+#define SMC_E_UNSUPPORTED (-4) /* formula outside the monitorable fragment     */
+#define SMC_E_STATE (-5)       /* call order: no model / property loaded       */
+#define SMC_E_NO_DEVICE (-6)   /* no CUDA device, or not a device of sm_103    */
+
+/* ---- per-instance status bits (smc_result.status) ----------------------- */
+#define SMC_STATUS_BUDGET 1 /* some trajectories exhausted the event budget */
+
+/* ---- arithmetic of the SSA path ----------------------------------------- */
+#define SMC_PLAIN_FP64 0 /* FP64 propensities, selection and clock          */
+#define SMC_MIXED 1      /* FP32 propensities and selection, exact int32
+                            counts, FP64 clock, FP64 renormalisation of a_0
+                            every 2^k events                                */
+
+/* ---- sample size rule (smc_estimate mode, bits 4..7) --------------------- */
+#define SMC_FIXED_N (0 << 4)      /* run exactly fixed_n trajectories           */
+#define SMC_ITERATIVE (1 << 4)    /* Fig. 2, starting from p = 1                */
+#define SMC_CONSERVATIVE (2 << 4) /* one batch of Wilson_sample(0.5) (Sec. 3.3.1) */
+
+/* ---- formula nodes (postfix order) -------------------------------------- */
+#define SMC_NODE_TRUE 0
+#define SMC_NODE_FALSE 1
+#define SMC_NODE_ATOM 2       /* arg = atom index                          */
+#define SMC_NODE_NOT 3        /* 1 operand                                 */
+#define SMC_NODE_AND 4        /* 2 operands                                */
+#define SMC_NODE_OR 5         /* 2 operands                                */
+#define SMC_NODE_IMPLIES 6    /* 2 operands                                */
+#define SMC_NODE_UNTIL 7      /* phi U[lo,hi] psi: 2 operands (phi first)  */
+#define SMC_NODE_EVENTUALLY 8 /* F[lo,hi] psi = tt U[lo,hi] psi            */
+#define SMC_NODE_ALWAYS 9     /* G[lo,hi] psi = not F[lo,hi] not psi       */
+
+/* ---- atom comparison operators ------------------------------------------ */
+#define SMC_OP_LT 0
+#define SMC_OP_LE 1
+#define SMC_OP_GE 2
+#define SMC_OP_GT 3
+#define SMC_OP_EQ 4
+#define SMC_OP_NE 5
+
+/* ---- options (smc_set_option) ------------------------------------------- */
+#define SMC_OPT_EVENT_BUDGET 0    /* max reactions per trajectory (default 2^24) */
+#define SMC_OPT_RENORM_LOG2 1     /* mixed path: a_0 renormalised every 2^k events (default 8) */
+#define SMC_OPT_AUTOTUNE 2        /* 1 = choose launch shape by timed trials (default 1) */
+#define SMC_OPT_WARPS_PER_BLOCK 3 /* fixed launch shape when autotune is 0 (default 4) */
+#define SMC_OPT_BLOCKS_PER_SM 4   /* 0 = as many as fit (default 0) */
+#define SMC_OPT_REFILL 5          /* refill a warp when >= this many lanes idle (default 1) */
+#define SMC_OPT_RECORD 6          /* 1 = keep per-trajectory verdicts of FIXED_N estimates */
+
+/* A node of the formula in postfix order: operands precede their operator. */
+typedef struct {
+    int32_t kind; /* SMC_NODE_*                                            */
+    int32_t arg;  /* atom index for SMC_NODE_ATOM, else ignored            */
+    double lo;    /* interval [lo, hi] of UNTIL / EVENTUALLY / ALWAYS,      */
+    double hi;    /* 0 <= lo <= hi; hi may be +inf (unbounded, see t_max)   */
+} smc_node;
+
+/* Per-instance estimate. */
+typedef struct {
+    double p_hat;         /* yes / n                                          */
+    double lo, hi;        /* Wilson score interval, Eq. 4                      */
+    uint64_t n;           /* trajectories with a verdict                       */
+    uint64_t yes;         /* trajectories that satisfy phi                     */
+    uint64_t launched;    /* trajectories simulated = n + budget_hits          */
+    uint64_t events;      /* reactions fired, summed over trajectories         */
+    uint64_t budget_hits; /* trajectories stopped by the event budget          */
+    int32_t status;       /* SMC_STATUS_* bits                                 */
+    int32_t iterations;   /* Fig. 2 iterations performed                       */
+} smc_result;
+
+/* Device-side outputs of smc_simulate (all device pointers; NULL = skip). */
+typedef struct {
+    uint64_t *counts; /* [n_inst][4]: yes, n, events, budget_hits; ADDED to  */
+    double *wilson;   /* [n_inst][3]: p_hat, lo, hi of the counts after the call */
+    uint8_t *verdict; /* [n_inst][n_traj]: 1 = phi holds                      */
+    uint8_t *status;  /* [n_inst][n_traj]: 0 decided, 1 event budget          */
+    uint64_t *events; /* [n_inst][n_traj]: reactions fired                    */
+    double *t_final;  /* [n_inst][n_traj]: entry time of the last state       */
+    int32_t *x_final; /* [n_inst][n_traj][S_max]: last state                  */
+} smc_sim_out;
+
+typedef struct smc_ctx smc_ctx;
+
+/* Creates a context on CUDA device `device`.  *out receives the handle.
+ * Errors: SMC_E_NO_DEVICE (no such device / not compute capability 10.3),
+ * SMC_E_OOM, SMC_E_CUDA. */
+int smc_create(smc_ctx **out, int device);
+
+/* Releases the context and its device memory.  NULL is ignored. */
+void smc_destroy(smc_ctx *ctx);
+
+/* Static description of an error code. */
+const char *smc_strerror(int code);
+
+/* Message of the last failure on ctx ("" if none). */
+const char *smc_last_error(const smc_ctx *ctx);
+
+/* Loads one reaction network (Sec. 2.2) with n_instances parameter sets.
+ *  reactants [R][2]: species index of each reactant or -1 (reaction order
+ *      <= 2; two equal indices = homodimer S_a + S_a, propensity
+ *      c x_a (x_a - 1) / 2; one index: c x_a; none: c; two: c x_a x_b).
+ *  stoich [R][S]: net change v_ji of species i when reaction j fires.
+ *  rates [n_instances][R]: stochastic rate constants c_j (finite, >= 0).
+ *  x0 [n_instances][S]: initial counts (>= 0).
+ * Replaces any previous model.  Errors: SMC_E_INVALID_ARG. */
+int smc_load_model(smc_ctx *ctx, int n_species, int n_reactions, const int32_t *reactants,
+                   const int32_t *stoich, const double *rates, const int32_t *x0,
+                   int n_instances);
+
+/* Loads n_instances networks of different sizes in one batch.
+ *  n_species[m], n_reactions[m]: sizes of instance m (1..255 each).
+ *  reactants, stoich, rates, x0: the per-instance arrays of
+ *  smc_load_model concatenated in instance order ([R_m][2], [R_m][S_m],
+ *  [R_m], [S_m]). */
+int smc_load_model_batch(smc_ctx *ctx, int n_instances, const int32_t *n_species,
+                         const int32_t *n_reactions, const int32_t *reactants,
+                         const int32_t *stoich, const double *rates, const int32_t *x0);
+
+/* Loads the property (Sec. 3.1): atoms  sum_i coef[a][i] x_i  <op[a]>  bound[a]
+ * with integer coefficients, and a formula over them in postfix order.
+ *  atom_coef [n_atoms][S] (single network) -- or, after
+ *      smc_load_model_batch, [n_inst] blocks of [n_atoms][S_m];
+ *  atom_op [n_atoms]: SMC_OP_*;  atom_bound [n_atoms] (or [n_inst][n_atoms]
+ *      when per_instance != 0): finite bounds;
+ *  t_max_unbounded: horizon of the pessimistic rule (Sec. 3.2) for
+ *      formulas with an infinite interval end: a trajectory still undecided
+ *      when its clock passes t_max is counted false.
+ * The library compiles the formula into a monitor automaton.  Supported:
+ * boolean combinations (<= 4 temporal operators, <= 6 distinct atoms) of
+ * U[a,b], F[a,b], G[a,b] whose left operand is a state formula and whose
+ * right operand is a state formula, or a state formula AND F[0,d] / G[0,d]
+ * of a state formula (after pushing negations inward).  Others:
+ * SMC_E_UNSUPPORTED. */
+int smc_load_property(smc_ctx *ctx, int n_atoms, const int32_t *atom_coef,
+                      const int32_t *atom_op, const double *atom_bound, int per_instance,
+                      const smc_node *nodes, int n_nodes, double t_max_unbounded);
+
+/* Sets an SMC_OPT_* option.  Errors: SMC_E_INVALID_ARG. */
+int smc_set_option(smc_ctx *ctx, int option, double value);
+
+/* Estimates P(phi) for every instance (Sec. 3.3).
+ *  confidence = 1 - alpha (0 < confidence < 1);
+ *  half_width = epsilon of Eq. 5 (> 0; unused for SMC_FIXED_N);
+ *  seed keys the counter-based random numbers;
+ *  mode = SMC_PLAIN_FP64 or SMC_MIXED, plus SMC_FIXED_N, SMC_ITERATIVE or
+ *      SMC_CONSERVATIVE;
+ *  fixed_n: trajectories per instance for SMC_FIXED_N;
+ *  out [n_instances]: host array receiving the results.
+ * Trajectory k of instance m always draws the same random numbers for a
+ * given seed, whatever the launch shape, so results are reproducible. */
+int smc_estimate(smc_ctx *ctx, double confidence, double half_width, uint64_t seed, int mode,
+                 uint64_t fixed_n, smc_result *out);
+
+/* Copies the per-trajectory verdicts ([n_inst][fixed_n], uint8) of the last
+ * SMC_FIXED_N smc_estimate run with SMC_OPT_RECORD = 1 into host memory.
+ * n must equal n_inst * fixed_n.  Errors: SMC_E_STATE (nothing recorded). */
+int smc_get_verdicts(smc_ctx *ctx, uint8_t *out, uint64_t n);
+
+/* Runs trajectories traj_begin .. traj_begin + n_traj - 1 of every
+ * instance on `stream` (a cudaStream_t; NULL = the context's stream) and
+ * writes the device outputs in *out (counts are added to, so ranges can be
+ * chained; wilson is computed with z for `confidence` from the counts after
+ * this call).  Does not synchronise. */
+int smc_simulate(smc_ctx *ctx, int precision, uint64_t seed, uint64_t traj_begin,
+                 uint64_t n_traj, double confidence, const smc_sim_out *out, void *stream);
+
+/* Diagnostic: replays given paths through the compiled monitor on the GPU
+ * (single-network models, atoms as loaded) -- the same device code that the
+ * SSA kernel steps after every event.  Host arrays: len[n_paths] states per
+ * path (>= 1), x[sum len][S] counts, t[sum len] entry times (t[0] = 0,
+ * non-decreasing), tmin[n_paths] lower bound of the next entry time after
+ * the last state, closed[n_paths] = 1 when the path has no further state.
+ * Outputs: verdict[n_paths] (0 undetermined, 1 false, 2 true) and
+ * decided_at[n_paths]: 2k when fixed by state k, 2k+1 when fixed by the
+ * entry time of state k+1 (or the end of the path), -1 if undetermined. */
+int smc_monitor_replay(smc_ctx *ctx, int n_paths, const int32_t *len, const int32_t *x,
+                       const double *t, const double *tmin, const uint8_t *closed,
+                       int32_t *verdict, int64_t *decided_at);
+
+/* Host utilities (no GPU needed). */
+double smc_normal_quantile(double p);                           /* Phi^{-1}(p) */
+int smc_wilson_interval(uint64_t yes, uint64_t n, double confidence, double *lo,
+                        double *hi);                            /* Eq. 4 */
+double smc_wilson_sample(double p, double half_width, double confidence); /* Eq. 5 */
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SMC_H */

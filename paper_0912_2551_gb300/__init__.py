@@ -1,0 +1,231 @@
+"""GB300-native statistical model checking of mass-action reaction networks.
+
+The hot path (Gillespie direct-method trajectories checked on the fly against a
+time-bounded BLTLc formula, reduced into the Wilson score interval with the
+iterative sample-size rule of Ballarini et al., PDMC 2009) runs in the CUDA
+library ``_build/libsmc.so`` behind the C ABI of ``include/smc.h``.  This
+package only marshals arguments to it; ``Context`` converts the seeded inputs
+of ``workloads`` (networks, parameter sets, properties) into the ABI's arrays.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+from typing import Dict, Optional, Sequence
+
+import numpy as np
+
+from . import _native as N
+from ._native import (SMC_CONSERVATIVE, SMC_FIXED_N, SMC_ITERATIVE, SMC_MIXED,  # noqa: F401
+                      SMC_PLAIN_FP64)
+
+
+class SmcError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f'{N.smc_strerror(code).decode()} ({code}): {msg}')
+        self.code = code
+
+
+def _p(a, ct):
+    return a.ctypes.data_as(ctypes.POINTER(ct))
+
+
+def postfix(formula) -> list:
+    """Formula tree of tuples (see ``workloads``) -> list of smc_node tuples."""
+    out = []
+
+    def rec(f):
+        k = f[0]
+        if k == 'atom':
+            out.append((N.NODE['atom'], int(f[1]), 0.0, 0.0))
+        elif k in ('true', 'false'):
+            out.append((N.NODE[k], 0, 0.0, 0.0))
+        elif k == 'not':
+            rec(f[1]); out.append((N.NODE['not'], 0, 0.0, 0.0))
+        elif k in ('and', 'or', 'implies'):
+            rec(f[1]); rec(f[2]); out.append((N.NODE[k], 0, 0.0, 0.0))
+        elif k == 'U':
+            rec(f[3]); rec(f[4]); out.append((N.NODE['U'], 0, float(f[1]), float(f[2])))
+        elif k in ('F', 'G'):
+            rec(f[3]); out.append((N.NODE[k], 0, float(f[1]), float(f[2])))
+        else:
+            raise ValueError(f'unknown formula node {k!r}')
+
+    rec(formula)
+    return out
+
+
+PRECISION = {'plain': SMC_PLAIN_FP64, 'fp64': SMC_PLAIN_FP64, 'mixed': SMC_MIXED}
+SAMPLING = {'fixed': SMC_FIXED_N, 'iterative': SMC_ITERATIVE, 'conservative': SMC_CONSERVATIVE}
+
+
+class Context:
+    """One smc_ctx on one CUDA device."""
+
+    def __init__(self, device: int = 0):
+        N.load()
+        h = ctypes.c_void_p()
+        rc = N.smc_create(ctypes.byref(h), int(device))
+        if rc != 0:
+            raise SmcError(rc, 'smc_create')
+        self.h = h
+        self.device = device
+        self.n_inst = 0
+        self.s_max = 0
+
+    def close(self):
+        if getattr(self, 'h', None):
+            N.smc_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def _check(self, rc, what):
+        if rc != 0:
+            raise SmcError(rc, f'{what}: {N.smc_last_error(self.h).decode()}')
+
+    # -- loading --------------------------------------------------------------
+    def load_model(self, model):
+        reac = np.ascontiguousarray(model.reactants, np.int32)
+        st = np.ascontiguousarray(model.stoich, np.int32)
+        rates = np.ascontiguousarray(model.rates, np.float64)
+        x0 = np.ascontiguousarray(model.x0, np.int32)
+        self._check(N.smc_load_model(self.h, model.n_species, model.n_reactions, _p(reac, ctypes.c_int32),
+                                     _p(st, ctypes.c_int32), _p(rates, ctypes.c_double),
+                                     _p(x0, ctypes.c_int32), model.n_inst), 'smc_load_model')
+        self.n_inst = model.n_inst
+        self.s_max = model.n_species
+        self._batch = None
+
+    def load_batch(self, batch):
+        ms = batch.models
+        S = np.asarray([m.n_species for m in ms], np.int32)
+        R = np.asarray([m.n_reactions for m in ms], np.int32)
+        reac = np.ascontiguousarray(np.concatenate([m.reactants.ravel() for m in ms]), np.int32)
+        st = np.ascontiguousarray(np.concatenate([m.stoich.ravel() for m in ms]), np.int32)
+        rates = np.ascontiguousarray(np.concatenate([m.rates[0] for m in ms]), np.float64)
+        x0 = np.ascontiguousarray(np.concatenate([m.x0[0] for m in ms]), np.int32)
+        self._check(N.smc_load_model_batch(self.h, len(ms), _p(S, ctypes.c_int32), _p(R, ctypes.c_int32),
+                                           _p(reac, ctypes.c_int32), _p(st, ctypes.c_int32),
+                                           _p(rates, ctypes.c_double), _p(x0, ctypes.c_int32)),
+                    'smc_load_model_batch')
+        self.n_inst = len(ms)
+        self.s_max = int(S.max())
+        self._batch = batch
+
+    def load_property(self, prop, t_max: float = math.inf, per_instance=None):
+        """``prop``: a workloads.Property, or (after load_batch) a list of
+        properties sharing one formula shape, one per instance."""
+        if isinstance(prop, (list, tuple)):
+            props = list(prop)
+            formula = props[0].formula
+            n_atoms = len(props[0].atoms)
+            coef = np.ascontiguousarray(np.concatenate(
+                [np.stack([a.coef for a in p.atoms]).ravel() for p in props]), np.int32)
+            op = np.asarray([N.OP[a.op] for a in props[0].atoms], np.int32)
+            bound = np.ascontiguousarray([a.bound for p in props for a in p.atoms], np.float64)
+            per = 1
+        else:
+            formula = prop.formula
+            n_atoms = len(prop.atoms)
+            coef = np.ascontiguousarray(np.stack([a.coef for a in prop.atoms]) if n_atoms else
+                                        np.zeros((1, 1)), np.int32)
+            op = np.asarray([N.OP[a.op] for a in prop.atoms] or [0], np.int32)
+            bound = np.asarray([a.bound for a in prop.atoms] or [0.0], np.float64)
+            per = 0
+            if self._batch is not None:
+                coef = np.ascontiguousarray(np.concatenate([coef.ravel()] * self.n_inst), np.int32)
+        nodes = postfix(formula)
+        arr = (N.smc_node * len(nodes))(*[N.smc_node(*n) for n in nodes])
+        self._check(N.smc_load_property(self.h, n_atoms, _p(coef, ctypes.c_int32), _p(op, ctypes.c_int32),
+                                        _p(bound, ctypes.c_double), per, arr, len(nodes),
+                                        float(t_max)), 'smc_load_property')
+
+    def set_option(self, name: str, value: float):
+        self._check(N.smc_set_option(self.h, N.OPT[name], float(value)), f'smc_set_option({name})')
+
+    # -- running --------------------------------------------------------------
+    def estimate(self, confidence: float, half_width: float = 0.01, seed: int = 0,
+                 precision: str = 'plain', sampling: str = 'iterative', fixed_n: int = 0):
+        res = (N.smc_result * self.n_inst)()
+        mode = PRECISION[precision] | SAMPLING[sampling]
+        self._check(N.smc_estimate(self.h, float(confidence), float(half_width), int(seed), mode,
+                                   int(fixed_n), res), 'smc_estimate')
+        return [r.as_dict() for r in res]
+
+    def get_verdicts(self, n: int) -> np.ndarray:
+        out = np.zeros(n, np.uint8)
+        self._check(N.smc_get_verdicts(self.h, _p(out, ctypes.c_uint8), n), 'smc_get_verdicts')
+        return out
+
+    def simulate(self, precision: str = 'plain', seed: int = 0, traj_begin: int = 0, n_traj: int = 1,
+                 confidence: float = 0.95, outputs: Sequence[str] = ('verdict', 'status', 'events', 't_final'),
+                 counts=None, stream=None) -> Dict[str, object]:
+        """Runs trajectories [traj_begin, traj_begin + n_traj) of every
+        instance on the GPU; returns torch CUDA tensors (counts [n_inst, 4],
+        wilson [n_inst, 3] and the requested per-trajectory outputs)."""
+        import torch
+        dev = torch.device('cuda', self.device)
+        n = self.n_inst
+        out = {}
+        if counts is None:
+            counts = torch.zeros((n, 4), dtype=torch.int64, device=dev)
+        out['counts'] = counts
+        out['wilson'] = torch.zeros((n, 3), dtype=torch.float64, device=dev)
+        spec = dict(verdict=(torch.uint8, ()), status=(torch.uint8, ()), events=(torch.int64, ()),
+                    t_final=(torch.float64, ()), x_final=(torch.int32, (self.s_max,)))
+        so = N.smc_sim_out()
+        so.counts = counts.data_ptr()
+        so.wilson = out['wilson'].data_ptr()
+        for k in outputs:
+            dt, extra = spec[k]
+            out[k] = torch.zeros((n, n_traj) + extra, dtype=dt, device=dev)
+            setattr(so, k, out[k].data_ptr())
+        s = stream if stream is not None else torch.cuda.current_stream(dev)
+        self._check(N.smc_simulate(self.h, PRECISION[precision], int(seed), int(traj_begin), int(n_traj),
+                                   float(confidence), ctypes.byref(so), ctypes.c_void_p(s.cuda_stream)),
+                    'smc_simulate')
+        return out
+
+    def monitor_replay(self, paths, S: int):
+        """paths: list of (x [n, S] ints, t [n] floats, tmin, closed)."""
+        lens = np.asarray([len(p[1]) for p in paths], np.int32)
+        x = np.ascontiguousarray(np.concatenate([np.asarray(p[0], np.int32).reshape(-1, S) for p in paths]),
+                                 np.int32)
+        t = np.ascontiguousarray(np.concatenate([np.asarray(p[1], np.float64) for p in paths]))
+        tmin = np.asarray([p[2] for p in paths], np.float64)
+        closed = np.asarray([1 if p[3] else 0 for p in paths], np.uint8)
+        v = np.zeros(len(paths), np.int32)
+        q = np.zeros(len(paths), np.int64)
+        self._check(N.smc_monitor_replay(self.h, len(paths), _p(lens, ctypes.c_int32), _p(x, ctypes.c_int32),
+                                         _p(t, ctypes.c_double), _p(tmin, ctypes.c_double),
+                                         _p(closed, ctypes.c_uint8), _p(v, ctypes.c_int32),
+                                         _p(q, ctypes.c_int64)), 'smc_monitor_replay')
+        return v, q
+
+
+def normal_quantile(p: float) -> float:
+    return N.smc_normal_quantile(float(p))
+
+
+def wilson_interval(yes: int, n: int, confidence: float):
+    lo = ctypes.c_double()
+    hi = ctypes.c_double()
+    rc = N.smc_wilson_interval(int(yes), int(n), float(confidence), ctypes.byref(lo), ctypes.byref(hi))
+    if rc != 0:
+        raise SmcError(rc, 'smc_wilson_interval')
+    return lo.value, hi.value
+
+
+def wilson_sample(p: float, half_width: float, confidence: float) -> float:
+    return N.smc_wilson_sample(float(p), float(half_width), float(confidence))

@@ -1,0 +1,42 @@
+// smc_compile.h -- host-side formula compiler and model-table builder.
+#pragma once
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/smc.h"
+#include "smc_internal.h"
+
+namespace smc {
+
+struct FNode {
+    int kind = 0, arg = -1;
+    double lo = 0.0, hi = 0.0;
+    int c0 = -1, c1 = -1;
+};
+
+// One instance's network, pointing into the context's host copies.
+struct InstanceModel {
+    int S = 0, R = 0;
+    const int32_t *reactants = nullptr;  // [R][2]
+    const int32_t *stoich = nullptr;     // [R][S]
+    const double *rates = nullptr;       // [R]
+    const int32_t *x0 = nullptr;         // [S]
+};
+
+int parse_formula(const smc_node *nodes, int n_nodes, int n_atoms, std::vector<FNode> &tree,
+                  int &root, std::string &err);
+
+// Compiles the formula tree into `prog`; used_atoms[bit] = original atom index.
+int compile_formula(const std::vector<FNode> &tree, int root, int n_atoms, double t_max,
+                    MonProg &prog, std::vector<int> &used_atoms, std::string &err);
+
+// atom  L <op> b  (L an integer)  as  lo <= L <= hi, negated when neg.
+void atom_threshold(int op, double b, int64_t &lo, int64_t &hi, bool &neg);
+
+// Builds the shared-memory table of one instance (layout: BlobHdr).
+int build_blob(const InstanceModel &M, int n_used, const int32_t *coef_used, const int32_t *op_used,
+               const double *bound_used, std::vector<uint32_t> &blob, std::string &err);
+
+}  // namespace smc

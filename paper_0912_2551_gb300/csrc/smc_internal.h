@@ -1,0 +1,134 @@
+// smc_internal.h -- layouts shared by the host side of the library and its
+// CUDA kernels: the compiled monitor program, the per-instance model table
+// ("blob") staged into shared memory, and the kernel parameter block.
+#pragma once
+#include <stdint.h>
+
+#define SMC_MAX_UNITS 4   // temporal operators (monitor units) per formula
+#define SMC_MAX_ATOMS 6   // distinct atoms (truth tables are 64-bit)
+#define SMC_MAX_SPECIES 255
+#define SMC_MAX_REACTIONS 255
+
+// ---------------------------------------------------------------------------
+// Monitor program.
+//
+// A formula is compiled into at most SMC_MAX_UNITS "units", each of the form
+//     L  U[a,b]  ( P  and  N )
+// anchored at time 0, where L, P, Q are state formulas over the atoms (held
+// as 64-entry truth tables indexed by the atom bit vector) and N is either
+// tt (nest = 0), F[0,d] Q (nest = 1) or G[0,d] Q (nest = 2).  F[a,b] psi is
+// tt U[a,b] psi; G[a,b] psi is compiled as the unit F[a,b] (not psi) whose
+// value the top-level table negates.  A bare state formula at the top level
+// is the unit ff U[0,0] P (decided at the initial state).
+//
+// The top-level boolean structure is a table over the units' Kleene values
+// (0 = undetermined, 1 = false, 2 = true), indexed by sum_u value_u * 3^u,
+// giving 0 (undetermined), 1 (false) or 2 (true).
+struct MonUnit {
+    uint64_t L, P, Q;  // truth tables over the atom bit vector
+    double a, b;       // window of the unit (entry time of a witness)
+    double d;          // window [0, d] of the nested operator
+    int32_t nest;      // 0 none, 1 F-nested, 2 G-nested
+    int32_t pad;
+};
+
+struct MonProg {
+    int32_t n_units, n_atoms;
+    int32_t unbounded;  // some window end is +inf: pessimistic rule at t_max
+    int32_t has_lower;  // some unit window starts after 0
+    double t_max;
+    MonUnit u[SMC_MAX_UNITS];
+    uint8_t table[81];  // 3^SMC_MAX_UNITS
+    uint8_t pad2[23];
+};
+static_assert(sizeof(MonUnit) == 56, "MonUnit layout");
+static_assert(sizeof(MonProg) % 16 == 0, "MonProg is copied in 16-byte words");
+
+// ---------------------------------------------------------------------------
+// Per-instance table ("blob"), 32-bit words, every section 2-word aligned.
+//   hdr[0..15]: S, R, n_atoms, total_words, then word offsets of the sections:
+enum BlobHdr {
+    BH_S = 0, BH_R, BH_NA, BH_WORDS,
+    BH_RATE_D,   // double [R]        stochastic rate constants
+    BH_RATE_F,   // float  [R]        the same, rounded to FP32
+    BH_REAC,     // u32    [R]        ra | rb << 8 | kind << 16
+    BH_ST_PTR,   // u32    [R+1]      CSR row pointers of the stoichiometry
+    BH_ST,       // u32    [nnz]      species | (delta << 8) (delta signed)
+    BH_DEP_PTR,  // u32    [R+1]      CSR row pointers of dep(j)
+    BH_DEP,      // u32    [ndep]     k: propensity a_k reads a species j changes
+    BH_ADELTA,   // i32    [R][NA]    change of each atom's linear form under j
+    BH_X0,       // i32    [S]        initial counts
+    BH_AL0,      // i64    [NA]       linear forms at x0
+    BH_ATHR,     // i64    [NA][2]    atom holds iff lo <= L <= hi (xor neg)
+    BH_ANEG,     // u32    [1]        neg bits
+    BH_COUNT = 16
+};
+// propensity kinds (Sec. 2.2): h = 1, x_a, x_a x_b, x_a (x_a - 1) / 2
+enum { RK_ZERO = 0, RK_ONE = 1, RK_HETERO = 2, RK_HOMO = 3 };
+
+// ---------------------------------------------------------------------------
+// Kernel parameters of the persistent SSA kernel.
+struct SsaParams {
+    const uint32_t *blobs;       // all instance tables, concatenated
+    const uint64_t *blob_off;    // word offset of instance m's table
+    const int32_t *inst_list;    // instances served by this launch
+    int32_t n_list;
+    int32_t n_inst;              // instances in the context
+    const uint64_t *tbegin;      // [n_inst] first trajectory index
+    const uint64_t *tend;        // [n_inst] one past the last index
+    uint64_t u_begin, u_end;     // the range of every instance when uniform
+    int32_t uniform;             // 1: ignore tbegin / tend
+    unsigned long long *tnext;   // [n_inst] work queue (starts at tbegin)
+    unsigned int *cursor;        // instance cursor (starts at 0)
+    unsigned int *ticket;        // blocks finished (starts at 0)
+    const MonProg *prog;
+    uint32_t rk0[10], rk1[10];   // Philox round keys
+    uint64_t budget;             // max reactions per trajectory
+    uint32_t renorm_mask;        // mixed path: renormalise when (e & mask) == 0
+    int32_t refill;              // refill when >= refill lanes are idle
+    int32_t blob_words;          // per-warp table area (words, multiple of 4)
+    int32_t s_max, r_max;        // per-lane state area
+    int32_t warp_bytes;          // shared memory per warp
+    // outputs
+    unsigned long long *counts;  // [n_inst][4] yes, n, events, budget hits
+    double *wilson;              // [n_inst][3] or null
+    double z;                    // normal quantile for the Wilson epilogue
+    uint8_t *o_verdict;          // per-trajectory outputs or null
+    uint8_t *o_status;
+    uint64_t *o_events;
+    double *o_tfinal;
+    int32_t *o_xfinal;
+    uint64_t out_base;           // trajectory index of output column 0
+    uint64_t out_stride;         // columns per instance row
+    int32_t x_stride;            // species per x_final row
+};
+
+// Monitor replay (tests): runs the compiled monitor over given paths.
+struct ReplayParams {
+    const MonProg *prog;
+    const int32_t *coef;     // [n_atoms][S] atom coefficients (compiled order)
+    const int64_t *athr;     // [n_atoms][2]
+    uint32_t aneg;
+    int32_t S;
+    int32_t n_paths;
+    const int32_t *len;      // [n_paths] states per path
+    const int64_t *off;      // [n_paths] first state of each path
+    const int32_t *x;        // [total][S]
+    const double *t;         // [total]
+    const double *tmin;      // [n_paths] entry time bound after the last state
+    const uint8_t *closed;   // [n_paths]
+    int32_t *verdict;        // [n_paths] 0 undetermined, 1 false, 2 true
+    int64_t *decided_at;     // [n_paths] 2k / 2k+1 decision point or -1
+};
+
+#ifdef __cplusplus
+extern "C++" {
+// host launch wrappers (smc_kernels.cu)
+int smc_launch_ssa(int plain, const SsaParams &p, int grid, int block, int smem_bytes,
+                   void *stream);
+int smc_ssa_max_blocks_per_sm(int plain, int block, int smem_bytes, int *out);
+int smc_ssa_set_smem_limit(int plain, int smem_bytes);
+int smc_launch_queue_init(const SsaParams &p, void *stream);
+int smc_launch_replay(const ReplayParams &p, void *stream);
+}
+#endif

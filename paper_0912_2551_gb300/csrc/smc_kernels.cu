@@ -1,0 +1,614 @@
+// smc_kernels.cu -- the persistent SSA + on-the-fly monitor kernel.
+//
+// One trajectory per thread (the "multiple replications in parallel" policy
+// of Sec. 4, one replica per lane instead of one per MPI process).  Each warp
+// works on one instance at a time and keeps that instance's model table in
+// its own slice of shared memory; each lane keeps its counts x and
+// propensities a in shared memory columns (lane-minor, so lane i always hits
+// bank i).  Lanes that finish a trajectory claim the next index of the
+// instance's work queue by warp ballot (one atomic per refill).
+//
+// Per event (Sec. 2.2, steps 1-5; Eq. 2a/2b):
+//   a0 = sum_j a_j                      (plain: fresh FP64 left-to-right sum;
+//                                        mixed: FP32, updated incrementally,
+//                                        renormalised in FP64 every 2^k events)
+//   (w0..w3) = Philox4x32-10(key = seed, counter = (event, trajectory, instance, 0))
+//   tau = -ln(u_tau) / a0,  t' = t + tau (FP64 clock)
+//   monitor: windows that t' closes                  (Sec. 3.2: stop as soon as
+//   j = first index with running sum > u_sel * a0      the verdict is fixed)
+//   x += v_j; a_k recomputed for k in dep(j)
+//   monitor: atoms and units at the new state
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "smc_internal.h"
+
+#define FULL_MASK 0xffffffffu
+
+namespace {
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two
+// 32x32->64-bit multiplies with the words permuted and the high halves xored
+// with the counter and the round key.  The round keys (key plus multiples of
+// the Weyl increments) are uniform over the launch, so they come precomputed
+// in the kernel parameters.
+__device__ __forceinline__ void philox10(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                         const uint32_t *rk0, const uint32_t *rk1,
+                                         uint32_t &w0, uint32_t &w1, uint32_t &w2, uint32_t &w3)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint64_t p0 = (uint64_t)0xD2511F53u * c0;
+        const uint64_t p1 = (uint64_t)0xCD9E8D57u * c2;
+        const uint32_t n0 = (uint32_t)(p1 >> 32) ^ c1 ^ rk0[r];
+        const uint32_t n2 = (uint32_t)(p0 >> 32) ^ c3 ^ rk1[r];
+        c1 = (uint32_t)p1;
+        c3 = (uint32_t)p0;
+        c0 = n0;
+        c2 = n2;
+    }
+    w0 = c0; w1 = c1; w2 = c2; w3 = c3;
+}
+
+// (0,1) from 52 bits: ((hi:lo) >> 12 + 1/2) 2^-52, exact, in [2^-53, 1 - 2^-53].
+__device__ __forceinline__ double u01_52(uint32_t hi, uint32_t lo)
+{
+    const uint64_t v = ((((uint64_t)hi) << 32) | (uint64_t)lo) >> 12;
+    return __dmul_rn(__dadd_rn(__ull2double_rn(v), 0.5), 0x1p-52);
+}
+
+// (0,1) in FP32 from 23 bits: (w >> 9 + 1/2) 2^-23, exact, in [2^-24, 1 - 2^-24].
+__device__ __forceinline__ float u01_23(uint32_t w)
+{
+    return __fmaf_rn((float)(w >> 9), 0x1p-23f, 0x1p-24f);
+}
+
+// x > y for x, y >= 0 (including +inf): ordered like their bit patterns,
+// so the compare runs on the integer pipe.
+__device__ __forceinline__ bool dgt(double x, double y)
+{
+    return __double_as_longlong(x) > __double_as_longlong(y);
+}
+
+// ---------------------------------------------------------------------------
+// Monitor (one per lane).  Unit semantics, in the knowledge order of the
+// event loop (entry times never decrease; after the draw of t' every later
+// state has entry time >= t'):
+//   witness at a state entered at t:  alive and a <= t <= b and P (and, for
+//     nest 1, Q now or later within [t, t + d]; for nest 2, Q at every state
+//     entered within [t, t + d]);
+//   alive: L held at every earlier state;
+//   nest 1 keeps the latest candidate (its window ends last), nest 2 the
+//   earliest since the last state violating Q (its window closes first).
+struct MonLane {
+    int64_t L[SMC_MAX_ATOMS];
+    double tc[SMC_MAX_UNITS];
+    long long hb;    // bits of min b over alive undecided units (-1: none)
+    uint32_t ab;     // atom bit vector of the current state
+    uint32_t alive, pend, done;
+    int32_t vidx;    // sum_u value_u 3^u
+};
+
+__device__ __constant__ int kPow3[SMC_MAX_UNITS] = {1, 3, 9, 27};
+
+__device__ __forceinline__ uint32_t atom_bits(const MonLane &ml, int na, const int64_t *thr,
+                                              uint32_t neg)
+{
+    uint32_t b = 0;
+#pragma unroll
+    for (int a = 0; a < SMC_MAX_ATOMS; ++a)
+        if (a < na) b |= (uint32_t)((ml.L[a] >= thr[2 * a]) & (ml.L[a] <= thr[2 * a + 1])) << a;
+    return b ^ neg;
+}
+
+__device__ __forceinline__ void mon_horizon(MonLane &ml, const MonProg &P)
+{
+    long long h = -1;
+#pragma unroll
+    for (int u = 0; u < SMC_MAX_UNITS; ++u) {
+        if (u < P.n_units && !((ml.done >> u) & 1u) && ((ml.alive >> u) & 1u)) {
+            const long long b = __double_as_longlong(P.u[u].b);
+            h = (h < 0 || b < h) ? b : h;
+        }
+    }
+    ml.hb = h;
+}
+
+__device__ __forceinline__ void mon_set(MonLane &ml, int u, int val)
+{
+    ml.done |= 1u << u;
+    ml.vidx += val * kPow3[u];
+}
+
+// The state just entered at time t (atom bits already in ml.ab).
+__device__ int mon_state(MonLane &ml, const MonProg &P, double t)
+{
+    bool changed = false;
+#pragma unroll
+    for (int u = 0; u < SMC_MAX_UNITS; ++u) {
+        if (u >= P.n_units || ((ml.done >> u) & 1u)) continue;
+        const MonUnit &U = P.u[u];
+        const uint32_t ab = ml.ab;
+        const bool l = (U.L >> ab) & 1ull, p = (U.P >> ab) & 1ull, q = (U.Q >> ab) & 1ull;
+        bool al = (ml.alive >> u) & 1u, pe = (ml.pend >> u) & 1u;
+        const bool inwin = al && !dgt(U.a, t) && !dgt(t, U.b);
+        int val = 0;
+        if (U.nest == 0) {
+            if (inwin && p) val = 2;
+        } else if (U.nest == 1) {
+            if (pe && q && !dgt(__dsub_rn(t, ml.tc[u]), U.d)) {
+                val = 2;
+            } else if (inwin && p) {
+                if (q) val = 2;
+                else { ml.tc[u] = t; pe = true; }
+            }
+        } else {
+            if (pe && !q) pe = false;
+            if (inwin && p && q && !pe) { ml.tc[u] = t; pe = true; }
+        }
+        if (!val) {
+            const bool al2 = al && l;
+            changed |= (al2 != al);
+            al = al2;
+            if (!(al && !dgt(t, U.b)) && !pe) val = 1;
+        }
+        ml.alive = (ml.alive & ~(1u << u)) | ((uint32_t)al << u);
+        ml.pend = (ml.pend & ~(1u << u)) | ((uint32_t)pe << u);
+        if (val) { mon_set(ml, u, val); changed = true; }
+    }
+    if (changed) mon_horizon(ml, P);
+    return P.table[ml.vidx];
+}
+
+// The next state's entry time tn has been drawn (not yet applied).
+__device__ int mon_draw(MonLane &ml, const MonProg &P, double tn)
+{
+    bool changed = false;
+#pragma unroll
+    for (int u = 0; u < SMC_MAX_UNITS; ++u) {
+        if (u >= P.n_units || ((ml.done >> u) & 1u)) continue;
+        const MonUnit &U = P.u[u];
+        const bool al = (ml.alive >> u) & 1u;
+        bool pe = (ml.pend >> u) & 1u;
+        int val = 0;
+        if (pe && dgt(__dsub_rn(tn, ml.tc[u]), U.d)) {
+            if (U.nest == 2) val = 2;
+            else pe = false;
+        }
+        if (!val && !(al && !dgt(tn, U.b)) && !pe) val = 1;
+        ml.pend = (ml.pend & ~(1u << u)) | ((uint32_t)pe << u);
+        if (val) { mon_set(ml, u, val); changed = true; }
+    }
+    if (changed) mon_horizon(ml, P);
+    return P.table[ml.vidx];
+}
+
+// The path has no further state (absorbing state).
+__device__ int mon_close(MonLane &ml, const MonProg &P)
+{
+#pragma unroll
+    for (int u = 0; u < SMC_MAX_UNITS; ++u) {
+        if (u >= P.n_units || ((ml.done >> u) & 1u)) continue;
+        const bool g_pending = P.u[u].nest == 2 && ((ml.pend >> u) & 1u);
+        mon_set(ml, u, g_pending ? 2 : 1);
+    }
+    return P.table[ml.vidx];
+}
+
+__device__ __forceinline__ void mon_start(MonLane &ml, const MonProg &P)
+{
+    ml.alive = (1u << P.n_units) - 1u;
+    ml.pend = 0;
+    ml.done = 0;
+    ml.vidx = 0;
+    mon_horizon(ml, P);
+}
+
+// ---------------------------------------------------------------------------
+// Eq. 4 in FP64, same operation order as the written-out formula:
+// (p + z^2/(2n) -+ z sqrt(p(1-p)/n + z^2/(4n^2))) / (1 + z^2/n).
+__device__ void wilson_eq4(unsigned long long yes, unsigned long long n, double z, double *out)
+{
+    if (n == 0) { out[0] = nan(""); out[1] = 0.0; out[2] = 1.0; return; }
+    const double dn = (double)n;
+    const double p = __ddiv_rn((double)yes, dn);
+    const double z2 = __dmul_rn(z, z);
+    const double centre = __dadd_rn(p, __ddiv_rn(z2, __dmul_rn(2.0, dn)));
+    const double var = __dadd_rn(__ddiv_rn(__dmul_rn(p, __dsub_rn(1.0, p)), dn),
+                                 __ddiv_rn(z2, __dmul_rn(__dmul_rn(4.0, dn), dn)));
+    const double half = __dmul_rn(z, __dsqrt_rn(var));
+    const double den = __dadd_rn(1.0, __ddiv_rn(z2, dn));
+    double lo = __ddiv_rn(__dsub_rn(centre, half), den);
+    double hi = __ddiv_rn(__dadd_rn(centre, half), den);
+    if (yes == 0) lo = 0.0;
+    if (yes == n) hi = 1.0;
+    out[0] = p;
+    out[1] = lo < 0.0 ? 0.0 : lo;
+    out[2] = hi > 1.0 ? 1.0 : hi;
+}
+
+__device__ __forceinline__ unsigned long long warp_sum(unsigned long long v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL_MASK, v, o);
+    return v;
+}
+
+// Claims an instance for the warp: first one each from the cursor, then any
+// instance whose queue is not yet exhausted.  Returns -1 when no work is
+// left.  Warp-collective.
+__device__ int acquire_instance(const SsaParams &p, bool &first, int gw, int lane)
+{
+    if (first) {
+        unsigned i = 0;
+        if (lane == 0) i = atomicAdd(p.cursor, 1u);
+        i = __shfl_sync(FULL_MASK, i, 0);
+        if ((int)i < p.n_list) return p.inst_list[i];
+        first = false;
+    }
+    const int n = p.n_list;
+    const int start = (int)(((unsigned)gw * 2654435761u) % (unsigned)n);
+    for (int k = 0; k < n; k += 32) {
+        bool ok = false;
+        int m = -1;
+        if (k + lane < n) {
+            int idx = start + k + lane;
+            if (idx >= n) idx -= n;
+            m = p.inst_list[idx];
+            ok = *((volatile unsigned long long *)&p.tnext[m]) < (p.uniform ? p.u_end : p.tend[m]);
+        }
+        const unsigned b = __ballot_sync(FULL_MASK, ok);
+        if (b) return __shfl_sync(FULL_MASK, m, __ffs(b) - 1);
+    }
+    return -1;
+}
+
+template <bool PLAIN>
+struct Prec;
+template <>
+struct Prec<true> { typedef double T; };
+template <>
+struct Prec<false> { typedef float T; };
+
+// a_j = c_j h_j(x) (Sec. 2.2), h_j an exact integer rounded once.
+template <bool PLAIN>
+__device__ __forceinline__ typename Prec<PLAIN>::T propensity(uint32_t rw, const int32_t *xs,
+                                                              const double *rate_d,
+                                                              const float *rate_f, int k)
+{
+    const int ra = rw & 255u, rb = (rw >> 8) & 255u, kind = (rw >> 16) & 3u;
+    long long h;
+    if (kind == RK_ZERO) h = 1;
+    else {
+        const long long xa = xs[ra * 32];
+        if (kind == RK_ONE) h = xa;
+        else if (kind == RK_HETERO) h = xa * (long long)xs[rb * 32];
+        else h = (xa * (xa - 1)) >> 1;
+    }
+    if (PLAIN) return __dmul_rn(rate_d[k], __ll2double_rn(h));
+    else return __fmul_rn(rate_f[k], __ll2float_rn(h));
+}
+
+template <bool PLAIN>
+__device__ void run_instance(const SsaParams &p, const MonProg &P, const int m,
+                             const uint32_t *blob, int32_t *xs,
+                             typename Prec<PLAIN>::T *as, const int lane)
+{
+    typedef typename Prec<PLAIN>::T T;
+    const int S = (int)blob[BH_S], R = (int)blob[BH_R], NA = (int)blob[BH_NA];
+    const double *rate_d = reinterpret_cast<const double *>(blob + blob[BH_RATE_D]);
+    const float *rate_f = reinterpret_cast<const float *>(blob + blob[BH_RATE_F]);
+    const uint32_t *reac = blob + blob[BH_REAC];
+    const uint32_t *stp = blob + blob[BH_ST_PTR];
+    const uint32_t *st = blob + blob[BH_ST];
+    const uint32_t *dpp = blob + blob[BH_DEP_PTR];
+    const uint32_t *dp = blob + blob[BH_DEP];
+    const int32_t *adelta = reinterpret_cast<const int32_t *>(blob + blob[BH_ADELTA]);
+    const int32_t *x0 = reinterpret_cast<const int32_t *>(blob + blob[BH_X0]);
+    const int64_t *al0 = reinterpret_cast<const int64_t *>(blob + blob[BH_AL0]);
+    const int64_t *athr = reinterpret_cast<const int64_t *>(blob + blob[BH_ATHR]);
+    const uint32_t aneg = blob[blob[BH_ANEG]];
+    const unsigned long long tend = p.uniform ? p.u_end : p.tend[m];
+    const bool skip_same = !P.has_lower;
+
+    bool active = false, exhausted = false;
+    uint32_t traj = 0, e = 0;
+    double t = 0.0;
+    T a0 = 0;
+    MonLane ml;
+    unsigned long long c_yes = 0, c_dec = 0, c_ev = 0, c_bud = 0;
+
+    // verdict codes: 1 false, 2 true, 3 event budget exhausted
+    auto finish = [&](int v) {
+        if (v == 3) ++c_bud;
+        else { ++c_dec; c_yes += (v == 2); }
+        c_ev += e;
+        if (p.o_verdict) {
+            const uint64_t idx = (uint64_t)m * p.out_stride + ((uint64_t)traj - p.out_base);
+            p.o_verdict[idx] = (v == 2);
+            if (p.o_status) p.o_status[idx] = (v == 3);
+            if (p.o_events) p.o_events[idx] = e;
+            if (p.o_tfinal) p.o_tfinal[idx] = t;
+            if (p.o_xfinal)
+                for (int i = 0; i < S; ++i) p.o_xfinal[idx * p.x_stride + i] = xs[i * 32];
+        }
+        active = false;
+    };
+
+    for (;;) {
+        if (!exhausted) {
+            const unsigned need = __ballot_sync(FULL_MASK, !active);
+            const int nneed = __popc(need);
+            if (nneed && (nneed >= p.refill || nneed == 32)) {
+                const int leader = __ffs(need) - 1;
+                unsigned long long base = 0;
+                if (lane == leader) base = atomicAdd(&p.tnext[m], (unsigned long long)nneed);
+                base = __shfl_sync(FULL_MASK, base, leader);
+                if (base + (unsigned long long)nneed >= tend) exhausted = true;
+                if (!active) {
+                    const unsigned long long id = base + __popc(need & ((1u << lane) - 1u));
+                    if (id < tend) {
+                        // start trajectory `id`: x = x0, fresh propensities, monitor at t = 0
+                        traj = (uint32_t)id;
+                        e = 0;
+                        t = 0.0;
+                        for (int i = 0; i < S; ++i) xs[i * 32] = x0[i];
+                        double s = 0.0;
+                        for (int k = 0; k < R; ++k) {
+                            const T ak = propensity<PLAIN>(reac[k], xs, rate_d, rate_f, k);
+                            as[k * 32] = ak;
+                            s = __dadd_rn(s, (double)ak);
+                        }
+                        a0 = (T)s;
+#pragma unroll
+                        for (int a = 0; a < SMC_MAX_ATOMS; ++a)
+                            if (a < NA) ml.L[a] = al0[a];
+                        ml.ab = atom_bits(ml, NA, athr, aneg);
+                        mon_start(ml, P);
+                        active = true;
+                        const int v = mon_state(ml, P, 0.0);
+                        if (v) finish(v);
+                    }
+                }
+            }
+        }
+        if (!__any_sync(FULL_MASK, active)) {
+            if (exhausted) break;
+            continue;
+        }
+        if (!active) continue;
+
+        // ---- one event -------------------------------------------------------
+        if (PLAIN) {  // step 1: a0 as a fresh left-to-right sum
+            double s = 0.0;
+            for (int k = 0; k < R; ++k) s = __dadd_rn(s, (double)as[k * 32]);
+            a0 = (T)s;
+        }
+        if (!PLAIN && !(a0 > (T)0)) {  // drifted running sum: renormalise in FP64
+            double s = 0.0;
+            for (int k = 0; k < R; ++k) s = __dadd_rn(s, (double)as[k * 32]);
+            a0 = (T)s;
+        }
+        if (!(a0 > (T)0)) {  // absorbing state: the path has no further position
+            finish(mon_close(ml, P));
+            continue;
+        }
+        uint32_t w0, w1, w2, w3;
+        philox10(e, traj, (uint32_t)m, 0u, p.rk0, p.rk1, w0, w1, w2, w3);
+        double tn;
+        T r;
+        if (PLAIN) {
+            const double ut = u01_52(w0, w1), us = u01_52(w2, w3);
+            tn = __dadd_rn(t, __ddiv_rn(-log(ut), (double)a0));
+            r = (T)__dmul_rn(us, (double)a0);
+        } else {
+            const float ut = u01_23(w0), us = u01_23(w2);
+            const float tau = __fdividef(-logf(ut), (float)a0);
+            tn = __dadd_rn(t, (double)tau);
+            r = (T)(us * (float)a0);
+        }
+        int v = 0;
+        if (ml.pend || __double_as_longlong(tn) > ml.hb) v = mon_draw(ml, P, tn);
+        if (!v && P.unbounded && tn > P.t_max) v = 1;  // pessimistic rule (Sec. 3.2)
+        if (v) { finish(v); continue; }
+
+        // step 2: selection, first j whose running sum exceeds r
+        int j = -1, last = -1;
+        T cum = (T)0;
+        for (int k = 0; k < R; ++k) {
+            const T ak = as[k * 32];
+            cum = cum + ak;
+            if (ak > (T)0) last = k;
+            if (cum > r) { j = k; break; }
+        }
+        if (j < 0) j = last;  // r reached the full sum (rounding, or a drifted a0)
+        if (j < 0) {          // every a_k is 0 (only a drifted FP32 a0 gets here)
+            finish(mon_close(ml, P));
+            continue;
+        }
+
+        // step 4: x += v_j, then the propensities that read a changed species
+        for (uint32_t q = stp[j], qe = stp[j + 1]; q < qe; ++q) {
+            const uint32_t w = st[q];
+            xs[(w & 255u) * 32] += ((int32_t)w) >> 8;
+        }
+        for (uint32_t q = dpp[j], qe = dpp[j + 1]; q < qe; ++q) {
+            const int k = (int)dp[q];
+            const T ak = propensity<PLAIN>(reac[k], xs, rate_d, rate_f, k);
+            if (!PLAIN) a0 = a0 + (ak - as[k * 32]);
+            as[k * 32] = ak;
+        }
+        ++e;
+        t = tn;
+        if (!PLAIN && (e & p.renorm_mask) == 0u) {  // FP64 renormalisation of a0
+            double s = 0.0;
+            for (int k = 0; k < R; ++k) s = __dadd_rn(s, (double)as[k * 32]);
+            a0 = (T)s;
+        }
+
+        // monitor at the new state
+        const uint32_t ab_old = ml.ab;
+#pragma unroll
+        for (int a = 0; a < SMC_MAX_ATOMS; ++a)
+            if (a < NA) ml.L[a] += adelta[j * NA + a];
+        ml.ab = atom_bits(ml, NA, athr, aneg);
+        if (!(skip_same && ml.ab == ab_old && !ml.pend)) v = mon_state(ml, P, t);
+        if (v) finish(v);
+        else if ((uint64_t)e >= p.budget) finish(3);
+    }
+
+    // warp reduction of the instance's counts, one atomic per counter
+    c_yes = warp_sum(c_yes);
+    c_dec = warp_sum(c_dec);
+    c_ev = warp_sum(c_ev);
+    c_bud = warp_sum(c_bud);
+    if (lane == 0 && (c_dec | c_bud)) {
+        atomicAdd(&p.counts[4 * m + 0], c_yes);
+        atomicAdd(&p.counts[4 * m + 1], c_dec);
+        atomicAdd(&p.counts[4 * m + 2], c_ev);
+        atomicAdd(&p.counts[4 * m + 3], c_bud);
+    }
+}
+
+template <bool PLAIN>
+__global__ void __launch_bounds__(256) ssa_kernel(const SsaParams p)
+{
+    typedef typename Prec<PLAIN>::T T;
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ int s_last;
+    {
+        const uint4 *src = reinterpret_cast<const uint4 *>(p.prog);
+        uint4 *dst = reinterpret_cast<uint4 *>(smem);
+        for (int i = threadIdx.x; i < (int)(sizeof(MonProg) / 16); i += blockDim.x) dst[i] = src[i];
+    }
+    __syncthreads();
+    const MonProg &P = *reinterpret_cast<const MonProg *>(smem);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    unsigned char *wb = smem + sizeof(MonProg) + (size_t)warp * p.warp_bytes;
+    uint32_t *blob = reinterpret_cast<uint32_t *>(wb);
+    int32_t *xs = reinterpret_cast<int32_t *>(wb + (size_t)p.blob_words * 4) + lane;
+    T *as = reinterpret_cast<T *>(wb + (size_t)p.blob_words * 4 + (size_t)p.s_max * 128) + lane;
+
+    bool first = true;
+    int cur = -1;
+    const int gw = blockIdx.x * (blockDim.x >> 5) + warp;
+    for (;;) {
+        const int m = acquire_instance(p, first, gw, lane);
+        if (m < 0) break;
+        if (m != cur) {
+            const uint32_t *src = p.blobs + p.blob_off[m];
+            const int words = (int)src[BH_WORDS];
+            for (int i = lane; i < words; i += 32) blob[i] = src[i];
+            __syncwarp();
+            cur = m;
+        }
+        run_instance<PLAIN>(p, P, m, blob, xs, as, lane);
+        __syncwarp();
+    }
+
+    // the last block to finish computes the Wilson interval of every instance
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const unsigned tk = atomicAdd(p.ticket, 1u);
+        s_last = (tk == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (s_last && p.wilson) {
+        __threadfence();
+        for (int i = threadIdx.x; i < p.n_list; i += blockDim.x) {
+            const int m = p.inst_list[i];
+            const volatile unsigned long long *c = p.counts + 4 * m;
+            wilson_eq4(c[0], c[1], p.z, p.wilson + 3 * m);
+        }
+    }
+}
+
+__global__ void queue_init_kernel(const SsaParams p)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < p.n_inst) p.tnext[i] = p.uniform ? p.u_begin : p.tbegin[i];
+    if (i == 0) { *p.cursor = 0u; *p.ticket = 0u; }
+}
+
+// Replays given paths through the compiled monitor (one thread per path).
+// decided_at is the point where the verdict was fixed: 2k after state k was
+// processed, 2k+1 after the entry time of state k+1 (or, after the last
+// state, tmin / the end of the path) was known.
+__global__ void replay_kernel(const ReplayParams rp)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= rp.n_paths) return;
+    const MonProg &P = *rp.prog;
+    const int na = P.n_atoms, S = rp.S, n = rp.len[i];
+    const int32_t *x = rp.x + rp.off[i] * S;
+    const double *t = rp.t + rp.off[i];
+    MonLane ml;
+    int v = 0;
+    long long q = -1;
+    for (int k = 0; k < n && !v; ++k) {
+        if (k > 0) {
+            if (ml.pend || __double_as_longlong(t[k]) > ml.hb) v = mon_draw(ml, P, t[k]);
+            if (v) { q = 2 * k - 1; break; }
+        }
+        for (int a = 0; a < na; ++a) {
+            long long L = 0;
+            for (int s = 0; s < S; ++s) L += (long long)rp.coef[a * S + s] * x[k * S + s];
+            ml.L[a] = L;
+        }
+        ml.ab = atom_bits(ml, na, rp.athr, rp.aneg);
+        if (k == 0) mon_start(ml, P);
+        v = mon_state(ml, P, t[k]);
+        if (v) q = 2 * k;
+    }
+    if (!v && n > 0) {
+        if (rp.closed[i]) v = mon_close(ml, P);
+        else v = mon_draw(ml, P, rp.tmin[i]);
+        if (v) q = 2 * (long long)n - 1;
+    }
+    rp.verdict[i] = v;
+    rp.decided_at[i] = q;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// host wrappers
+
+static int to_code(cudaError_t e) { return e == cudaSuccess ? 0 : -3; }
+
+int smc_ssa_set_smem_limit(int plain, int smem_bytes)
+{
+    const void *f = plain ? (const void *)ssa_kernel<true> : (const void *)ssa_kernel<false>;
+    return to_code(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes));
+}
+
+int smc_ssa_max_blocks_per_sm(int plain, int block, int smem_bytes, int *out)
+{
+    const void *f = plain ? (const void *)ssa_kernel<true> : (const void *)ssa_kernel<false>;
+    return to_code(cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, f, block, smem_bytes));
+}
+
+int smc_launch_ssa(int plain, const SsaParams &p, int grid, int block, int smem_bytes, void *stream)
+{
+    cudaStream_t s = (cudaStream_t)stream;
+    if (plain) ssa_kernel<true><<<grid, block, smem_bytes, s>>>(p);
+    else ssa_kernel<false><<<grid, block, smem_bytes, s>>>(p);
+    return to_code(cudaGetLastError());
+}
+
+int smc_launch_queue_init(const SsaParams &p, void *stream)
+{
+    const int n = p.n_inst > 0 ? p.n_inst : 1;
+    queue_init_kernel<<<(n + 255) / 256, 256, 0, (cudaStream_t)stream>>>(p);
+    return to_code(cudaGetLastError());
+}
+
+int smc_launch_replay(const ReplayParams &rp, void *stream)
+{
+    const int n = rp.n_paths > 0 ? rp.n_paths : 1;
+    replay_kernel<<<(n + 127) / 128, 128, 0, (cudaStream_t)stream>>>(rp);
+    return to_code(cudaGetLastError());
+}

@@ -1,0 +1,76 @@
+"""The C-ABI library builds, loads without a GPU, exports every entry point
+declared in include/smc.h, and its host-side utilities (normal quantile,
+Eq. 4, Eq. 5) agree with the oracle and with SciPy."""
+import ctypes
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+from scipy import special
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope='module')
+def native():
+    from paper_0912_2551_gb300 import _native
+    _native.load()
+    return _native
+
+
+def _declared():
+    txt = open(os.path.join(ROOT, 'include', 'smc.h')).read()
+    txt = re.sub(r'/\*.*?\*/', '', txt, flags=re.S)
+    return sorted(set(re.findall(r'\b(smc_[a-z_0-9]+)\s*\(', txt)))
+
+
+def test_every_declared_symbol_is_exported(native):
+    lib = native.LIB_PATH
+    out = subprocess.run(['nm', '-D', '--defined-only', lib], capture_output=True, text=True).stdout
+    exported = set(re.findall(r' T (smc_[a-z_0-9]+)', out))
+    declared = _declared()
+    assert declared, 'no declarations parsed'
+    missing = [d for d in declared if d not in exported]
+    assert not missing, missing
+    for d in declared:
+        assert d in native.SIGNATURES, f'{d} has no binding'
+
+
+def test_create_without_gpu_reports_no_device(native):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip('a GPU is present')
+    h = ctypes.c_void_p()
+    assert native.smc_create(ctypes.byref(h), 0) == native.SMC_E_NO_DEVICE
+    assert native.smc_strerror(native.SMC_E_NO_DEVICE) == b'no suitable CUDA device'
+
+
+def test_as241_against_scipy(native):
+    for p in [1e-12, 1e-6, 0.01, 0.025, 0.3, 0.5, 0.7, 0.975, 0.995, 0.99995, 1 - 1e-9]:
+        z = native.smc_normal_quantile(p)
+        assert abs(z - special.ndtri(p)) <= 4e-15 * max(1.0, abs(z)), p
+
+
+def test_wilson_host_matches_oracle(native, orc):
+    from oracle import wilson
+    import paper_0912_2551_gb300 as smc
+    for yes, n in [(0, 10), (10, 10), (253, 2648), (19, 2648), (1547, 2495), (7, 1000000)]:
+        for conf in (0.95, 0.99, 0.9999):
+            lo, hi = smc.wilson_interval(yes, n, conf)
+            _, olo, ohi = wilson.wilson_interval(yes, n, conf)
+            assert abs(lo - olo) <= 1e-12 * max(abs(olo), 1e-300) + 1e-300
+            assert abs(hi - ohi) <= 1e-12 * abs(ohi)
+    for p in [0.0, 0.01, 0.5, 0.9, 1.0]:
+        a = smc.wilson_sample(p, 0.025, 0.99)
+        b = wilson.wilson_sample_real(p, 0.025, 0.99)
+        assert abs(a - b) <= 1e-9 * b
+
+
+def test_formula_postfix():
+    import paper_0912_2551_gb300 as smc
+    f = ('U', 0.0, 200.0, ('atom', 0), ('and', ('atom', 1), ('F', 0.0, 50.0, ('atom', 2))))
+    nodes = smc.postfix(f)
+    assert [n[0] for n in nodes] == [2, 2, 2, 8, 4, 7]
+    assert nodes[3][2:] == (0.0, 50.0) and nodes[5][2:] == (0.0, 200.0)
