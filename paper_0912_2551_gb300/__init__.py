@@ -170,7 +170,7 @@ class Context:
 
     def simulate(self, precision: str = 'plain', seed: int = 0, traj_begin: int = 0, n_traj: int = 1,
                  confidence: float = 0.95, outputs: Sequence[str] = ('verdict', 'status', 'events', 't_final'),
-                 counts=None, stream=None) -> Dict[str, object]:
+                 counts=None, wilson=None, stream=None) -> Dict[str, object]:
         """Runs trajectories [traj_begin, traj_begin + n_traj) of every
         instance on the GPU; returns torch CUDA tensors (counts [n_inst, 4],
         wilson [n_inst, 3] and the requested per-trajectory outputs)."""
@@ -181,7 +181,7 @@ class Context:
         if counts is None:
             counts = torch.zeros((n, 4), dtype=torch.int64, device=dev)
         out['counts'] = counts
-        out['wilson'] = torch.zeros((n, 3), dtype=torch.float64, device=dev)
+        out['wilson'] = wilson if wilson is not None else torch.zeros((n, 3), dtype=torch.float64, device=dev)
         spec = dict(verdict=(torch.uint8, ()), status=(torch.uint8, ()), events=(torch.int64, ()),
                     t_final=(torch.float64, ()), x_final=(torch.int32, (self.s_max,)))
         so = N.smc_sim_out()
