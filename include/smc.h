@@ -217,6 +217,32 @@ int smc_monitor_replay(smc_ctx *ctx, int n_paths, const int32_t *len, const int3
                        const double *t, const double *tmin, const uint8_t *closed,
                        int32_t *verdict, int64_t *decided_at);
 
+/* Allocation-free variant of smc_simulate (the paper has no counterpart:
+ * this serves callers that must not allocate device memory when they run,
+ * for example code whose device memory is owned by another allocator, or a
+ * loop that must not block in cudaMalloc / cudaFree).
+ *
+ * Same arguments and outputs as smc_simulate; the caller passes the outputs
+ * in *out (device pointers, counts required).  Instead of the context's own
+ * work-queue buffers, the SSA kernel uses a fixed device array of the
+ * library (SMC_NOALLOC_MAX_INSTANCES 64-bit queue counters plus two 32-bit
+ * words, about 32 KiB, held by every GPU that loads the library until the
+ * process exits).  The call allocates nothing:
+ *  - the context's model tables must already be on the device: call
+ *    smc_simulate or smc_estimate once after loading the model and property
+ *    (otherwise SMC_E_STATE);
+ *  - more than SMC_NOALLOC_MAX_INSTANCES instances: SMC_E_INVALID_ARG;
+ *  - the first call on a device looks up the array's device address
+ *    (cudaGetSymbolAddress) and caches it; make that first call before any
+ *    stream capture;
+ *  - every call on a device shares the array; each call resets the counters
+ *    it uses before its kernel runs, so consecutive calls are independent,
+ *    but calls whose work overlaps on the GPU (other streams or host
+ *    threads) race on the array and must be serialised by the caller. */
+#define SMC_NOALLOC_MAX_INSTANCES 4096
+int smc_simulate_noalloc(smc_ctx *ctx, int precision, uint64_t seed, uint64_t traj_begin,
+                         uint64_t n_traj, double confidence, const smc_sim_out *out, void *stream);
+
 /* Host utilities (no GPU needed). */
 double smc_normal_quantile(double p);                           /* Phi^{-1}(p) */
 int smc_wilson_interval(uint64_t yes, uint64_t n, double confidence, double *lo,

@@ -79,6 +79,9 @@ SIGNATURES = {
     'smc_simulate': (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_uint64, ctypes.c_uint64,
                                     ctypes.c_uint64, ctypes.c_double, ctypes.POINTER(smc_sim_out),
                                     ctypes.c_void_p]),
+    'smc_simulate_noalloc': (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_uint64, ctypes.c_uint64,
+                                            ctypes.c_uint64, ctypes.c_double, ctypes.POINTER(smc_sim_out),
+                                            ctypes.c_void_p]),
     'smc_monitor_replay': (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, c_i32p, c_i32p, c_f64p, c_f64p,
                                           c_u8p, c_i32p, c_i64p]),
     'smc_normal_quantile': (ctypes.c_double, [ctypes.c_double]),

@@ -613,6 +613,87 @@ int smc_simulate(smc_ctx *ctx, int precision, uint64_t seed, uint64_t traj_begin
     return launch_all(ctx, precision == SMC_PLAIN_FP64, seed, z, *out, traj_begin, n_traj, s, true);
 }
 
+// smc_simulate without any device allocation: the model tables must already
+// be resident (an earlier smc_simulate / smc_estimate put them there) and the
+// SSA kernel's work queue, instance cursor and finish ticket live in the
+// library's fixed scratch array (smc_noalloc_scratch) instead of buffers of
+// the context.  Nothing here calls cudaMalloc, cudaFree or an allocating
+// library routine: only attribute and occupancy queries and two launches per
+// size class (queue reset, SSA kernel) on the caller's stream.
+int smc_simulate_noalloc(smc_ctx *ctx, int precision, uint64_t seed, uint64_t traj_begin,
+                         uint64_t n_traj, double confidence, const smc_sim_out *out, void *stream)
+{
+    if (!ctx) return SMC_E_INVALID_ARG;
+    if (!out || !out->counts) return fail(ctx, SMC_E_INVALID_ARG, "counts output required");
+    if (precision != SMC_PLAIN_FP64 && precision != SMC_MIXED) return fail(ctx, SMC_E_INVALID_ARG, "bad precision");
+    if (traj_begin + n_traj > (1ull << 32)) return fail(ctx, SMC_E_INVALID_ARG, "trajectory index >= 2^32");
+    if (out->wilson && !(confidence > 0.0 && confidence < 1.0))
+        return fail(ctx, SMC_E_INVALID_ARG, "confidence must lie in (0,1)");
+    if (!ctx->have_model || !ctx->have_prop || ctx->dirty || !ctx->d_blobs)
+        return fail(ctx, SMC_E_STATE,
+                    "model tables not on the device: call smc_simulate or smc_estimate once first");
+    if (ctx->n_inst > SMC_NOALLOC_MAX_INSTANCES)
+        return fail(ctx, SMC_E_INVALID_ARG,
+                    "smc_simulate_noalloc supports at most SMC_NOALLOC_MAX_INSTANCES (4096) instances");
+    CK(cudaSetDevice(ctx->device));
+    unsigned long long *queue = nullptr;
+    unsigned int *sync = nullptr;
+    if (smc_noalloc_scratch(ctx->device, &queue, &sync))
+        return fail(ctx, SMC_E_CUDA, "cudaGetSymbolAddress of the scratch array failed");
+    cudaStream_t s = stream ? (cudaStream_t)stream : ctx->stream;
+    const int plain = precision == SMC_PLAIN_FP64;
+    SsaParams p;
+    std::memset(&p, 0, sizeof(p));
+    p.blobs = ctx->d_blobs;
+    p.blob_off = ctx->d_blob_off;
+    p.n_inst = ctx->n_inst;
+    p.uniform = 1;
+    p.u_begin = traj_begin;
+    p.u_end = traj_begin + n_traj;
+    p.tnext = queue;
+    p.cursor = sync;
+    p.ticket = sync + 1;
+    p.prog = ctx->d_prog;
+    round_keys(seed, p.rk0, p.rk1);
+    p.budget = ctx->budget;
+    p.renorm_mask = (1u << ctx->renorm_log2) - 1u;
+    p.counts = (unsigned long long *)out->counts;
+    p.wilson = out->wilson;
+    p.z = out->wilson ? z_of(confidence) : 0.0;
+    p.o_verdict = out->verdict;
+    p.o_status = out->status;
+    p.o_events = out->events;
+    p.o_tfinal = out->t_final;
+    p.o_xfinal = out->x_final;
+    p.out_base = traj_begin;
+    p.out_stride = n_traj;
+    p.x_stride = ctx->s_max;
+    for (auto &c : ctx->classes) {
+        const Shape &sh = c.shape[plain ? 1 : 0];
+        p.inst_list = c.d_list;
+        p.n_list = (int)c.inst.size();
+        p.refill = sh.refill;
+        p.blob_words = (c.blob_words + 3) & ~3;
+        p.s_max = c.s_max;
+        p.r_max = c.r_max;
+        p.warp_bytes = warp_bytes_of(c, plain);
+        const int block = 32 * sh.warps;
+        const int smem = (int)sizeof(MonProg) + sh.warps * p.warp_bytes;
+        if ((size_t)smem > ctx->smem_optin)
+            return fail(ctx, SMC_E_UNSUPPORTED, "model tables do not fit in shared memory");
+        if (smc_ssa_set_smem_limit(plain, smem)) return fail(ctx, SMC_E_CUDA, "cudaFuncSetAttribute failed");
+        int per_sm = 0;
+        if (smc_ssa_max_blocks_per_sm(plain, block, smem, &per_sm) || per_sm < 1)
+            return fail(ctx, SMC_E_CUDA, "occupancy query failed");
+        if (sh.blocks_sm > 0) per_sm = std::min(per_sm, sh.blocks_sm);
+        // resets this launch's queue counters, cursor and ticket in the scratch array
+        if (smc_launch_queue_init(p, s)) return fail(ctx, SMC_E_CUDA, "queue reset launch failed");
+        if (smc_launch_ssa(plain, p, ctx->n_sm * per_sm, block, smem, s))
+            return fail(ctx, SMC_E_CUDA, std::string("ssa launch: ") + cudaGetErrorString(cudaGetLastError()));
+    }
+    return SMC_OK;
+}
+
 int smc_estimate(smc_ctx *ctx, double confidence, double half_width, uint64_t seed, int mode,
                  uint64_t fixed_n, smc_result *out)
 {

@@ -130,5 +130,8 @@ int smc_ssa_max_blocks_per_sm(int plain, int block, int smem_bytes, int *out);
 int smc_ssa_set_smem_limit(int plain, int smem_bytes);
 int smc_launch_queue_init(const SsaParams &p, void *stream);
 int smc_launch_replay(const ReplayParams &p, void *stream);
+// fixed scratch of smc_simulate_noalloc (see smc_kernels.cu)
+#define SMC_NOALLOC_MAX_DEVICES 64
+int smc_noalloc_scratch(int device, unsigned long long **queue, unsigned int **sync);
 }
 #endif

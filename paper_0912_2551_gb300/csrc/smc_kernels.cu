@@ -22,6 +22,10 @@
 #include <math.h>
 #include <stdint.h>
 
+#include <mutex>
+
+#include "smc.h"
+
 #include "smc_internal.h"
 
 #define FULL_MASK 0xffffffffu
@@ -611,4 +615,34 @@ int smc_launch_replay(const ReplayParams &rp, void *stream)
     const int n = rp.n_paths > 0 ? rp.n_paths : 1;
     replay_kernel<<<(n + 127) / 128, 128, 0, (cudaStream_t)stream>>>(rp);
     return to_code(cudaGetLastError());
+}
+
+// ---------------------------------------------------------------------------
+// Scratch of smc_simulate_noalloc: the SSA kernel's work queue (one 64-bit
+// counter per instance) followed by its instance cursor and finish ticket,
+// in a fixed array that every GPU loading this library holds until the
+// process exits (SMC_NOALLOC_MAX_INSTANCES + 2 words, about 32 KiB).  It is
+// shared by every call on a device: each call resets the counters it uses
+// (queue_init_kernel) before its SSA launch, and calls whose launches
+// overlap on the GPU race on it.
+static __device__ __align__(256) unsigned long long g_noalloc_scratch[SMC_NOALLOC_MAX_INSTANCES + 2];
+
+// Device address of the array on `device`, which must be the current
+// device.  Looked up with cudaGetSymbolAddress on the first call per device
+// (host code may not use the array's name as an address) and cached.
+int smc_noalloc_scratch(int device, unsigned long long **queue, unsigned int **sync)
+{
+    static std::mutex mu;
+    static unsigned long long *addr[SMC_NOALLOC_MAX_DEVICES] = {};
+    if (device < 0 || device >= SMC_NOALLOC_MAX_DEVICES || !queue || !sync) return -1;
+    std::lock_guard<std::mutex> lock(mu);
+    if (!addr[device]) {
+        void *p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p) return -3;
+        addr[device] = static_cast<unsigned long long *>(p);
+    }
+    *queue = addr[device];
+    *sync = reinterpret_cast<unsigned int *>(addr[device] + SMC_NOALLOC_MAX_INSTANCES);
+    return 0;
 }
