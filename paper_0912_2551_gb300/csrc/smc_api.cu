@@ -332,10 +332,19 @@ int prepare(smc_ctx *ctx)
     return SMC_OK;
 }
 
-int warp_bytes_of(const SizeClass &c, int plain)
+// candidate clocks per warp: only formulas with a nested F / G keep them
+int tc_bytes_of(const MonProg &prog)
+{
+    for (int u = 0; u < prog.n_units; ++u)
+        if (prog.u[u].nest) return SMC_MAX_UNITS * 32 * 8;
+    return 0;
+}
+
+// warp slice: table | x[(s_max + 1)][32] | tc | a[r_max][32]
+int warp_bytes_of(const SizeClass &c, int plain, int tc_bytes)
 {
     const int blob_words = (c.blob_words + 3) & ~3;
-    const int b = blob_words * 4 + c.s_max * 128 + c.r_max * 32 * (plain ? 8 : 4);
+    const int b = blob_words * 4 + (c.s_max + 1) * 128 + tc_bytes + c.r_max * 32 * (plain ? 8 : 4);
     return (b + 15) & ~15;
 }
 
@@ -380,7 +389,8 @@ int launch_all(smc_ctx *ctx, int plain, uint64_t seed, double z, const smc_sim_o
         p.blob_words = (c.blob_words + 3) & ~3;
         p.s_max = c.s_max;
         p.r_max = c.r_max;
-        p.warp_bytes = warp_bytes_of(c, plain);
+        p.tc_bytes = tc_bytes_of(ctx->prog);
+        p.warp_bytes = warp_bytes_of(c, plain, p.tc_bytes);
         const int block = 32 * sh.warps;
         const int smem = (int)sizeof(MonProg) + sh.warps * p.warp_bytes;
         if ((size_t)smem > ctx->smem_optin)
@@ -676,7 +686,8 @@ int smc_simulate_noalloc(smc_ctx *ctx, int precision, uint64_t seed, uint64_t tr
         p.blob_words = (c.blob_words + 3) & ~3;
         p.s_max = c.s_max;
         p.r_max = c.r_max;
-        p.warp_bytes = warp_bytes_of(c, plain);
+        p.tc_bytes = tc_bytes_of(ctx->prog);
+        p.warp_bytes = warp_bytes_of(c, plain, p.tc_bytes);
         const int block = 32 * sh.warps;
         const int smem = (int)sizeof(MonProg) + sh.warps * p.warp_bytes;
         if ((size_t)smem > ctx->smem_optin)

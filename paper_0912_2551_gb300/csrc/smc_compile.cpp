@@ -338,17 +338,17 @@ int build_blob(const InstanceModel &M, int n_used, const int32_t *coef_used /*[n
         }
     }
     st_ptr[R] = (uint32_t)st.size();
-    // reactant words
-    std::vector<uint32_t> reac(R);
+    // propensity words: k | ra << 8 | rb << 16 | homo << 24, with species
+    // index S standing for a constant-1 column, so h = x_ra (x_rb - homo) >> homo
+    std::vector<uint32_t> pw(R);
     for (int k = 0; k < R; ++k) {
         int ra = M.reactants[2 * k], rb = M.reactants[2 * k + 1];
         if (ra < 0 && rb >= 0) { ra = rb; rb = -1; }
-        uint32_t kind;
-        if (ra < 0) kind = RK_ZERO;
-        else if (rb < 0) kind = RK_ONE;
-        else if (ra == rb) kind = RK_HOMO;
-        else kind = RK_HETERO;
-        reac[k] = (uint32_t)(ra < 0 ? 0 : ra) | ((uint32_t)(rb < 0 ? 0 : rb) << 8) | (kind << 16);
+        uint32_t homo = 0;
+        if (ra < 0) { ra = S; rb = S; }
+        else if (rb < 0) rb = S;
+        else if (ra == rb) homo = 1;
+        pw[k] = (uint32_t)k | ((uint32_t)ra << 8) | ((uint32_t)rb << 16) | (homo << 24);
     }
     // dependency graph: k in dep(j) iff a_k reads a species that j changes
     std::vector<uint32_t> dep_ptr(R + 1, 0), dep;
@@ -356,35 +356,35 @@ int build_blob(const InstanceModel &M, int n_used, const int32_t *coef_used /*[n
         dep_ptr[j] = (uint32_t)dep.size();
         for (int k = 0; k < R; ++k) {
             const int ra = M.reactants[2 * k], rb = M.reactants[2 * k + 1];
-            if ((ra >= 0 && changes[j][ra]) || (rb >= 0 && changes[j][rb])) dep.push_back((uint32_t)k);
+            if ((ra >= 0 && changes[j][ra]) || (rb >= 0 && changes[j][rb])) dep.push_back(pw[k]);
         }
     }
     dep_ptr[R] = (uint32_t)dep.size();
-    // atoms: per-reaction deltas, initial values, thresholds
-    std::vector<int32_t> adelta((size_t)R * n_used);
-    std::vector<int64_t> al0(n_used), athr(2 * (size_t)n_used);
+    // atoms: sparse terms, thresholds, and which reactions move each atom
+    std::vector<uint32_t> aterm_ptr(n_used + 1, 0), aterm, amask(R, 0);
+    std::vector<int64_t> athr(2 * (size_t)n_used);
     uint32_t aneg = 0;
     for (int a = 0; a < n_used; ++a) {
         const int32_t *c = coef_used + (size_t)a * S;
-        for (int i = 0; i < S; ++i)
+        aterm_ptr[a] = (uint32_t)aterm.size();
+        for (int i = 0; i < S; ++i) {
             if (c[i] > (1 << 20) || c[i] < -(1 << 20)) {
                 err = "atom coefficients must lie in [-2^20, 2^20]";
                 return SMC_E_INVALID_ARG;
             }
-        int64_t L = 0;
-        for (int i = 0; i < S; ++i) L += (int64_t)c[i] * M.x0[i];
-        al0[a] = L;
+            if (c[i] != 0) aterm.push_back((uint32_t)i | ((uint32_t)c[i] << 8));
+        }
         for (int j = 0; j < R; ++j) {
             int64_t d = 0;
             for (int i = 0; i < S; ++i) d += (int64_t)c[i] * M.stoich[(size_t)j * S + i];
-            if (d > INT32_MAX || d < INT32_MIN) { err = "atom change per reaction exceeds int32"; return SMC_E_INVALID_ARG; }
-            adelta[(size_t)j * n_used + a] = (int32_t)d;
+            if (d != 0) amask[j] |= 1u << a;
         }
         if (!std::isfinite(bound_used[a])) { err = "atom bounds must be finite"; return SMC_E_INVALID_ARG; }
         bool neg;
         atom_threshold(op_used[a], bound_used[a], athr[2 * a], athr[2 * a + 1], neg);
         if (neg) aneg |= 1u << a;
     }
+    aterm_ptr[n_used] = (uint32_t)aterm.size();
     // layout
     blob.assign(BH_COUNT, 0);
     auto align2 = [&]() { if (blob.size() & 1) blob.push_back(0); };
@@ -404,7 +404,7 @@ int build_blob(const InstanceModel &M, int n_used, const int32_t *coef_used /*[n
         blob.push_back(w);
     }
     section(BH_REAC);
-    blob.insert(blob.end(), reac.begin(), reac.end());
+    blob.insert(blob.end(), pw.begin(), pw.end());
     section(BH_ST_PTR);
     blob.insert(blob.end(), st_ptr.begin(), st_ptr.end());
     section(BH_ST);
@@ -413,16 +413,40 @@ int build_blob(const InstanceModel &M, int n_used, const int32_t *coef_used /*[n
     blob.insert(blob.end(), dep_ptr.begin(), dep_ptr.end());
     section(BH_DEP);
     blob.insert(blob.end(), dep.begin(), dep.end());
-    section(BH_ADELTA);
-    for (int32_t v : adelta) blob.push_back((uint32_t)v);
+    section(BH_AMASK);
+    blob.insert(blob.end(), amask.begin(), amask.end());
+    section(BH_ATERM_PTR);
+    blob.insert(blob.end(), aterm_ptr.begin(), aterm_ptr.end());
+    section(BH_ATERM);
+    blob.insert(blob.end(), aterm.begin(), aterm.end());
+    bool small = S <= SMC_SMALL_MAX && R <= SMC_SMALL_MAX;
+    for (size_t q = 0; q < st.size() && small; ++q) {
+        const int32_t d = ((int32_t)st[q]) >> 8;
+        if (d > 127 || d < -127) small = false;
+    }
+    if (small) {
+        section(BH_DENSE);
+        for (int j = 0; j < R; ++j) {
+            uint32_t w[2] = {0, 0};
+            for (int i = 0; i < S; ++i)
+                w[i >> 2] |= ((uint32_t)(uint8_t)(int8_t)M.stoich[(size_t)j * S + i]) << (8 * (i & 3));
+            blob.push_back(w[0]);
+            blob.push_back(w[1]);
+        }
+    }
     section(BH_X0);
     for (int i = 0; i < S; ++i) blob.push_back((uint32_t)M.x0[i]);
-    section(BH_AL0);
-    for (int64_t v : al0) { blob.push_back((uint32_t)(uint64_t)v); blob.push_back((uint32_t)((uint64_t)v >> 32)); }
-    section(BH_ATHR);
-    for (int64_t v : athr) { blob.push_back((uint32_t)(uint64_t)v); blob.push_back((uint32_t)((uint64_t)v >> 32)); }
-    section(BH_ANEG);
-    blob.push_back(aneg);
+    section(BH_ATOM);
+    for (int a = 0; a < n_used; ++a) {
+        const uint32_t nt = aterm_ptr[a + 1] - aterm_ptr[a];
+        blob.push_back(nt == 1 ? aterm[aterm_ptr[a]] : 0xFFFFFFFFu);
+        blob.push_back((aneg >> a) & 1u);
+        for (int h = 0; h < 2; ++h) {
+            const uint64_t v = (uint64_t)athr[2 * a + h];
+            blob.push_back((uint32_t)v);
+            blob.push_back((uint32_t)(v >> 32));
+        }
+    }
     while (blob.size() & 3) blob.push_back(0);
     blob[BH_S] = (uint32_t)S;
     blob[BH_R] = (uint32_t)R;

@@ -49,22 +49,34 @@ static_assert(sizeof(MonProg) % 16 == 0, "MonProg is copied in 16-byte words");
 //   hdr[0..15]: S, R, n_atoms, total_words, then word offsets of the sections:
 enum BlobHdr {
     BH_S = 0, BH_R, BH_NA, BH_WORDS,
-    BH_RATE_D,   // double [R]        stochastic rate constants
-    BH_RATE_F,   // float  [R]        the same, rounded to FP32
-    BH_REAC,     // u32    [R]        ra | rb << 8 | kind << 16
-    BH_ST_PTR,   // u32    [R+1]      CSR row pointers of the stoichiometry
-    BH_ST,       // u32    [nnz]      species | (delta << 8) (delta signed)
-    BH_DEP_PTR,  // u32    [R+1]      CSR row pointers of dep(j)
-    BH_DEP,      // u32    [ndep]     k: propensity a_k reads a species j changes
-    BH_ADELTA,   // i32    [R][NA]    change of each atom's linear form under j
-    BH_X0,       // i32    [S]        initial counts
-    BH_AL0,      // i64    [NA]       linear forms at x0
-    BH_ATHR,     // i64    [NA][2]    atom holds iff lo <= L <= hi (xor neg)
-    BH_ANEG,     // u32    [1]        neg bits
-    BH_COUNT = 16
+    BH_RATE_D,    // double [R]      stochastic rate constants
+    BH_RATE_F,    // float  [R]      the same, rounded to FP32
+    BH_REAC,      // u32    [R]      propensity word of reaction k (below)
+    BH_ST_PTR,    // u32    [R+1]    CSR row pointers of the stoichiometry
+    BH_ST,        // u32    [nnz]    species | (delta << 8) (delta signed)
+    BH_DEP_PTR,   // u32    [R+1]    CSR row pointers of dep(j)
+    BH_DEP,       // u32    [ndep]   propensity words of the k in dep(j)
+    BH_AMASK,     // u32    [R]      atoms whose linear form reaction j changes
+    BH_ATERM_PTR, // u32    [NA+1]   CSR row pointers of the atoms' terms
+    BH_ATERM,     // u32    [nterm]  species | (coef << 8) (coef signed)
+    BH_X0,        // i32    [S]      initial counts
+    BH_ATOM,      // u32    [NA][6]  atom record (below)
+    BH_DENSE,     // u32    [R][2]   small networks only (else offset 0): the
+                  //                 net changes of species 0..7 as int8 bytes
+    BH_COUNT = 20
 };
-// propensity kinds (Sec. 2.2): h = 1, x_a, x_a x_b, x_a (x_a - 1) / 2
-enum { RK_ZERO = 0, RK_ONE = 1, RK_HETERO = 2, RK_HOMO = 3 };
+// Small networks (S <= 8, R <= 8, |v_ji| <= 127) are stepped with warp-uniform
+// loops: every propensity recomputed per event, selection on the prefix sums
+// kept in registers, stoichiometry from the dense byte rows.
+#define SMC_SMALL_MAX 8
+// Atom record (6 words): [0] the single term species | coef << 8, or
+// 0xFFFFFFFF when the atom has several terms (then the ATERM rows hold
+// them); [1] neg (0/1); [2..3] lo and [4..5] hi (int64): the atom holds iff
+// (lo <= L <= hi) xor neg, L = sum of coef * x over its terms.
+// Propensity word: k | ra << 8 | rb << 16 | homo << 24.  Species index S is
+// a constant-1 column of the lane state, so every mass-action propensity
+// (Sec. 2.2) is a_k = c_k h with h = x_ra (x_rb - homo) >> homo:
+// 1 (ra = rb = S), x_a (rb = S), x_a x_b, or x_a (x_a - 1) / 2 (homo = 1).
 
 // ---------------------------------------------------------------------------
 // Kernel parameters of the persistent SSA kernel.
@@ -88,6 +100,7 @@ struct SsaParams {
     int32_t refill;              // refill when >= refill lanes are idle
     int32_t blob_words;          // per-warp table area (words, multiple of 4)
     int32_t s_max, r_max;        // per-lane state area
+    int32_t tc_bytes;            // per-warp candidate clocks (0: no nested unit)
     int32_t warp_bytes;          // shared memory per warp
     // outputs
     unsigned long long *counts;  // [n_inst][4] yes, n, events, budget hits

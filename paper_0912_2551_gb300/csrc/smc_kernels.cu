@@ -17,7 +17,7 @@
 //   monitor: windows that t' closes                  (Sec. 3.2: stop as soon as
 //   j = first index with running sum > u_sel * a0      the verdict is fixed)
 //   x += v_j; a_k recomputed for k in dep(j)
-//   monitor: atoms and units at the new state
+//   monitor: atoms moved by j, then the units at the new state
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -25,7 +25,6 @@
 #include <mutex>
 
 #include "smc.h"
-
 #include "smc_internal.h"
 
 #define FULL_MASK 0xffffffffu
@@ -56,17 +55,34 @@ __device__ __forceinline__ void philox10(uint32_t c0, uint32_t c1, uint32_t c2, 
     w0 = c0; w1 = c1; w2 = c2; w3 = c3;
 }
 
-// (0,1) from 52 bits: ((hi:lo) >> 12 + 1/2) 2^-52, exact, in [2^-53, 1 - 2^-53].
+// The double holding m * 2^e0 for an integer 0 < m < 2^53, assembled on the
+// integer pipe (exact: no rounding is needed below 2^53).
+__device__ __forceinline__ double exact_scaled(uint64_t m, int e0)
+{
+    const int p = 63 - __clzll((long long)m);  // position of the leading one
+    const uint64_t mant = (m << (52 - p)) & 0x000FFFFFFFFFFFFFull;
+    return __longlong_as_double((long long)(((uint64_t)(1023 + p + e0) << 52) | mant));
+}
+
+// (0,1) from 52 bits: ((hi:lo) >> 12 + 1/2) 2^-52 = (2v + 1) 2^-53, exact, in
+// [2^-53, 1 - 2^-53].
 __device__ __forceinline__ double u01_52(uint32_t hi, uint32_t lo)
 {
     const uint64_t v = ((((uint64_t)hi) << 32) | (uint64_t)lo) >> 12;
-    return __dmul_rn(__dadd_rn(__ull2double_rn(v), 0.5), 0x1p-52);
+    return exact_scaled((v << 1) | 1ull, -53);
 }
 
 // (0,1) in FP32 from 23 bits: (w >> 9 + 1/2) 2^-23, exact, in [2^-24, 1 - 2^-24].
 __device__ __forceinline__ float u01_23(uint32_t w)
 {
     return __fmaf_rn((float)(w >> 9), 0x1p-23f, 0x1p-24f);
+}
+
+// An integer h (exact for 0 <= h < 2^53, rounded once otherwise) as a double.
+__device__ __forceinline__ double int_to_double(long long h)
+{
+    if ((unsigned long long)h < (1ull << 53)) return h ? exact_scaled((uint64_t)h, 0) : 0.0;
+    return __ll2double_rn(h);
 }
 
 // x > y for x, y >= 0 (including +inf): ordered like their bit patterns,
@@ -86,9 +102,8 @@ __device__ __forceinline__ bool dgt(double x, double y)
 //   alive: L held at every earlier state;
 //   nest 1 keeps the latest candidate (its window ends last), nest 2 the
 //   earliest since the last state violating Q (its window closes first).
+// The candidates' entry times live in the lane's shared-memory column tc[u * 32].
 struct MonLane {
-    int64_t L[SMC_MAX_ATOMS];
-    double tc[SMC_MAX_UNITS];
     long long hb;    // bits of min b over alive undecided units (-1: none)
     uint32_t ab;     // atom bit vector of the current state
     uint32_t alive, pend, done;
@@ -96,16 +111,6 @@ struct MonLane {
 };
 
 __device__ __constant__ int kPow3[SMC_MAX_UNITS] = {1, 3, 9, 27};
-
-__device__ __forceinline__ uint32_t atom_bits(const MonLane &ml, int na, const int64_t *thr,
-                                              uint32_t neg)
-{
-    uint32_t b = 0;
-#pragma unroll
-    for (int a = 0; a < SMC_MAX_ATOMS; ++a)
-        if (a < na) b |= (uint32_t)((ml.L[a] >= thr[2 * a]) & (ml.L[a] <= thr[2 * a + 1])) << a;
-    return b ^ neg;
-}
 
 __device__ __forceinline__ void mon_horizon(MonLane &ml, const MonProg &P)
 {
@@ -127,7 +132,7 @@ __device__ __forceinline__ void mon_set(MonLane &ml, int u, int val)
 }
 
 // The state just entered at time t (atom bits already in ml.ab).
-__device__ int mon_state(MonLane &ml, const MonProg &P, double t)
+__device__ __noinline__ int mon_state(MonLane &ml, const MonProg &P, double t, double *tc)
 {
     bool changed = false;
 #pragma unroll
@@ -142,15 +147,15 @@ __device__ int mon_state(MonLane &ml, const MonProg &P, double t)
         if (U.nest == 0) {
             if (inwin && p) val = 2;
         } else if (U.nest == 1) {
-            if (pe && q && !dgt(__dsub_rn(t, ml.tc[u]), U.d)) {
+            if (pe && q && !dgt(__dsub_rn(t, tc[u * 32]), U.d)) {
                 val = 2;
             } else if (inwin && p) {
                 if (q) val = 2;
-                else { ml.tc[u] = t; pe = true; }
+                else { tc[u * 32] = t; pe = true; }
             }
         } else {
             if (pe && !q) pe = false;
-            if (inwin && p && q && !pe) { ml.tc[u] = t; pe = true; }
+            if (inwin && p && q && !pe) { tc[u * 32] = t; pe = true; }
         }
         if (!val) {
             const bool al2 = al && l;
@@ -167,7 +172,7 @@ __device__ int mon_state(MonLane &ml, const MonProg &P, double t)
 }
 
 // The next state's entry time tn has been drawn (not yet applied).
-__device__ int mon_draw(MonLane &ml, const MonProg &P, double tn)
+__device__ __noinline__ int mon_draw(MonLane &ml, const MonProg &P, double tn, const double *tc)
 {
     bool changed = false;
 #pragma unroll
@@ -177,7 +182,7 @@ __device__ int mon_draw(MonLane &ml, const MonProg &P, double tn)
         const bool al = (ml.alive >> u) & 1u;
         bool pe = (ml.pend >> u) & 1u;
         int val = 0;
-        if (pe && dgt(__dsub_rn(tn, ml.tc[u]), U.d)) {
+        if (pe && dgt(__dsub_rn(tn, tc[u * 32]), U.d)) {
             if (U.nest == 2) val = 2;
             else pe = false;
         }
@@ -190,7 +195,7 @@ __device__ int mon_draw(MonLane &ml, const MonProg &P, double tn)
 }
 
 // The path has no further state (absorbing state).
-__device__ int mon_close(MonLane &ml, const MonProg &P)
+__device__ __noinline__ int mon_close(MonLane &ml, const MonProg &P)
 {
 #pragma unroll
     for (int u = 0; u < SMC_MAX_UNITS; ++u) {
@@ -208,6 +213,28 @@ __device__ __forceinline__ void mon_start(MonLane &ml, const MonProg &P)
     ml.done = 0;
     ml.vidx = 0;
     mon_horizon(ml, P);
+}
+
+// Atom a at the lane's current state: L = sum of coef * x over the atom's
+// terms (exact int64), bit = (lo <= L <= hi) xor neg, placed at bit a.
+__device__ __forceinline__ uint32_t atom_bit(const uint32_t *atoms, const uint32_t *tptr,
+                                             const uint32_t *terms, const int32_t *xs, int a)
+{
+    const uint32_t *A = atoms + 6 * a;
+    const uint32_t w1 = A[0];
+    long long L;
+    if (w1 != 0xFFFFFFFFu) {  // single term
+        L = (long long)xs[(w1 & 255u) * 32] * (long long)(((int32_t)w1) >> 8);
+    } else {
+        L = 0;
+        for (uint32_t q = tptr[a], qe = tptr[a + 1]; q < qe; ++q) {
+            const uint32_t w = terms[q];
+            L += (long long)xs[(w & 255u) * 32] * (long long)(((int32_t)w) >> 8);
+        }
+    }
+    const long long lo = *reinterpret_cast<const long long *>(A + 2);
+    const long long hi = *reinterpret_cast<const long long *>(A + 4);
+    return (((uint32_t)((L >= lo) & (L <= hi))) ^ A[1]) << a;
 }
 
 // ---------------------------------------------------------------------------
@@ -276,29 +303,30 @@ struct Prec<true> { typedef double T; };
 template <>
 struct Prec<false> { typedef float T; };
 
-// a_j = c_j h_j(x) (Sec. 2.2), h_j an exact integer rounded once.
+// a_k = c_k h_k(x) (Sec. 2.2) from a propensity word (see smc_internal.h).
+// FP64 path: h as an exact integer, rounded once; mixed path: h in FP32.
 template <bool PLAIN>
-__device__ __forceinline__ typename Prec<PLAIN>::T propensity(uint32_t rw, const int32_t *xs,
+__device__ __forceinline__ typename Prec<PLAIN>::T propensity(uint32_t pw, const int32_t *xs,
                                                               const double *rate_d,
-                                                              const float *rate_f, int k)
+                                                              const float *rate_f)
 {
-    const int ra = rw & 255u, rb = (rw >> 8) & 255u, kind = (rw >> 16) & 3u;
-    long long h;
-    if (kind == RK_ZERO) h = 1;
-    else {
-        const long long xa = xs[ra * 32];
-        if (kind == RK_ONE) h = xa;
-        else if (kind == RK_HETERO) h = xa * (long long)xs[rb * 32];
-        else h = (xa * (xa - 1)) >> 1;
+    const int k = pw & 255u, ra = (pw >> 8) & 255u, rb = (pw >> 16) & 255u;
+    const int homo = (pw >> 24) & 1u;
+    const int32_t xa = xs[ra * 32], xb = xs[rb * 32];
+    if (PLAIN) {
+        const long long h = ((long long)xa * (long long)(xb - homo)) >> homo;
+        return __dmul_rn(rate_d[k], int_to_double(h));
+    } else {
+        const float s = homo ? 0.5f : 1.0f;
+        const float h = (float)xa * __fmaf_rn((float)xb, s, homo ? -0.5f : 0.0f);
+        return rate_f[k] * h;
     }
-    if (PLAIN) return __dmul_rn(rate_d[k], __ll2double_rn(h));
-    else return __fmul_rn(rate_f[k], __ll2float_rn(h));
 }
 
 template <bool PLAIN>
-__device__ void run_instance(const SsaParams &p, const MonProg &P, const int m,
-                             const uint32_t *blob, int32_t *xs,
-                             typename Prec<PLAIN>::T *as, const int lane)
+__device__ __forceinline__ void run_instance(const SsaParams &p, const MonProg &P, const int m,
+                                             const uint32_t *blob, int32_t *xs, double *tc,
+                                             typename Prec<PLAIN>::T *as, const int lane)
 {
     typedef typename Prec<PLAIN>::T T;
     const int S = (int)blob[BH_S], R = (int)blob[BH_R], NA = (int)blob[BH_NA];
@@ -309,20 +337,27 @@ __device__ void run_instance(const SsaParams &p, const MonProg &P, const int m,
     const uint32_t *st = blob + blob[BH_ST];
     const uint32_t *dpp = blob + blob[BH_DEP_PTR];
     const uint32_t *dp = blob + blob[BH_DEP];
-    const int32_t *adelta = reinterpret_cast<const int32_t *>(blob + blob[BH_ADELTA]);
+    const uint32_t *amask = blob + blob[BH_AMASK];
+    const uint32_t *tptr = blob + blob[BH_ATERM_PTR];
+    const uint32_t *terms = blob + blob[BH_ATERM];
     const int32_t *x0 = reinterpret_cast<const int32_t *>(blob + blob[BH_X0]);
-    const int64_t *al0 = reinterpret_cast<const int64_t *>(blob + blob[BH_AL0]);
-    const int64_t *athr = reinterpret_cast<const int64_t *>(blob + blob[BH_ATHR]);
-    const uint32_t aneg = blob[blob[BH_ANEG]];
+    const uint32_t *atoms = blob + blob[BH_ATOM];
+    const uint32_t *dense = blob + blob[BH_DENSE];
+    const bool small = blob[BH_DENSE] != 0;
     const unsigned long long tend = p.uniform ? p.u_end : p.tend[m];
-    const bool skip_same = !P.has_lower;
+    const bool always_step = P.has_lower != 0;
+    const bool unbounded = P.unbounded != 0;
+    const double t_max = P.t_max;
+    const uint32_t renorm_mask = p.renorm_mask;
+    const uint64_t budget = p.budget;
 
     bool active = false, exhausted = false;
     uint32_t traj = 0, e = 0;
     double t = 0.0;
     T a0 = 0;
     MonLane ml;
-    unsigned long long c_yes = 0, c_dec = 0, c_ev = 0, c_bud = 0;
+    uint32_t c_yes = 0, c_dec = 0, c_bud = 0;
+    unsigned long long c_ev = 0;
 
     // verdict codes: 1 false, 2 true, 3 event budget exhausted
     auto finish = [&](int v) {
@@ -354,25 +389,26 @@ __device__ void run_instance(const SsaParams &p, const MonProg &P, const int m,
                 if (!active) {
                     const unsigned long long id = base + __popc(need & ((1u << lane) - 1u));
                     if (id < tend) {
-                        // start trajectory `id`: x = x0, fresh propensities, monitor at t = 0
+                        // start trajectory `id`: x = x0 (plus the constant-1
+                        // column), fresh propensities, monitor at t = 0
                         traj = (uint32_t)id;
                         e = 0;
                         t = 0.0;
                         for (int i = 0; i < S; ++i) xs[i * 32] = x0[i];
+                        xs[S * 32] = 1;
                         double s = 0.0;
                         for (int k = 0; k < R; ++k) {
-                            const T ak = propensity<PLAIN>(reac[k], xs, rate_d, rate_f, k);
+                            const T ak = propensity<PLAIN>(reac[k], xs, rate_d, rate_f);
                             as[k * 32] = ak;
                             s = __dadd_rn(s, (double)ak);
                         }
                         a0 = (T)s;
-#pragma unroll
-                        for (int a = 0; a < SMC_MAX_ATOMS; ++a)
-                            if (a < NA) ml.L[a] = al0[a];
-                        ml.ab = atom_bits(ml, NA, athr, aneg);
+                        uint32_t ab = 0;
+                        for (int a = 0; a < NA; ++a) ab |= atom_bit(atoms, tptr, terms, xs, a);
+                        ml.ab = ab;
                         mon_start(ml, P);
                         active = true;
-                        const int v = mon_state(ml, P, 0.0);
+                        const int v = mon_state(ml, P, 0.0, tc);
                         if (v) finish(v);
                     }
                 }
@@ -385,18 +421,33 @@ __device__ void run_instance(const SsaParams &p, const MonProg &P, const int m,
         if (!active) continue;
 
         // ---- one event -------------------------------------------------------
-        if (PLAIN) {  // step 1: a0 as a fresh left-to-right sum
+        T pre[SMC_SMALL_MAX];  // small networks: running sums a_0 + ... + a_k
+        uint32_t pos = 0;      // small networks: bit k set iff a_k > 0
+        if (small) {  // step 1 from scratch: every propensity of the current state
+            T acc = (T)0;
+#pragma unroll
+            for (int k = 0; k < SMC_SMALL_MAX; ++k) {
+                if (k < R) {
+                    const T ak = propensity<PLAIN>(reac[k], xs, rate_d, rate_f);
+                    const bool positive =
+                        PLAIN ? __double_as_longlong((double)ak) > 0 : ak > (T)0;
+                    pos |= (uint32_t)positive << k;
+                    acc = PLAIN ? (T)__dadd_rn((double)acc, (double)ak) : acc + ak;
+                    pre[k] = acc;
+                }
+            }
+            a0 = acc;
+        } else if (PLAIN) {  // step 1: a0 as a fresh left-to-right sum
+            double s = 0.0;
+            for (int k = 0; k < R; ++k) s = __dadd_rn(s, (double)as[k * 32]);
+            a0 = (T)s;
+        } else if (!(a0 > (T)0)) {  // drifted running sum: renormalise in FP64
             double s = 0.0;
             for (int k = 0; k < R; ++k) s = __dadd_rn(s, (double)as[k * 32]);
             a0 = (T)s;
         }
-        if (!PLAIN && !(a0 > (T)0)) {  // drifted running sum: renormalise in FP64
-            double s = 0.0;
-            for (int k = 0; k < R; ++k) s = __dadd_rn(s, (double)as[k * 32]);
-            a0 = (T)s;
-        }
-        if (!(a0 > (T)0)) {  // absorbing state: the path has no further position
-            finish(mon_close(ml, P));
+        if (PLAIN ? __double_as_longlong((double)a0) <= 0 : !(a0 > (T)0)) {
+            finish(mon_close(ml, P));  // absorbing state: no further position
             continue;
         }
         uint32_t w0, w1, w2, w3;
@@ -409,23 +460,43 @@ __device__ void run_instance(const SsaParams &p, const MonProg &P, const int m,
             r = (T)__dmul_rn(us, (double)a0);
         } else {
             const float ut = u01_23(w0), us = u01_23(w2);
-            const float tau = __fdividef(-logf(ut), (float)a0);
+            const float tau = __fdividef(-__logf(ut), (float)a0);
             tn = __dadd_rn(t, (double)tau);
             r = (T)(us * (float)a0);
         }
         int v = 0;
-        if (ml.pend || __double_as_longlong(tn) > ml.hb) v = mon_draw(ml, P, tn);
-        if (!v && P.unbounded && tn > P.t_max) v = 1;  // pessimistic rule (Sec. 3.2)
+        if (ml.pend || __double_as_longlong(tn) > ml.hb) v = mon_draw(ml, P, tn, tc);
+        if (!v && unbounded && tn > t_max) v = 1;  // pessimistic rule (Sec. 3.2)
         if (v) { finish(v); continue; }
 
         // step 2: selection, first j whose running sum exceeds r
         int j = -1, last = -1;
-        T cum = (T)0;
-        for (int k = 0; k < R; ++k) {
-            const T ak = as[k * 32];
-            cum = cum + ak;
-            if (ak > (T)0) last = k;
-            if (cum > r) { j = k; break; }
+        if (small) {  // the running sums are already in registers
+#pragma unroll
+            for (int k = 0; k < SMC_SMALL_MAX; ++k) {
+                const bool hit = PLAIN ? __double_as_longlong((double)pre[k]) >
+                                             __double_as_longlong((double)r)
+                                       : pre[k] > r;
+                if (k < R && j < 0 && hit) j = k;
+            }
+            last = pos ? 31 - __clz(pos) : -1;
+        } else if (PLAIN) {
+            const long long rb = __double_as_longlong((double)r);
+            double cum = 0.0;
+            for (int k = 0; k < R; ++k) {
+                const double ak = (double)as[k * 32];
+                cum = __dadd_rn(cum, ak);
+                if (__double_as_longlong(ak) > 0) last = k;
+                if (__double_as_longlong(cum) > rb) { j = k; break; }
+            }
+        } else {
+            float cum = 0.0f;
+            for (int k = 0; k < R; ++k) {
+                const float ak = (float)as[k * 32];
+                cum += ak;
+                if (ak > 0.0f) last = k;
+                if (cum > (float)r) { j = k; break; }
+            }
         }
         if (j < 0) j = last;  // r reached the full sum (rounding, or a drifted a0)
         if (j < 0) {          // every a_k is 0 (only a drifted FP32 a0 gets here)
@@ -434,50 +505,66 @@ __device__ void run_instance(const SsaParams &p, const MonProg &P, const int m,
         }
 
         // step 4: x += v_j, then the propensities that read a changed species
-        for (uint32_t q = stp[j], qe = stp[j + 1]; q < qe; ++q) {
-            const uint32_t w = st[q];
-            xs[(w & 255u) * 32] += ((int32_t)w) >> 8;
-        }
-        for (uint32_t q = dpp[j], qe = dpp[j + 1]; q < qe; ++q) {
-            const int k = (int)dp[q];
-            const T ak = propensity<PLAIN>(reac[k], xs, rate_d, rate_f, k);
-            if (!PLAIN) a0 = a0 + (ak - as[k * 32]);
-            as[k * 32] = ak;
-        }
-        ++e;
-        t = tn;
-        if (!PLAIN && (e & p.renorm_mask) == 0u) {  // FP64 renormalisation of a0
-            double s = 0.0;
-            for (int k = 0; k < R; ++k) s = __dadd_rn(s, (double)as[k * 32]);
-            a0 = (T)s;
-        }
-
-        // monitor at the new state
-        const uint32_t ab_old = ml.ab;
+        uint32_t ab = ml.ab;
+        if (small) {  // dense byte row of v_j; atoms re-evaluated in full
+            const uint32_t d0 = dense[2 * j], d1 = dense[2 * j + 1];
 #pragma unroll
-        for (int a = 0; a < SMC_MAX_ATOMS; ++a)
-            if (a < NA) ml.L[a] += adelta[j * NA + a];
-        ml.ab = atom_bits(ml, NA, athr, aneg);
-        if (!(skip_same && ml.ab == ab_old && !ml.pend)) v = mon_state(ml, P, t);
+            for (int i = 0; i < SMC_SMALL_MAX; ++i)
+                if (i < S) xs[i * 32] += (int32_t)(int8_t)((i < 4 ? d0 : d1) >> (8 * (i & 3)));
+            ++e;
+            t = tn;
+            ab = 0;
+            for (int a = 0; a < NA; ++a) ab |= atom_bit(atoms, tptr, terms, xs, a);
+        } else {
+            for (uint32_t q = stp[j], qe = stp[j + 1]; q < qe; ++q) {
+                const uint32_t w = st[q];
+                xs[(w & 255u) * 32] += ((int32_t)w) >> 8;
+            }
+            for (uint32_t q = dpp[j], qe = dpp[j + 1]; q < qe; ++q) {
+                const uint32_t pw = dp[q];
+                const int k = pw & 255u;
+                const T ak = propensity<PLAIN>(pw, xs, rate_d, rate_f);
+                if (!PLAIN) a0 = a0 + (ak - as[k * 32]);
+                as[k * 32] = ak;
+            }
+            ++e;
+            t = tn;
+            if (!PLAIN && (e & renorm_mask) == 0u) {  // FP64 renormalisation of a0
+                double s = 0.0;
+                for (int k = 0; k < R; ++k) s = __dadd_rn(s, (double)as[k * 32]);
+                a0 = (T)s;
+            }
+            // monitor at the new state: re-evaluate the atoms that j moves
+            uint32_t am = amask[j];
+            while (am) {
+                const int a = __ffs(am) - 1;
+                am &= am - 1u;
+                ab = (ab & ~(1u << a)) | atom_bit(atoms, tptr, terms, xs, a);
+            }
+        }
+        if (always_step || ab != ml.ab || ml.pend) {
+            ml.ab = ab;
+            v = mon_state(ml, P, t, tc);
+        }
         if (v) finish(v);
-        else if ((uint64_t)e >= p.budget) finish(3);
+        else if ((uint64_t)e >= budget) finish(3);
     }
 
     // warp reduction of the instance's counts, one atomic per counter
-    c_yes = warp_sum(c_yes);
-    c_dec = warp_sum(c_dec);
-    c_ev = warp_sum(c_ev);
-    c_bud = warp_sum(c_bud);
-    if (lane == 0 && (c_dec | c_bud)) {
-        atomicAdd(&p.counts[4 * m + 0], c_yes);
-        atomicAdd(&p.counts[4 * m + 1], c_dec);
-        atomicAdd(&p.counts[4 * m + 2], c_ev);
-        atomicAdd(&p.counts[4 * m + 3], c_bud);
+    const unsigned long long s_yes = warp_sum(c_yes), s_dec = warp_sum(c_dec);
+    const unsigned long long s_ev = warp_sum(c_ev), s_bud = warp_sum(c_bud);
+    if (lane == 0 && (s_dec | s_bud)) {
+        atomicAdd(&p.counts[4 * m + 0], s_yes);
+        atomicAdd(&p.counts[4 * m + 1], s_dec);
+        atomicAdd(&p.counts[4 * m + 2], s_ev);
+        atomicAdd(&p.counts[4 * m + 3], s_bud);
     }
 }
 
+// Register budget: 64 per thread for the mixed path (32 resident warps per
+// SM), 80 for the FP64 path (24 warps; its FP64 pipe saturates before issue).
 template <bool PLAIN>
-__global__ void __launch_bounds__(256) ssa_kernel(const SsaParams p)
+__global__ void __launch_bounds__(256, PLAIN ? 3 : 4) ssa_kernel(const SsaParams p)
 {
     typedef typename Prec<PLAIN>::T T;
     extern __shared__ __align__(16) unsigned char smem[];
@@ -490,10 +577,15 @@ __global__ void __launch_bounds__(256) ssa_kernel(const SsaParams p)
     __syncthreads();
     const MonProg &P = *reinterpret_cast<const MonProg *>(smem);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    // warp slice: table | x[(s_max + 1)][32] | tc[units][32] | a[r_max][32]
     unsigned char *wb = smem + sizeof(MonProg) + (size_t)warp * p.warp_bytes;
     uint32_t *blob = reinterpret_cast<uint32_t *>(wb);
-    int32_t *xs = reinterpret_cast<int32_t *>(wb + (size_t)p.blob_words * 4) + lane;
-    T *as = reinterpret_cast<T *>(wb + (size_t)p.blob_words * 4 + (size_t)p.s_max * 128) + lane;
+    unsigned char *lanes = wb + (size_t)p.blob_words * 4;
+    int32_t *xs = reinterpret_cast<int32_t *>(lanes) + lane;
+    lanes += (size_t)(p.s_max + 1) * 128;
+    double *tc = reinterpret_cast<double *>(lanes) + lane;
+    lanes += (size_t)p.tc_bytes;
+    T *as = reinterpret_cast<T *>(lanes) + lane;
 
     bool first = true;
     int cur = -1;
@@ -508,7 +600,7 @@ __global__ void __launch_bounds__(256) ssa_kernel(const SsaParams p)
             __syncwarp();
             cur = m;
         }
-        run_instance<PLAIN>(p, P, m, blob, xs, as, lane);
+        run_instance<PLAIN>(p, P, m, blob, xs, tc, as, lane);
         __syncwarp();
     }
 
@@ -549,27 +641,31 @@ __global__ void replay_kernel(const ReplayParams rp)
     const int na = P.n_atoms, S = rp.S, n = rp.len[i];
     const int32_t *x = rp.x + rp.off[i] * S;
     const double *t = rp.t + rp.off[i];
+    double tc_local[SMC_MAX_UNITS * 32];
+    double *tc = tc_local;
     MonLane ml;
     int v = 0;
     long long q = -1;
     for (int k = 0; k < n && !v; ++k) {
         if (k > 0) {
-            if (ml.pend || __double_as_longlong(t[k]) > ml.hb) v = mon_draw(ml, P, t[k]);
+            if (ml.pend || __double_as_longlong(t[k]) > ml.hb) v = mon_draw(ml, P, t[k], tc);
             if (v) { q = 2 * k - 1; break; }
         }
+        uint32_t ab = 0;
         for (int a = 0; a < na; ++a) {
             long long L = 0;
             for (int s = 0; s < S; ++s) L += (long long)rp.coef[a * S + s] * x[k * S + s];
-            ml.L[a] = L;
+            const uint32_t in = (L >= rp.athr[2 * a]) & (L <= rp.athr[2 * a + 1]);
+            ab |= (in ^ ((rp.aneg >> a) & 1u)) << a;
         }
-        ml.ab = atom_bits(ml, na, rp.athr, rp.aneg);
+        ml.ab = ab;
         if (k == 0) mon_start(ml, P);
-        v = mon_state(ml, P, t[k]);
+        v = mon_state(ml, P, t[k], tc);
         if (v) q = 2 * k;
     }
     if (!v && n > 0) {
         if (rp.closed[i]) v = mon_close(ml, P);
-        else v = mon_draw(ml, P, rp.tmin[i]);
+        else v = mon_draw(ml, P, rp.tmin[i], tc);
         if (v) q = 2 * (long long)n - 1;
     }
     rp.verdict[i] = v;
