@@ -243,6 +243,79 @@ int smc_monitor_replay(smc_ctx *ctx, int n_paths, const int32_t *len, const int3
 int smc_simulate_noalloc(smc_ctx *ctx, int precision, uint64_t seed, uint64_t traj_begin,
                          uint64_t n_traj, double confidence, const smc_sim_out *out, void *stream);
 
+/* ---- surrogate control variate ----------------------------------------------
+ * Not in the paper: a learned predictor g(state at t_c) of P(phi | prefix),
+ * used as a control variate.  The plain estimator of Sec. 3.3 stays the
+ * reference: for any fixed g and beta the control-variate estimate is
+ * unbiased. */
+
+/* smc_simulate with a checkpoint snapshot: for each trajectory, snap = 0 and
+ * x_snap = the state occupied at time t_snap, or snap = 1 when the verdict
+ * was fixed before t_snap (verdict in out->verdict).  stop_at_snap != 0
+ * stops every trajectory at its snapshot (prefix-only run; those are not
+ * counted in out->counts and get status 2).  Device arrays: snap
+ * [n_inst][n_traj] (uint8), x_snap [n_inst][n_traj][S_max] (int32).
+ * out->verdict must be given.  Does not synchronise. */
+int smc_simulate_snapshot(smc_ctx *ctx, int precision, uint64_t seed, uint64_t traj_begin,
+                          uint64_t n_traj, double t_snap, int stop_at_snap, const smc_sim_out *out,
+                          uint8_t *snap, int32_t *x_snap, void *stream);
+
+/* Features of snapshots (single-network contexts): row (m, k) of feat
+ * [n_inst * n_traj][S + 1 + R] (FP32, device) = x_snap / x_scale (S values),
+ * t_snap / t_scale, then the log rate constants of instance m centred on
+ * their mean over the instances.  x_scale: host [S]. */
+int smc_snapshot_features(smc_ctx *ctx, uint64_t n_traj, const int32_t *x_snap, double t_snap,
+                          const float *x_scale, float t_scale, float *feat, void *stream);
+
+/* The network: n_in (<= 16) -> 128 -> 128 -> 128 -> 1, ReLU, logistic
+ * output; BF16 tensor-core kernels with FP32 accumulation, FP32 master
+ * weights (SMC_MLP_NPARAM floats: W1[128][16], b1, W2[128][128], b2,
+ * W3[128][128], b3, w4[128], b4), Adam. */
+#define SMC_MLP_NPARAM 35329
+#define SMC_MLP_MAX_BATCH 8192
+typedef struct smc_mlp smc_mlp;
+int smc_mlp_create(smc_mlp **out, int device, int n_in, uint64_t seed); /* He-uniform init */
+void smc_mlp_destroy(smc_mlp *mlp);
+const char *smc_mlp_last_error(const smc_mlp *mlp);
+int smc_mlp_get_params(smc_mlp *mlp, float *host_params);       /* [SMC_MLP_NPARAM] */
+int smc_mlp_set_params(smc_mlp *mlp, const float *host_params);
+/* Gradient of the mean binary cross-entropy over n <= SMC_MLP_MAX_BATCH rows
+ * (device x [n][n_in], y [n] in {0,1}); host outputs. */
+int smc_mlp_gradient(smc_mlp *mlp, const float *x, const float *y, int n, float *grad_host,
+                     float *loss_host);
+/* Adam training: epochs x ceil(n / batch) steps, batches drawn with
+ * replacement (counter-based hash of seed, step, row). loss_host: [epochs]
+ * mean loss per epoch or NULL. */
+int smc_mlp_train(smc_mlp *mlp, const float *x, const float *y, uint64_t n, int epochs, int batch,
+                  float lr, uint64_t seed, float *loss_host, void *stream);
+/* g[i] = network output for row i of x (device [n][n_in] -> device [n]). */
+int smc_mlp_predict(smc_mlp *mlp, const float *x, uint64_t n, float *g, void *stream);
+
+/* Control-variate estimate for a single-instance context (two-phase
+ * sampling): n_full trajectories run to their verdict Y, n_prefix further
+ * trajectories only to t_snap; G = Y when the verdict was fixed before t_snap,
+ * else G = g(snapshot features).  p_hat = mean_full(Y - beta G) +
+ * beta mean_all(G), unbiased for any fixed beta.  Var is estimated from the
+ * samples, n_eff = p_hat (1 - p_hat) / Var, and [lo, hi] is Eq. 4 at n_eff.
+ * The sample sizes grow (cost-optimal split between full and prefix runs,
+ * events per run measured) until n_eff >= Wilson_sample(p', half_width)
+ * with p' = p_hat +- half_width as in Fig. 2.  Prefix runs use trajectory
+ * indices from 2^31 up, full runs below 2^31.  x_scale [S] (host), t_scale:
+ * feature scaling as in smc_snapshot_features; pilot: initial size of both
+ * samples. */
+typedef struct {
+    double p_hat, lo, hi;
+    double n_eff;      /* p_hat (1 - p_hat) / var */
+    double var;        /* estimated variance of p_hat */
+    double beta;
+    uint64_t n_full, n_prefix;
+    uint64_t events_full, events_prefix; /* reactions fired by each sample */
+    int32_t iterations, status;
+} smc_cv_result;
+int smc_estimate_cv(smc_ctx *ctx, smc_mlp *mlp, double confidence, double half_width, uint64_t seed,
+                    int precision, double t_snap, const float *x_scale, float t_scale, double beta,
+                    uint64_t pilot, smc_cv_result *out);
+
 /* Host utilities (no GPU needed). */
 double smc_normal_quantile(double p);                           /* Phi^{-1}(p) */
 int smc_wilson_interval(uint64_t yes, uint64_t n, double confidence, double *lo,

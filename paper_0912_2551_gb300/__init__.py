@@ -30,6 +30,16 @@ def _p(a, ct):
     return a.ctypes.data_as(ctypes.POINTER(ct))
 
 
+CUDA_STREAM_LEGACY = 0x1  # cudaStreamLegacy
+
+
+def _stream(s):
+    """cudaStream_t of a torch stream.  Torch's default stream has handle 0,
+    which the C ABI reads as "the library's own stream"; pass the legacy
+    default stream instead so the work is ordered with torch's."""
+    return ctypes.c_void_p(s.cuda_stream or CUDA_STREAM_LEGACY)
+
+
 def postfix(formula) -> list:
     """Formula tree of tuples (see ``workloads``) -> list of smc_node tuples."""
     out = []
@@ -105,6 +115,7 @@ class Context:
                                      _p(x0, ctypes.c_int32), model.n_inst), 'smc_load_model')
         self.n_inst = model.n_inst
         self.s_max = model.n_species
+        self._n_reactions = model.n_reactions
         self._batch = None
 
     def load_batch(self, batch):
@@ -193,9 +204,58 @@ class Context:
             setattr(so, k, out[k].data_ptr())
         s = stream if stream is not None else torch.cuda.current_stream(dev)
         self._check(N.smc_simulate(self.h, PRECISION[precision], int(seed), int(traj_begin), int(n_traj),
-                                   float(confidence), ctypes.byref(so), ctypes.c_void_p(s.cuda_stream)),
+                                   float(confidence), ctypes.byref(so), _stream(s)),
                     'smc_simulate')
         return out
+
+    def simulate_snapshot(self, precision: str = 'mixed', seed: int = 0, traj_begin: int = 0, n_traj: int = 1,
+                          t_snap: float = 5.0, stop: bool = False, stream=None) -> Dict[str, object]:
+        """smc_simulate_snapshot: counts, verdict, status, snap and x_snap
+        (torch CUDA tensors, [n_inst, n_traj] / [n_inst, n_traj, S_max])."""
+        import torch
+        dev = torch.device('cuda', self.device)
+        n = self.n_inst
+        out = dict(counts=torch.zeros((n, 4), dtype=torch.int64, device=dev),
+                   verdict=torch.zeros((n, n_traj), dtype=torch.uint8, device=dev),
+                   status=torch.zeros((n, n_traj), dtype=torch.uint8, device=dev),
+                   snap=torch.zeros((n, n_traj), dtype=torch.uint8, device=dev),
+                   x_snap=torch.zeros((n, n_traj, self.s_max), dtype=torch.int32, device=dev))
+        so = N.smc_sim_out()
+        so.counts = out['counts'].data_ptr()
+        so.verdict = out['verdict'].data_ptr()
+        so.status = out['status'].data_ptr()
+        s = stream if stream is not None else torch.cuda.current_stream(dev)
+        self._check(N.smc_simulate_snapshot(self.h, PRECISION[precision], int(seed), int(traj_begin), int(n_traj),
+                                            float(t_snap), int(bool(stop)), ctypes.byref(so),
+                                            ctypes.c_void_p(out['snap'].data_ptr()),
+                                            ctypes.c_void_p(out['x_snap'].data_ptr()),
+                                            _stream(s)), 'smc_simulate_snapshot')
+        return out
+
+    def snapshot_features(self, x_snap, t_snap: float, x_scale, t_scale: float, stream=None):
+        """Features [n_inst * n_traj, S + 1 + R] (torch CUDA float32) of x_snap."""
+        import torch
+        n_traj = x_snap.shape[1]
+        S, R = self.s_max, int(self._n_reactions)
+        feat = torch.zeros((self.n_inst * n_traj, S + 1 + R), dtype=torch.float32, device=x_snap.device)
+        xs = np.ascontiguousarray(x_scale, np.float32)
+        s = stream if stream is not None else torch.cuda.current_stream(x_snap.device)
+        self._check(N.smc_snapshot_features(self.h, n_traj, ctypes.c_void_p(x_snap.data_ptr()), float(t_snap),
+                                            xs.ctypes.data_as(ctypes.c_void_p), float(t_scale),
+                                            ctypes.c_void_p(feat.data_ptr()), _stream(s)),
+                    'smc_snapshot_features')
+        return feat
+
+    def estimate_cv(self, mlp, confidence: float, half_width: float, seed: int = 0, precision: str = 'mixed',
+                    t_snap: float = 5.0, x_scale=None, t_scale: float = 30.0, beta: float = 1.0,
+                    pilot: int = 2000):
+        xs = np.ascontiguousarray(x_scale, np.float32)
+        res = N.smc_cv_result()
+        self._check(N.smc_estimate_cv(self.h, mlp.h, float(confidence), float(half_width), int(seed),
+                                      PRECISION[precision], float(t_snap), xs.ctypes.data_as(ctypes.c_void_p),
+                                      float(t_scale), float(beta), int(pilot), ctypes.byref(res)),
+                    'smc_estimate_cv')
+        return res.as_dict()
 
     def monitor_replay(self, paths, S: int):
         """paths: list of (x [n, S] ints, t [n] floats, tmin, closed)."""
@@ -212,6 +272,76 @@ class Context:
                                          _p(closed, ctypes.c_uint8), _p(v, ctypes.c_int32),
                                          _p(q, ctypes.c_int64)), 'smc_monitor_replay')
         return v, q
+
+
+class Mlp:
+    """The surrogate network (smc_mlp_*): n_in -> 128 -> 128 -> 128 -> 1,
+    BF16 tensor-core kernels, FP32 master weights, Adam."""
+    NPARAM = N.SMC_MLP_NPARAM
+
+    def __init__(self, n_in: int, device: int = 0, seed: int = 0):
+        N.load()
+        h = ctypes.c_void_p()
+        rc = N.smc_mlp_create(ctypes.byref(h), int(device), int(n_in), int(seed))
+        if rc != 0:
+            raise SmcError(rc, 'smc_mlp_create')
+        self.h = h
+        self.n_in = n_in
+        self.device = device
+
+    def close(self):
+        if getattr(self, 'h', None):
+            N.smc_mlp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc, what):
+        if rc != 0:
+            raise SmcError(rc, f'{what}: {N.smc_mlp_last_error(self.h).decode()}')
+
+    def get_params(self) -> np.ndarray:
+        out = np.zeros(self.NPARAM, np.float32)
+        self._check(N.smc_mlp_get_params(self.h, out.ctypes.data_as(ctypes.c_void_p)), 'smc_mlp_get_params')
+        return out
+
+    def set_params(self, params):
+        p = np.ascontiguousarray(params, np.float32)
+        assert p.size == self.NPARAM
+        self._check(N.smc_mlp_set_params(self.h, p.ctypes.data_as(ctypes.c_void_p)), 'smc_mlp_set_params')
+
+    def gradient(self, x, y):
+        """x: CUDA float32 [n, n_in], y: CUDA float32 [n] -> (grad [NPARAM], mean loss)."""
+        import torch
+        torch.cuda.current_stream(x.device).synchronize()  # the library runs this on its own stream
+        g = np.zeros(self.NPARAM, np.float32)
+        loss = np.zeros(1, np.float32)
+        self._check(N.smc_mlp_gradient(self.h, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(y.data_ptr()),
+                                       int(x.shape[0]), g.ctypes.data_as(ctypes.c_void_p),
+                                       loss.ctypes.data_as(ctypes.c_void_p)), 'smc_mlp_gradient')
+        return g, float(loss[0])
+
+    def train(self, x, y, epochs: int, batch: int = 4096, lr: float = 1e-3, seed: int = 0):
+        import torch
+        loss = np.zeros(epochs, np.float32)
+        s = torch.cuda.current_stream(x.device)
+        self._check(N.smc_mlp_train(self.h, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(y.data_ptr()),
+                                    int(x.shape[0]), int(epochs), int(batch), float(lr), int(seed),
+                                    loss.ctypes.data_as(ctypes.c_void_p), _stream(s)), 'smc_mlp_train')
+        return loss
+
+    def predict(self, x):
+        import torch
+        g = torch.empty((x.shape[0],), dtype=torch.float32, device=x.device)
+        s = torch.cuda.current_stream(x.device)
+        self._check(N.smc_mlp_predict(self.h, ctypes.c_void_p(x.data_ptr()), int(x.shape[0]),
+                                      ctypes.c_void_p(g.data_ptr()), _stream(s)),
+                    'smc_mlp_predict')
+        return g
 
 
 def normal_quantile(p: float) -> float:

@@ -57,6 +57,21 @@ class smc_sim_out(ctypes.Structure):
                 ('x_final', ctypes.c_void_p)]
 
 
+class smc_cv_result(ctypes.Structure):
+    _fields_ = [('p_hat', ctypes.c_double), ('lo', ctypes.c_double), ('hi', ctypes.c_double),
+                ('n_eff', ctypes.c_double), ('var', ctypes.c_double), ('beta', ctypes.c_double),
+                ('n_full', ctypes.c_uint64), ('n_prefix', ctypes.c_uint64), ('events_full', ctypes.c_uint64),
+                ('events_prefix', ctypes.c_uint64),
+                ('iterations', ctypes.c_int32), ('status', ctypes.c_int32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+SMC_MLP_NPARAM = 35329
+SMC_MLP_MAX_BATCH = 8192
+c_f32p = ctypes.POINTER(ctypes.c_float)
+
 _lib = None
 
 # name -> (restype, argtypes)
@@ -84,6 +99,29 @@ SIGNATURES = {
                                             ctypes.c_void_p]),
     'smc_monitor_replay': (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, c_i32p, c_i32p, c_f64p, c_f64p,
                                           c_u8p, c_i32p, c_i64p]),
+    'smc_simulate_snapshot': (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_uint64, ctypes.c_uint64,
+                                             ctypes.c_uint64, ctypes.c_double, ctypes.c_int,
+                                             ctypes.POINTER(smc_sim_out), ctypes.c_void_p, ctypes.c_void_p,
+                                             ctypes.c_void_p]),
+    'smc_snapshot_features': (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p, ctypes.c_double,
+                                             ctypes.c_void_p, ctypes.c_float, ctypes.c_void_p, ctypes.c_void_p]),
+    'smc_mlp_create': (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, ctypes.c_int,
+                                      ctypes.c_uint64]),
+    'smc_mlp_destroy': (None, [ctypes.c_void_p]),
+    'smc_mlp_last_error': (ctypes.c_char_p, [ctypes.c_void_p]),
+    'smc_mlp_get_params': (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    'smc_mlp_set_params': (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    'smc_mlp_gradient': (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
+                                        ctypes.c_void_p, ctypes.c_void_p]),
+    'smc_mlp_train': (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64,
+                                     ctypes.c_int, ctypes.c_int, ctypes.c_float, ctypes.c_uint64, ctypes.c_void_p,
+                                     ctypes.c_void_p]),
+    'smc_mlp_predict': (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p,
+                                       ctypes.c_void_p]),
+    'smc_estimate_cv': (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double, ctypes.c_double,
+                                       ctypes.c_uint64, ctypes.c_int, ctypes.c_double, ctypes.c_void_p,
+                                       ctypes.c_float, ctypes.c_double, ctypes.c_uint64,
+                                       ctypes.POINTER(smc_cv_result)]),
     'smc_normal_quantile': (ctypes.c_double, [ctypes.c_double]),
     'smc_wilson_interval': (ctypes.c_int, [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_double, c_f64p,
                                            c_f64p]),

@@ -68,7 +68,11 @@ struct smc_ctx {
     uint32_t *d_blobs = nullptr;
     uint64_t *d_blob_off = nullptr;
     MonProg *d_prog = nullptr;
-    std::vector<SizeClass> classes;
+    std::vector<SizeClass> classes;  // instances grouped by reaction count
+    SizeClass single;                // every instance in one launch
+    bool use_single[2] = {false, false};
+    bool tuned[2] = {false, false};
+    unsigned long long *d_trial = nullptr;  // autotuner counts
     uint64_t *d_tbegin = nullptr, *d_tend = nullptr;
     unsigned long long *d_tnext = nullptr;
     unsigned int *d_sync = nullptr;  // cursor, ticket
@@ -79,11 +83,14 @@ struct smc_ctx {
     double *h_wilson = nullptr;
     uint8_t *d_record = nullptr;
     uint64_t record_n = 0, record_valid = 0;
+    float *d_feat_aux = nullptr;  // feature scales and centred log rates
+    size_t feat_aux_n = 0;
 
     // options
     uint64_t budget = 1ull << 24;
     int renorm_log2 = 8;
     int autotune = 1;
+    bool explicit_shape = false;  // a shape option was set: do not tune
     int warps = 4;
     int blocks_sm = 0;
     int refill = 1;
@@ -120,6 +127,11 @@ void free_device(smc_ctx *ctx)
     dfree(ctx->d_prog);
     for (auto &c : ctx->classes) dfree(c.d_list);
     ctx->classes.clear();
+    dfree(ctx->single.d_list);
+    ctx->single = SizeClass();
+    dfree(ctx->d_trial);
+    ctx->use_single[0] = ctx->use_single[1] = false;
+    ctx->tuned[0] = ctx->tuned[1] = false;
     dfree(ctx->d_tbegin);
     dfree(ctx->d_tend);
     dfree(ctx->d_tnext);
@@ -127,6 +139,8 @@ void free_device(smc_ctx *ctx)
     dfree(ctx->d_counts);
     dfree(ctx->d_wilson);
     dfree(ctx->d_record);
+    dfree(ctx->d_feat_aux);
+    ctx->feat_aux_n = 0;
     if (ctx->h_range) cudaFreeHost(ctx->h_range);
     if (ctx->h_counts) cudaFreeHost(ctx->h_counts);
     if (ctx->h_wilson) cudaFreeHost(ctx->h_wilson);
@@ -304,21 +318,31 @@ int prepare(smc_ctx *ctx)
         }
         if (!c.inst.empty()) ctx->classes.push_back(c);
     }
+    for (int m = 0; m < n; ++m) {
+        ctx->single.inst.push_back(m);
+        ctx->single.s_max = std::max(ctx->single.s_max, ctx->S[m]);
+        ctx->single.r_max = std::max(ctx->single.r_max, ctx->R[m]);
+        ctx->single.blob_words = std::max(ctx->single.blob_words, words[m]);
+    }
     CK(cudaMalloc(&ctx->d_blobs, all.size() * 4));
     CK(cudaMemcpy(ctx->d_blobs, all.data(), all.size() * 4, cudaMemcpyHostToDevice));
     CK(cudaMalloc(&ctx->d_blob_off, n * 8));
     CK(cudaMemcpy(ctx->d_blob_off, off.data(), n * 8, cudaMemcpyHostToDevice));
     CK(cudaMalloc(&ctx->d_prog, sizeof(MonProg)));
     CK(cudaMemcpy(ctx->d_prog, &ctx->prog, sizeof(MonProg), cudaMemcpyHostToDevice));
-    for (auto &c : ctx->classes) {
-        CK(cudaMalloc(&c.d_list, c.inst.size() * 4));
-        CK(cudaMemcpy(c.d_list, c.inst.data(), c.inst.size() * 4, cudaMemcpyHostToDevice));
+    std::vector<SizeClass *> all_classes;
+    for (auto &c : ctx->classes) all_classes.push_back(&c);
+    all_classes.push_back(&ctx->single);
+    for (SizeClass *c : all_classes) {
+        CK(cudaMalloc(&c->d_list, c->inst.size() * 4));
+        CK(cudaMemcpy(c->d_list, c->inst.data(), c->inst.size() * 4, cudaMemcpyHostToDevice));
         for (int pl = 0; pl < 2; ++pl) {
-            c.shape[pl].warps = ctx->warps;
-            c.shape[pl].blocks_sm = ctx->blocks_sm;
-            c.shape[pl].refill = ctx->refill;
+            c->shape[pl].warps = ctx->warps;
+            c->shape[pl].blocks_sm = ctx->blocks_sm;
+            c->shape[pl].refill = ctx->refill;
         }
     }
+    CK(cudaMalloc(&ctx->d_trial, (size_t)n * 4 * 8));
     CK(cudaMalloc(&ctx->d_tbegin, n * 8));
     CK(cudaMalloc(&ctx->d_tend, n * 8));
     CK(cudaMalloc(&ctx->d_tnext, n * 8));
@@ -348,12 +372,68 @@ int warp_bytes_of(const SizeClass &c, int plain, int tc_bytes)
     return (b + 15) & ~15;
 }
 
-// Launches queue initialisation and the SSA kernel for every size class.
-// Ranges (d_tbegin, d_tend) must already be on the device.
-int launch_all(smc_ctx *ctx, int plain, uint64_t seed, double z, const smc_sim_out &out,
-               uint64_t out_base, uint64_t out_stride, cudaStream_t s, bool uniform)
+// One planned launch of the SSA kernel for a set of instances.
+struct Launch {
+    const SizeClass *c = nullptr;
+    int grid = 0, block = 0, smem = 0, warp_bytes = 0, tc_bytes = 0, refill = 1;
+};
+
+// The instance partition in use for a precision: the size classes, or one
+// launch over every instance (chosen by the autotuner).
+std::vector<const SizeClass *> active_classes(const smc_ctx *ctx, int plain)
 {
-    SsaParams p;
+    std::vector<const SizeClass *> v;
+    if (ctx->use_single[plain] && ctx->classes.size() > 1) v.push_back(&ctx->single);
+    else
+        for (const auto &c : ctx->classes) v.push_back(&c);
+    return v;
+}
+
+// Launch geometry of class c with shape sh (sets the kernel's shared-memory
+// limit; call outside stream capture).  Returns SMC_E_UNSUPPORTED if it does
+// not fit.
+int plan_class(smc_ctx *ctx, int plain, const SizeClass &c, const Shape &sh, Launch &L)
+{
+    L.c = &c;
+    L.tc_bytes = tc_bytes_of(ctx->prog);
+    L.warp_bytes = warp_bytes_of(c, plain, L.tc_bytes);
+    L.block = 32 * sh.warps;
+    L.smem = (int)sizeof(MonProg) + sh.warps * L.warp_bytes;
+    L.refill = sh.refill;
+    if ((size_t)L.smem > ctx->smem_optin)
+        return fail(ctx, SMC_E_UNSUPPORTED, "model tables do not fit in shared memory");
+    if (smc_ssa_set_smem_limit(plain, L.smem)) return fail(ctx, SMC_E_CUDA, "cudaFuncSetAttribute failed");
+    int per_sm = 0;
+    if (smc_ssa_max_blocks_per_sm(plain, L.block, L.smem, &per_sm) || per_sm < 1)
+        return fail(ctx, SMC_E_UNSUPPORTED, "no block of this shape fits on an SM");
+    if (sh.blocks_sm > 0) per_sm = std::min(per_sm, sh.blocks_sm);
+    L.grid = ctx->n_sm * per_sm;
+    return SMC_OK;
+}
+
+// Queue reset + SSA kernel for one planned launch (stream operations only,
+// so it may be captured in a CUDA graph).
+int issue_class(smc_ctx *ctx, int plain, const SsaParams &common, const Launch &L, cudaStream_t s)
+{
+    SsaParams p = common;
+    p.inst_list = L.c->d_list;
+    p.n_list = (int)L.c->inst.size();
+    p.refill = L.refill;
+    p.blob_words = (L.c->blob_words + 3) & ~3;
+    p.s_max = L.c->s_max;
+    p.r_max = L.c->r_max;
+    p.tc_bytes = L.tc_bytes;
+    p.warp_bytes = L.warp_bytes;
+    if (smc_launch_queue_init(p, s))
+        return fail(ctx, SMC_E_CUDA, std::string("queue init: ") + cudaGetErrorString(cudaGetLastError()));
+    if (smc_launch_ssa(plain, p, L.grid, L.block, L.smem, s))
+        return fail(ctx, SMC_E_CUDA, std::string("ssa launch: ") + cudaGetErrorString(cudaGetLastError()));
+    return SMC_OK;
+}
+
+void fill_common(smc_ctx *ctx, SsaParams &p, uint64_t seed, double z, const smc_sim_out &out,
+                 uint64_t out_base, uint64_t out_stride, bool uniform)
+{
     std::memset(&p, 0, sizeof(p));
     p.blobs = ctx->d_blobs;
     p.blob_off = ctx->d_blob_off;
@@ -381,29 +461,102 @@ int launch_all(smc_ctx *ctx, int plain, uint64_t seed, double z, const smc_sim_o
     p.out_base = out_base;
     p.out_stride = out_stride;
     p.x_stride = ctx->s_max;
+}
+
+// Autotuner: for each precision, times short trial launches (a fixed trial
+// seed, about one trajectory per resident lane, counts into a scratch
+// buffer) over warps per block {2, 4, 8} x refill threshold {1, 8} for every
+// size class, then the best per-class shapes against one launch over all
+// instances, and keeps the fastest.  Results do not depend on the choice
+// (random numbers are keyed by trajectory, not by lane).  Synchronous: call
+// outside stream capture.
+int autotune(smc_ctx *ctx, int plain, cudaStream_t s)
+{
+    if (!ctx->autotune || ctx->explicit_shape || ctx->tuned[plain]) return SMC_OK;
+    const uint64_t n = (uint64_t)ctx->n_inst;
+    const uint64_t lanes = (uint64_t)ctx->n_sm * 1024;
+    const uint64_t per = std::max<uint64_t>(1, (lanes + n - 1) / n);
+    smc_sim_out o;
+    std::memset(&o, 0, sizeof(o));
+    o.counts = (uint64_t *)ctx->d_trial;
+    SsaParams pc;
+    fill_common(ctx, pc, 0x5EED5EED5EEDull, 0.0, o, 0, per, true);
+    // trials measure the bulk throughput: a short event budget keeps a rare
+    // very long trajectory from dominating every trial
+    pc.budget = std::min<uint64_t>(pc.budget, 1u << 13);
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    auto time_it = [&](const SizeClass &c, const Shape &sh, float &ms) -> int {
+        Launch L;
+        if (plan_class(ctx, plain, c, sh, L) != SMC_OK) { ms = 1e30f; ctx->err.clear(); return SMC_OK; }
+        CK(cudaEventRecord(e0, s));
+        int rc = issue_class(ctx, plain, pc, L, s);
+        if (rc) return rc;
+        CK(cudaEventRecord(e1, s));
+        CK(cudaEventSynchronize(e1));
+        CK(cudaEventElapsedTime(&ms, e0, e1));
+        return SMC_OK;
+    };
+    const int warps_c[] = {2, 4, 8}, refill_c[] = {1, 8};
+    int rc = SMC_OK;
+    float split_total = 0.0f, ms = 0.0f;
     for (auto &c : ctx->classes) {
-        const Shape &sh = c.shape[plain ? 1 : 0];
-        p.inst_list = c.d_list;
-        p.n_list = (int)c.inst.size();
-        p.refill = sh.refill;
-        p.blob_words = (c.blob_words + 3) & ~3;
-        p.s_max = c.s_max;
-        p.r_max = c.r_max;
-        p.tc_bytes = tc_bytes_of(ctx->prog);
-        p.warp_bytes = warp_bytes_of(c, plain, p.tc_bytes);
-        const int block = 32 * sh.warps;
-        const int smem = (int)sizeof(MonProg) + sh.warps * p.warp_bytes;
-        if ((size_t)smem > ctx->smem_optin)
-            return fail(ctx, SMC_E_UNSUPPORTED, "model tables do not fit in shared memory");
-        if (smc_ssa_set_smem_limit(plain, smem)) return fail(ctx, SMC_E_CUDA, "cudaFuncSetAttribute failed");
-        int per_sm = 0;
-        if (smc_ssa_max_blocks_per_sm(plain, block, smem, &per_sm) || per_sm < 1)
-            return fail(ctx, SMC_E_CUDA, "occupancy query failed");
-        if (sh.blocks_sm > 0) per_sm = std::min(per_sm, sh.blocks_sm);
-        const int grid = ctx->n_sm * per_sm;
-        if (smc_launch_queue_init(p, s)) return fail(ctx, SMC_E_CUDA, std::string("queue init: ") + cudaGetErrorString(cudaGetLastError()));
-        if (smc_launch_ssa(plain, p, grid, block, smem, s))
-            return fail(ctx, SMC_E_CUDA, std::string("ssa launch: ") + cudaGetErrorString(cudaGetLastError()));
+        Shape best = c.shape[plain];
+        float best_ms = 1e30f;
+        rc = time_it(c, best, ms);  // warm-up (module load, clocks)
+        for (int w : warps_c)
+            for (int r : refill_c) {
+                if (rc) break;
+                Shape sh;
+                sh.warps = w;
+                sh.refill = r;
+                sh.blocks_sm = 0;
+                rc = time_it(c, sh, ms);
+                if (ms < best_ms) { best_ms = ms; best = sh; }
+            }
+        best.tuned = true;
+        c.shape[plain] = best;
+        split_total += best_ms;
+    }
+    ctx->use_single[plain] = false;
+    if (!rc && ctx->classes.size() > 1) {
+        float best_ms = 1e30f;
+        Shape best = ctx->single.shape[plain];
+        for (int w : warps_c)
+            for (int r : refill_c) {
+                if (rc) break;
+                Shape sh;
+                sh.warps = w;
+                sh.refill = r;
+                sh.blocks_sm = 0;
+                rc = time_it(ctx->single, sh, ms);
+                if (ms < best_ms) { best_ms = ms; best = sh; }
+            }
+        best.tuned = true;
+        ctx->single.shape[plain] = best;
+        ctx->use_single[plain] = best_ms < split_total;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc) return rc;
+    ctx->tuned[plain] = true;
+    return SMC_OK;
+}
+
+// Launches queue initialisation and the SSA kernel for every class of the
+// partition in use.  Ranges (d_tbegin, d_tend) must already be on the device.
+int launch_all(smc_ctx *ctx, int plain, uint64_t seed, double z, const smc_sim_out &out,
+               uint64_t out_base, uint64_t out_stride, cudaStream_t s, bool uniform)
+{
+    SsaParams pc;
+    fill_common(ctx, pc, seed, z, out, out_base, out_stride, uniform);
+    for (const SizeClass *c : active_classes(ctx, plain)) {
+        Launch L;
+        int rc = plan_class(ctx, plain, *c, c->shape[plain ? 1 : 0], L);
+        if (rc) return rc;
+        rc = issue_class(ctx, plain, pc, L, s);
+        if (rc) return rc;
     }
     return SMC_OK;
 }
@@ -581,7 +734,11 @@ int smc_set_option(smc_ctx *ctx, int option, double value)
         if (!(value >= 0.0 && value <= 24.0)) return fail(ctx, SMC_E_INVALID_ARG, "renorm log2 0..24");
         ctx->renorm_log2 = (int)value;
         return SMC_OK;
-    case SMC_OPT_AUTOTUNE: ctx->autotune = value != 0.0; return SMC_OK;
+    case SMC_OPT_AUTOTUNE:
+        ctx->autotune = value != 0.0;
+        ctx->explicit_shape = false;
+        ctx->tuned[0] = ctx->tuned[1] = false;
+        return SMC_OK;
     case SMC_OPT_WARPS_PER_BLOCK:
         if (!(value >= 1.0 && value <= 8.0)) return fail(ctx, SMC_E_INVALID_ARG, "warps per block 1..8");
         ctx->warps = (int)value;
@@ -597,12 +754,18 @@ int smc_set_option(smc_ctx *ctx, int option, double value)
     case SMC_OPT_RECORD: ctx->record = value != 0.0; return SMC_OK;
     default: return fail(ctx, SMC_E_INVALID_ARG, "unknown option");
     }
-    for (auto &c : ctx->classes)
+    std::vector<SizeClass *> all_classes;
+    for (auto &c : ctx->classes) all_classes.push_back(&c);
+    all_classes.push_back(&ctx->single);
+    for (SizeClass *c : all_classes)
         for (int pl = 0; pl < 2; ++pl) {
-            c.shape[pl].warps = ctx->warps;
-            c.shape[pl].blocks_sm = ctx->blocks_sm;
-            c.shape[pl].refill = ctx->refill;
+            c->shape[pl].warps = ctx->warps;
+            c->shape[pl].blocks_sm = ctx->blocks_sm;
+            c->shape[pl].refill = ctx->refill;
         }
+    // an explicit shape replaces the tuned one (and the split partition)
+    ctx->use_single[0] = ctx->use_single[1] = false;
+    ctx->explicit_shape = true;
     return SMC_OK;
 }
 
@@ -619,6 +782,8 @@ int smc_simulate(smc_ctx *ctx, int precision, uint64_t seed, uint64_t traj_begin
     if (rc) return rc;
     CK(cudaSetDevice(ctx->device));
     cudaStream_t s = stream ? (cudaStream_t)stream : ctx->stream;
+    rc = autotune(ctx, precision == SMC_PLAIN_FP64, s);
+    if (rc) return rc;
     const double z = out->wilson ? z_of(confidence) : 0.0;
     return launch_all(ctx, precision == SMC_PLAIN_FP64, seed, z, *out, traj_begin, n_traj, s, true);
 }
@@ -678,29 +843,13 @@ int smc_simulate_noalloc(smc_ctx *ctx, int precision, uint64_t seed, uint64_t tr
     p.out_base = traj_begin;
     p.out_stride = n_traj;
     p.x_stride = ctx->s_max;
-    for (auto &c : ctx->classes) {
-        const Shape &sh = c.shape[plain ? 1 : 0];
-        p.inst_list = c.d_list;
-        p.n_list = (int)c.inst.size();
-        p.refill = sh.refill;
-        p.blob_words = (c.blob_words + 3) & ~3;
-        p.s_max = c.s_max;
-        p.r_max = c.r_max;
-        p.tc_bytes = tc_bytes_of(ctx->prog);
-        p.warp_bytes = warp_bytes_of(c, plain, p.tc_bytes);
-        const int block = 32 * sh.warps;
-        const int smem = (int)sizeof(MonProg) + sh.warps * p.warp_bytes;
-        if ((size_t)smem > ctx->smem_optin)
-            return fail(ctx, SMC_E_UNSUPPORTED, "model tables do not fit in shared memory");
-        if (smc_ssa_set_smem_limit(plain, smem)) return fail(ctx, SMC_E_CUDA, "cudaFuncSetAttribute failed");
-        int per_sm = 0;
-        if (smc_ssa_max_blocks_per_sm(plain, block, smem, &per_sm) || per_sm < 1)
-            return fail(ctx, SMC_E_CUDA, "occupancy query failed");
-        if (sh.blocks_sm > 0) per_sm = std::min(per_sm, sh.blocks_sm);
-        // resets this launch's queue counters, cursor and ticket in the scratch array
-        if (smc_launch_queue_init(p, s)) return fail(ctx, SMC_E_CUDA, "queue reset launch failed");
-        if (smc_launch_ssa(plain, p, ctx->n_sm * per_sm, block, smem, s))
-            return fail(ctx, SMC_E_CUDA, std::string("ssa launch: ") + cudaGetErrorString(cudaGetLastError()));
+    for (const SizeClass *c : active_classes(ctx, plain)) {
+        Launch L;
+        int rc = plan_class(ctx, plain, *c, c->shape[plain ? 1 : 0], L);
+        if (rc) return rc;
+        // queue reset (the counters, cursor and ticket in the scratch array), then the SSA kernel
+        rc = issue_class(ctx, plain, p, L, s);
+        if (rc) return rc;
     }
     return SMC_OK;
 }
@@ -747,6 +896,47 @@ int smc_estimate(smc_ctx *ctx, double confidence, double half_width, uint64_t se
     o.counts = (uint64_t *)ctx->d_counts;
     o.wilson = ctx->d_wilson;
     if (record) o.verdict = ctx->d_record;
+    // One Fig. 2 iteration = ranges up, queue reset + SSA kernel per class,
+    // counts and interval down: captured once into a CUDA graph and replayed
+    // for every iteration (the pinned range buffer is rewritten in between).
+    const int plain = precision == SMC_PLAIN_FP64;
+    rc = autotune(ctx, plain, s);
+    if (rc) return rc;
+    SsaParams pc;
+    fill_common(ctx, pc, seed, z, o, 0, record ? fixed_n : 0, false);
+    std::vector<Launch> plan;
+    for (const SizeClass *c : active_classes(ctx, plain)) {
+        Launch L;
+        rc = plan_class(ctx, plain, *c, c->shape[plain], L);
+        if (rc) return rc;
+        plan.push_back(L);
+    }
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    {
+        cudaError_t e1 = cudaMemcpyAsync(ctx->d_tbegin, ctx->h_range, n * 8, cudaMemcpyHostToDevice, s);
+        cudaError_t e2 = cudaMemcpyAsync(ctx->d_tend, ctx->h_range + n, n * 8, cudaMemcpyHostToDevice, s);
+        int lrc = (e1 == cudaSuccess && e2 == cudaSuccess) ? SMC_OK : SMC_E_CUDA;
+        for (const Launch &L : plan)
+            if (lrc == SMC_OK) lrc = issue_class(ctx, plain, pc, L, s);
+        cudaError_t e3 = cudaMemcpyAsync(ctx->h_counts, ctx->d_counts, (size_t)n * 4 * 8, cudaMemcpyDeviceToHost, s);
+        cudaError_t e4 = cudaMemcpyAsync(ctx->h_wilson, ctx->d_wilson, (size_t)n * 3 * 8, cudaMemcpyDeviceToHost, s);
+        cudaError_t e5 = cudaStreamEndCapture(s, &graph);
+        if (lrc != SMC_OK || e3 != cudaSuccess || e4 != cudaSuccess || e5 != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            return fail(ctx, SMC_E_CUDA, "capturing the estimate's launch sequence failed: " + ctx->err);
+        }
+    }
+    if (cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) {
+        cudaGraphDestroy(graph);
+        return fail(ctx, SMC_E_CUDA, "cudaGraphInstantiate failed");
+    }
+    struct GraphGuard {
+        cudaGraph_t g;
+        cudaGraphExec_t x;
+        ~GraphGuard() { cudaGraphExecDestroy(x); cudaGraphDestroy(g); }
+    } guard{graph, exec};
     int iters = 0;
     for (;;) {
         ++iters;
@@ -755,12 +945,7 @@ int smc_estimate(smc_ctx *ctx, double confidence, double half_width, uint64_t se
             ctx->h_range[n + m] = n_tot[m] + want[m];
             if (ctx->h_range[n + m] > (1ull << 32)) return fail(ctx, SMC_E_INVALID_ARG, "more than 2^32 trajectories");
         }
-        CK(cudaMemcpyAsync(ctx->d_tbegin, ctx->h_range, n * 8, cudaMemcpyHostToDevice, s));
-        CK(cudaMemcpyAsync(ctx->d_tend, ctx->h_range + n, n * 8, cudaMemcpyHostToDevice, s));
-        rc = launch_all(ctx, precision == SMC_PLAIN_FP64, seed, z, o, 0, record ? fixed_n : 0, s, false);
-        if (rc) return rc;
-        CK(cudaMemcpyAsync(ctx->h_counts, ctx->d_counts, (size_t)n * 4 * 8, cudaMemcpyDeviceToHost, s));
-        CK(cudaMemcpyAsync(ctx->h_wilson, ctx->d_wilson, (size_t)n * 3 * 8, cudaMemcpyDeviceToHost, s));
+        CK(cudaGraphLaunch(exec, s));
         CK(cudaStreamSynchronize(s));
         bool more = false;
         for (int m = 0; m < n; ++m) {
@@ -900,6 +1085,223 @@ int smc_monitor_replay(smc_ctx *ctx, int n_paths, const int32_t *len, const int3
     dfree(d_prog); dfree(d_coef); dfree(d_thr); dfree(d_len); dfree(d_off); dfree(d_x);
     dfree(d_t); dfree(d_tmin); dfree(d_closed); dfree(d_v); dfree(d_q);
     return rc;
+}
+
+int smc_simulate_snapshot(smc_ctx *ctx, int precision, uint64_t seed, uint64_t traj_begin, uint64_t n_traj,
+                          double t_snap, int stop_at_snap, const smc_sim_out *out, uint8_t *snap,
+                          int32_t *x_snap, void *stream)
+{
+    if (!ctx) return SMC_E_INVALID_ARG;
+    if (!out || !out->counts || !out->verdict || !snap || !x_snap)
+        return fail(ctx, SMC_E_INVALID_ARG, "counts, verdict, snap and x_snap outputs required");
+    if (precision != SMC_PLAIN_FP64 && precision != SMC_MIXED) return fail(ctx, SMC_E_INVALID_ARG, "bad precision");
+    if (traj_begin + n_traj > (1ull << 32)) return fail(ctx, SMC_E_INVALID_ARG, "trajectory index >= 2^32");
+    if (!(t_snap >= 0.0) || !std::isfinite(t_snap)) return fail(ctx, SMC_E_INVALID_ARG, "t_snap must be finite, >= 0");
+    int rc = prepare(ctx);
+    if (rc) return rc;
+    CK(cudaSetDevice(ctx->device));
+    cudaStream_t s = stream ? (cudaStream_t)stream : ctx->stream;
+    const int plain = precision == SMC_PLAIN_FP64;
+    rc = autotune(ctx, plain, s);
+    if (rc) return rc;
+    smc_sim_out o = *out;
+    o.wilson = nullptr;
+    SsaParams pc;
+    fill_common(ctx, pc, seed, 0.0, o, traj_begin, n_traj, true);
+    pc.snap_mode = stop_at_snap ? 2 : 1;
+    pc.t_snap = t_snap;
+    pc.o_snap = snap;
+    pc.o_xsnap = x_snap;
+    for (const SizeClass *c : active_classes(ctx, plain)) {
+        Launch L;
+        rc = plan_class(ctx, plain, *c, c->shape[plain], L);
+        if (rc) return rc;
+        rc = issue_class(ctx, plain, pc, L, s);
+        if (rc) return rc;
+    }
+    return SMC_OK;
+}
+
+int smc_snapshot_features(smc_ctx *ctx, uint64_t n_traj, const int32_t *x_snap, double t_snap,
+                          const float *x_scale, float t_scale, float *feat, void *stream)
+{
+    if (!ctx) return SMC_E_INVALID_ARG;
+    if (!ctx->have_model) return fail(ctx, SMC_E_STATE, "load a model first");
+    if (ctx->batch) return fail(ctx, SMC_E_UNSUPPORTED, "features need a single network");
+    if (!x_snap || !x_scale || !feat || !(t_scale > 0.0f)) return fail(ctx, SMC_E_INVALID_ARG, "bad feature arguments");
+    const int S = ctx->S[0], R = ctx->R[0], n = ctx->n_inst;
+    if (S + 1 + R > 16) return fail(ctx, SMC_E_UNSUPPORTED, "more than 16 features (S + 1 + R)");
+    for (int i = 0; i < S; ++i)
+        if (!(x_scale[i] > 0.0f)) return fail(ctx, SMC_E_INVALID_ARG, "x_scale must be > 0");
+    CK(cudaSetDevice(ctx->device));
+    cudaStream_t s = stream ? (cudaStream_t)stream : ctx->stream;
+    // centred log rate constants per instance
+    std::vector<float> lr((size_t)n * R), aux(S + (size_t)n * R);
+    for (int j = 0; j < R; ++j) {
+        double mean = 0.0;
+        for (int m = 0; m < n; ++m) {
+            const double c = ctx->rates[ctx->rate_off[m] + j];
+            mean += c > 0.0 ? std::log(c) : 0.0;
+        }
+        mean /= n;
+        for (int m = 0; m < n; ++m) {
+            const double c = ctx->rates[ctx->rate_off[m] + j];
+            lr[(size_t)m * R + j] = (float)((c > 0.0 ? std::log(c) : 0.0) - mean);
+        }
+    }
+    std::memcpy(aux.data(), x_scale, S * sizeof(float));
+    std::memcpy(aux.data() + S, lr.data(), lr.size() * sizeof(float));
+    if (ctx->feat_aux_n < aux.size()) {
+        dfree(ctx->d_feat_aux);
+        CK(cudaMalloc(&ctx->d_feat_aux, aux.size() * sizeof(float)));
+        ctx->feat_aux_n = aux.size();
+    }
+    CK(cudaMemcpyAsync(ctx->d_feat_aux, aux.data(), aux.size() * sizeof(float), cudaMemcpyHostToDevice, s));
+    CK(cudaStreamSynchronize(s));  // aux is a host temporary
+    if (smc_launch_snapshot_features((uint64_t)n * n_traj, n_traj, S, R, ctx->s_max, x_snap, ctx->d_feat_aux,
+                                     (float)(t_snap / t_scale), ctx->d_feat_aux + S, feat, s))
+        return fail(ctx, SMC_E_CUDA, "feature kernel launch failed");
+    return SMC_OK;
+}
+
+int smc_estimate_cv(smc_ctx *ctx, smc_mlp *mlp, double confidence, double half_width, uint64_t seed,
+                    int precision, double t_snap, const float *x_scale, float t_scale, double beta,
+                    uint64_t pilot, smc_cv_result *out)
+{
+    if (!ctx) return SMC_E_INVALID_ARG;
+    if (!mlp || !out || !x_scale) return fail(ctx, SMC_E_INVALID_ARG, "null argument");
+    if (!ctx->have_model || !ctx->have_prop) return fail(ctx, SMC_E_STATE, "load a model and a property first");
+    if (ctx->n_inst != 1 || ctx->batch) return fail(ctx, SMC_E_UNSUPPORTED, "control variate needs one instance");
+    if (!(confidence > 0.0 && confidence < 1.0) || !(half_width > 0.0 && half_width < 0.5) || pilot < 2 ||
+        !std::isfinite(beta))
+        return fail(ctx, SMC_E_INVALID_ARG, "bad confidence, half width, pilot or beta");
+    const uint64_t kPrefixBase = 1ull << 31;
+    const int S = ctx->S[0], R = ctx->R[0], F = S + 1 + R;
+    const double z = z_of(confidence);
+    int rc = prepare(ctx);
+    if (rc) return rc;
+    CK(cudaSetDevice(ctx->device));
+    cudaStream_t s = ctx->stream;
+    // device buffers, grown on demand
+    struct Buf {
+        uint8_t *y = nullptr, *snap = nullptr;
+        int32_t *x = nullptr;
+        float *feat = nullptr, *g = nullptr;
+        uint64_t *counts = nullptr;
+        double *sums = nullptr;
+        uint64_t cap = 0;
+        ~Buf()
+        {
+            cudaFree(y); cudaFree(snap); cudaFree(x); cudaFree(feat); cudaFree(g); cudaFree(counts); cudaFree(sums);
+        }
+    } b;
+    auto grow = [&](uint64_t n) -> int {
+        if (n <= b.cap) return SMC_OK;
+        uint64_t c = std::max<uint64_t>(n, 2 * b.cap);
+        cudaFree(b.y); cudaFree(b.snap); cudaFree(b.x); cudaFree(b.feat); cudaFree(b.g);
+        b.y = b.snap = nullptr; b.x = nullptr; b.feat = b.g = nullptr;
+        CK(cudaMalloc(&b.y, c));
+        CK(cudaMalloc(&b.snap, c));
+        CK(cudaMalloc(&b.x, c * ctx->s_max * 4));
+        CK(cudaMalloc(&b.feat, c * F * 4));
+        CK(cudaMalloc(&b.g, c * 4));
+        b.cap = c;
+        return SMC_OK;
+    };
+    CK(cudaMalloc(&b.counts, 2 * 4 * 8));
+    CK(cudaMalloc(&b.sums, 12 * 8));
+    CK(cudaMemsetAsync(b.counts, 0, 2 * 4 * 8, s));
+    CK(cudaMemsetAsync(b.sums, 0, 12 * 8, s));
+    // runs trajectories [lo, hi) (full or prefix-only) and accumulates their sums
+    auto run = [&](uint64_t lo, uint64_t hi, bool prefix) -> int {
+        if (hi <= lo) return SMC_OK;
+        const uint64_t n = hi - lo;
+        int r = grow(n);
+        if (r) return r;
+        smc_sim_out o;
+        std::memset(&o, 0, sizeof(o));
+        o.counts = b.counts + (prefix ? 4 : 0);
+        o.verdict = b.y;
+        r = smc_simulate_snapshot(ctx, precision, seed, lo, n, t_snap, prefix ? 1 : 0, &o, b.snap, b.x, s);
+        if (r) return r;
+        r = smc_snapshot_features(ctx, n, b.x, t_snap, x_scale, t_scale, b.feat, s);
+        if (r) return r;
+        if (smc_mlp_predict(mlp, b.feat, n, b.g, s) != SMC_OK)
+            return fail(ctx, SMC_E_CUDA, std::string("surrogate prediction: ") + smc_mlp_last_error(mlp));
+        if (smc_launch_cv_sums(n, b.y, b.snap, b.g, prefix ? 1 : 0, b.sums + (prefix ? 6 : 0), s))
+            return fail(ctx, SMC_E_CUDA, "cv sums launch failed");
+        return SMC_OK;
+    };
+    uint64_t n1 = 0, n2 = 0, want1 = pilot, want2 = pilot;
+    double hs[12];
+    uint64_t hc[8];
+    int iters = 0;
+    double p = 0.0, V = 0.0, neff = 0.0;
+    for (;;) {
+        ++iters;
+        if (want1 >= kPrefixBase || want2 >= kPrefixBase) return fail(ctx, SMC_E_INVALID_ARG, "sample sizes exceed 2^31");
+        rc = run(n1, want1, false);
+        if (rc) return rc;
+        rc = run(kPrefixBase + n2, kPrefixBase + want2, true);
+        if (rc) return rc;
+        n1 = want1;
+        n2 = want2;
+        CK(cudaMemcpyAsync(hs, b.sums, sizeof(hs), cudaMemcpyDeviceToHost, s));
+        CK(cudaMemcpyAsync(hc, b.counts, sizeof(hc), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        // S1: full runs (Y, G); S2: prefix runs (G only)
+        const double c1n = hs[0], sY = hs[1], sG1 = hs[2], sYY = hs[3], sGG1 = hs[4], sYG = hs[5];
+        const double c2n = hs[6], sG2 = hs[8], sGG2 = hs[10];
+        const double nn = c1n + c2n;
+        const double mD = (sY - beta * sG1) / c1n, mG1 = sG1 / c1n, mG = (sG1 + sG2) / nn;
+        p = mD + beta * mG;
+        const double sDD = sYY - 2.0 * beta * sYG + beta * beta * sGG1, sDG = sYG - beta * sGG1;
+        const double vD = std::max(0.0, (sDD - c1n * mD * mD) / (c1n - 1.0));
+        const double vG = std::max(0.0, (sGG1 + sGG2 - nn * mG * mG) / (nn - 1.0));
+        const double cDG = (sDG - c1n * mD * mG1) / (c1n - 1.0);
+        const double a = vD, bb = std::max(0.0, beta * beta * vG + 2.0 * beta * cDG);
+        V = a / c1n + bb / nn;
+        const bool interior = p > 0.0 && p < 1.0 && V > 0.0;
+        neff = interior ? p * (1.0 - p) / V : c1n;
+        const double pp = p <= 0.5 ? p + half_width : p - half_width;
+        const double target = wilson_sample_real(pp, half_width, z);
+        if (neff >= target || iters >= 64) break;
+        // cost-optimal sizes for the target variance (events per run measured)
+        const double c_full = std::max(1.0, (double)hc[2] / c1n), c_pre = std::max(1.0, (double)hc[6] / c2n);
+        const double dcost = std::max(c_full - c_pre, 1e-3 * c_full);
+        uint64_t t1, t2;
+        if (!interior) {  // no variance information yet: grow the full sample as Fig. 2 does
+            t1 = (uint64_t)std::ceil(target);
+            t2 = n2;
+        } else {
+            const double Vt = p * (1.0 - p) / target;
+            const double k = std::sqrt(a * dcost) + std::sqrt(bb * c_pre);
+            double o1 = std::sqrt(a / dcost) * k / Vt, on = bb > 0.0 ? std::sqrt(bb / c_pre) * k / Vt : 0.0;
+            if (on < o1) { o1 = (a + bb) / Vt; on = o1; }
+            t1 = (uint64_t)std::ceil(o1);
+            t2 = (uint64_t)std::ceil(std::max(0.0, on - o1));
+        }
+        want1 = std::min(std::max(t1, n1 + 1), 4 * n1);
+        want2 = std::min(std::max(t2, n2), 4 * std::max<uint64_t>(n2, 1));
+    }
+    out->p_hat = p;
+    out->var = V;
+    out->n_eff = neff;
+    out->beta = beta;
+    // Eq. 4 at the effective sample size
+    const double dn = std::max(neff, 1.0), z2 = z * z, pc = std::min(1.0, std::max(0.0, p));
+    const double centre = pc + z2 / (2.0 * dn);
+    const double half = z * std::sqrt(pc * (1.0 - pc) / dn + z2 / (4.0 * dn * dn));
+    const double den = 1.0 + z2 / dn;
+    out->lo = std::max(0.0, (centre - half) / den);
+    out->hi = std::min(1.0, (centre + half) / den);
+    out->n_full = n1;
+    out->n_prefix = n2;
+    out->events_full = hc[2];
+    out->events_prefix = hc[6];
+    out->iterations = iters;
+    out->status = (hc[3] || hc[7]) ? SMC_STATUS_BUDGET : 0;
+    return SMC_OK;
 }
 
 }  // extern "C"

@@ -113,7 +113,15 @@ struct SsaParams {
     int32_t *o_xfinal;
     uint64_t out_base;           // trajectory index of output column 0
     uint64_t out_stride;         // columns per instance row
-    int32_t x_stride;            // species per x_final row
+    int32_t x_stride;            // species per x_final / x_snap row
+    // checkpoint snapshot (surrogate control variate): the state occupied at
+    // t_snap is written to o_xsnap and o_snap = 0; a trajectory decided
+    // before t_snap gets o_snap = 1.  snap_mode 2 stops every trajectory at
+    // its snapshot (prefix-only run; such trajectories are not counted).
+    int32_t snap_mode;           // 0 none, 1 snapshot, 2 snapshot and stop
+    double t_snap;
+    uint8_t *o_snap;             // [n_inst][out_stride]
+    int32_t *o_xsnap;            // [n_inst][out_stride][x_stride]
 };
 
 // Monitor replay (tests): runs the compiled monitor over given paths.
@@ -143,6 +151,11 @@ int smc_ssa_max_blocks_per_sm(int plain, int block, int smem_bytes, int *out);
 int smc_ssa_set_smem_limit(int plain, int smem_bytes);
 int smc_launch_queue_init(const SsaParams &p, void *stream);
 int smc_launch_replay(const ReplayParams &p, void *stream);
+int smc_launch_snapshot_features(uint64_t n_rows, uint64_t n_traj, int S, int R, int x_stride,
+                                 const int32_t *x_snap, const float *x_scale, float t_feat,
+                                 const float *lograte, float *feat, void *stream);
+int smc_launch_cv_sums(uint64_t n, const uint8_t *y, const uint8_t *snap, const float *g, int prefix,
+                       double *sums, void *stream);
 // fixed scratch of smc_simulate_noalloc (see smc_kernels.cu)
 #define SMC_NOALLOC_MAX_DEVICES 64
 int smc_noalloc_scratch(int device, unsigned long long **queue, unsigned int **sync);

@@ -22,6 +22,7 @@
 #include <math.h>
 #include <stdint.h>
 
+#include <algorithm>
 #include <mutex>
 
 #include "smc.h"
@@ -267,9 +268,10 @@ __device__ __forceinline__ unsigned long long warp_sum(unsigned long long v)
     return v;
 }
 
-// Claims an instance for the warp: first one each from the cursor, then any
-// instance whose queue is not yet exhausted.  Returns -1 when no work is
-// left.  Warp-collective.
+// Claims an instance for the warp: first one each from the cursor, then the
+// instance with the most trajectories left (so that warps whose instance ran
+// dry help the slowest ones).  Returns -1 when no work is left.
+// Warp-collective.
 __device__ int acquire_instance(const SsaParams &p, bool &first, int gw, int lane)
 {
     if (first) {
@@ -281,19 +283,24 @@ __device__ int acquire_instance(const SsaParams &p, bool &first, int gw, int lan
     }
     const int n = p.n_list;
     const int start = (int)(((unsigned)gw * 2654435761u) % (unsigned)n);
-    for (int k = 0; k < n; k += 32) {
-        bool ok = false;
-        int m = -1;
-        if (k + lane < n) {
-            int idx = start + k + lane;
-            if (idx >= n) idx -= n;
-            m = p.inst_list[idx];
-            ok = *((volatile unsigned long long *)&p.tnext[m]) < (p.uniform ? p.u_end : p.tend[m]);
-        }
-        const unsigned b = __ballot_sync(FULL_MASK, ok);
-        if (b) return __shfl_sync(FULL_MASK, m, __ffs(b) - 1);
+    unsigned long long best = 0;
+    int best_m = -1;
+    for (int k = lane; k < n; k += 32) {
+        int idx = start + k;
+        if (idx >= n) idx -= n;
+        const int m = p.inst_list[idx];
+        const unsigned long long nx = *((volatile unsigned long long *)&p.tnext[m]);
+        const unsigned long long end = p.uniform ? p.u_end : p.tend[m];
+        const unsigned long long left = nx < end ? end - nx : 0;
+        if (left > best) { best = left; best_m = m; }
     }
-    return -1;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long ob = __shfl_xor_sync(FULL_MASK, best, o);
+        const int om = __shfl_xor_sync(FULL_MASK, best_m, o);
+        if (ob > best || (ob == best && om > best_m)) { best = ob; best_m = om; }
+    }
+    return best ? best_m : -1;
 }
 
 template <bool PLAIN>
@@ -351,28 +358,32 @@ __device__ __forceinline__ void run_instance(const SsaParams &p, const MonProg &
     const uint32_t renorm_mask = p.renorm_mask;
     const uint64_t budget = p.budget;
 
-    bool active = false, exhausted = false;
+    bool active = false, exhausted = false, snapped = false;
     uint32_t traj = 0, e = 0;
     double t = 0.0;
     T a0 = 0;
     MonLane ml;
     uint32_t c_yes = 0, c_dec = 0, c_bud = 0;
     unsigned long long c_ev = 0;
+    const int snap_mode = p.snap_mode;
+    const double t_snap = p.t_snap;
 
-    // verdict codes: 1 false, 2 true, 3 event budget exhausted
+    // verdict codes: 1 false, 2 true, 3 event budget exhausted, 4 stopped at
+    // the snapshot (prefix-only run: no verdict, not counted)
     auto finish = [&](int v) {
         if (v == 3) ++c_bud;
-        else { ++c_dec; c_yes += (v == 2); }
+        else if (v != 4) { ++c_dec; c_yes += (v == 2); }
         c_ev += e;
+        const uint64_t idx = (uint64_t)m * p.out_stride + ((uint64_t)traj - p.out_base);
         if (p.o_verdict) {
-            const uint64_t idx = (uint64_t)m * p.out_stride + ((uint64_t)traj - p.out_base);
             p.o_verdict[idx] = (v == 2);
-            if (p.o_status) p.o_status[idx] = (v == 3);
+            if (p.o_status) p.o_status[idx] = (v == 3) ? 1 : (v == 4 ? 2 : 0);
             if (p.o_events) p.o_events[idx] = e;
             if (p.o_tfinal) p.o_tfinal[idx] = t;
             if (p.o_xfinal)
                 for (int i = 0; i < S; ++i) p.o_xfinal[idx * p.x_stride + i] = xs[i * 32];
         }
+        if (snap_mode && !snapped) p.o_snap[idx] = 1;  // decided before t_snap
         active = false;
     };
 
@@ -394,6 +405,7 @@ __device__ __forceinline__ void run_instance(const SsaParams &p, const MonProg &
                         traj = (uint32_t)id;
                         e = 0;
                         t = 0.0;
+                        snapped = false;
                         for (int i = 0; i < S; ++i) xs[i * 32] = x0[i];
                         xs[S * 32] = 1;
                         double s = 0.0;
@@ -463,6 +475,15 @@ __device__ __forceinline__ void run_instance(const SsaParams &p, const MonProg &
             const float tau = __fdividef(-__logf(ut), (float)a0);
             tn = __dadd_rn(t, (double)tau);
             r = (T)(us * (float)a0);
+        }
+        if (snap_mode && !snapped && dgt(tn, t_snap)) {
+            // the current state is the one occupied at t_snap, and the
+            // verdict was not fixed by anything known up to t_snap
+            snapped = true;
+            const uint64_t idx = (uint64_t)m * p.out_stride + ((uint64_t)traj - p.out_base);
+            p.o_snap[idx] = 0;
+            for (int i = 0; i < S; ++i) p.o_xsnap[idx * p.x_stride + i] = xs[i * 32];
+            if (snap_mode == 2) { finish(4); continue; }
         }
         int v = 0;
         if (ml.pend || __double_as_longlong(tn) > ml.hb) v = mon_draw(ml, P, tn, tc);
@@ -710,6 +731,70 @@ int smc_launch_replay(const ReplayParams &rp, void *stream)
 {
     const int n = rp.n_paths > 0 ? rp.n_paths : 1;
     replay_kernel<<<(n + 127) / 128, 128, 0, (cudaStream_t)stream>>>(rp);
+    return to_code(cudaGetLastError());
+}
+
+// ---------------------------------------------------------------------------
+// Snapshot features: row (m, k) = x_snap / x_scale, t_snap / t_scale, the
+// instance's centred log rate constants (zero for rows without a snapshot).
+__global__ void snapshot_features_kernel(uint64_t n_rows, uint64_t n_traj, int S, int R, int x_stride,
+                                         const int32_t *x_snap, const float *x_scale, float t_feat,
+                                         const float *lograte, float *feat)
+{
+    const uint64_t row = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (row >= n_rows) return;
+    const uint64_t m = row / n_traj;
+    const int F = S + 1 + R;
+    float *f = feat + row * F;
+    for (int i = 0; i < S; ++i) f[i] = (float)x_snap[row * x_stride + i] / x_scale[i];
+    f[S] = t_feat;
+    for (int j = 0; j < R; ++j) f[S + 1 + j] = lograte[m * R + j];
+}
+
+int smc_launch_snapshot_features(uint64_t n_rows, uint64_t n_traj, int S, int R, int x_stride,
+                                 const int32_t *x_snap, const float *x_scale, float t_feat,
+                                 const float *lograte, float *feat, void *stream)
+{
+    if (n_rows == 0) return 0;
+    snapshot_features_kernel<<<(unsigned)((n_rows + 255) / 256), 256, 0, (cudaStream_t)stream>>>(
+        n_rows, n_traj, S, R, x_stride, x_snap, x_scale, t_feat, lograte, feat);
+    return to_code(cudaGetLastError());
+}
+
+// Control-variate sums over n trajectories: G = g for trajectories alive at
+// the snapshot, G = Y for those decided before it; sums[0..5] += (count,
+// sum Y, sum G, sum Y^2, sum G^2, sum Y G) in FP64 (Y ignored for prefix-only
+// runs, whose verdict is unknown: they contribute count and the G sums, with
+// G = Y only when decided before the snapshot).
+__global__ void cv_sums_kernel(uint64_t n, const uint8_t *y, const uint8_t *snap, const float *g, int prefix,
+                               double *sums)
+{
+    double s[6] = {0, 0, 0, 0, 0, 0};
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        const double Y = y[i];
+        const double G = snap[i] ? Y : (double)g[i];
+        s[0] += 1.0;
+        s[1] += prefix ? 0.0 : Y;
+        s[2] += G;
+        s[3] += prefix ? 0.0 : Y * Y;
+        s[4] += G * G;
+        s[5] += prefix ? 0.0 : Y * G;
+    }
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+        double v = s[k];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL_MASK, v, o);
+        if ((threadIdx.x & 31) == 0) atomicAdd(&sums[k], v);
+    }
+}
+
+int smc_launch_cv_sums(uint64_t n, const uint8_t *y, const uint8_t *snap, const float *g, int prefix,
+                       double *sums, void *stream)
+{
+    if (n == 0) return 0;
+    const unsigned blocks = (unsigned)std::min<uint64_t>(1024, (n + 255) / 256);
+    cv_sums_kernel<<<blocks, 256, 0, (cudaStream_t)stream>>>(n, y, snap, g, prefix, sums);
     return to_code(cudaGetLastError());
 }
 
