@@ -179,12 +179,18 @@ def main():
     ap.add_argument('--no-cpu-baseline', action='store_true')
     ap.add_argument('--no-e2e', action='store_true')
     ap.add_argument('--traj', type=int, default=N_TRAJ, help='trajectories per step (profiling runs)')
+    ap.add_argument('--config', default='lotka_volterra',
+                    choices=['lotka_volterra', 'immigration_death', 'random_networks', 'surrogate', 'cascade'])
     args = ap.parse_args()
     N_TRAJ = args.traj
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == 'reference':
         run_reference(args)
+        return
+    if args.config != 'lotka_volterra':
+        import bench_configs
+        bench_configs.run(args)
         return
 
     import numpy as np
