@@ -81,7 +81,9 @@ extern "C" {
 /* ---- options (smc_set_option) ------------------------------------------- */
 #define SMC_OPT_EVENT_BUDGET 0    /* max reactions per trajectory (default 2^24) */
 #define SMC_OPT_RENORM_LOG2 1     /* mixed path: a_0 renormalised every 2^k events (default 8) */
-#define SMC_OPT_AUTOTUNE 2        /* 1 = choose launch shape by timed trials (default 1) */
+#define SMC_OPT_AUTOTUNE 2        /* 1 = choose launch shape by timed trials (default 1);
+                                     the result is kept for later loads of a model of
+                                     the same structure (instances, S, R per size class) */
 #define SMC_OPT_WARPS_PER_BLOCK 3 /* fixed launch shape when autotune is 0 (default 4) */
 #define SMC_OPT_BLOCKS_PER_SM 4   /* 0 = as many as fit (default 0) */
 #define SMC_OPT_REFILL 5          /* refill a warp when >= this many lanes idle (default 1) */
@@ -177,6 +179,18 @@ int smc_load_property(smc_ctx *ctx, int n_atoms, const int32_t *atom_coef,
 
 /* Sets an SMC_OPT_* option.  Errors: SMC_E_INVALID_ARG. */
 int smc_set_option(smc_ctx *ctx, int option, double value);
+
+/* Launch shape in use for `precision` (no counterpart in the paper: the
+ * batching of Sec. 4's replicas into persistent launches is this library's).
+ * The instances are served by *n_launches launches (one per size class, or
+ * one over all instances, as the autotuner chose); launch `index` uses
+ * *warps_per_block warps per block, *blocks_per_sm resident blocks per SM,
+ * refill threshold *refill, and serves *n_instances instances.  Any output
+ * pointer may be null.  Valid after an estimate or simulation of the loaded
+ * model.  Errors: SMC_E_STATE before that, SMC_E_INVALID_ARG for a bad
+ * precision or index (*n_launches is still written). */
+int smc_get_launch_shape(smc_ctx *ctx, int precision, int index, int *n_launches, int *warps_per_block,
+                         int *blocks_per_sm, int *refill, int *n_instances);
 
 /* Estimates P(phi) for every instance (Sec. 3.3).
  *  confidence = 1 - alpha (0 < confidence < 1);
@@ -315,6 +329,16 @@ typedef struct {
 int smc_estimate_cv(smc_ctx *ctx, smc_mlp *mlp, double confidence, double half_width, uint64_t seed,
                     int precision, double t_snap, const float *x_scale, float t_scale, double beta,
                     uint64_t pilot, smc_cv_result *out);
+
+/* The natural logarithm used by the FP64 path for tau = -ln(u) / a_0
+ * (Eq. 2a): a table-driven method after Tang (ACM TOMS 16, 1990) with an
+ * exact argument reduction, 15 FP64 operations (GB300 runs FP64 at 1/64 of
+ * FP32), within about half an ulp (correctly rounded but for values within
+ * ~2^-6 ulp of a rounding midpoint).  Diagnostic entry point (tests).
+ * u, out: device arrays of n doubles, caller-owned; out[i] = ln(u[i]),
+ * enqueued on `stream` (0: the context's stream).  Errors: INVALID_ARG for
+ * null pointers with n > 0, CUDA for a failed launch. */
+int smc_log_fp64(smc_ctx *ctx, const double *u, uint64_t n, double *out, void *stream);
 
 /* Host utilities (no GPU needed). */
 double smc_normal_quantile(double p);                           /* Phi^{-1}(p) */

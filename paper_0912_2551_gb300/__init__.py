@@ -165,6 +165,20 @@ class Context:
     def set_option(self, name: str, value: float):
         self._check(N.smc_set_option(self.h, N.OPT[name], float(value)), f'smc_set_option({name})')
 
+    def launch_shapes(self, precision: str = 'mixed'):
+        """The launches serving the loaded model (after an estimate or a
+        simulation): list of dicts warps_per_block, blocks_per_sm, refill,
+        n_instances."""
+        out, i, n = [], 0, ctypes.c_int32(1)
+        while i < n.value:
+            w, b, r, m = (ctypes.c_int32() for _ in range(4))
+            self._check(N.smc_get_launch_shape(self.h, PRECISION[precision], i, ctypes.byref(n), ctypes.byref(w),
+                                               ctypes.byref(b), ctypes.byref(r), ctypes.byref(m)),
+                        'smc_get_launch_shape')
+            out.append(dict(warps_per_block=w.value, blocks_per_sm=b.value, refill=r.value, n_instances=m.value))
+            i += 1
+        return out
+
     # -- running --------------------------------------------------------------
     def estimate(self, confidence: float, half_width: float = 0.01, seed: int = 0,
                  precision: str = 'plain', sampling: str = 'iterative', fixed_n: int = 0):

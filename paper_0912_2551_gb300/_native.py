@@ -88,6 +88,8 @@ SIGNATURES = {
                                          ctypes.c_int, ctypes.POINTER(smc_node), ctypes.c_int,
                                          ctypes.c_double]),
     'smc_set_option': (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_double]),
+    'smc_get_launch_shape': (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, c_i32p, c_i32p, c_i32p,
+                                            c_i32p, c_i32p]),
     'smc_estimate': (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_double, ctypes.c_uint64,
                                     ctypes.c_int, ctypes.c_uint64, ctypes.POINTER(smc_result)]),
     'smc_get_verdicts': (ctypes.c_int, [ctypes.c_void_p, c_u8p, ctypes.c_uint64]),
@@ -122,6 +124,8 @@ SIGNATURES = {
                                        ctypes.c_uint64, ctypes.c_int, ctypes.c_double, ctypes.c_void_p,
                                        ctypes.c_float, ctypes.c_double, ctypes.c_uint64,
                                        ctypes.POINTER(smc_cv_result)]),
+    'smc_log_fp64': (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p,
+                                    ctypes.c_void_p]),
     'smc_normal_quantile': (ctypes.c_double, [ctypes.c_double]),
     'smc_wilson_interval': (ctypes.c_int, [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_double, c_f64p,
                                            c_f64p]),

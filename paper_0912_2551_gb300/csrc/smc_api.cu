@@ -72,6 +72,15 @@ struct smc_ctx {
     SizeClass single;                // every instance in one launch
     bool use_single[2] = {false, false};
     bool tuned[2] = {false, false};
+    // autotuner results of the last tuned model structure, per precision:
+    // reused when a model of the same structure is loaded again
+    struct TuneMemo {
+        bool valid = false;
+        std::vector<int64_t> sig;
+        std::vector<Shape> cls;
+        Shape single;
+        bool use_single = false;
+    } memo[2];
     unsigned long long *d_trial = nullptr;  // autotuner counts
     uint64_t *d_tbegin = nullptr, *d_tend = nullptr;
     unsigned long long *d_tnext = nullptr;
@@ -85,6 +94,7 @@ struct smc_ctx {
     uint64_t record_n = 0, record_valid = 0;
     float *d_feat_aux = nullptr;  // feature scales and centred log rates
     size_t feat_aux_n = 0;
+    double *d_logtab = nullptr;   // table of the FP64 path's logarithm (lives with the context)
 
     // options
     uint64_t budget = 1ull << 24;
@@ -198,6 +208,41 @@ double as241(double p)
 }
 
 double z_of(double confidence) { return as241(1.0 - (1.0 - confidence) / 2.0); }
+
+// Table of the FP64 path's logarithm (Tang 1990, exact-reduction form): for
+// the bucket of m around F_j = 0.75 + j/256, a 9-bit G_j ~ 1/F_j and
+// ln(1/G_j) split into a high double and the low remainder (long double);
+// then ln 2 the same way.  Empty if some bucket's reduction is not exact.
+std::vector<double> log_table_host()
+{
+    std::vector<double> t(SMC_LOGTAB_BYTES / 8, 0.0);
+    // high part: the nearest multiple of 2^-42; low part: the remainder
+    auto split = [](long double L, double &hi, double &lo) {
+        hi = (double)(roundl(L * 0x1p42L) * 0x1p-42L);
+        lo = (double)(L - (long double)hi);
+    };
+    for (int j = 0; j < SMC_LOGTAB_N; ++j) {
+        // bucket of m: [F - 1/512, F + 1/512] within [0.75, 1.5)
+        const double F = 0.75 + j / 256.0;
+        const long double m_lo = std::max(F - 1.0 / 512, 0.75), m_hi = std::min(F + 1.0 / 512, 1.5);
+        // G = n / q with 9 significant bits (q = 256 above 1, 512 below),
+        // the one with the smallest max |m G - 1| over the bucket
+        const long double inv = 1.0L / F;
+        const int q = inv > 1 ? 256 : 512;
+        long double best = 1, G = 1;
+        for (long n = (long)floorl(inv * q) - 2; n <= (long)floorl(inv * q) + 3; ++n) {
+            const long double g = (long double)n / q;
+            if ((g > 1 && q != 256) || (g < 1 && q != 512)) continue;
+            const long double e = std::max(fabsl(m_lo * g - 1), fabsl(m_hi * g - 1));
+            if (e < best) { best = e; G = g; }
+        }
+        if (!(best < 1.0L / 256)) return {};  // the reduction would not be exact
+        t[j] = (double)G;
+        split(-logl(G), t[SMC_LOGTAB_N + j], t[2 * SMC_LOGTAB_N + j]);
+    }
+    split(logl(2.0L), t[3 * SMC_LOGTAB_N], t[3 * SMC_LOGTAB_N + 1]);
+    return t;
+}
 
 // Eq. 5
 double wilson_sample_real(double p, double eps, double z)
@@ -398,7 +443,7 @@ int plan_class(smc_ctx *ctx, int plain, const SizeClass &c, const Shape &sh, Lau
     L.tc_bytes = tc_bytes_of(ctx->prog);
     L.warp_bytes = warp_bytes_of(c, plain, L.tc_bytes);
     L.block = 32 * sh.warps;
-    L.smem = (int)sizeof(MonProg) + sh.warps * L.warp_bytes;
+    L.smem = (int)sizeof(MonProg) + (plain ? SMC_LOGTAB_BYTES : 0) + sh.warps * L.warp_bytes;
     L.refill = sh.refill;
     if ((size_t)L.smem > ctx->smem_optin)
         return fail(ctx, SMC_E_UNSUPPORTED, "model tables do not fit in shared memory");
@@ -424,6 +469,8 @@ int issue_class(smc_ctx *ctx, int plain, const SsaParams &common, const Launch &
     p.r_max = L.c->r_max;
     p.tc_bytes = L.tc_bytes;
     p.warp_bytes = L.warp_bytes;
+    p.logtab = ctx->d_logtab;
+    p.logtab_bytes = plain ? SMC_LOGTAB_BYTES : 0;
     if (smc_launch_queue_init(p, s))
         return fail(ctx, SMC_E_CUDA, std::string("queue init: ") + cudaGetErrorString(cudaGetLastError()));
     if (smc_launch_ssa(plain, p, L.grid, L.block, L.smem, s))
@@ -470,11 +517,37 @@ void fill_common(smc_ctx *ctx, SsaParams &p, uint64_t seed, double z, const smc_
 // instances, and keeps the fastest.  Results do not depend on the choice
 // (random numbers are keyed by trajectory, not by lane).  Synchronous: call
 // outside stream capture.
+// Structure of the loaded problem as far as launch shapes depend on it: the
+// size classes (instances, species, reactions, table words) and the
+// monitor's per-warp clock area.
+std::vector<int64_t> tune_signature(const smc_ctx *ctx)
+{
+    std::vector<int64_t> sig{ctx->n_inst, tc_bytes_of(ctx->prog), (int64_t)ctx->classes.size()};
+    for (const auto &c : ctx->classes) {
+        sig.push_back((int64_t)c.inst.size());
+        sig.push_back(c.s_max);
+        sig.push_back(c.r_max);
+        sig.push_back(c.blob_words);
+    }
+    return sig;
+}
+
 int autotune(smc_ctx *ctx, int plain, cudaStream_t s)
 {
     if (!ctx->autotune || ctx->explicit_shape || ctx->tuned[plain]) return SMC_OK;
+    const std::vector<int64_t> sig = tune_signature(ctx);
+    auto &memo = ctx->memo[plain];
+    if (memo.valid && memo.sig == sig) {
+        for (size_t i = 0; i < ctx->classes.size(); ++i) ctx->classes[i].shape[plain] = memo.cls[i];
+        ctx->single.shape[plain] = memo.single;
+        ctx->use_single[plain] = memo.use_single;
+        ctx->tuned[plain] = true;
+        return SMC_OK;
+    }
     const uint64_t n = (uint64_t)ctx->n_inst;
-    const uint64_t lanes = (uint64_t)ctx->n_sm * 1024;
+    // about four trajectories per resident lane, so that the trial sees lanes
+    // being refilled (one wave would measure only its slowest trajectory)
+    const uint64_t lanes = (uint64_t)ctx->n_sm * 1024 * 4;
     const uint64_t per = std::max<uint64_t>(1, (lanes + n - 1) / n);
     smc_sim_out o;
     std::memset(&o, 0, sizeof(o));
@@ -541,6 +614,12 @@ int autotune(smc_ctx *ctx, int plain, cudaStream_t s)
     cudaEventDestroy(e1);
     if (rc) return rc;
     ctx->tuned[plain] = true;
+    memo.valid = true;
+    memo.sig = sig;
+    memo.cls.clear();
+    for (const auto &c : ctx->classes) memo.cls.push_back(c.shape[plain]);
+    memo.single = ctx->single.shape[plain];
+    memo.use_single = ctx->use_single[plain];
     return SMC_OK;
 }
 
@@ -601,6 +680,16 @@ int smc_create(smc_ctx **out, int device)
         delete ctx;
         return SMC_E_CUDA;
     }
+    const std::vector<double> tab = log_table_host();
+    if (tab.empty()) {
+        smc_destroy(ctx);
+        return SMC_E_UNSUPPORTED;
+    }
+    if (cudaMalloc(&ctx->d_logtab, SMC_LOGTAB_BYTES) != cudaSuccess ||
+        cudaMemcpy(ctx->d_logtab, tab.data(), SMC_LOGTAB_BYTES, cudaMemcpyHostToDevice) != cudaSuccess) {
+        smc_destroy(ctx);
+        return SMC_E_CUDA;
+    }
     *out = ctx;
     return SMC_OK;
 }
@@ -611,8 +700,19 @@ void smc_destroy(smc_ctx *ctx)
     cudaSetDevice(ctx->device);
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
     free_device(ctx);
+    dfree(ctx->d_logtab);
     if (ctx->stream) cudaStreamDestroy(ctx->stream);
     delete ctx;
+}
+
+int smc_log_fp64(smc_ctx *ctx, const double *u, uint64_t n, double *out, void *stream)
+{
+    if (!ctx) return SMC_E_INVALID_ARG;
+    if (!u || !out) return fail(ctx, SMC_E_INVALID_ARG, "null array");
+    CK(cudaSetDevice(ctx->device));
+    cudaStream_t s = stream ? (cudaStream_t)stream : ctx->stream;
+    if (smc_launch_log_batch(ctx->d_logtab, u, n, out, s)) return fail(ctx, SMC_E_CUDA, "log kernel launch failed");
+    return SMC_OK;
 }
 
 static int load_common(smc_ctx *ctx, int n_inst, const int32_t *S, const int32_t *R,
@@ -738,6 +838,7 @@ int smc_set_option(smc_ctx *ctx, int option, double value)
         ctx->autotune = value != 0.0;
         ctx->explicit_shape = false;
         ctx->tuned[0] = ctx->tuned[1] = false;
+        ctx->memo[0].valid = ctx->memo[1].valid = false;
         return SMC_OK;
     case SMC_OPT_WARPS_PER_BLOCK:
         if (!(value >= 1.0 && value <= 8.0)) return fail(ctx, SMC_E_INVALID_ARG, "warps per block 1..8");
@@ -766,6 +867,33 @@ int smc_set_option(smc_ctx *ctx, int option, double value)
     // an explicit shape replaces the tuned one (and the split partition)
     ctx->use_single[0] = ctx->use_single[1] = false;
     ctx->explicit_shape = true;
+    ctx->memo[0].valid = ctx->memo[1].valid = false;
+    return SMC_OK;
+}
+
+int smc_get_launch_shape(smc_ctx *ctx, int precision, int index, int *n_launches, int *warps_per_block,
+                         int *blocks_per_sm, int *refill, int *n_instances)
+{
+    if (!ctx) return SMC_E_INVALID_ARG;
+    if (precision != SMC_PLAIN_FP64 && precision != SMC_MIXED) return fail(ctx, SMC_E_INVALID_ARG, "bad precision");
+    if (ctx->dirty) return fail(ctx, SMC_E_STATE, "no prepared model: run an estimate or a simulation first");
+    const int plain = precision == SMC_PLAIN_FP64;
+    const std::vector<const SizeClass *> v = active_classes(ctx, plain);
+    if (n_launches) *n_launches = (int)v.size();
+    if (index < 0 || index >= (int)v.size()) return fail(ctx, SMC_E_INVALID_ARG, "launch index out of range");
+    const SizeClass &c = *v[index];
+    const Shape &sh = c.shape[plain];
+    int per_sm = sh.blocks_sm;
+    if (per_sm == 0) {  // as many as fit
+        Launch L;
+        int rc = plan_class(ctx, plain, c, sh, L);
+        if (rc) return rc;
+        per_sm = L.grid / ctx->n_sm;
+    }
+    if (warps_per_block) *warps_per_block = sh.warps;
+    if (blocks_per_sm) *blocks_per_sm = per_sm;
+    if (refill) *refill = sh.refill;
+    if (n_instances) *n_instances = (int)c.inst.size();
     return SMC_OK;
 }
 

@@ -4,6 +4,13 @@
 #pragma once
 #include <stdint.h>
 
+// Natural logarithm of the FP64 path (table-driven, Tang 1990): buckets
+// around F_j = 0.75 + j / 256, j = 0..192; table = G_j [193] (9-bit
+// approximations of 1/F_j) | ln(1/G_j) high [193] | ln(1/G_j) low [193] |
+// ln 2 high | ln 2 low | pad.  The high parts are multiples of 2^-42, so
+// k ln2_high + ln(1/G_j) high is exact for |k| <= 1075.
+#define SMC_LOGTAB_N 193
+#define SMC_LOGTAB_BYTES ((SMC_LOGTAB_N * 3 + 3) * 8)  // a multiple of 16 bytes
 #define SMC_MAX_UNITS 4   // temporal operators (monitor units) per formula
 #define SMC_MAX_ATOMS 6   // distinct atoms (truth tables are 64-bit)
 #define SMC_MAX_SPECIES 255
@@ -94,6 +101,8 @@ struct SsaParams {
     unsigned int *cursor;        // instance cursor (starts at 0)
     unsigned int *ticket;        // blocks finished (starts at 0)
     const MonProg *prog;
+    const double *logtab;        // FP64 path: ln table (SMC_LOGTAB_BYTES, layout above)
+    int32_t logtab_bytes;        // its shared-memory footprint (0: mixed path)
     uint32_t rk0[10], rk1[10];   // Philox round keys
     uint64_t budget;             // max reactions per trajectory
     uint32_t renorm_mask;        // mixed path: renormalise when (e & mask) == 0
@@ -151,6 +160,7 @@ int smc_ssa_max_blocks_per_sm(int plain, int block, int smem_bytes, int *out);
 int smc_ssa_set_smem_limit(int plain, int smem_bytes);
 int smc_launch_queue_init(const SsaParams &p, void *stream);
 int smc_launch_replay(const ReplayParams &p, void *stream);
+int smc_launch_log_batch(const double *tab, const double *u, uint64_t n, double *out, void *stream);
 int smc_launch_snapshot_features(uint64_t n_rows, uint64_t n_traj, int S, int R, int x_stride,
                                  const int32_t *x_snap, const float *x_scale, float t_feat,
                                  const float *lograte, float *feat, void *stream);

@@ -86,6 +86,51 @@ __device__ __forceinline__ double int_to_double(long long h)
     return __ll2double_rn(h);
 }
 
+// Natural logarithm for the FP64 path, table-driven (Tang, ACM TOMS 16,
+// 1990), with a reduction that is exact: u = 2^k m, m in [0.75, 1.5) taken
+// from the bit pattern; j = the multiple of 1/256 nearest m (j = 0..192);
+// G_j ~ 1/F_j, F_j = 0.75 + j/256, has 9 significant bits and is chosen so
+// that |m G_j - 1| < 2^-8 over the whole bucket, which makes
+// r = fma(m, G_j, -1) exact (m G_j has no bit below 2^-61).  Then
+//   ln u = k ln 2 + ln(1/G_j) + ln(1 + r),
+// ln(1 + r) = r + r^2 s(r), s the Taylor series of (ln(1+r) - r)/r^2 to r^5;
+// H = k ln2_hi + ln(1/G_j)_hi is exact (both multiples of 2^-42), H + r is
+// split into sum and error by Fast2Sum (|H| >= |r| or H = 0), and the small
+// terms join the error: at most about half an ulp plus 2^-6 ulp.  Fifteen
+// FP64 operations.  tab: G_j | ln(1/G_j) high | low | ln 2 high | low.
+__device__ __forceinline__ double exact_scaled(uint64_t m, int e0);
+__device__ __forceinline__ double log_table(double u, const double *tab)
+{
+    const unsigned long long b = (unsigned long long)__double_as_longlong(u);
+    const int e = (int)((b >> 52) & 0x7FF);
+    if (e == 0 || e == 0x7FF || (b >> 63)) return log(u);  // zero, subnormal, inf, nan, negative
+    const unsigned long long mant = b & 0x000FFFFFFFFFFFFFull;
+    int k = e - 1023, j;
+    unsigned long long mb;
+    if (mant >= (1ull << 51)) {  // m in [1.5, 2): use m / 2 in [0.75, 1)
+        k += 1;
+        j = (int)(((mant - (1ull << 51)) + (1ull << 44)) >> 45);
+        mb = (1022ull << 52) | mant;
+    } else {
+        j = 64 + (int)((mant + (1ull << 43)) >> 44);
+        mb = (1023ull << 52) | mant;
+    }
+    const double m = __longlong_as_double((long long)mb);
+    const double r = __fma_rn(m, tab[j], -1.0);  // exact
+    double s = __fma_rn(r, 1.0 / 7.0, -1.0 / 6.0);
+    s = __fma_rn(r, s, 1.0 / 5.0);
+    s = __fma_rn(r, s, -0.25);
+    s = __fma_rn(r, s, 1.0 / 3.0);
+    s = __fma_rn(r, s, -0.5);
+    const double kd = k > 0 ? exact_scaled((uint64_t)k, 0) : (k < 0 ? -exact_scaled((uint64_t)(-k), 0) : 0.0);
+    const double H = __fma_rn(kd, tab[3 * SMC_LOGTAB_N], tab[SMC_LOGTAB_N + j]);            // exact
+    const double lo = __fma_rn(kd, tab[3 * SMC_LOGTAB_N + 1], tab[2 * SMC_LOGTAB_N + j]);
+    const double S = __dadd_rn(H, r);
+    const double err = __dsub_rn(r, __dsub_rn(S, H));                                      // H + r = S + err
+    const double small = __fma_rn(__dmul_rn(r, r), s, lo);
+    return __dadd_rn(S, __dadd_rn(err, small));
+}
+
 // x > y for x, y >= 0 (including +inf): ordered like their bit patterns,
 // so the compare runs on the integer pipe.
 __device__ __forceinline__ bool dgt(double x, double y)
@@ -331,8 +376,8 @@ __device__ __forceinline__ typename Prec<PLAIN>::T propensity(uint32_t pw, const
 }
 
 template <bool PLAIN>
-__device__ __forceinline__ void run_instance(const SsaParams &p, const MonProg &P, const int m,
-                                             const uint32_t *blob, int32_t *xs, double *tc,
+__device__ __forceinline__ void run_instance(const SsaParams &p, const MonProg &P, const double *ltab,
+                                             const int m, const uint32_t *blob, int32_t *xs, double *tc,
                                              typename Prec<PLAIN>::T *as, const int lane)
 {
     typedef typename Prec<PLAIN>::T T;
@@ -468,7 +513,7 @@ __device__ __forceinline__ void run_instance(const SsaParams &p, const MonProg &
         T r;
         if (PLAIN) {
             const double ut = u01_52(w0, w1), us = u01_52(w2, w3);
-            tn = __dadd_rn(t, __ddiv_rn(-log(ut), (double)a0));
+            tn = __dadd_rn(t, __ddiv_rn(-log_table(ut, ltab), (double)a0));
             r = (T)__dmul_rn(us, (double)a0);
         } else {
             const float ut = u01_23(w0), us = u01_23(w2);
@@ -594,12 +639,18 @@ __global__ void __launch_bounds__(256, PLAIN ? 3 : 4) ssa_kernel(const SsaParams
         const uint4 *src = reinterpret_cast<const uint4 *>(p.prog);
         uint4 *dst = reinterpret_cast<uint4 *>(smem);
         for (int i = threadIdx.x; i < (int)(sizeof(MonProg) / 16); i += blockDim.x) dst[i] = src[i];
+        if (PLAIN) {  // the logarithm's table after the monitor program
+            const uint4 *ls = reinterpret_cast<const uint4 *>(p.logtab);
+            uint4 *ld = reinterpret_cast<uint4 *>(smem + sizeof(MonProg));
+            for (int i = threadIdx.x; i < p.logtab_bytes / 16; i += blockDim.x) ld[i] = ls[i];
+        }
     }
     __syncthreads();
     const MonProg &P = *reinterpret_cast<const MonProg *>(smem);
+    const double *ltab = reinterpret_cast<const double *>(smem + sizeof(MonProg));
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     // warp slice: table | x[(s_max + 1)][32] | tc[units][32] | a[r_max][32]
-    unsigned char *wb = smem + sizeof(MonProg) + (size_t)warp * p.warp_bytes;
+    unsigned char *wb = smem + sizeof(MonProg) + p.logtab_bytes + (size_t)warp * p.warp_bytes;
     uint32_t *blob = reinterpret_cast<uint32_t *>(wb);
     unsigned char *lanes = wb + (size_t)p.blob_words * 4;
     int32_t *xs = reinterpret_cast<int32_t *>(lanes) + lane;
@@ -621,7 +672,7 @@ __global__ void __launch_bounds__(256, PLAIN ? 3 : 4) ssa_kernel(const SsaParams
             __syncwarp();
             cur = m;
         }
-        run_instance<PLAIN>(p, P, m, blob, xs, tc, as, lane);
+        run_instance<PLAIN>(p, P, ltab, m, blob, xs, tc, as, lane);
         __syncwarp();
     }
 
@@ -731,6 +782,26 @@ int smc_launch_replay(const ReplayParams &rp, void *stream)
 {
     const int n = rp.n_paths > 0 ? rp.n_paths : 1;
     replay_kernel<<<(n + 127) / 128, 128, 0, (cudaStream_t)stream>>>(rp);
+    return to_code(cudaGetLastError());
+}
+
+// ---------------------------------------------------------------------------
+// The FP64 path's logarithm on an array (tests and callers that want the
+// same function).
+__global__ void log_batch_kernel(const double *tab_g, const double *u, uint64_t n, double *out)
+{
+    __shared__ double tab[SMC_LOGTAB_BYTES / 8];
+    for (int i = threadIdx.x; i < SMC_LOGTAB_BYTES / 8; i += blockDim.x) tab[i] = tab_g[i];
+    __syncthreads();
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x)
+        out[i] = log_table(u[i], tab);
+}
+
+int smc_launch_log_batch(const double *tab, const double *u, uint64_t n, double *out, void *stream)
+{
+    if (n == 0) return 0;
+    const unsigned blocks = (unsigned)std::min<uint64_t>(4096, (n + 255) / 256);
+    log_batch_kernel<<<blocks, 256, 0, (cudaStream_t)stream>>>(tab, u, n, out);
     return to_code(cudaGetLastError());
 }
 

@@ -105,3 +105,28 @@ def test_autotuned_and_fixed_shapes_give_identical_counts(smc, batch):
             res = ctx.estimate(0.95, 0.02, seed=5, precision='mixed', sampling='iterative')
             results.append([(r['yes'], r['n'], r['events'], r['launched']) for r in res])
     assert results[0] == results[1]
+
+
+def test_launch_shapes_cover_instances_and_survive_reload(smc, batch):
+    sub = _sub(batch, list(range(0, 4096, 16)))
+    with smc.Context(0) as ctx:
+        ctx.load_batch(sub)
+        ctx.load_property(sub.properties)
+        first = ctx.estimate(0.95, 0.05, seed=7, precision='mixed', sampling='fixed', fixed_n=64)
+        shapes = ctx.launch_shapes('mixed')
+        assert sum(s['n_instances'] for s in shapes) == len(sub.models)
+        for s in shapes:
+            assert s['warps_per_block'] in (2, 4, 8) and s['refill'] in (1, 8) and s['blocks_per_sm'] >= 1
+        # same structure loaded again: the tuned shapes are kept (no new trials)
+        ctx.load_batch(sub)
+        ctx.load_property(sub.properties)
+        again = ctx.estimate(0.95, 0.05, seed=7, precision='mixed', sampling='fixed', fixed_n=64)
+        assert ctx.launch_shapes('mixed') == shapes
+        assert [(r['yes'], r['events']) for r in again] == [(r['yes'], r['events']) for r in first]
+        # an explicit shape replaces the tuned one
+        ctx.set_option('warps_per_block', 2)
+        ctx.set_option('refill', 4)
+        ctx.estimate(0.95, 0.05, seed=7, precision='mixed', sampling='fixed', fixed_n=64)
+        fixed = ctx.launch_shapes('mixed')
+        assert all(s['warps_per_block'] == 2 and s['refill'] == 4 for s in fixed)
+        assert sum(s['n_instances'] for s in fixed) == len(sub.models)
