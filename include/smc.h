@@ -88,6 +88,9 @@ extern "C" {
 #define SMC_OPT_BLOCKS_PER_SM 4   /* 0 = as many as fit (default 0) */
 #define SMC_OPT_REFILL 5          /* refill a warp when >= this many lanes idle (default 1) */
 #define SMC_OPT_RECORD 6          /* 1 = keep per-trajectory verdicts of FIXED_N estimates */
+#define SMC_OPT_JIT 7             /* 1 = model-specialized kernels when every instance shares one
+                                     structure with S, R <= 8 (default 1; compiled at run time
+                                     with NVRTC, same results as the generic kernels) */
 
 /* A node of the formula in postfix order: operands precede their operator. */
 typedef struct {
@@ -185,12 +188,14 @@ int smc_set_option(smc_ctx *ctx, int option, double value);
  * The instances are served by *n_launches launches (one per size class, or
  * one over all instances, as the autotuner chose); launch `index` uses
  * *warps_per_block warps per block, *blocks_per_sm resident blocks per SM,
- * refill threshold *refill, and serves *n_instances instances.  Any output
- * pointer may be null.  Valid after an estimate or simulation of the loaded
- * model.  Errors: SMC_E_STATE before that, SMC_E_INVALID_ARG for a bad
- * precision or index (*n_launches is still written). */
+ * refill threshold *refill, serves *n_instances instances, and runs the
+ * model-specialized kernel (*specialized = 1, see SMC_OPT_JIT) or the
+ * generic one (0).  Any output pointer may be null.  Valid after an estimate
+ * or simulation of the loaded model.  Errors: SMC_E_STATE before that,
+ * SMC_E_INVALID_ARG for a bad precision or index (*n_launches is still
+ * written). */
 int smc_get_launch_shape(smc_ctx *ctx, int precision, int index, int *n_launches, int *warps_per_block,
-                         int *blocks_per_sm, int *refill, int *n_instances);
+                         int *blocks_per_sm, int *refill, int *n_instances, int *specialized);
 
 /* Estimates P(phi) for every instance (Sec. 3.3).
  *  confidence = 1 - alpha (0 < confidence < 1);

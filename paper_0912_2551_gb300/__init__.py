@@ -168,14 +168,15 @@ class Context:
     def launch_shapes(self, precision: str = 'mixed'):
         """The launches serving the loaded model (after an estimate or a
         simulation): list of dicts warps_per_block, blocks_per_sm, refill,
-        n_instances."""
+        n_instances, specialized."""
         out, i, n = [], 0, ctypes.c_int32(1)
         while i < n.value:
-            w, b, r, m = (ctypes.c_int32() for _ in range(4))
+            w, b, r, m, sp = (ctypes.c_int32() for _ in range(5))
             self._check(N.smc_get_launch_shape(self.h, PRECISION[precision], i, ctypes.byref(n), ctypes.byref(w),
-                                               ctypes.byref(b), ctypes.byref(r), ctypes.byref(m)),
+                                               ctypes.byref(b), ctypes.byref(r), ctypes.byref(m), ctypes.byref(sp)),
                         'smc_get_launch_shape')
-            out.append(dict(warps_per_block=w.value, blocks_per_sm=b.value, refill=r.value, n_instances=m.value))
+            out.append(dict(warps_per_block=w.value, blocks_per_sm=b.value, refill=r.value, n_instances=m.value,
+                            specialized=bool(sp.value)))
             i += 1
         return out
 

@@ -28,7 +28,7 @@ SMC_CONSERVATIVE = 2 << 4
 NODE = dict(true=0, false=1, atom=2, **{'not': 3, 'and': 4, 'or': 5, 'implies': 6}, U=7, F=8, G=9)
 OP = {'<': 0, '<=': 1, '>=': 2, '>': 3, '==': 4, '!=': 5}
 OPT = dict(event_budget=0, renorm_log2=1, autotune=2, warps_per_block=3, blocks_per_sm=4,
-           refill=5, record=6)
+           refill=5, record=6, jit=7)
 
 c_i32p = ctypes.POINTER(ctypes.c_int32)
 c_u8p = ctypes.POINTER(ctypes.c_uint8)
@@ -89,7 +89,7 @@ SIGNATURES = {
                                          ctypes.c_double]),
     'smc_set_option': (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_double]),
     'smc_get_launch_shape': (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, c_i32p, c_i32p, c_i32p,
-                                            c_i32p, c_i32p]),
+                                            c_i32p, c_i32p, c_i32p]),
     'smc_estimate': (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_double, ctypes.c_uint64,
                                     ctypes.c_int, ctypes.c_uint64, ctypes.POINTER(smc_result)]),
     'smc_get_verdicts': (ctypes.c_int, [ctypes.c_void_p, c_u8p, ctypes.c_uint64]),

@@ -11,8 +11,13 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, 'csrc')
 BUILD = os.path.join(HERE, '_build')
 LIB = os.path.join(BUILD, 'libsmc.so')
-SOURCES = ['smc_kernels.cu', 'smc_api.cu', 'smc_compile.cpp', 'smc_mlp.cu']
-HEADERS = ['smc_internal.h', 'smc_compile.h', 'smc_mlp.h']
+SOURCES = ['smc_kernels.cu', 'smc_api.cu', 'smc_compile.cpp', 'smc_mlp.cu', 'smc_jit.cpp']
+HEADERS = ['smc_internal.h', 'smc_compile.h', 'smc_mlp.h', 'smc_device.cuh', 'smc_jit.h',
+           'smc_jit_kernel.cuh', 'nvrtc_stdint.h']
+# sources of the run-time compiled kernels, embedded into the library as
+# (include name, file) pairs
+JIT_EMBED = [('stdint.h', 'nvrtc_stdint.h'), ('smc_internal.h', 'smc_internal.h'),
+             ('smc_device.cuh', 'smc_device.cuh'), ('smc_jit_kernel.cuh', 'smc_jit_kernel.cuh')]
 ARCH = ['-gencode', 'arch=compute_103a,code=sm_103a']
 
 
@@ -38,14 +43,38 @@ def up_to_date() -> bool:
     return all(os.path.getmtime(f) <= t for f in srcs + hdrs + [__file__])
 
 
+def _write_embedded_sources():
+    """_build/smc_jit_sources.inc: the run-time compiled kernel's headers as
+    C++ raw string literals."""
+    names, bodies = [], []
+    for name, fname in JIT_EMBED:
+        with open(os.path.join(CSRC, fname)) as f:
+            text = f.read()
+        if ')SMCJIT"' in text:
+            raise RuntimeError(f'{fname} contains the raw-string delimiter')
+        names.append(name)
+        bodies.append(text)
+    out = ['// generated by build.py from csrc/: do not edit']
+    out.append('static const char *const kJitHeaderNames[] = {' + ', '.join(f'"{n}"' for n in names) + '};')
+    out.append('static const char *const kJitHeaderSources[] = {')
+    out += [f'R"SMCJIT({b})SMCJIT",' for b in bodies]
+    out.append('};')
+    path = os.path.join(BUILD, 'smc_jit_sources.inc')
+    text = '\n'.join(out) + '\n'
+    if not os.path.exists(path) or open(path).read() != text:
+        with open(path, 'w') as f:
+            f.write(text)
+
+
 def build(force: bool = False, verbose: bool = False) -> str:
     if not force and up_to_date():
         return LIB
     os.makedirs(BUILD, exist_ok=True)
+    _write_embedded_sources()
     nvcc = _nvcc()
     srcs, _ = _inputs()
     common = ARCH + ['-O3', '-lineinfo', '-std=c++17', '-Xcompiler', '-fPIC', '-Xcompiler', '-O2',
-                     '-I', CSRC, '-I', os.path.join(os.path.dirname(HERE), 'include')]
+                     '-I', CSRC, '-I', BUILD, '-I', os.path.join(os.path.dirname(HERE), 'include')]
     if verbose:
         common += ['-Xptxas', '-v']
 

@@ -15,6 +15,7 @@
 #include "../../include/smc.h"
 #include "smc_compile.h"
 #include "smc_internal.h"
+#include "smc_jit.h"
 
 namespace {
 
@@ -105,6 +106,11 @@ struct smc_ctx {
     int blocks_sm = 0;
     int refill = 1;
     int record = 0;
+    int jit = 1;                  // model-specialized kernels when eligible
+    // specialized kernels of the loaded structure (null: the generic ones run)
+    smc::JitKernels jit_k;
+    bool jit_ready = false;
+    std::string jit_why;          // why they are not in use
 };
 
 namespace {
@@ -312,6 +318,64 @@ int validate_params(smc_ctx *ctx, int S, int R, const double *rates, const int32
     return SMC_OK;
 }
 
+// Model-specialized kernels: when every instance shares one structure
+// (species, reactions, reactants, stoichiometry, monitored atoms and their
+// thresholds), the structure is compiled into the kernel; rates and x0 stay
+// data.  Otherwise (or without NVRTC) the generic kernels run.
+void try_specialize(smc_ctx *ctx)
+{
+    ctx->jit_ready = false;
+    ctx->jit_why.clear();
+    if (!ctx->jit) { ctx->jit_why = "disabled by option"; return; }
+    const int n = ctx->n_inst, S = ctx->S[0], R = ctx->R[0], nu = (int)ctx->used_atoms.size();
+    std::vector<int32_t> coef0((size_t)nu * S);
+    std::vector<int64_t> lo0(nu), hi0(nu);
+    std::vector<uint8_t> neg0(nu);
+    for (int m = 0; m < n; ++m) {
+        if (ctx->S[m] != S || ctx->R[m] != R) { ctx->jit_why = "instances differ in structure"; return; }
+        if (m > 0 && (std::memcmp(ctx->reactants.data() + ctx->reac_off[m], ctx->reactants.data() + ctx->reac_off[0],
+                                  sizeof(int32_t) * 2 * R) ||
+                      std::memcmp(ctx->stoich.data() + ctx->st_off[m], ctx->stoich.data() + ctx->st_off[0],
+                                  sizeof(int32_t) * (size_t)R * S))) {
+            ctx->jit_why = "instances differ in structure";
+            return;
+        }
+        for (int b = 0; b < nu; ++b) {
+            const int a = ctx->used_atoms[b];
+            const int32_t *c = ctx->atom_coef.data() + ctx->coef_off[m] + (size_t)a * S;
+            const double bnd = ctx->per_instance_bound ? ctx->atom_bound[(size_t)m * ctx->n_atoms + a] : ctx->atom_bound[a];
+            int64_t lo, hi;
+            bool neg;
+            smc::atom_threshold(ctx->atom_op[a], bnd, lo, hi, neg);
+            if (m == 0) {
+                std::memcpy(&coef0[(size_t)b * S], c, sizeof(int32_t) * S);
+                lo0[b] = lo;
+                hi0[b] = hi;
+                neg0[b] = neg;
+            } else if (std::memcmp(&coef0[(size_t)b * S], c, sizeof(int32_t) * S) || lo != lo0[b] || hi != hi0[b] ||
+                       (uint8_t)neg != neg0[b]) {
+                ctx->jit_why = "instances differ in their atoms";
+                return;
+            }
+        }
+    }
+    smc::JitModel M;
+    M.S = S;
+    M.R = R;
+    M.reactants = ctx->reactants.data() + ctx->reac_off[0];
+    M.stoich = ctx->stoich.data() + ctx->st_off[0];
+    M.n_atoms = nu;
+    M.coef = coef0.data();
+    M.lo = lo0.data();
+    M.hi = hi0.data();
+    M.neg = neg0.data();
+    const std::string header = smc::jit_model_header(M, ctx->jit_why);
+    if (header.empty()) return;
+    std::string err;
+    if (smc::jit_compile(header, ctx->jit_k, err)) { ctx->jit_why = err; return; }
+    ctx->jit_ready = true;
+}
+
 // Builds the instance tables, size classes and work buffers on the device.
 int prepare(smc_ctx *ctx)
 {
@@ -397,6 +461,7 @@ int prepare(smc_ctx *ctx)
     CK(cudaMallocHost(&ctx->h_range, (size_t)n * 2 * 8));
     CK(cudaMallocHost(&ctx->h_counts, (size_t)n * 4 * 8));
     CK(cudaMallocHost(&ctx->h_wilson, (size_t)n * 3 * 8));
+    try_specialize(ctx);
     ctx->dirty = false;
     return SMC_OK;
 }
@@ -420,6 +485,7 @@ int warp_bytes_of(const SizeClass &c, int plain, int tc_bytes)
 // One planned launch of the SSA kernel for a set of instances.
 struct Launch {
     const SizeClass *c = nullptr;
+    void *kernel = nullptr;  // model-specialized kernel, or null for the generic one
     int grid = 0, block = 0, smem = 0, warp_bytes = 0, tc_bytes = 0, refill = 1;
 };
 
@@ -441,16 +507,21 @@ int plan_class(smc_ctx *ctx, int plain, const SizeClass &c, const Shape &sh, Lau
 {
     L.c = &c;
     L.tc_bytes = tc_bytes_of(ctx->prog);
-    L.warp_bytes = warp_bytes_of(c, plain, L.tc_bytes);
+    // the specialized kernel keeps counts and propensities in registers: its
+    // warp slice holds only the nested operators' candidate clocks
+    L.kernel = ctx->jit_ready ? (plain ? ctx->jit_k.plain : ctx->jit_k.mixed) : nullptr;
+    L.warp_bytes = L.kernel ? L.tc_bytes : warp_bytes_of(c, plain, L.tc_bytes);
     L.block = 32 * sh.warps;
     L.smem = (int)sizeof(MonProg) + (plain ? SMC_LOGTAB_BYTES : 0) + sh.warps * L.warp_bytes;
     L.refill = sh.refill;
     if ((size_t)L.smem > ctx->smem_optin)
         return fail(ctx, SMC_E_UNSUPPORTED, "model tables do not fit in shared memory");
-    if (smc_ssa_set_smem_limit(plain, L.smem)) return fail(ctx, SMC_E_CUDA, "cudaFuncSetAttribute failed");
+    const int set_rc = L.kernel ? smc_jit_set_smem_limit(L.kernel, L.smem) : smc_ssa_set_smem_limit(plain, L.smem);
+    if (set_rc) return fail(ctx, SMC_E_CUDA, "cudaFuncSetAttribute failed");
     int per_sm = 0;
-    if (smc_ssa_max_blocks_per_sm(plain, L.block, L.smem, &per_sm) || per_sm < 1)
-        return fail(ctx, SMC_E_UNSUPPORTED, "no block of this shape fits on an SM");
+    const int occ_rc = L.kernel ? smc_jit_max_blocks_per_sm(L.kernel, L.block, L.smem, &per_sm)
+                                : smc_ssa_max_blocks_per_sm(plain, L.block, L.smem, &per_sm);
+    if (occ_rc || per_sm < 1) return fail(ctx, SMC_E_UNSUPPORTED, "no block of this shape fits on an SM");
     if (sh.blocks_sm > 0) per_sm = std::min(per_sm, sh.blocks_sm);
     L.grid = ctx->n_sm * per_sm;
     return SMC_OK;
@@ -473,8 +544,9 @@ int issue_class(smc_ctx *ctx, int plain, const SsaParams &common, const Launch &
     p.logtab_bytes = plain ? SMC_LOGTAB_BYTES : 0;
     if (smc_launch_queue_init(p, s))
         return fail(ctx, SMC_E_CUDA, std::string("queue init: ") + cudaGetErrorString(cudaGetLastError()));
-    if (smc_launch_ssa(plain, p, L.grid, L.block, L.smem, s))
-        return fail(ctx, SMC_E_CUDA, std::string("ssa launch: ") + cudaGetErrorString(cudaGetLastError()));
+    const int lrc = L.kernel ? smc_jit_launch(L.kernel, p, L.grid, L.block, L.smem, s)
+                             : smc_launch_ssa(plain, p, L.grid, L.block, L.smem, s);
+    if (lrc) return fail(ctx, SMC_E_CUDA, std::string("ssa launch: ") + cudaGetErrorString(cudaGetLastError()));
     return SMC_OK;
 }
 
@@ -522,7 +594,7 @@ void fill_common(smc_ctx *ctx, SsaParams &p, uint64_t seed, double z, const smc_
 // monitor's per-warp clock area.
 std::vector<int64_t> tune_signature(const smc_ctx *ctx)
 {
-    std::vector<int64_t> sig{ctx->n_inst, tc_bytes_of(ctx->prog), (int64_t)ctx->classes.size()};
+    std::vector<int64_t> sig{ctx->n_inst, tc_bytes_of(ctx->prog), (int64_t)ctx->classes.size(), ctx->jit_ready};
     for (const auto &c : ctx->classes) {
         sig.push_back((int64_t)c.inst.size());
         sig.push_back(c.s_max);
@@ -853,6 +925,11 @@ int smc_set_option(smc_ctx *ctx, int option, double value)
         ctx->refill = (int)value;
         break;
     case SMC_OPT_RECORD: ctx->record = value != 0.0; return SMC_OK;
+    case SMC_OPT_JIT:
+        ctx->jit = value != 0.0;
+        ctx->dirty = true;  // re-prepare: kernels and tuned shapes change
+        ctx->memo[0].valid = ctx->memo[1].valid = false;
+        return SMC_OK;
     default: return fail(ctx, SMC_E_INVALID_ARG, "unknown option");
     }
     std::vector<SizeClass *> all_classes;
@@ -872,7 +949,7 @@ int smc_set_option(smc_ctx *ctx, int option, double value)
 }
 
 int smc_get_launch_shape(smc_ctx *ctx, int precision, int index, int *n_launches, int *warps_per_block,
-                         int *blocks_per_sm, int *refill, int *n_instances)
+                         int *blocks_per_sm, int *refill, int *n_instances, int *specialized)
 {
     if (!ctx) return SMC_E_INVALID_ARG;
     if (precision != SMC_PLAIN_FP64 && precision != SMC_MIXED) return fail(ctx, SMC_E_INVALID_ARG, "bad precision");
@@ -894,6 +971,7 @@ int smc_get_launch_shape(smc_ctx *ctx, int precision, int index, int *n_launches
     if (blocks_per_sm) *blocks_per_sm = per_sm;
     if (refill) *refill = sh.refill;
     if (n_instances) *n_instances = (int)c.inst.size();
+    if (specialized) *specialized = ctx->jit_ready ? 1 : 0;
     return SMC_OK;
 }
 

@@ -1,0 +1,399 @@
+// smc_device.cuh -- device code shared by the generic SSA kernels
+// (smc_kernels.cu) and the model-specialized ones compiled at run time
+// (smc_jit_kernel.cuh): Philox4x32-10, the uniform maps, the FP64 path's
+// logarithm, the compiled BLTLc monitor, instance acquisition, the Wilson
+// interval (Eq. 4) and the launch prologue / epilogue.
+#pragma once
+#include <stdint.h>
+
+#include "smc_internal.h"
+
+#ifndef FULL_MASK
+#define FULL_MASK 0xffffffffu
+#endif
+
+namespace {
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two
+// 32x32->64-bit multiplies with the words permuted and the high halves xored
+// with the counter and the round key.  The round keys (key plus multiples of
+// the Weyl increments) are uniform over the launch, so they come precomputed
+// in the kernel parameters.
+__device__ __forceinline__ void philox10(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                         const uint32_t *rk0, const uint32_t *rk1,
+                                         uint32_t &w0, uint32_t &w1, uint32_t &w2, uint32_t &w3)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint64_t p0 = (uint64_t)0xD2511F53u * c0;
+        const uint64_t p1 = (uint64_t)0xCD9E8D57u * c2;
+        const uint32_t n0 = (uint32_t)(p1 >> 32) ^ c1 ^ rk0[r];
+        const uint32_t n2 = (uint32_t)(p0 >> 32) ^ c3 ^ rk1[r];
+        c1 = (uint32_t)p1;
+        c3 = (uint32_t)p0;
+        c0 = n0;
+        c2 = n2;
+    }
+    w0 = c0; w1 = c1; w2 = c2; w3 = c3;
+}
+
+// The double holding m * 2^e0 for an integer 0 < m < 2^53, assembled on the
+// integer pipe (exact: no rounding is needed below 2^53).
+__device__ __forceinline__ double exact_scaled(uint64_t m, int e0)
+{
+    const int p = 63 - __clzll((long long)m);  // position of the leading one
+    const uint64_t mant = (m << (52 - p)) & 0x000FFFFFFFFFFFFFull;
+    return __longlong_as_double((long long)(((uint64_t)(1023 + p + e0) << 52) | mant));
+}
+
+// (0,1) from 52 bits: ((hi:lo) >> 12 + 1/2) 2^-52 = (2v + 1) 2^-53, exact, in
+// [2^-53, 1 - 2^-53].
+__device__ __forceinline__ double u01_52(uint32_t hi, uint32_t lo)
+{
+    const uint64_t v = ((((uint64_t)hi) << 32) | (uint64_t)lo) >> 12;
+    return exact_scaled((v << 1) | 1ull, -53);
+}
+
+// A positive normal float as a double, built on the integer pipe (exact:
+// exponent rebiased by 1023 - 127, mantissa shifted into place); anything
+// else goes through the conversion instruction.
+__device__ __forceinline__ double f32_to_f64(float f)
+{
+    const uint32_t b = __float_as_uint(f);
+    if (__builtin_expect(b - 0x00800000u >= 0x7F000000u, 0)) return (double)f;
+    return __hiloint2double((int)((b >> 3) + (896u << 20)), (int)(b << 29));
+}
+
+// (0,1) in FP32 from 23 bits: (w >> 9 + 1/2) 2^-23, exact, in [2^-24, 1 - 2^-24].
+__device__ __forceinline__ float u01_23(uint32_t w)
+{
+    return __fmaf_rn((float)(w >> 9), 0x1p-23f, 0x1p-24f);
+}
+
+// An integer h (exact for 0 <= h < 2^53, rounded once otherwise) as a double.
+__device__ __forceinline__ double int_to_double(long long h)
+{
+    if ((unsigned long long)h < (1ull << 53)) return h ? exact_scaled((uint64_t)h, 0) : 0.0;
+    return __ll2double_rn(h);
+}
+
+// Natural logarithm for the FP64 path, table-driven (Tang, ACM TOMS 16,
+// 1990), with a reduction that is exact: u = 2^k m, m in [0.75, 1.5) taken
+// from the bit pattern; j = the multiple of 1/256 nearest m (j = 0..192);
+// G_j ~ 1/F_j, F_j = 0.75 + j/256, has 9 significant bits and is chosen so
+// that |m G_j - 1| < 2^-8 over the whole bucket, which makes
+// r = fma(m, G_j, -1) exact (m G_j has no bit below 2^-61).  Then
+//   ln u = k ln 2 + ln(1/G_j) + ln(1 + r),
+// ln(1 + r) = r + r^2 s(r), s the Taylor series of (ln(1+r) - r)/r^2 to r^5;
+// H = k ln2_hi + ln(1/G_j)_hi is exact (both multiples of 2^-42), H + r is
+// split into sum and error by Fast2Sum (|H| >= |r| or H = 0), and the small
+// terms join the error: at most about half an ulp plus 2^-6 ulp.  Fifteen
+// FP64 operations.  tab: G_j | ln(1/G_j) high | low | ln 2 high | low.
+__device__ __forceinline__ double exact_scaled(uint64_t m, int e0);
+__device__ __forceinline__ double log_table(double u, const double *tab)
+{
+    const unsigned long long b = (unsigned long long)__double_as_longlong(u);
+    const int e = (int)((b >> 52) & 0x7FF);
+    if (e == 0 || e == 0x7FF || (b >> 63)) return log(u);  // zero, subnormal, inf, nan, negative
+    const unsigned long long mant = b & 0x000FFFFFFFFFFFFFull;
+    int k = e - 1023, j;
+    unsigned long long mb;
+    if (mant >= (1ull << 51)) {  // m in [1.5, 2): use m / 2 in [0.75, 1)
+        k += 1;
+        j = (int)(((mant - (1ull << 51)) + (1ull << 44)) >> 45);
+        mb = (1022ull << 52) | mant;
+    } else {
+        j = 64 + (int)((mant + (1ull << 43)) >> 44);
+        mb = (1023ull << 52) | mant;
+    }
+    const double m = __longlong_as_double((long long)mb);
+    const double r = __fma_rn(m, tab[j], -1.0);  // exact
+    double s = __fma_rn(r, 1.0 / 7.0, -1.0 / 6.0);
+    s = __fma_rn(r, s, 1.0 / 5.0);
+    s = __fma_rn(r, s, -0.25);
+    s = __fma_rn(r, s, 1.0 / 3.0);
+    s = __fma_rn(r, s, -0.5);
+    const double kd = k > 0 ? exact_scaled((uint64_t)k, 0) : (k < 0 ? -exact_scaled((uint64_t)(-k), 0) : 0.0);
+    const double H = __fma_rn(kd, tab[3 * SMC_LOGTAB_N], tab[SMC_LOGTAB_N + j]);            // exact
+    const double lo = __fma_rn(kd, tab[3 * SMC_LOGTAB_N + 1], tab[2 * SMC_LOGTAB_N + j]);
+    const double S = __dadd_rn(H, r);
+    const double err = __dsub_rn(r, __dsub_rn(S, H));                                      // H + r = S + err
+    const double small = __fma_rn(__dmul_rn(r, r), s, lo);
+    return __dadd_rn(S, __dadd_rn(err, small));
+}
+
+// x > y for x, y >= 0 (including +inf): ordered like their bit patterns,
+// so the compare runs on the integer pipe.
+__device__ __forceinline__ bool dgt(double x, double y)
+{
+    return __double_as_longlong(x) > __double_as_longlong(y);
+}
+
+// ---------------------------------------------------------------------------
+// Monitor (one per lane).  Unit semantics, in the knowledge order of the
+// event loop (entry times never decrease; after the draw of t' every later
+// state has entry time >= t'):
+//   witness at a state entered at t:  alive and a <= t <= b and P (and, for
+//     nest 1, Q now or later within [t, t + d]; for nest 2, Q at every state
+//     entered within [t, t + d]);
+//   alive: L held at every earlier state;
+//   nest 1 keeps the latest candidate (its window ends last), nest 2 the
+//   earliest since the last state violating Q (its window closes first).
+// The candidates' entry times live in the lane's shared-memory column tc[u * 32].
+struct MonLane {
+    long long hb;    // bits of min b over alive undecided units (-1: none)
+    uint32_t ab;     // atom bit vector of the current state
+    uint32_t alive, pend, done;
+    int32_t vidx;    // sum_u value_u 3^u
+};
+
+// Register copies of the monitor fields the event loop reads every event;
+// the MonLane itself is touched only around the (rare) monitor calls.
+struct MonHot {
+    long long hb;
+    uint32_t pend, ab;
+    __device__ __forceinline__ void load(const MonLane &ml)
+    {
+        hb = ml.hb;
+        pend = ml.pend;
+        ab = ml.ab;
+    }
+};
+
+__device__ __constant__ int kPow3[SMC_MAX_UNITS] = {1, 3, 9, 27};
+
+__device__ __forceinline__ void mon_horizon(MonLane &ml, const MonProg &P)
+{
+    long long h = -1;
+#pragma unroll
+    for (int u = 0; u < SMC_MAX_UNITS; ++u) {
+        if (u < P.n_units && !((ml.done >> u) & 1u) && ((ml.alive >> u) & 1u)) {
+            const long long b = __double_as_longlong(P.u[u].b);
+            h = (h < 0 || b < h) ? b : h;
+        }
+    }
+    ml.hb = h;
+}
+
+__device__ __forceinline__ void mon_set(MonLane &ml, int u, int val)
+{
+    ml.done |= 1u << u;
+    ml.vidx += val * kPow3[u];
+}
+
+// The state just entered at time t (atom bits already in ml.ab).
+__device__ __noinline__ int mon_state(MonLane &ml, const MonProg &P, double t, double *tc)
+{
+    bool changed = false;
+#pragma unroll
+    for (int u = 0; u < SMC_MAX_UNITS; ++u) {
+        if (u >= P.n_units || ((ml.done >> u) & 1u)) continue;
+        const MonUnit &U = P.u[u];
+        const uint32_t ab = ml.ab;
+        const bool l = (U.L >> ab) & 1ull, p = (U.P >> ab) & 1ull, q = (U.Q >> ab) & 1ull;
+        bool al = (ml.alive >> u) & 1u, pe = (ml.pend >> u) & 1u;
+        const bool inwin = al && !dgt(U.a, t) && !dgt(t, U.b);
+        int val = 0;
+        if (U.nest == 0) {
+            if (inwin && p) val = 2;
+        } else if (U.nest == 1) {
+            if (pe && q && !dgt(__dsub_rn(t, tc[u * 32]), U.d)) {
+                val = 2;
+            } else if (inwin && p) {
+                if (q) val = 2;
+                else { tc[u * 32] = t; pe = true; }
+            }
+        } else {
+            if (pe && !q) pe = false;
+            if (inwin && p && q && !pe) { tc[u * 32] = t; pe = true; }
+        }
+        if (!val) {
+            const bool al2 = al && l;
+            changed |= (al2 != al);
+            al = al2;
+            if (!(al && !dgt(t, U.b)) && !pe) val = 1;
+        }
+        ml.alive = (ml.alive & ~(1u << u)) | ((uint32_t)al << u);
+        ml.pend = (ml.pend & ~(1u << u)) | ((uint32_t)pe << u);
+        if (val) { mon_set(ml, u, val); changed = true; }
+    }
+    if (changed) mon_horizon(ml, P);
+    return P.table[ml.vidx];
+}
+
+// The next state's entry time tn has been drawn (not yet applied).
+__device__ __noinline__ int mon_draw(MonLane &ml, const MonProg &P, double tn, const double *tc)
+{
+    bool changed = false;
+#pragma unroll
+    for (int u = 0; u < SMC_MAX_UNITS; ++u) {
+        if (u >= P.n_units || ((ml.done >> u) & 1u)) continue;
+        const MonUnit &U = P.u[u];
+        const bool al = (ml.alive >> u) & 1u;
+        bool pe = (ml.pend >> u) & 1u;
+        int val = 0;
+        if (pe && dgt(__dsub_rn(tn, tc[u * 32]), U.d)) {
+            if (U.nest == 2) val = 2;
+            else pe = false;
+        }
+        if (!val && !(al && !dgt(tn, U.b)) && !pe) val = 1;
+        ml.pend = (ml.pend & ~(1u << u)) | ((uint32_t)pe << u);
+        if (val) { mon_set(ml, u, val); changed = true; }
+    }
+    if (changed) mon_horizon(ml, P);
+    return P.table[ml.vidx];
+}
+
+// The path has no further state (absorbing state).
+__device__ __noinline__ int mon_close(MonLane &ml, const MonProg &P)
+{
+#pragma unroll
+    for (int u = 0; u < SMC_MAX_UNITS; ++u) {
+        if (u >= P.n_units || ((ml.done >> u) & 1u)) continue;
+        const bool g_pending = P.u[u].nest == 2 && ((ml.pend >> u) & 1u);
+        mon_set(ml, u, g_pending ? 2 : 1);
+    }
+    return P.table[ml.vidx];
+}
+
+__device__ __forceinline__ void mon_start(MonLane &ml, const MonProg &P)
+{
+    ml.alive = (1u << P.n_units) - 1u;
+    ml.pend = 0;
+    ml.done = 0;
+    ml.vidx = 0;
+    mon_horizon(ml, P);
+}
+
+// Atom a at the lane's current state: L = sum of coef * x over the atom's
+// terms (exact int64), bit = (lo <= L <= hi) xor neg, placed at bit a.
+__device__ __forceinline__ uint32_t atom_bit(const uint32_t *atoms, const uint32_t *tptr,
+                                             const uint32_t *terms, const int32_t *xs, int a)
+{
+    const uint32_t *A = atoms + 6 * a;
+    const uint32_t w1 = A[0];
+    long long L;
+    if (w1 != 0xFFFFFFFFu) {  // single term
+        L = (long long)xs[(w1 & 255u) * 32] * (long long)(((int32_t)w1) >> 8);
+    } else {
+        L = 0;
+        for (uint32_t q = tptr[a], qe = tptr[a + 1]; q < qe; ++q) {
+            const uint32_t w = terms[q];
+            L += (long long)xs[(w & 255u) * 32] * (long long)(((int32_t)w) >> 8);
+        }
+    }
+    const long long lo = *reinterpret_cast<const long long *>(A + 2);
+    const long long hi = *reinterpret_cast<const long long *>(A + 4);
+    return (((uint32_t)((L >= lo) & (L <= hi))) ^ A[1]) << a;
+}
+
+// ---------------------------------------------------------------------------
+// Eq. 4 in FP64, same operation order as the written-out formula:
+// (p + z^2/(2n) -+ z sqrt(p(1-p)/n + z^2/(4n^2))) / (1 + z^2/n).
+__device__ void wilson_eq4(unsigned long long yes, unsigned long long n, double z, double *out)
+{
+    if (n == 0) { out[0] = nan(""); out[1] = 0.0; out[2] = 1.0; return; }
+    const double dn = (double)n;
+    const double p = __ddiv_rn((double)yes, dn);
+    const double z2 = __dmul_rn(z, z);
+    const double centre = __dadd_rn(p, __ddiv_rn(z2, __dmul_rn(2.0, dn)));
+    const double var = __dadd_rn(__ddiv_rn(__dmul_rn(p, __dsub_rn(1.0, p)), dn),
+                                 __ddiv_rn(z2, __dmul_rn(__dmul_rn(4.0, dn), dn)));
+    const double half = __dmul_rn(z, __dsqrt_rn(var));
+    const double den = __dadd_rn(1.0, __ddiv_rn(z2, dn));
+    double lo = __ddiv_rn(__dsub_rn(centre, half), den);
+    double hi = __ddiv_rn(__dadd_rn(centre, half), den);
+    if (yes == 0) lo = 0.0;
+    if (yes == n) hi = 1.0;
+    out[0] = p;
+    out[1] = lo < 0.0 ? 0.0 : lo;
+    out[2] = hi > 1.0 ? 1.0 : hi;
+}
+
+__device__ __forceinline__ unsigned long long warp_sum(unsigned long long v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL_MASK, v, o);
+    return v;
+}
+
+// Claims an instance for the warp: first one each from the cursor, then the
+// instance with the most trajectories left (so that warps whose instance ran
+// dry help the slowest ones).  Returns -1 when no work is left.
+// Warp-collective.
+__device__ int acquire_instance(const SsaParams &p, bool &first, int gw, int lane)
+{
+    if (first) {
+        unsigned i = 0;
+        if (lane == 0) i = atomicAdd(p.cursor, 1u);
+        i = __shfl_sync(FULL_MASK, i, 0);
+        if ((int)i < p.n_list) return p.inst_list[i];
+        first = false;
+    }
+    const int n = p.n_list;
+    const int start = (int)(((unsigned)gw * 2654435761u) % (unsigned)n);
+    unsigned long long best = 0;
+    int best_m = -1;
+    for (int k = lane; k < n; k += 32) {
+        int idx = start + k;
+        if (idx >= n) idx -= n;
+        const int m = p.inst_list[idx];
+        const unsigned long long nx = *((volatile unsigned long long *)&p.tnext[m]);
+        const unsigned long long end = p.uniform ? p.u_end : p.tend[m];
+        const unsigned long long left = nx < end ? end - nx : 0;
+        if (left > best) { best = left; best_m = m; }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long ob = __shfl_xor_sync(FULL_MASK, best, o);
+        const int om = __shfl_xor_sync(FULL_MASK, best_m, o);
+        if (ob > best || (ob == best && om > best_m)) { best = ob; best_m = om; }
+    }
+    return best ? best_m : -1;
+}
+
+template <bool PLAIN>
+struct Prec;
+template <>
+struct Prec<true> { typedef double T; };
+template <>
+struct Prec<false> { typedef float T; };
+
+// Block prologue: the monitor program and, on the FP64 path, the
+// logarithm's table are copied into the front of shared memory.
+__device__ __forceinline__ void stage_block_tables(const SsaParams &p, unsigned char *smem, bool plain)
+{
+    const uint4 *src = reinterpret_cast<const uint4 *>(p.prog);
+    uint4 *dst = reinterpret_cast<uint4 *>(smem);
+    for (int i = threadIdx.x; i < (int)(sizeof(MonProg) / 16); i += blockDim.x) dst[i] = src[i];
+    if (plain) {
+        const uint4 *ls = reinterpret_cast<const uint4 *>(p.logtab);
+        uint4 *ld = reinterpret_cast<uint4 *>(smem + sizeof(MonProg));
+        for (int i = threadIdx.x; i < p.logtab_bytes / 16; i += blockDim.x) ld[i] = ls[i];
+    }
+    __syncthreads();
+}
+
+// Block epilogue: the last block to finish computes the Wilson interval of
+// every instance of the launch.
+__device__ __forceinline__ void wilson_epilogue(const SsaParams &p, int *s_last)
+{
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const unsigned tk = atomicAdd(p.ticket, 1u);
+        *s_last = (tk == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (*s_last && p.wilson) {
+        __threadfence();
+        for (int i = threadIdx.x; i < p.n_list; i += blockDim.x) {
+            const int m = p.inst_list[i];
+            const volatile unsigned long long *c = p.counts + 4 * m;
+            wilson_eq4(c[0], c[1], p.z, p.wilson + 3 * m);
+        }
+    }
+}
+
+}  // namespace

@@ -151,7 +151,7 @@ struct ReplayParams {
     int64_t *decided_at;     // [n_paths] 2k / 2k+1 decision point or -1
 };
 
-#ifdef __cplusplus
+#if defined(__cplusplus) && !defined(__CUDACC_RTC__)  // host code only (not in run-time compilation)
 extern "C++" {
 // host launch wrappers (smc_kernels.cu)
 int smc_launch_ssa(int plain, const SsaParams &p, int grid, int block, int smem_bytes,
@@ -166,6 +166,11 @@ int smc_launch_snapshot_features(uint64_t n_rows, uint64_t n_traj, int S, int R,
                                  const float *lograte, float *feat, void *stream);
 int smc_launch_cv_sums(uint64_t n, const uint8_t *y, const uint8_t *snap, const float *g, int prefix,
                        double *sums, void *stream);
+// model-specialized kernels (smc_jit.cpp): the same contract as the three
+// above, for a kernel handle returned by smc::jit_compile
+int smc_jit_set_smem_limit(void *kernel, int smem_bytes);
+int smc_jit_max_blocks_per_sm(void *kernel, int block, int smem_bytes, int *out);
+int smc_jit_launch(void *kernel, const SsaParams &p, int grid, int block, int smem_bytes, void *stream);
 // fixed scratch of smc_simulate_noalloc (see smc_kernels.cu)
 #define SMC_NOALLOC_MAX_DEVICES 64
 int smc_noalloc_scratch(int device, unsigned long long **queue, unsigned int **sync);

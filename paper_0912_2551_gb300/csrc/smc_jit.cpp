@@ -1,0 +1,241 @@
+// smc_jit.cpp -- code generation, run-time compilation (NVRTC) and launch of
+// the model-specialized SSA kernels (smc_jit_kernel.cuh).
+#include "smc_jit.h"
+
+#include <cuda_runtime.h>
+#include <dlfcn.h>
+#include <nvrtc.h>
+
+#include <cstdio>
+#include <cstdlib>
+#include <limits>
+#include <map>
+#include <mutex>
+#include <sstream>
+#include <type_traits>
+#include <vector>
+
+#include "smc_internal.h"
+#include "smc_jit_sources.inc"  // kJitHeaderNames / kJitHeaderSources, written by build.py
+
+namespace smc {
+namespace {
+
+// NVRTC entry points, resolved with dlopen so that the library loads (and
+// the generic kernels run) on a machine without it.
+struct Nvrtc {
+    bool ok = false;
+    std::string why;
+    decltype(&nvrtcCreateProgram) create = nullptr;
+    decltype(&nvrtcCompileProgram) compile = nullptr;
+    decltype(&nvrtcGetProgramLogSize) log_size = nullptr;
+    decltype(&nvrtcGetProgramLog) log = nullptr;
+    decltype(&nvrtcGetCUBINSize) cubin_size = nullptr;
+    decltype(&nvrtcGetCUBIN) cubin = nullptr;
+    decltype(&nvrtcDestroyProgram) destroy = nullptr;
+    decltype(&nvrtcGetErrorString) error_string = nullptr;
+};
+
+Nvrtc &nvrtc()
+{
+    static Nvrtc api;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        std::vector<std::string> names = {"libnvrtc.so.13", "libnvrtc.so"};
+        for (const char *env : {"CUDA_HOME", "CUDA_PATH"})
+            if (const char *h = std::getenv(env)) names.push_back(std::string(h) + "/lib64/libnvrtc.so.13");
+        names.push_back("/usr/local/cuda/lib64/libnvrtc.so.13");
+        void *h = nullptr;
+        for (const auto &n : names)
+            if ((h = dlopen(n.c_str(), RTLD_NOW | RTLD_LOCAL))) break;
+        if (!h) { api.why = "NVRTC (libnvrtc.so.13) not found"; return; }
+        auto sym = [&](auto &fn, const char *name) {
+            fn = reinterpret_cast<std::remove_reference_t<decltype(fn)>>(dlsym(h, name));
+            return fn != nullptr;
+        };
+        api.ok = sym(api.create, "nvrtcCreateProgram") && sym(api.compile, "nvrtcCompileProgram") &&
+                 sym(api.log_size, "nvrtcGetProgramLogSize") && sym(api.log, "nvrtcGetProgramLog") &&
+                 sym(api.cubin_size, "nvrtcGetCUBINSize") && sym(api.cubin, "nvrtcGetCUBIN") &&
+                 sym(api.destroy, "nvrtcDestroyProgram") && sym(api.error_string, "nvrtcGetErrorString");
+        if (!api.ok) api.why = "NVRTC is missing an entry point";
+    });
+    return api;
+}
+
+std::mutex g_cache_mu;
+std::map<std::string, JitKernels> g_cache;  // generated header -> kernels (never unloaded)
+
+}  // namespace
+
+std::string jit_model_header(const JitModel &M, std::string &why)
+{
+    const int S = M.S, R = M.R;
+    if (S < 1 || S > SMC_JIT_MAX_S || R < 1 || R > SMC_JIT_MAX_R) {
+        why = "network larger than the specialized kernels' limit";
+        return "";
+    }
+    std::ostringstream o;
+    o << "// generated: one network structure as code (see smc_jit_kernel.cuh)\n#pragma once\n";
+    o << "#define JS " << S << "\n#define JR " << R << "\n#define JNA " << M.n_atoms << "\n";
+    // propensities, both precisions, in the generic kernel's arithmetic
+    for (int plain = 1; plain >= 0; --plain) {
+        const char *T = plain ? "double" : "float";
+        o << "__device__ __forceinline__ void jit_props_" << (plain ? "plain" : "mixed")
+          << "(const int32_t *x, const " << T << " *c, " << T << " *pre, uint32_t &pos)\n{\n    " << T
+          << " acc, a;\n";
+        for (int k = 0; k < R; ++k) {
+            int ra = M.reactants[2 * k], rb = M.reactants[2 * k + 1];
+            if (ra < 0 && rb >= 0) { ra = rb; rb = -1; }
+            std::ostringstream h;
+            if (ra < 0) {
+                o << "    a = c[" << k << "];\n";  // zeroth order: h = 1
+            } else {
+                if (plain) {
+                    if (rb < 0) h << "(long long)x[" << ra << "]";
+                    else if (ra != rb) h << "(long long)x[" << ra << "] * (long long)x[" << rb << "]";
+                    else h << "((long long)x[" << ra << "] * (long long)(x[" << ra << "] - 1)) >> 1";
+                    o << "    a = __dmul_rn(c[" << k << "], int_to_double(" << h.str() << "));\n";
+                } else {
+                    if (rb < 0) h << "(float)x[" << ra << "]";
+                    else if (ra != rb) h << "__fmul_rn((float)x[" << ra << "], (float)x[" << rb << "])";
+                    else h << "__fmul_rn((float)x[" << ra << "], __fmaf_rn((float)x[" << ra << "], 0.5f, -0.5f))";
+                    o << "    a = __fmul_rn(c[" << k << "], " << h.str() << ");\n";
+                }
+            }
+            o << "    pos |= (uint32_t)(" << (plain ? "__double_as_longlong(a) > 0" : "a > 0.0f") << ") << " << k
+              << ";\n";
+            if (k == 0) o << "    acc = a;\n";
+            else o << "    acc = " << (plain ? "__dadd_rn" : "__fadd_rn") << "(acc, a);\n";
+            o << "    pre[" << k << "] = acc;\n";
+        }
+        o << "}\n";
+    }
+    // x += v_j as selects (no divergent branch on j)
+    o << "__device__ __forceinline__ void jit_apply(int j, int32_t *x)\n{\n";
+    for (int i = 0; i < S; ++i) {
+        std::ostringstream d;
+        for (int k = 0; k < R; ++k) {
+            const int32_t v = M.stoich[(size_t)k * S + i];
+            if (v) d << (d.tellp() > 0 ? " + " : "") << "(j == " << k << " ? " << v << " : 0)";
+        }
+        if (d.tellp() > 0) o << "    x[" << i << "] += " << d.str() << ";\n";
+    }
+    o << "}\n";
+    // atoms: (lo <= L <= hi) xor neg, L = sum coef x (exact int64)
+    o << "__device__ __forceinline__ uint32_t jit_atoms(const int32_t *x)\n{\n    uint32_t ab = 0;\n";
+    const int64_t MIN64 = std::numeric_limits<int64_t>::min(), MAX64 = std::numeric_limits<int64_t>::max();
+    for (int a = 0; a < M.n_atoms; ++a) {
+        std::ostringstream L;
+        int nterm = 0, single = -1;
+        for (int i = 0; i < S; ++i) {
+            const int32_t c = M.coef[(size_t)a * S + i];
+            if (!c) continue;
+            ++nterm;
+            single = (c == 1) ? i : -2;
+            L << (L.tellp() > 0 ? " + " : "") << "(long long)x[" << i << "]";
+            if (c != 1) L << " * " << c << "LL";
+        }
+        const int64_t lo = M.lo[a], hi = M.hi[a];
+        std::ostringstream cond;
+        if (lo > hi) cond << "false";
+        else if (nterm == 0) cond << ((lo <= 0 && 0 <= hi) ? "true" : "false");
+        else if (nterm == 1 && single >= 0) {  // L = x_i, an int32: compare in 32 bits
+            const int64_t I32MIN = std::numeric_limits<int32_t>::min(), I32MAX = std::numeric_limits<int32_t>::max();
+            if (lo > I32MAX || hi < I32MIN) cond << "false";
+            else {
+                std::vector<std::string> parts;
+                if (lo > I32MIN) parts.push_back("x[" + std::to_string(single) + "] >= " + std::to_string(lo));
+                if (hi < I32MAX) parts.push_back("x[" + std::to_string(single) + "] <= " + std::to_string(hi));
+                if (parts.empty()) cond << "true";
+                else cond << parts[0] << (parts.size() > 1 ? " && " + parts[1] : "");
+            }
+        } else {
+            std::vector<std::string> parts;
+            if (lo != MIN64) parts.push_back("(" + L.str() + ") >= " + std::to_string(lo) + "LL");
+            if (hi != MAX64) parts.push_back("(" + L.str() + ") <= " + std::to_string(hi) + "LL");
+            if (parts.empty()) cond << "true";
+            else cond << parts[0] << (parts.size() > 1 ? " && " + parts[1] : "");
+        }
+        o << "    ab |= ((uint32_t)(" << cond.str() << ")" << (M.neg[a] ? " ^ 1u" : "") << ") << " << a << ";\n";
+    }
+    o << "    return ab;\n}\n";
+    return o.str();
+}
+
+int jit_compile(const std::string &model_header, JitKernels &out, std::string &err)
+{
+    std::lock_guard<std::mutex> lk(g_cache_mu);
+    auto it = g_cache.find(model_header);
+    if (it != g_cache.end()) {
+        out = it->second;
+        return 0;
+    }
+    Nvrtc &api = nvrtc();
+    if (!api.ok) { err = api.why; return -1; }
+    std::vector<const char *> names, srcs;
+    for (size_t i = 0; i < sizeof(kJitHeaderNames) / sizeof(kJitHeaderNames[0]); ++i) {
+        names.push_back(kJitHeaderNames[i]);
+        srcs.push_back(kJitHeaderSources[i]);
+    }
+    names.push_back("smc_jit_model.h");
+    srcs.push_back(model_header.c_str());
+    nvrtcProgram prog;
+    nvrtcResult r = api.create(&prog, "#include \"smc_jit_kernel.cuh\"\n", "smc_jit.cu", (int)names.size(),
+                               srcs.data(), names.data());
+    if (r != NVRTC_SUCCESS) { err = std::string("nvrtcCreateProgram: ") + api.error_string(r); return -1; }
+    const char *opts[] = {"--gpu-architecture=sm_103a", "-std=c++17", "-lineinfo", "--fmad=true"};
+    r = api.compile(prog, (int)(sizeof(opts) / sizeof(opts[0])), opts);
+    if (r != NVRTC_SUCCESS) {
+        size_t n = 0;
+        api.log_size(prog, &n);
+        std::string log(n, '\0');
+        if (n) api.log(prog, &log[0]);
+        api.destroy(&prog);
+        err = std::string("NVRTC compile failed: ") + log.substr(0, 2000);
+        return -1;
+    }
+    size_t n = 0;
+    api.cubin_size(prog, &n);
+    std::vector<char> cubin(n);
+    api.cubin(prog, cubin.data());
+    api.destroy(&prog);
+    cudaLibrary_t lib = nullptr;
+    cudaError_t e = cudaLibraryLoadData(&lib, cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0);
+    if (e != cudaSuccess) { err = std::string("cudaLibraryLoadData: ") + cudaGetErrorString(e); return -1; }
+    cudaKernel_t kp = nullptr, km = nullptr;
+    if ((e = cudaLibraryGetKernel(&kp, lib, "smc_jit_ssa_plain")) != cudaSuccess ||
+        (e = cudaLibraryGetKernel(&km, lib, "smc_jit_ssa_mixed")) != cudaSuccess) {
+        err = std::string("cudaLibraryGetKernel: ") + cudaGetErrorString(e);
+        return -1;
+    }
+    JitKernels k;
+    k.plain = (void *)kp;
+    k.mixed = (void *)km;
+    g_cache[model_header] = k;
+    out = k;
+    return 0;
+}
+
+}  // namespace smc
+
+// launch helpers for the specialized kernels (same contract as the generic
+// ones in smc_kernels.cu)
+static int to_code(cudaError_t e) { return e == cudaSuccess ? 0 : -3; }
+
+int smc_jit_set_smem_limit(void *kernel, int smem_bytes)
+{
+    return to_code(cudaFuncSetAttribute((const void *)kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes));
+}
+
+int smc_jit_max_blocks_per_sm(void *kernel, int block, int smem_bytes, int *out)
+{
+    return to_code(cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, (const void *)kernel, block, smem_bytes));
+}
+
+int smc_jit_launch(void *kernel, const SsaParams &p, int grid, int block, int smem_bytes, void *stream)
+{
+    SsaParams copy = p;
+    void *args[] = {&copy};
+    return to_code(cudaLaunchKernel((const void *)kernel, dim3(grid), dim3(block), args, (size_t)smem_bytes,
+                                    (cudaStream_t)stream));
+}

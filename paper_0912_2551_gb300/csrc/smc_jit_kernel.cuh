@@ -1,0 +1,219 @@
+// smc_jit_kernel.cuh -- the persistent SSA + monitor kernel specialized to one
+// network structure, compiled at run time (NVRTC) when a model is loaded.
+//
+// The generated header "smc_jit_model.h" fixes the structure as code:
+//   JS, JR, JNA                  species, reactions, atoms
+//   jit_props_plain / _mixed     a_k = c_k h_k(x) for every k, their running
+//                                sums (the selection table of Eq. 2b) and the
+//                                bit set of positive a_k
+//   jit_apply(j, x)              x += v_j
+//   jit_atoms(x)                 the atom bit vector of the monitor
+// so each lane keeps its counts x in registers and no table is read per
+// event.  Rates (and x0) stay data, read once per instance, so one compiled
+// kernel serves every parameter set of the structure.  The arithmetic, its
+// order and the random-number use are those of the generic kernel's
+// small-network branch: both produce the same trajectories bit for bit.
+#pragma once
+#include "smc_device.cuh"
+#include "smc_jit_model.h"
+
+namespace {
+
+template <bool PLAIN>
+__device__ __forceinline__ void jit_run_instance(const SsaParams &p, const MonProg &P, const double *ltab,
+                                                 const int m, double *tc, const int lane)
+{
+    typedef typename Prec<PLAIN>::T T;
+    const uint32_t *blob = p.blobs + p.blob_off[m];
+    T c[JR];
+    if constexpr (PLAIN) {
+        const double *rd = reinterpret_cast<const double *>(blob + blob[BH_RATE_D]);
+#pragma unroll
+        for (int k = 0; k < JR; ++k) c[k] = rd[k];
+    } else {
+        const float *rf = reinterpret_cast<const float *>(blob + blob[BH_RATE_F]);
+#pragma unroll
+        for (int k = 0; k < JR; ++k) c[k] = rf[k];
+    }
+    const int32_t *x0 = reinterpret_cast<const int32_t *>(blob + blob[BH_X0]);
+    const unsigned long long tend = p.uniform ? p.u_end : p.tend[m];
+    const bool always_step = P.has_lower != 0;
+    const bool unbounded = P.unbounded != 0;
+    const double t_max = P.t_max;
+    const uint64_t budget = p.budget;
+    const int snap_mode = p.snap_mode;
+    const double t_snap = p.t_snap;
+
+    bool active = false, exhausted = false, snapped = false;
+    uint32_t traj = 0, e = 0;
+    double t = 0.0;
+    int32_t x[JS];
+    MonLane ml;
+    MonHot mh;
+    uint32_t c_yes = 0, c_dec = 0, c_bud = 0;
+    unsigned long long c_ev = 0;
+
+    // verdict codes: 1 false, 2 true, 3 event budget exhausted, 4 stopped at
+    // the snapshot (prefix-only run: no verdict, not counted)
+    auto finish = [&](int v) {
+        if (v == 3) ++c_bud;
+        else if (v != 4) { ++c_dec; c_yes += (v == 2); }
+        c_ev += e;
+        const uint64_t idx = (uint64_t)m * p.out_stride + ((uint64_t)traj - p.out_base);
+        if (p.o_verdict) {
+            p.o_verdict[idx] = (v == 2);
+            if (p.o_status) p.o_status[idx] = (v == 3) ? 1 : (v == 4 ? 2 : 0);
+            if (p.o_events) p.o_events[idx] = e;
+            if (p.o_tfinal) p.o_tfinal[idx] = t;
+            if (p.o_xfinal) {
+#pragma unroll
+                for (int i = 0; i < JS; ++i) p.o_xfinal[idx * p.x_stride + i] = x[i];
+            }
+        }
+        if (snap_mode && !snapped) p.o_snap[idx] = 1;  // decided before t_snap
+        active = false;
+    };
+
+    for (;;) {
+        if (!exhausted) {
+            const unsigned need = __ballot_sync(FULL_MASK, !active);
+            const int nneed = __popc(need);
+            if (nneed && (nneed >= p.refill || nneed == 32)) {
+                const int leader = __ffs(need) - 1;
+                unsigned long long base = 0;
+                if (lane == leader) base = atomicAdd(&p.tnext[m], (unsigned long long)nneed);
+                base = __shfl_sync(FULL_MASK, base, leader);
+                if (base + (unsigned long long)nneed >= tend) exhausted = true;
+                if (!active) {
+                    const unsigned long long id = base + __popc(need & ((1u << lane) - 1u));
+                    if (id < tend) {
+                        traj = (uint32_t)id;
+                        e = 0;
+                        t = 0.0;
+                        snapped = false;
+#pragma unroll
+                        for (int i = 0; i < JS; ++i) x[i] = x0[i];
+                        ml.ab = jit_atoms(x);
+                        mon_start(ml, P);
+                        active = true;
+                        const int v = mon_state(ml, P, 0.0, tc);
+                        mh.load(ml);
+                        if (v) finish(v);
+                    }
+                }
+            }
+        }
+        if (!__any_sync(FULL_MASK, active)) {
+            if (exhausted) break;
+            continue;
+        }
+        if (!active) continue;
+
+        // ---- one event (Sec. 2.2 steps 1-5) ----------------------------------
+        T pre[JR];
+        uint32_t pos = 0;
+        if constexpr (PLAIN) jit_props_plain(x, c, pre, pos);
+        else jit_props_mixed(x, c, pre, pos);
+        const T a0 = pre[JR - 1];
+        if (PLAIN ? __double_as_longlong((double)a0) <= 0 : !(a0 > (T)0)) {
+            finish(mon_close(ml, P));  // absorbing state: no further position
+            continue;
+        }
+        uint32_t w0, w1, w2, w3;
+        philox10(e, traj, (uint32_t)m, 0u, p.rk0, p.rk1, w0, w1, w2, w3);
+        double tn;
+        T r;
+        if (PLAIN) {
+            const double ut = u01_52(w0, w1), us = u01_52(w2, w3);
+            tn = __dadd_rn(t, __ddiv_rn(-log_table(ut, ltab), (double)a0));
+            r = (T)__dmul_rn(us, (double)a0);
+        } else {
+            const float ut = u01_23(w0), us = u01_23(w2);
+            const float tau = __fdividef(-__logf(ut), (float)a0);
+            tn = __dadd_rn(t, f32_to_f64(tau));
+            r = (T)__fmul_rn(us, (float)a0);
+        }
+        if (snap_mode && !snapped && dgt(tn, t_snap)) {
+            snapped = true;
+            const uint64_t idx = (uint64_t)m * p.out_stride + ((uint64_t)traj - p.out_base);
+            p.o_snap[idx] = 0;
+#pragma unroll
+            for (int i = 0; i < JS; ++i) p.o_xsnap[idx * p.x_stride + i] = x[i];
+            if (snap_mode == 2) { finish(4); continue; }
+        }
+        int v = 0;
+        if (mh.pend || __double_as_longlong(tn) > mh.hb) {
+            v = mon_draw(ml, P, tn, tc);
+            mh.load(ml);
+        }
+        if (!v && unbounded && dgt(tn, t_max)) v = 1;  // pessimistic rule (Sec. 3.2)
+        if (v) { finish(v); continue; }
+
+        // step 2: the first j whose running sum exceeds r
+        int j = -1;
+#pragma unroll
+        for (int k = JR - 1; k >= 0; --k) {
+            const bool hit = PLAIN ? __double_as_longlong((double)pre[k]) > __double_as_longlong((double)r)
+                                   : pre[k] > r;
+            if (hit) j = k;
+        }
+        if (j < 0) j = 31 - __clz(pos);  // r reached the full sum: last positive a_k
+
+        // step 4: x += v_j, then the monitor at the new state
+        jit_apply(j, x);
+        ++e;
+        t = tn;
+        const uint32_t ab = jit_atoms(x);
+        if (always_step || ab != mh.ab || mh.pend) {
+            ml.ab = ab;
+            v = mon_state(ml, P, t, tc);
+            mh.load(ml);
+        }
+        if (v) finish(v);
+        else if ((uint64_t)e >= budget) finish(3);
+    }
+
+    const unsigned long long s_yes = warp_sum(c_yes), s_dec = warp_sum(c_dec);
+    const unsigned long long s_ev = warp_sum(c_ev), s_bud = warp_sum(c_bud);
+    if (lane == 0 && (s_dec | s_bud)) {
+        atomicAdd(&p.counts[4 * m + 0], s_yes);
+        atomicAdd(&p.counts[4 * m + 1], s_dec);
+        atomicAdd(&p.counts[4 * m + 2], s_ev);
+        atomicAdd(&p.counts[4 * m + 3], s_bud);
+    }
+}
+
+template <bool PLAIN>
+__device__ __forceinline__ void jit_kernel_body(const SsaParams &p)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ int s_last;
+    stage_block_tables(p, smem, PLAIN);
+    const MonProg &P = *reinterpret_cast<const MonProg *>(smem);
+    const double *ltab = reinterpret_cast<const double *>(smem + sizeof(MonProg));
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    // warp slice: the nested operators' candidate clocks tc[units][32]
+    double *tc = reinterpret_cast<double *>(smem + sizeof(MonProg) + p.logtab_bytes +
+                                            (size_t)warp * p.warp_bytes) + lane;
+    bool first = true;
+    const int gw = blockIdx.x * (blockDim.x >> 5) + warp;
+    for (;;) {
+        const int m = acquire_instance(p, first, gw, lane);
+        if (m < 0) break;
+        jit_run_instance<PLAIN>(p, P, ltab, m, tc, lane);
+        __syncwarp();
+    }
+    wilson_epilogue(p, &s_last);
+}
+
+}  // namespace
+
+extern "C" __global__ void __launch_bounds__(256, 3) smc_jit_ssa_plain(const SsaParams p)
+{
+    jit_kernel_body<true>(p);
+}
+
+extern "C" __global__ void __launch_bounds__(256, 4) smc_jit_ssa_mixed(const SsaParams p)
+{
+    jit_kernel_body<false>(p);
+}

@@ -1,0 +1,137 @@
+"""Model-specialized kernels (SMC_OPT_JIT): the run-time compiled kernel of a
+network structure must reproduce the generic kernel bit for bit -- same
+random numbers, same arithmetic in the same order -- on the FP64 and the
+mixed path: per-trajectory verdicts, statuses, event counts, final clocks and
+states, snapshots, and the device-side counts and Wilson interval.  The FP64
+path's agreement with the oracle is covered by the parity tests, which run
+through the specialized kernel by default."""
+import math
+
+import numpy as np
+import pytest
+
+import workloads
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope='module')
+def smc():
+    torch = pytest.importorskip('torch')
+    if not torch.cuda.is_available():
+        pytest.skip('no GPU')
+    import paper_0912_2551_gb300 as smc
+    return smc
+
+
+def _nested_lv():
+    """Lotka-Volterra with a nested monitor (candidate clocks in use):
+    (X < 3000) U[0,10] (Y >= 1500 & F[0,0.5] Y < 1000)."""
+    m, _ = workloads.lotka_volterra(1)
+    sp = m.species
+    p = workloads.Property([workloads.atom(sp, 'X', '<', 3000), workloads.atom(sp, 'Y', '>=', 1500),
+                            workloads.atom(sp, 'Y', '<', 1000)],
+                           ('U', 0.0, 10.0, ('atom', 0), ('and', ('atom', 1), ('F', 0.0, 0.5, ('atom', 2)))))
+    return m, p
+
+
+def _weighted_atom():
+    """Dimerisation watched through a multi-term atom A + 2B (conserved up to
+    immigration) with a lower window bound: F[2,20](A + 2B >= 160)."""
+    m, _ = workloads.dimerisation(1)
+    sp = m.species
+    p = workloads.Property([workloads.atom(sp, {'A': 1, 'B': 2}, '>=', 160)], ('F', 2.0, 20.0, ('atom', 0)))
+    return m, p
+
+
+MODELS = {
+    'lotka_volterra': lambda: workloads.lotka_volterra(1),
+    'lv_family': lambda: workloads.lotka_volterra_family(6, seed=4),
+    'immigration_death': lambda: workloads.immigration_death(1),
+    'dimerisation': lambda: workloads.dimerisation(1),
+    'pure_decay': lambda: workloads.pure_decay(),
+    'nested_lv': _nested_lv,
+    'weighted_atom': _weighted_atom,
+}
+OUTPUTS = ('verdict', 'status', 'events', 't_final', 'x_final')
+
+
+def _run(smc, model, prop, jit, precision, n, t_max=math.inf):
+    import torch
+    with smc.Context(0) as ctx:
+        ctx.set_option('jit', jit)
+        ctx.load_model(model)
+        ctx.load_property(prop, t_max=t_max)
+        out = ctx.simulate(precision, seed=17, traj_begin=1000, n_traj=n, confidence=0.95, outputs=OUTPUTS)
+        torch.cuda.synchronize()
+        shapes = ctx.launch_shapes(precision)
+        return {k: v.cpu().numpy() for k, v in out.items()}, shapes
+
+
+@pytest.mark.parametrize('precision', ['plain', 'mixed'])
+@pytest.mark.parametrize('name', sorted(MODELS))
+def test_specialized_kernel_reproduces_generic(smc, name, precision):
+    model, prop = MODELS[name]()
+    n = 3000 if name != 'lotka_volterra' else 1500
+    spec, s1 = _run(smc, model, prop, 1, precision, n)
+    gen, s0 = _run(smc, model, prop, 0, precision, n)
+    assert all(s['specialized'] for s in s1), s1
+    assert not any(s['specialized'] for s in s0)
+    for k in OUTPUTS + ('counts',):
+        assert np.array_equal(spec[k], gen[k]), (k, np.argwhere(spec[k] != gen[k])[:5])
+    assert np.array_equal(spec['wilson'], gen['wilson'])
+    assert spec['counts'][:, 1].sum() + spec['counts'][:, 3].sum() == model.n_inst * n
+
+
+@pytest.mark.parametrize('precision', ['plain', 'mixed'])
+def test_specialized_snapshots_reproduce_generic(smc, precision):
+    import torch
+    model, prop = workloads.lotka_volterra_family(4, seed=9)
+    res = []
+    for jit in (1, 0):
+        with smc.Context(0) as ctx:
+            ctx.set_option('jit', jit)
+            ctx.load_model(model)
+            ctx.load_property(prop)
+            for stop in (False, True):
+                o = ctx.simulate_snapshot(precision, seed=3, traj_begin=0, n_traj=2048, t_snap=0.6, stop=stop)
+                torch.cuda.synchronize()
+                res.append({k: v.cpu().numpy() for k, v in o.items()})
+    for a, b in zip(res[:2], res[2:]):
+        for k in a:
+            assert np.array_equal(a[k], b[k]), k
+    assert (res[0]['snap'] == 0).any() and (res[0]['snap'] == 1).any()
+
+
+def test_ineligible_models_run_generic(smc):
+    import torch
+    # more than 8 species: the cascade
+    m, p = workloads.mapk_cascade(2, seed=5)
+    with smc.Context(0) as ctx:
+        ctx.load_model(m)
+        ctx.load_property(p)
+        ctx.simulate('mixed', seed=1, n_traj=64, outputs=())
+        torch.cuda.synchronize()
+        assert not any(s['specialized'] for s in ctx.launch_shapes('mixed'))
+    # heterogeneous batch
+    b = workloads.random_networks(16, seed=3)
+    with smc.Context(0) as ctx:
+        ctx.load_batch(b)
+        ctx.load_property(b.properties)
+        ctx.simulate('mixed', seed=1, n_traj=64, outputs=())
+        torch.cuda.synchronize()
+        assert not any(s['specialized'] for s in ctx.launch_shapes('mixed'))
+
+
+def test_specialized_estimate_matches_generic(smc):
+    """The graph-captured Fig. 2 loop through the specialized kernel."""
+    model, prop = workloads.immigration_death(1)
+    res = []
+    for jit in (1, 0):
+        with smc.Context(0) as ctx:
+            ctx.set_option('jit', jit)
+            ctx.load_model(model)
+            ctx.load_property(prop)
+            r = ctx.estimate(0.99, 0.01, seed=5, precision='plain', sampling='iterative')[0]
+            res.append((r['yes'], r['n'], r['events'], r['iterations'], r['p_hat'], r['lo'], r['hi']))
+    assert res[0] == res[1]

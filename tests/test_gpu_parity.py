@@ -2,8 +2,8 @@
 same seeded inputs.
 
 FP64 path: per-trajectory verdicts must agree on >= 99.99% of trajectories
-(in practice all: the reaction sequence is bit-identical, only CUDA's and
-glibc's log may differ by an ulp in the clock), event counts likewise,
+(in practice all: the reaction sequence is bit-identical, only the FP64
+path's table-driven log and glibc's may differ in the last bit of the clock), event counts likewise,
 |p_hat difference| <= 1e-3, and the Wilson bounds computed on the device from
 the integer counts agree with Eq. 4 to 1e-12 relative.
 Mixed path: statistical agreement (p_hat inside the combined intervals) and a
