@@ -38,6 +38,31 @@ WORKLOAD = ('Lotka-Volterra X->2X 1.0, X+Y->2Y 0.005, Y->0 0.6, X0=Y0=1000; G[0,
             '1,000,000 trajectories per step; 99% Wilson half-width 0.001')
 
 
+def nvtx_push(name):
+    """Opens an NVTX range (lets a profiler select one loop's launches)."""
+    try:
+        import torch
+        torch.cuda.nvtx.range_push(name)
+    except Exception:  # NVTX not available in this torch build
+        pass
+
+
+def nvtx_pop():
+    try:
+        import torch
+        torch.cuda.nvtx.range_pop()
+    except Exception:
+        pass
+
+
+def kernel_name(ctx, precision):
+    """The SSA kernel serving ctx's model for a precision ('plain' / 'mixed')."""
+    spec = all(sh['specialized'] for sh in ctx.launch_shapes(precision))
+    if spec:
+        return f'smc_jit_ssa_{precision} (model-specialized)'
+    return 'ssa_kernel<plain FP64>' if precision == 'plain' else 'ssa_kernel<mixed>'
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, 'MEASURED_PEAKS.json')) as f:
@@ -178,11 +203,13 @@ def main():
     ap.add_argument('--impl', default='native', choices=['native', 'reference'])
     ap.add_argument('--no-cpu-baseline', action='store_true')
     ap.add_argument('--no-e2e', action='store_true')
-    ap.add_argument('--traj', type=int, default=N_TRAJ, help='trajectories per step (profiling runs)')
+    ap.add_argument('--traj', type=int, default=None,
+                    help='trajectories per step (per instance for --config workloads; profiling runs)')
     ap.add_argument('--config', default='lotka_volterra',
                     choices=['lotka_volterra', 'immigration_death', 'random_networks', 'surrogate', 'cascade'])
     args = ap.parse_args()
-    N_TRAJ = args.traj
+    if args.traj is not None and args.config == 'lotka_volterra':
+        N_TRAJ = args.traj
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == 'reference':
@@ -220,18 +247,6 @@ def main():
         torch.cuda.synchronize(dev)
         if dist is not None:
             dist.barrier()
-
-    def nvtx_push(name):
-        try:
-            torch.cuda.nvtx.range_push(name)
-        except Exception:  # NVTX not available in this torch build
-            pass
-
-    def nvtx_pop():
-        try:
-            torch.cuda.nvtx.range_pop()
-        except Exception:
-            pass
 
     def timed(precision):
         counts = torch.zeros((1, 4), dtype=torch.int64, device=dev)
@@ -335,6 +350,15 @@ def main():
     w_mixed = algorithmic_ops_per_event(model, 2, False)
     ach_plain = w_plain * res['plain']['events_s'] / max(world, 1)
     ach_mixed = w_mixed * res['mixed']['events_s'] / max(world, 1)
+    # The FP64 path's tighter bound: GB300 issues 2 FP64 operations per clock
+    # per SM.  Per event it runs R products and R - 1 sums (Eq. 1), 15 for the
+    # logarithm, the correctly rounded division (9.75 as counted by ncu on
+    # this kernel), the clock add and u_sel * a_0 (ncu total for this
+    # workload: 31.75 = 9.75 DADD + 16 DFMA + 6 DMUL).
+    R = model.n_reactions
+    fp64_per_event = 2 * R - 1 + 15 + 9.75 + 2
+    fp64_peak = n_sm * 2 * f_clk
+    fp64_ach = fp64_per_event * res['plain']['events_s'] / max(world, 1)
 
     line = {
         'metric': METRIC,
@@ -366,12 +390,16 @@ def main():
                    'iterative_wilson': {'half_width': HALF_WIDTH, 'confidence': CONFIDENCE,
                                         'n': it['launched'], 'p_hat': it['p_hat'], 'lo': it['lo'],
                                         'hi': it['hi'], 'iterations': it['iterations']}},
-        'roofline': {'bound': 'alu', 'kernel': 'ssa_kernel<plain FP64>',
+        'roofline': {'bound': 'alu', 'kernel': kernel_name(ctx, 'plain'),
                      'achieved': ach_plain / 1e9, 'peak': peak_ops / 1e9, 'unit': 'Gop/s',
                      'frac': ach_plain / peak_ops, 'traffic': None,
                      'ops_per_event': w_plain,
                      'peak_source': f'{n_sm} SMs x 4 issue slots x 32 lanes x {f_clk / 1e6:.0f} MHz '
                                     f'({pk_src} max SM clock)'},
+        'fp64_pipe': {'kernel': kernel_name(ctx, 'plain'), 'fp64_ops_per_event': fp64_per_event,
+                      'achieved': fp64_ach / 1e9, 'peak': fp64_peak / 1e9, 'unit': 'G FP64 ops/s',
+                      'frac': fp64_ach / fp64_peak,
+                      'peak_source': f'{n_sm} SMs x 2 FP64 ops/clk x {f_clk / 1e6:.0f} MHz'},
         'e2e': {'value': e2e_value, 'unit': 'trajectories/s', 'h2d_bytes_per_step': h2d,
                 'd2h_bytes_per_step': d2h},
         'gpu_launches': 2 * args.steps,

@@ -6,11 +6,13 @@
   x 10,000 trajectories, F[0,50](X_k >= theta), one graph-captured estimate
   per step, mixed path.
 * surrogate: Lotka-Volterra family (rates x log-uniform [0.7, 1.3]),
-  G[0,30](X>0 & Y>0): 2,000,000 snapshots at t_c = 5 of trajectories still
-  undecided there, labelled by their verdicts, train the BF16 network, then
-  reach a 95% Wilson half-width of 0.002 on held-out instances with the
-  plain estimator (Fig. 2) and with the control-variate estimator; value =
-  effective verified trajectories per second of the latter.
+  G[0,30](X>0 & Y>0): for each checkpoint t_c in {0.5, 1, 2, 5}, 1,000,000
+  snapshots at t_c of trajectories still undecided there, labelled by their
+  verdicts, train the BF16 network; then reach a 95% Wilson half-width of
+  0.002 on held-out instances with the plain estimator (Fig. 2, FP64 and
+  mixed) and with the control-variate estimator; value = effective verified
+  trajectories per second of the latter at the best t_c.  The same on a
+  linear birth-death survival problem, where the checkpoint pays.
 * cascade: three-tier phosphorylation cascade, 256 rate-perturbed instances,
   literal and variant properties, mixed path.
 """
@@ -46,7 +48,7 @@ def _issue_roofline(events_per_s, ops_per_event, kernel):
             'peak_source': f'{n_sm} SMs x 4 x 32 lanes x {f / 1e6:.0f} MHz ({src})'}
 
 
-def _timed_simulate(ctx, precision, n, steps, warmup, seed=0, confidence=0.95):
+def _timed_simulate(ctx, precision, n, steps, warmup, seed=0, confidence=0.95, label='steps'):
     import torch
     dev = torch.device('cuda', 0)
     stream = torch.cuda.Stream(dev)
@@ -61,12 +63,14 @@ def _timed_simulate(ctx, precision, n, steps, warmup, seed=0, confidence=0.95):
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
     clocks = bench.Clocks(0)
     clocks.start()
+    bench.nvtx_push(f'{label}_{precision}_steps')
     with torch.cuda.stream(stream):
         for s in range(steps):
             ev[s][0].record(stream)
             ctx.simulate(precision, seed=seed, traj_begin=0, n_traj=n, confidence=confidence, outputs=(),
                          counts=counts, wilson=wil, stream=stream)
             ev[s][1].record(stream)
+    bench.nvtx_pop()
     torch.cuda.synchronize()
     clk = clocks.stop()
     ms = sum(a.elapsed_time(b) for a, b in ev) / steps
@@ -83,6 +87,7 @@ def immigration_death(args):
         ctx.load_model(m)
         ctx.load_property(p)
         ms, c, wil, clk = _timed_simulate(ctx, 'plain', n, args.steps, args.warmup, seed=0)
+        kname = bench.kernel_name(ctx, 'plain')
         it = ctx.estimate(0.95, 0.005, seed=0, precision='plain', sampling='iterative')[0]
     t0 = time.perf_counter()
     r = oracle.run(m, p, seed=0, n_traj=n)
@@ -95,8 +100,7 @@ def immigration_death(args):
                       'oracle_p_hat': float(r['verdict'].mean()),
                       'iterative_eps_0.005': {'n': it['launched'], 'p_hat': it['p_hat'], 'lo': it['lo'],
                                               'hi': it['hi']}},
-           'roofline': _issue_roofline(ev / (ms / 1e3), bench.algorithmic_ops_per_event(m, 1, True),
-                                       'ssa_kernel<plain FP64>'),
+           'roofline': _issue_roofline(ev / (ms / 1e3), bench.algorithmic_ops_per_event(m, 1, True), kname),
            'cpu_baseline': {'value': n / cpu, 'unit': 'trajectories/s', 'cores': os.cpu_count(),
                             'kind': 'oracle', 'sample': f'the full {n} trajectories, {cpu:.2f} s'}})
 
@@ -106,7 +110,7 @@ def random_networks(args):
     import paper_0912_2551_gb300 as smc
     import workloads
     b = workloads.random_networks(4096, seed=3)
-    n = 10000
+    n = args.traj or 10000
     steps = max(1, min(args.steps, 3))
     with smc.Context(0) as ctx:
         ctx.load_batch(b)
@@ -116,10 +120,12 @@ def random_networks(args):
         clocks.start()
         t0 = time.perf_counter()
         tot = None
+        bench.nvtx_push('batch_mixed_steps')
         for s in range(steps):
             res = ctx.estimate(0.95, 0.01, seed=1 + s, precision='mixed', sampling='fixed', fixed_n=n)
             ev = sum(r['events'] for r in res)
             tot = ev if tot is None else tot + ev
+        bench.nvtx_pop()
         dt = (time.perf_counter() - t0) / steps
         clk = clocks.stop()
         ev_step = tot / steps
@@ -133,18 +139,20 @@ def random_networks(args):
     R = np.array([mm.n_reactions for mm in b.models])
     ops = 40 + 4 + 1 + 2 + float(np.mean(R + 1)) + 2.5 + 3 * 6 + 2 + 2
     _line(4096 * n / dt, 'trajectories/s', steps, 1, 1e3 * dt, 'mixed (f32 propensities, f64 clock)',
-          '4096 random mass-action networks (S 2..32, R 4..64) x 10,000 trajectories, F[0,50](X_k>=theta), '
+          f'4096 random mass-action networks (S 2..32, R 4..64) x {n:,} trajectories, F[0,50](X_k>=theta), '
           'one graph-captured estimate per step',
           {'events_per_s': ev_step / dt, 'events_per_trajectory': ev_step / (4096 * n), 'clocks': clk,
            'roofline': _issue_roofline(ev_step / dt, ops, 'ssa_kernel<mixed>'),
-           'note': 'host-timed smc_estimate (graph launch, ranges up, counts down); tail-bound: the '
-                   'longest trajectories reach ~8e5 events',
+           'note': 'host-timed smc_estimate (graph launch, ranges up, counts down); throughput-bound at '
+                   '10,000 trajectories per instance (6.2e10 events per step; the longest trajectories, '
+                   '~8e5 events, bound the step only below ~1,000 per instance)',
            'cpu_baseline': {'value': k / cpu, 'unit': 'trajectories/s', 'cores': os.cpu_count(),
                             'kind': 'oracle', 'sample': f'2 trajectories of every 16th instance, {cpu:.1f} s'}})
 
 
-def _collect_snapshots(ctx, smc, torch, t_c, want, per_call, x_scale, t_scale, seed):
-    """Snapshots at t_c of trajectories still undecided there, with verdicts."""
+def _collect_snapshots(ctx, torch, t_c, want, per_call, x_scale, t_scale, seed):
+    """Snapshots at t_c of trajectories still undecided there, labelled by
+    their verdicts (full runs)."""
     xs, ys = [], []
     got, begin = 0, 0
     while got < want:
@@ -160,81 +168,143 @@ def _collect_snapshots(ctx, smc, torch, t_c, want, per_call, x_scale, t_scale, s
     return x, y, begin
 
 
+def _held_out(ctx, net, t_c, x_scale, t_scale, seed, n):
+    """On held-out trajectories: beta = Cov(Y, G) / Var(G), the share of
+    Var(Y) that beta G leaves, and r = the events a prefix run to t_c costs
+    as a share of a full run's (both measured on the same full runs)."""
+    o = ctx.simulate_snapshot('mixed', seed=seed, traj_begin=0, n_traj=n, t_snap=t_c)
+    g = net.predict(ctx.snapshot_features(o['x_snap'], t_c, x_scale, t_scale)).cpu().numpy()
+    y = o['verdict'].reshape(-1).cpu().numpy().astype(float)
+    dec = o['snap'].reshape(-1).cpu().numpy() == 1
+    G = np.where(dec, y, g)
+    beta = float(np.cov(y, G)[0, 1] / max(np.var(G, ddof=1), 1e-300))
+    resid = float(np.var(y - beta * G) / max(np.var(y), 1e-300))
+    r = float(o['e_snap'].double().sum().item() / o['counts'][:, 2].double().sum().item())
+    return beta, resid, r, float((~dec).mean())
+
+
+def _predicted_cost_ratio(resid, r):
+    """Cost of the two-phase control variate over the plain estimator's for
+    the same variance, at the optimal split: (sqrt(resid (1-r)) +
+    sqrt((1-resid) r))^2 when r < 1 - resid, else 1 (no prefix runs)."""
+    rho2 = 1.0 - resid
+    if r >= rho2:
+        return 1.0
+    return (math.sqrt(resid * (1 - r)) + math.sqrt(rho2 * r)) ** 2
+
+
+def _three_arms(smc, torch, inst, prop, net, t_c, x_scale, t_scale, beta, conf, eps, seed):
+    """One held-out instance to the same Wilson half-width three ways: plain
+    FP64 (Fig. 2), plain mixed (Fig. 2), and mixed + control variate."""
+    out = {}
+    with smc.Context(0) as ctx:
+        ctx.load_model(inst)
+        ctx.load_property(prop)
+        for prec in ('plain', 'mixed'):
+            ctx.estimate(conf, eps, seed=seed + 500, precision=prec, sampling='fixed', fixed_n=1000)  # warm
+        torch.cuda.synchronize()
+        for prec in ('plain', 'mixed'):
+            t0 = time.perf_counter()
+            r = ctx.estimate(conf, eps, seed=seed, precision=prec, sampling='iterative')[0]
+            out[prec] = dict(s=time.perf_counter() - t0, n=r['launched'], events=r['events'], p=r['p_hat'],
+                             half=(r['hi'] - r['lo']) / 2)
+        ctx.estimate_cv(net, conf, eps, seed=seed + 2, precision='mixed', t_snap=t_c, x_scale=x_scale,
+                        t_scale=t_scale, beta=beta, pilot=1000)  # warm (buffers, tuned shapes)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        cv = ctx.estimate_cv(net, conf, eps, seed=seed + 1, precision='mixed', t_snap=t_c, x_scale=x_scale,
+                             t_scale=t_scale, beta=beta, pilot=1000)
+        out['cv'] = dict(s=time.perf_counter() - t0, n_eff=cv['n_eff'], n_full=cv['n_full'],
+                         n_prefix=cv['n_prefix'], events=cv['events_full'] + cv['events_prefix'],
+                         p=cv['p_hat'], half=(cv['hi'] - cv['lo']) / 2)
+    return out
+
+
+def _train(ctx, smc, torch, t_c, n_snap, x_scale, t_scale, seed):
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    x, y, used = _collect_snapshots(ctx, torch, t_c, n_snap, 4096, x_scale, t_scale, seed)
+    torch.cuda.synchronize()
+    t_data = time.perf_counter() - t0
+    net = smc.Mlp(x.shape[1], seed=7)
+    epochs, batch = 4, 8192
+    t1 = time.perf_counter()
+    loss = net.train(x, y, epochs=epochs, batch=batch, lr=1e-3, seed=3)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t1
+    steps = epochs * math.ceil(x.shape[0] / batch)
+    flops = steps * batch * 3 * 2 * (16 * 128 + 2 * 128 * 128 + 128)  # forward + 2x backward
+    return net, dict(snapshots=int(x.shape[0]), trajectories_simulated=int(used * ctx.n_inst), data_seconds=t_data,
+                     train_seconds=t_train, epochs=epochs, batch=batch, loss=[float(v) for v in loss],
+                     tflops=flops / t_train / 1e12)
+
+
 def surrogate(args):
+    """Control variate on the Lotka-Volterra family (the configured
+    workload): a sweep over the checkpoint t_c, each point training its own
+    network; then the same estimator on a linear birth-death survival
+    problem, where a checkpoint settles the verdict early."""
     import torch
     import paper_0912_2551_gb300 as smc
     import workloads
-    t_c, eps, conf = 5.0, 0.002, 0.95
+    eps, conf = 0.002, 0.95
     x_scale, t_scale = np.array([1000.0, 1000.0], np.float32), 30.0
     fam, p = workloads.lotka_volterra_family(512, seed=1)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    with smc.Context(0) as ctx:
-        ctx.load_model(fam)
-        ctx.load_property(p)
-        x, y, used = _collect_snapshots(ctx, smc, torch, t_c, 2_000_000, 4096, x_scale, t_scale, seed=11)
-        torch.cuda.synchronize()
-        t_data = time.perf_counter() - t0
-        net = smc.Mlp(x.shape[1], seed=7)
-        epochs, batch = 4, 8192
-        t1 = time.perf_counter()
-        loss = net.train(x, y, epochs=epochs, batch=batch, lr=1e-3, seed=3)
-        torch.cuda.synchronize()
-        t_train = time.perf_counter() - t1
-        steps = epochs * math.ceil(x.shape[0] / batch)
-        flops = steps * batch * 3 * 2 * (16 * 128 + 2 * 128 * 128 + 128)  # forward + 2x backward
-        # beta from held-out trajectories of the family (another seed)
-        h = ctx.simulate_snapshot('mixed', seed=12, traj_begin=0, n_traj=256, t_snap=t_c)
-        gh = net.predict(ctx.snapshot_features(h['x_snap'], t_c, x_scale, t_scale)).cpu().numpy()
-        yh = h['verdict'].reshape(-1).cpu().numpy().astype(float)
-        dec = h['snap'].reshape(-1).cpu().numpy() == 1
-        G = np.where(dec, yh, gh)
-        beta = float(np.cov(yh, G)[0, 1] / np.var(G, ddof=1))
-        resid = float(np.var(yh - beta * G) / np.var(yh))
-    # held-out instances: plain Fig. 2 vs control variate, same target width
-    test, _ = workloads.lotka_volterra_family(8, seed=2)
-    rows = []
-    for i in range(test.n_inst):
-        inst = test.instance(i)
+    test, _ = workloads.lotka_volterra_family(4, seed=2)
+    sweep = []
+    for t_c in (0.5, 1.0, 2.0, 5.0):
         with smc.Context(0) as ctx:
-            ctx.load_model(inst)
+            ctx.load_model(fam)
             ctx.load_property(p)
-            ctx.estimate(conf, eps, seed=500 + i, precision='mixed', sampling='fixed', fixed_n=1000)  # warm
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            pl = ctx.estimate(conf, eps, seed=1000 + i, precision='mixed', sampling='iterative')[0]
-            tp = time.perf_counter() - t0
-            t0 = time.perf_counter()
-            cv = ctx.estimate_cv(net, conf, eps, seed=2000 + i, precision='mixed', t_snap=t_c, x_scale=x_scale,
-                                 t_scale=t_scale, beta=beta, pilot=2000)
-            tc = time.perf_counter() - t0
-        rows.append(dict(plain_s=tp, cv_s=tc, plain_n=pl['launched'], plain_events=pl['events'],
-                         plain_p=pl['p_hat'], plain_half=(pl['hi'] - pl['lo']) / 2, cv_p=cv['p_hat'],
-                         cv_half=(cv['hi'] - cv['lo']) / 2, cv_neff=cv['n_eff'], cv_full=cv['n_full'],
-                         cv_prefix=cv['n_prefix'], cv_events=cv['events_full'] + cv['events_prefix']))
-    T_p = sum(r['plain_s'] for r in rows)
-    T_c = sum(r['cv_s'] for r in rows)
-    E_p = sum(r['plain_events'] for r in rows)
-    E_c = sum(r['cv_events'] for r in rows)
-    n_eff = sum(r['cv_neff'] for r in rows)
-    n_plain = sum(r['plain_n'] for r in rows)
+            net, tr = _train(ctx, smc, torch, t_c, 1_000_000, x_scale, t_scale, seed=11)
+            beta, resid, r, alive = _held_out(ctx, net, t_c, x_scale, t_scale, seed=12, n=256)
+        rows = [_three_arms(smc, torch, test.instance(i), p, net, t_c, x_scale, t_scale, beta, conf, eps,
+                            1000 + 10 * i) for i in range(test.n_inst)]
+        T = {k: sum(rw[k]['s'] for rw in rows) for k in ('plain', 'mixed', 'cv')}
+        E = {k: sum(rw[k]['events'] for rw in rows) for k in ('plain', 'mixed', 'cv')}
+        sweep.append(dict(t_c=t_c, alive_share=alive, prefix_cost_share=r, residual_variance_share=resid,
+                          beta=beta, predicted_cost_ratio=_predicted_cost_ratio(resid, r),
+                          measured_event_ratio_cv_over_plain=E['cv'] / E['mixed'],
+                          wall_s=T, n_eff=sum(rw['cv']['n_eff'] for rw in rows),
+                          n_prefix=sum(rw['cv']['n_prefix'] for rw in rows),
+                          n_plain=sum(rw['mixed']['n'] for rw in rows), training=tr, per_instance=rows))
+    best = min(sweep, key=lambda d: d['wall_s']['cv'])
+    # birth-death survival: G[0,20](A > 0), checkpoint t = 8
+    bd, bp = workloads.birth_death_survival(1)
+    bx, bt = np.array([50.0], np.float32), 20.0
+    with smc.Context(0) as ctx:
+        ctx.load_model(bd)
+        ctx.load_property(bp)
+        bnet, btr = _train(ctx, smc, torch, 8.0, 500_000, bx, bt, seed=31)
+        bbeta, bresid, br, balive = _held_out(ctx, bnet, 8.0, bx, bt, seed=32, n=100000)
+    brows = {h: _three_arms(smc, torch, bd, bp, bnet, 8.0, bx, bt, bbeta, conf, h, 77) for h in (eps, eps / 4)}
+
+    def _bd(brow):
+        return {'measured_event_ratio_cv_over_plain': brow['cv']['events'] / (
+                    brow['cv']['n_eff'] * brow['mixed']['events'] / brow['mixed']['n']),
+                'wall_time_ratio_plain_fp64_over_cv': brow['plain']['s'] / brow['cv']['s'],
+                'wall_time_ratio_plain_mixed_over_cv': brow['mixed']['s'] / brow['cv']['s'], 'arms': brow}
     pk, src = bench.peaks()
-    _line(n_eff / T_c, 'effective trajectories/s', len(rows), 1, 1e3 * T_c / len(rows), 'mixed + bf16 surrogate',
-          'Lotka-Volterra family (rates x log-uniform [0.7,1.3]), G[0,30](X>0 & Y>0), checkpoint t=5, '
-          '95% Wilson half-width 0.002, 8 held-out instances',
-          {'plain': {'value': n_plain / T_p, 'unit': 'trajectories/s', 'seconds': T_p, 'events': E_p},
-           'control_variate': {'seconds': T_c, 'events': E_c, 'n_eff': n_eff,
-                               'wall_time_ratio_plain_over_cv': T_p / T_c,
-                               'event_ratio_plain_over_cv': E_p / E_c, 'beta': beta,
-                               'residual_variance_share': resid},
-           'training': {'snapshots': int(x.shape[0]), 'trajectories_simulated': int(used * fam.n_inst),
-                        'data_seconds': t_data, 'train_seconds': t_train, 'epochs': epochs, 'batch': batch,
-                        'loss': [float(v) for v in loss]},
+    T_c = best['wall_s']['cv']
+    tf = best['training']['tflops']
+    _line(best['n_eff'] / T_c, 'effective trajectories/s', len(best['per_instance']), 1,
+          1e3 * T_c / len(best['per_instance']), 'mixed + bf16 surrogate',
+          'Lotka-Volterra family (rates x log-uniform [0.7,1.3]), G[0,30](X>0 & Y>0), 95% Wilson half-width '
+          '0.002, 4 held-out instances; checkpoint sweep t_c in {0.5, 1, 2, 5}',
+          {'best_t_c': best['t_c'],
+           'wall_time_ratio_plain_fp64_over_cv': best['wall_s']['plain'] / T_c,
+           'wall_time_ratio_plain_mixed_over_cv': best['wall_s']['mixed'] / T_c,
+           'sweep': sweep,
+           'birth_death_survival': {
+               'workload': 'A -> 2A (1.0), A -> 0 (0.8 A), A0 = 5, G[0,20](A > 0), checkpoint t = 8',
+               'prefix_cost_share': br, 'residual_variance_share': bresid, 'beta': bbeta,
+               'predicted_cost_ratio': _predicted_cost_ratio(bresid, br),
+               'half_width_0.002': _bd(brows[eps]), 'half_width_0.0005': _bd(brows[eps / 4]),
+               'training': btr},
            'roofline': {'bound': 'tensor', 'kernel': 'surrogate training (mma.sync bf16)',
-                        'achieved': flops / t_train / 1e12, 'peak': float(pk.get('bf16_tflops', 1899.0)),
-                        'unit': 'TFLOP/s', 'frac': flops / t_train / 1e12 / float(pk.get('bf16_tflops', 1899.0)),
-                        'traffic': None, 'peak_source': f'cuBLAS bf16 burst ({src})'},
-           'per_instance': rows})
+                        'achieved': tf, 'peak': float(pk.get('bf16_tflops', 1899.0)), 'unit': 'TFLOP/s',
+                        'frac': tf / float(pk.get('bf16_tflops', 1899.0)), 'traffic': None,
+                        'peak_source': f'cuBLAS bf16 burst ({src})'}})
 
 
 def cascade(args):
@@ -242,18 +312,19 @@ def cascade(args):
     import paper_0912_2551_gb300 as smc
     import workloads
     out = {}
-    n = 2000
+    n = args.traj or 2000
     for variant in (False, True):
         m, p = workloads.mapk_cascade(256, seed=5, variant=variant)
+        name = 'variant' if variant else 'literal'
         with smc.Context(0) as ctx:
             ctx.load_model(m)
             ctx.load_property(p)
-            ms, c, wil, clk = _timed_simulate(ctx, 'mixed', n, max(1, min(args.steps, 3)), 1, seed=0)
-            msp, cp, _, _ = _timed_simulate(ctx, 'plain', 200, 1, 1, seed=0)
+            ms, c, wil, clk = _timed_simulate(ctx, 'mixed', n, max(1, min(args.steps, 3)), 1, seed=0, label=name)
+            msp, cp, _, _ = _timed_simulate(ctx, 'plain', min(n, 200), 1, 1, seed=0, label=name)
         ev = float(c[:, 2].sum())
-        out['variant' if variant else 'literal'] = dict(
+        out[name] = dict(
             ms=ms, traj_s=256 * n / (ms / 1e3), events_per_s=ev / (ms / 1e3), events_per_traj=ev / (256 * n),
-            yes=int(c[:, 0].sum()), plain_traj_s=256 * 200 / (msp / 1e3), clocks=clk)
+            yes=int(c[:, 0].sum()), plain_traj_s=256 * min(n, 200) / (msp / 1e3), clocks=clk)
     t0 = time.perf_counter()
     m, p = workloads.mapk_cascade(4, seed=5, variant=False)
     oracle.run(m, p, seed=0, instance=0, n_traj=64)
@@ -262,7 +333,7 @@ def cascade(args):
     ops = 40 + 4 + 1 + 2 + 31 + 2 + 3 * 5 + 2 * 3 + 2
     _line(lit['traj_s'], 'trajectories/s', max(1, min(args.steps, 3)), 1, lit['ms'],
           'mixed (f32 propensities, f64 clock)',
-          'three-tier cascade, 22 species, 30 reactions, 256 rate-perturbed instances x 2,000 trajectories, '
+          f'three-tier cascade, 22 species, 30 reactions, 256 rate-perturbed instances x {n:,} trajectories, '
           '(KPP<500) U[0,200] (KPP>=2000 & F[0,50] KPP<500) and the KPP<2000 variant',
           {'events_per_s': lit['events_per_s'], 'configs': out,
            'roofline': _issue_roofline(lit['events_per_s'], ops, 'ssa_kernel<mixed>'),

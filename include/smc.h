@@ -180,6 +180,29 @@ int smc_load_property(smc_ctx *ctx, int n_atoms, const int32_t *atom_coef,
                       const int32_t *atom_op, const double *atom_bound, int per_instance,
                       const smc_node *nodes, int n_nodes, double t_max_unbounded);
 
+/* Rate-law factors beyond mass action.  Sec. 2.2 uses mass-action
+ * propensities; the cell-cycle model of Sec. 5 needs rational rate laws
+ * (Michaelis-Menten and Hill terms, J + alpha y denominators).  Factor q
+ * multiplies the propensity of reaction reaction[q] by
+ *     (a0 + a1 x^n) / (b0 + b1 x^n),   x = count of species species[q],
+ * n = power[q] in 1..4, (a0, a1, b0, b1) = params[4q .. 4q+3], finite, with
+ * a0, a1, b1 >= 0 and b0 > 0 (so the factor is finite and >= 0), at most 2
+ * factors per reaction, applied in the order given:
+ *     a = c h (mass action);  per factor: xn = x, then xn *= x (n - 1
+ *     times); num = a0 + a1 xn; den = b0 + b1 xn; a = a * (num / den),
+ * every operation rounded once (FP64 on the FP64 path, FP32 on the mixed
+ * path).  A factor with a0 = 0 vanishes with its species, which lets a
+ * reaction consume a species it does not take as a mass-action reactant
+ * (e.g. Michaelis-Menten degradation: zeroth-order mass action, stoichiometry
+ * -1, factor x / (K + x)); keeping counts non-negative is the model's
+ * responsibility, as for mass action.  Applies to every instance of the model
+ * loaded with smc_load_model (host arrays, copied); a later smc_load_model
+ * clears the factors; n_factors = 0 removes them.  Errors: SMC_E_STATE before
+ * a model is loaded, SMC_E_UNSUPPORTED after smc_load_model_batch,
+ * SMC_E_INVALID_ARG for an index, power, parameter or count out of range. */
+int smc_load_rate_factors(smc_ctx *ctx, int n_factors, const int32_t *reaction, const int32_t *species,
+                          const int32_t *power, const double *params);
+
 /* Sets an SMC_OPT_* option.  Errors: SMC_E_INVALID_ARG. */
 int smc_set_option(smc_ctx *ctx, int option, double value);
 
@@ -273,11 +296,14 @@ int smc_simulate_noalloc(smc_ctx *ctx, int precision, uint64_t seed, uint64_t tr
  * was fixed before t_snap (verdict in out->verdict).  stop_at_snap != 0
  * stops every trajectory at its snapshot (prefix-only run; those are not
  * counted in out->counts and get status 2).  Device arrays: snap
- * [n_inst][n_traj] (uint8), x_snap [n_inst][n_traj][S_max] (int32).
- * out->verdict must be given.  Does not synchronise. */
+ * [n_inst][n_traj] (uint8), x_snap [n_inst][n_traj][S_max] (int32), and
+ * optionally e_snap [n_inst][n_traj] (uint32, may be null): the events up to
+ * the snapshot, or up to the verdict when it was fixed before t_snap (what a
+ * prefix-only run of that trajectory costs).  out->verdict must be given.
+ * Does not synchronise. */
 int smc_simulate_snapshot(smc_ctx *ctx, int precision, uint64_t seed, uint64_t traj_begin,
                           uint64_t n_traj, double t_snap, int stop_at_snap, const smc_sim_out *out,
-                          uint8_t *snap, int32_t *x_snap, void *stream);
+                          uint8_t *snap, int32_t *x_snap, uint32_t *e_snap, void *stream);
 
 /* Features of snapshots (single-network contexts): row (m, k) of feat
  * [n_inst * n_traj][S + 1 + R] (FP32, device) = x_snap / x_scale (S values),
@@ -307,8 +333,15 @@ int smc_mlp_gradient(smc_mlp *mlp, const float *x, const float *y, int n, float 
  * mean loss per epoch or NULL. */
 int smc_mlp_train(smc_mlp *mlp, const float *x, const float *y, uint64_t n, int epochs, int batch,
                   float lr, uint64_t seed, float *loss_host, void *stream);
-/* g[i] = network output for row i of x (device [n][n_in] -> device [n]). */
+/* g[i] = network output for row i of x (device [n][n_in] -> device [n]):
+ * one persistent launch, features rounded to BF16 as in training. */
 int smc_mlp_predict(smc_mlp *mlp, const float *x, uint64_t n, float *g, void *stream);
+/* The same, computing only rows with skip[i] == 0 (device uint8 [n], may be
+ * NULL): other entries of g are left as they were (16-row tiles whose rows
+ * all skip are not computed).  Used for trajectories decided before the
+ * checkpoint, whose control variate is their verdict. */
+int smc_mlp_predict_masked(smc_mlp *mlp, const float *x, uint64_t n, const uint8_t *skip, float *g,
+                           void *stream);
 
 /* Control-variate estimate for a single-instance context (two-phase
  * sampling): n_full trajectories run to their verdict Y, n_prefix further
@@ -317,11 +350,17 @@ int smc_mlp_predict(smc_mlp *mlp, const float *x, uint64_t n, float *g, void *st
  * beta mean_all(G), unbiased for any fixed beta.  Var is estimated from the
  * samples, n_eff = p_hat (1 - p_hat) / Var, and [lo, hi] is Eq. 4 at n_eff.
  * The sample sizes grow (cost-optimal split between full and prefix runs,
- * events per run measured) until n_eff >= Wilson_sample(p', half_width)
- * with p' = p_hat +- half_width as in Fig. 2.  Prefix runs use trajectory
- * indices from 2^31 up, full runs below 2^31.  x_scale [S] (host), t_scale:
- * feature scaling as in smc_snapshot_features; pilot: initial size of both
- * samples. */
+ * with the events per full run and per prefix run measured on the full
+ * runs) until n_eff >= Wilson_sample(p', half_width) with p' = p_hat +-
+ * half_width as in Fig. 2; prefix runs are drawn only while they lower the
+ * cost of the target variance (they do when the prefix's share of a run's
+ * cost is below the share of Var(Y) that G explains).  Prefix runs use
+ * trajectory indices from 2^31 up, full runs below 2^31.  x_scale [S]
+ * (host), t_scale: feature scaling as in smc_snapshot_features; pilot: the
+ * least first sample of full runs (>= 2; at least Fig. 2's first batch,
+ * Wilson_sample(1, half_width)); later iterations go straight to the
+ * cost-optimal sizes (at most 64x growth).  Device buffers are kept in the
+ * context for later calls. */
 typedef struct {
     double p_hat, lo, hi;
     double n_eff;      /* p_hat (1 - p_hat) / var */

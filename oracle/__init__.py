@@ -156,6 +156,19 @@ def eval_prefix(prop, S: int, x: np.ndarray, t: np.ndarray, tmin: float, closed:
                              _ptr(x, ctypes.c_int32), float(tmin), int(bool(closed)))
 
 
+def _factor_arrays(model):
+    """Rate-law factors of a workloads.Model as (reaction, species, power,
+    params[n][4]) arrays (empty for pure mass action)."""
+    fac = list(getattr(model, 'factors', None) or [])
+    fr = np.ascontiguousarray([f[0] for f in fac] or [0], np.int32)
+    fs = np.ascontiguousarray([f[1] for f in fac] or [0], np.int32)
+    fn = np.ascontiguousarray([f[2] for f in fac] or [1], np.int32)
+    fp = np.ascontiguousarray([f[3:7] for f in fac] or [[0.0, 0.0, 1.0, 0.0]], np.float64)
+    if not fac:
+        fr, fs, fn, fp = fr[:0], fs[:0], fn[:0], fp[:0]
+    return fr, fs, fn, fp
+
+
 def run(model, prop, seed: int, instance: int = 0, traj_begin: int = 0, n_traj: int = 1,
         budget: int = 1 << 40, t_max: float = float('inf'), threads: Optional[int] = None,
         want_x: bool = False):
@@ -174,6 +187,7 @@ def run(model, prop, seed: int, instance: int = 0, traj_begin: int = 0, n_traj: 
     st = np.ascontiguousarray(model.stoich, np.int32)
     nodes, root = flatten_formula(prop.formula)
     n_at, coef, op, bound = _atom_arrays(prop, S)
+    fr, fs, fn, fp = _factor_arrays(model)
     n = int(n_traj)
     out = dict(verdict=np.zeros(n, np.uint8), status=np.zeros(n, np.uint8),
                events=np.zeros(n, np.uint64), t_final=np.zeros(n, np.float64))
@@ -184,14 +198,17 @@ def run(model, prop, seed: int, instance: int = 0, traj_begin: int = 0, n_traj: 
     L = lib()
     P = ctypes.POINTER
     L.orc_run.argtypes = [ctypes.c_int, ctypes.c_int, P(ctypes.c_int32), P(ctypes.c_int32),
-                          P(ctypes.c_double), P(ctypes.c_int32), ctypes.c_int, ctypes.c_int,
+                          P(ctypes.c_double), P(ctypes.c_int32), ctypes.c_int, P(ctypes.c_int32),
+                          P(ctypes.c_int32), P(ctypes.c_int32), P(ctypes.c_double), ctypes.c_int, ctypes.c_int,
                           P(_Node), ctypes.c_int, P(ctypes.c_int32), P(ctypes.c_int32),
                           P(ctypes.c_double), ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint64,
                           ctypes.c_uint64, ctypes.c_uint64, ctypes.c_double, ctypes.c_int,
                           P(ctypes.c_uint8), P(ctypes.c_uint8), P(ctypes.c_uint64),
                           P(ctypes.c_double), P(ctypes.c_int32)]
     rc = L.orc_run(S, R, _ptr(reac, ctypes.c_int32), _ptr(st, ctypes.c_int32),
-                   _ptr(rates, ctypes.c_double), _ptr(x0, ctypes.c_int32), len(nodes), root, nodes,
+                   _ptr(rates, ctypes.c_double), _ptr(x0, ctypes.c_int32), len(fr),
+                   _ptr(fr, ctypes.c_int32), _ptr(fs, ctypes.c_int32), _ptr(fn, ctypes.c_int32),
+                   _ptr(fp, ctypes.c_double), len(nodes), root, nodes,
                    n_at, _ptr(coef, ctypes.c_int32), _ptr(op, ctypes.c_int32),
                    _ptr(bound, ctypes.c_double), int(seed) & ((1 << 64) - 1), int(instance),
                    int(traj_begin), n, int(budget), float(t_max), int(threads),

@@ -14,7 +14,9 @@
  *    (event, trajectory, instance, 0).  The paper only asks for one seed per
  *    replica (Sec. 4); the counter keying replaces that seed stream.
  *  - The SSA direct method, Sec. 2.2 steps 1-5 with Eq. 1, 2a, 2b:
- *    propensities a_j = c_j * h_j(x) recomputed from scratch every event,
+ *    propensities a_j = c_j * h_j(x) (times optional rational rate-law
+ *    factors of single species, beyond the paper's mass action) recomputed
+ *    from scratch every event,
  *    a_0 their left-to-right sum, tau = -ln(u_tau)/a_0, j the first index
  *    whose running sum exceeds u_j * a_0.
  *  - The full trace of the trajectory and the BLTLc semantics of Sec. 3.1
@@ -78,6 +80,12 @@ typedef struct {
     const int32_t *stoich;    /* [R][S] net change                          */
     const double *rates;      /* [R]                                        */
     const int32_t *x0;        /* [S]                                        */
+    /* rate-law factors (none for pure mass action): factor q multiplies the
+     * propensity of reaction fr[q] by (a0 + a1 x^n) / (b0 + b1 x^n), x the
+     * count of species fs[q], n = fn[q], (a0, a1, b0, b1) = fp[4q..4q+3]   */
+    int n_fact;
+    const int32_t *fr, *fs, *fn;
+    const double *fp;
 } orc_model;
 
 enum { K_TRUE = 0, K_FALSE, K_ATOM, K_NOT, K_AND, K_OR, K_IMPLIES, K_UNTIL, K_EVENTUALLY, K_ALWAYS };
@@ -269,7 +277,21 @@ static double propensity(const orc_model *M, int j, const int32_t *x)
     else if (ra < 0) h = x[rb];
     else if (ra == rb) h = (int64_t)x[ra] * ((int64_t)x[ra] - 1) / 2;
     else h = (int64_t)x[ra] * (int64_t)x[rb];
-    return M->rates[j] * (double)h;
+    double a = M->rates[j] * (double)h;
+    /* rate-law factors of reaction j, in the order given: x^n by repeated
+     * multiplication, then numerator, denominator, their quotient, and the
+     * product with the propensity, each rounded once */
+    for (int q = 0; q < M->n_fact; ++q) {
+        if (M->fr[q] != j) continue;
+        const double xv = (double)x[M->fs[q]];
+        double xn = xv;
+        for (int i = 1; i < M->fn[q]; ++i) xn = xn * xv;
+        const double *c = M->fp + 4 * q;
+        const double num = c[0] + c[1] * xn;
+        const double den = c[2] + c[3] * xn;
+        a = a * (num / den);
+    }
+    return a;
 }
 
 /* knowledge point q: q = 2k -> positions 0..k known, tmin = t_k;
@@ -450,13 +472,15 @@ static void *worker(void *arg)
  * Output arrays (any may be NULL) have n_traj entries (x_final: n_traj*S).
  * Returns 0, or -1 if a trajectory failed (allocation, undecided path).  */
 int orc_run(int S, int R, const int32_t *reactants, const int32_t *stoich, const double *rates,
-            const int32_t *x0, int n_nodes, int root, const orc_node *nodes, int n_atoms,
-            const int32_t *coef, const int32_t *op, const double *bound, uint64_t seed,
-            uint32_t instance, uint64_t traj_begin, uint64_t n_traj, uint64_t budget, double t_max,
-            int n_threads, uint8_t *verdict, uint8_t *status, uint64_t *events, double *t_final,
-            int32_t *x_final)
+            const int32_t *x0, int n_fact, const int32_t *fact_reaction, const int32_t *fact_species,
+            const int32_t *fact_power, const double *fact_param, int n_nodes, int root,
+            const orc_node *nodes, int n_atoms, const int32_t *coef, const int32_t *op,
+            const double *bound, uint64_t seed, uint32_t instance, uint64_t traj_begin, uint64_t n_traj,
+            uint64_t budget, double t_max, int n_threads, uint8_t *verdict, uint8_t *status,
+            uint64_t *events, double *t_final, int32_t *x_final)
 {
-    orc_model M = {S, R, reactants, stoich, rates, x0};
+    orc_model M = {S, R, reactants, stoich, rates, x0, n_fact, fact_reaction, fact_species, fact_power,
+                   fact_param};
     orc_formula f = {n_nodes, root, nodes, n_atoms, S, coef, op, bound};
     orc_job J;
     memset(&J, 0, sizeof(J));

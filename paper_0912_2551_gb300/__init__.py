@@ -117,6 +117,20 @@ class Context:
         self.s_max = model.n_species
         self._n_reactions = model.n_reactions
         self._batch = None
+        factors = list(getattr(model, 'factors', None) or [])
+        if factors:
+            self.load_rate_factors(factors)
+
+    def load_rate_factors(self, factors):
+        """Rate-law factors (reaction, species, power, a0, a1, b0, b1) for
+        the loaded model (smc_load_rate_factors)."""
+        fr = np.ascontiguousarray([f[0] for f in factors] or [0], np.int32)
+        fs = np.ascontiguousarray([f[1] for f in factors] or [0], np.int32)
+        fn = np.ascontiguousarray([f[2] for f in factors] or [1], np.int32)
+        fp = np.ascontiguousarray([list(f[3:7]) for f in factors] or [[0.0, 0.0, 1.0, 0.0]], np.float64)
+        self._check(N.smc_load_rate_factors(self.h, len(factors), _p(fr, ctypes.c_int32), _p(fs, ctypes.c_int32),
+                                            _p(fn, ctypes.c_int32), _p(fp, ctypes.c_double)),
+                    'smc_load_rate_factors')
 
     def load_batch(self, batch):
         ms = batch.models
@@ -225,8 +239,9 @@ class Context:
 
     def simulate_snapshot(self, precision: str = 'mixed', seed: int = 0, traj_begin: int = 0, n_traj: int = 1,
                           t_snap: float = 5.0, stop: bool = False, stream=None) -> Dict[str, object]:
-        """smc_simulate_snapshot: counts, verdict, status, snap and x_snap
-        (torch CUDA tensors, [n_inst, n_traj] / [n_inst, n_traj, S_max])."""
+        """smc_simulate_snapshot: counts, verdict, status, snap, x_snap and
+        e_snap (torch CUDA tensors, [n_inst, n_traj] / [n_inst, n_traj, S_max];
+        e_snap holds int32 copies of the uint32 event counts)."""
         import torch
         dev = torch.device('cuda', self.device)
         n = self.n_inst
@@ -234,7 +249,8 @@ class Context:
                    verdict=torch.zeros((n, n_traj), dtype=torch.uint8, device=dev),
                    status=torch.zeros((n, n_traj), dtype=torch.uint8, device=dev),
                    snap=torch.zeros((n, n_traj), dtype=torch.uint8, device=dev),
-                   x_snap=torch.zeros((n, n_traj, self.s_max), dtype=torch.int32, device=dev))
+                   x_snap=torch.zeros((n, n_traj, self.s_max), dtype=torch.int32, device=dev),
+                   e_snap=torch.zeros((n, n_traj), dtype=torch.int32, device=dev))
         so = N.smc_sim_out()
         so.counts = out['counts'].data_ptr()
         so.verdict = out['verdict'].data_ptr()
@@ -244,6 +260,7 @@ class Context:
                                             float(t_snap), int(bool(stop)), ctypes.byref(so),
                                             ctypes.c_void_p(out['snap'].data_ptr()),
                                             ctypes.c_void_p(out['x_snap'].data_ptr()),
+                                            ctypes.c_void_p(out['e_snap'].data_ptr()),
                                             _stream(s)), 'smc_simulate_snapshot')
         return out
 

@@ -88,6 +88,7 @@ SIGNATURES = {
                                          ctypes.c_int, ctypes.POINTER(smc_node), ctypes.c_int,
                                          ctypes.c_double]),
     'smc_set_option': (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_double]),
+    'smc_load_rate_factors': (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, c_i32p, c_i32p, c_i32p, c_f64p]),
     'smc_get_launch_shape': (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, c_i32p, c_i32p, c_i32p,
                                             c_i32p, c_i32p, c_i32p]),
     'smc_estimate': (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_double, ctypes.c_uint64,
@@ -104,7 +105,7 @@ SIGNATURES = {
     'smc_simulate_snapshot': (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_uint64, ctypes.c_uint64,
                                              ctypes.c_uint64, ctypes.c_double, ctypes.c_int,
                                              ctypes.POINTER(smc_sim_out), ctypes.c_void_p, ctypes.c_void_p,
-                                             ctypes.c_void_p]),
+                                             ctypes.c_void_p, ctypes.c_void_p]),
     'smc_snapshot_features': (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p, ctypes.c_double,
                                              ctypes.c_void_p, ctypes.c_float, ctypes.c_void_p, ctypes.c_void_p]),
     'smc_mlp_create': (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, ctypes.c_int,
@@ -120,6 +121,8 @@ SIGNATURES = {
                                      ctypes.c_void_p]),
     'smc_mlp_predict': (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p,
                                        ctypes.c_void_p]),
+    'smc_mlp_predict_masked': (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p,
+                                              ctypes.c_void_p, ctypes.c_void_p]),
     'smc_estimate_cv': (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double, ctypes.c_double,
                                        ctypes.c_uint64, ctypes.c_int, ctypes.c_double, ctypes.c_void_p,
                                        ctypes.c_float, ctypes.c_double, ctypes.c_uint64,

@@ -52,6 +52,9 @@ struct smc_ctx {
     std::vector<int32_t> reactants, stoich, x0;
     std::vector<double> rates;
     int s_max = 0;
+    // rate-law factors (smc_load_rate_factors), shared by all instances
+    std::vector<int32_t> f_reac, f_spec, f_pow;
+    std::vector<double> f_par;
 
     // property
     bool have_prop = false;
@@ -96,6 +99,24 @@ struct smc_ctx {
     float *d_feat_aux = nullptr;  // feature scales and centred log rates
     size_t feat_aux_n = 0;
     double *d_logtab = nullptr;   // table of the FP64 path's logarithm (lives with the context)
+    // control-variate estimator's buffers, grown on demand and kept (a
+    // cudaFree per call would synchronise the device)
+    struct CvBuf {
+        uint8_t *y = nullptr, *snap = nullptr;
+        int32_t *x = nullptr;
+        uint32_t *e = nullptr;
+        float *feat = nullptr, *g = nullptr;
+        uint64_t *counts = nullptr;
+        double *sums = nullptr;
+        uint64_t cap = 0;
+        int s_cap = 0, f_cap = 0;
+        void release()
+        {
+            cudaFree(y); cudaFree(snap); cudaFree(x); cudaFree(e); cudaFree(feat); cudaFree(g);
+            cudaFree(counts); cudaFree(sums);
+            *this = CvBuf();
+        }
+    } cv;
 
     // options
     uint64_t budget = 1ull << 24;
@@ -369,10 +390,16 @@ void try_specialize(smc_ctx *ctx)
     M.lo = lo0.data();
     M.hi = hi0.data();
     M.neg = neg0.data();
+    M.n_fact = (int)ctx->f_reac.size();
+    M.f_reac = ctx->f_reac.data();
+    M.f_spec = ctx->f_spec.data();
+    M.f_pow = ctx->f_pow.data();
+    M.f_par = ctx->f_par.data();
     const std::string header = smc::jit_model_header(M, ctx->jit_why);
     if (header.empty()) return;
     std::string err;
     if (smc::jit_compile(header, ctx->jit_k, err)) { ctx->jit_why = err; return; }
+    smc::jit_layout(M, ctx->jit_k.delta_bytes, ctx->jit_k.rate_count);
     ctx->jit_ready = true;
 }
 
@@ -396,6 +423,11 @@ int prepare(smc_ctx *ctx)
         M.stoich = ctx->stoich.data() + ctx->st_off[m];
         M.rates = ctx->rates.data() + ctx->rate_off[m];
         M.x0 = ctx->x0.data() + ctx->x0_off[m];
+        M.n_fact = (int)ctx->f_reac.size();
+        M.f_reac = ctx->f_reac.data();
+        M.f_spec = ctx->f_spec.data();
+        M.f_pow = ctx->f_pow.data();
+        M.f_par = ctx->f_par.data();
         std::vector<int32_t> coef((size_t)nu * M.S), op(nu);
         std::vector<double> bnd(nu);
         for (int b = 0; b < nu; ++b) {
@@ -510,9 +542,11 @@ int plan_class(smc_ctx *ctx, int plain, const SizeClass &c, const Shape &sh, Lau
     // the specialized kernel keeps counts and propensities in registers: its
     // warp slice holds only the nested operators' candidate clocks
     L.kernel = ctx->jit_ready ? (plain ? ctx->jit_k.plain : ctx->jit_k.mixed) : nullptr;
-    L.warp_bytes = L.kernel ? L.tc_bytes : warp_bytes_of(c, plain, L.tc_bytes);
+    const int rate_bytes = (ctx->jit_k.rate_count * (plain ? 8 : 4) + 15) / 16 * 16;
+    L.warp_bytes = L.kernel ? L.tc_bytes + rate_bytes : warp_bytes_of(c, plain, L.tc_bytes);
     L.block = 32 * sh.warps;
-    L.smem = (int)sizeof(MonProg) + (plain ? SMC_LOGTAB_BYTES : 0) + sh.warps * L.warp_bytes;
+    L.smem = (int)sizeof(MonProg) + (plain ? SMC_LOGTAB_BYTES : 0) + (L.kernel ? ctx->jit_k.delta_bytes : 0) +
+             sh.warps * L.warp_bytes;
     L.refill = sh.refill;
     if ((size_t)L.smem > ctx->smem_optin)
         return fail(ctx, SMC_E_UNSUPPORTED, "model tables do not fit in shared memory");
@@ -773,6 +807,7 @@ void smc_destroy(smc_ctx *ctx)
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
     free_device(ctx);
     dfree(ctx->d_logtab);
+    ctx->cv.release();
     if (ctx->stream) cudaStreamDestroy(ctx->stream);
     delete ctx;
 }
@@ -832,6 +867,10 @@ static int load_common(smc_ctx *ctx, int n_inst, const int32_t *S, const int32_t
     ctx->s_max = *std::max_element(Sv.begin(), Sv.end());
     ctx->batch = !same_network;
     ctx->have_model = true;
+    ctx->f_reac.clear();
+    ctx->f_spec.clear();
+    ctx->f_pow.clear();
+    ctx->f_par.clear();
     ctx->have_prop = false;  // atoms refer to the species of the model
     ctx->dirty = true;
     return SMC_OK;
@@ -841,6 +880,37 @@ int smc_load_model(smc_ctx *ctx, int n_species, int n_reactions, const int32_t *
                    const int32_t *stoich, const double *rates, const int32_t *x0, int n_instances)
 {
     return load_common(ctx, n_instances, &n_species, &n_reactions, reactants, stoich, rates, x0, true);
+}
+
+int smc_load_rate_factors(smc_ctx *ctx, int n_factors, const int32_t *reaction, const int32_t *species,
+                          const int32_t *power, const double *params)
+{
+    if (!ctx) return SMC_E_INVALID_ARG;
+    if (!ctx->have_model) return fail(ctx, SMC_E_STATE, "load a model first");
+    if (ctx->batch) return fail(ctx, SMC_E_UNSUPPORTED, "rate-law factors need a single network");
+    if (n_factors < 0 || (n_factors > 0 && (!reaction || !species || !power || !params)))
+        return fail(ctx, SMC_E_INVALID_ARG, "bad factor arrays");
+    const int S = ctx->S[0], R = ctx->R[0];
+    std::vector<int> per(R, 0);
+    for (int q = 0; q < n_factors; ++q) {
+        if (reaction[q] < 0 || reaction[q] >= R || species[q] < 0 || species[q] >= S)
+            return fail(ctx, SMC_E_INVALID_ARG, "factor reaction or species out of range");
+        if (power[q] < 1 || power[q] > SMC_MAX_FACTOR_POWER)
+            return fail(ctx, SMC_E_INVALID_ARG, "factor power must be 1..4");
+        if (++per[reaction[q]] > SMC_MAX_FACTORS_PER_REACTION)
+            return fail(ctx, SMC_E_INVALID_ARG, "at most 2 factors per reaction");
+        const double *c = params + 4 * q;
+        for (int i = 0; i < 4; ++i)
+            if (!std::isfinite(c[i])) return fail(ctx, SMC_E_INVALID_ARG, "factor parameters must be finite");
+        if (!(c[0] >= 0.0 && c[1] >= 0.0 && c[2] > 0.0 && c[3] >= 0.0))
+            return fail(ctx, SMC_E_INVALID_ARG, "factor needs a0, a1, b1 >= 0 and b0 > 0");
+    }
+    ctx->f_reac.assign(reaction, reaction + n_factors);
+    ctx->f_spec.assign(species, species + n_factors);
+    ctx->f_pow.assign(power, power + n_factors);
+    ctx->f_par.assign(params, params + 4 * (size_t)n_factors);
+    ctx->dirty = true;
+    return SMC_OK;
 }
 
 int smc_load_model_batch(smc_ctx *ctx, int n_instances, const int32_t *n_species,
@@ -1295,7 +1365,7 @@ int smc_monitor_replay(smc_ctx *ctx, int n_paths, const int32_t *len, const int3
 
 int smc_simulate_snapshot(smc_ctx *ctx, int precision, uint64_t seed, uint64_t traj_begin, uint64_t n_traj,
                           double t_snap, int stop_at_snap, const smc_sim_out *out, uint8_t *snap,
-                          int32_t *x_snap, void *stream)
+                          int32_t *x_snap, uint32_t *e_snap, void *stream)
 {
     if (!ctx) return SMC_E_INVALID_ARG;
     if (!out || !out->counts || !out->verdict || !snap || !x_snap)
@@ -1318,6 +1388,7 @@ int smc_simulate_snapshot(smc_ctx *ctx, int precision, uint64_t seed, uint64_t t
     pc.t_snap = t_snap;
     pc.o_snap = snap;
     pc.o_xsnap = x_snap;
+    pc.o_esnap = e_snap;
     for (const SizeClass *c : active_classes(ctx, plain)) {
         Launch L;
         rc = plan_class(ctx, plain, *c, c->shape[plain], L);
@@ -1388,36 +1459,33 @@ int smc_estimate_cv(smc_ctx *ctx, smc_mlp *mlp, double confidence, double half_w
     if (rc) return rc;
     CK(cudaSetDevice(ctx->device));
     cudaStream_t s = ctx->stream;
-    // device buffers, grown on demand
-    struct Buf {
-        uint8_t *y = nullptr, *snap = nullptr;
-        int32_t *x = nullptr;
-        float *feat = nullptr, *g = nullptr;
-        uint64_t *counts = nullptr;
-        double *sums = nullptr;
-        uint64_t cap = 0;
-        ~Buf()
-        {
-            cudaFree(y); cudaFree(snap); cudaFree(x); cudaFree(feat); cudaFree(g); cudaFree(counts); cudaFree(sums);
-        }
-    } b;
+    // device buffers of the context, grown on demand
+    auto &b = ctx->cv;
     auto grow = [&](uint64_t n) -> int {
-        if (n <= b.cap) return SMC_OK;
-        uint64_t c = std::max<uint64_t>(n, 2 * b.cap);
-        cudaFree(b.y); cudaFree(b.snap); cudaFree(b.x); cudaFree(b.feat); cudaFree(b.g);
-        b.y = b.snap = nullptr; b.x = nullptr; b.feat = b.g = nullptr;
+        if (n <= b.cap && ctx->s_max <= b.s_cap && F <= b.f_cap) return SMC_OK;
+        const uint64_t c = std::max<uint64_t>(n, 2 * b.cap);
+        uint64_t *counts = b.counts;
+        double *sums = b.sums;
+        b.counts = nullptr;
+        b.sums = nullptr;
+        b.release();
+        b.counts = counts;
+        b.sums = sums;
         CK(cudaMalloc(&b.y, c));
         CK(cudaMalloc(&b.snap, c));
         CK(cudaMalloc(&b.x, c * ctx->s_max * 4));
+        CK(cudaMalloc(&b.e, c * 4));
         CK(cudaMalloc(&b.feat, c * F * 4));
         CK(cudaMalloc(&b.g, c * 4));
         b.cap = c;
+        b.s_cap = ctx->s_max;
+        b.f_cap = F;
         return SMC_OK;
     };
-    CK(cudaMalloc(&b.counts, 2 * 4 * 8));
-    CK(cudaMalloc(&b.sums, 12 * 8));
+    if (!b.counts) CK(cudaMalloc(&b.counts, 2 * 4 * 8));
+    if (!b.sums) CK(cudaMalloc(&b.sums, 14 * 8));
     CK(cudaMemsetAsync(b.counts, 0, 2 * 4 * 8, s));
-    CK(cudaMemsetAsync(b.sums, 0, 12 * 8, s));
+    CK(cudaMemsetAsync(b.sums, 0, 14 * 8, s));
     // runs trajectories [lo, hi) (full or prefix-only) and accumulates their sums
     auto run = [&](uint64_t lo, uint64_t hi, bool prefix) -> int {
         if (hi <= lo) return SMC_OK;
@@ -1428,18 +1496,22 @@ int smc_estimate_cv(smc_ctx *ctx, smc_mlp *mlp, double confidence, double half_w
         std::memset(&o, 0, sizeof(o));
         o.counts = b.counts + (prefix ? 4 : 0);
         o.verdict = b.y;
-        r = smc_simulate_snapshot(ctx, precision, seed, lo, n, t_snap, prefix ? 1 : 0, &o, b.snap, b.x, s);
+        r = smc_simulate_snapshot(ctx, precision, seed, lo, n, t_snap, prefix ? 1 : 0, &o, b.snap, b.x, b.e, s);
         if (r) return r;
         r = smc_snapshot_features(ctx, n, b.x, t_snap, x_scale, t_scale, b.feat, s);
         if (r) return r;
-        if (smc_mlp_predict(mlp, b.feat, n, b.g, s) != SMC_OK)
+        if (smc_mlp_predict_masked(mlp, b.feat, n, b.snap, b.g, s) != SMC_OK)
             return fail(ctx, SMC_E_CUDA, std::string("surrogate prediction: ") + smc_mlp_last_error(mlp));
-        if (smc_launch_cv_sums(n, b.y, b.snap, b.g, prefix ? 1 : 0, b.sums + (prefix ? 6 : 0), s))
+        if (smc_launch_cv_sums(n, b.y, b.snap, b.g, b.e, prefix ? 1 : 0, b.sums + (prefix ? 7 : 0), s))
             return fail(ctx, SMC_E_CUDA, "cv sums launch failed");
         return SMC_OK;
     };
-    uint64_t n1 = 0, n2 = 0, want1 = pilot, want2 = pilot;
-    double hs[12];
+    // pilot: full runs only, at least Fig. 2's first batch (W_s at p = 1);
+    // they also measure what a prefix run would cost.  Every iteration pays
+    // the latency of its longest trajectory, so the loop jumps to the
+    // cost-optimal sizes rather than creeping towards them.
+    uint64_t n1 = 0, n2 = 0, want1 = std::max<uint64_t>(pilot, wilson_sample_n(1.0, half_width, z)), want2 = 0;
+    double hs[14];
     uint64_t hc[8];
     int iters = 0;
     double p = 0.0, V = 0.0, neff = 0.0;
@@ -1457,7 +1529,8 @@ int smc_estimate_cv(smc_ctx *ctx, smc_mlp *mlp, double confidence, double half_w
         CK(cudaStreamSynchronize(s));
         // S1: full runs (Y, G); S2: prefix runs (G only)
         const double c1n = hs[0], sY = hs[1], sG1 = hs[2], sYY = hs[3], sGG1 = hs[4], sYG = hs[5];
-        const double c2n = hs[6], sG2 = hs[8], sGG2 = hs[10];
+        const double sE1 = hs[6];  // events the full runs spent up to the snapshot (or their verdict)
+        const double c2n = hs[7], sG2 = hs[9], sGG2 = hs[11];
         const double nn = c1n + c2n;
         const double mD = (sY - beta * sG1) / c1n, mG1 = sG1 / c1n, mG = (sG1 + sG2) / nn;
         p = mD + beta * mG;
@@ -1473,7 +1546,7 @@ int smc_estimate_cv(smc_ctx *ctx, smc_mlp *mlp, double confidence, double half_w
         const double target = wilson_sample_real(pp, half_width, z);
         if (neff >= target || iters >= 64) break;
         // cost-optimal sizes for the target variance (events per run measured)
-        const double c_full = std::max(1.0, (double)hc[2] / c1n), c_pre = std::max(1.0, (double)hc[6] / c2n);
+        const double c_full = std::max(1.0, (double)hc[2] / c1n), c_pre = std::max(1.0, sE1 / c1n);
         const double dcost = std::max(c_full - c_pre, 1e-3 * c_full);
         uint64_t t1, t2;
         if (!interior) {  // no variance information yet: grow the full sample as Fig. 2 does
@@ -1487,8 +1560,9 @@ int smc_estimate_cv(smc_ctx *ctx, smc_mlp *mlp, double confidence, double half_w
             t1 = (uint64_t)std::ceil(o1);
             t2 = (uint64_t)std::ceil(std::max(0.0, on - o1));
         }
-        want1 = std::min(std::max(t1, n1 + 1), 4 * n1);
-        want2 = std::min(std::max(t2, n2), 4 * std::max<uint64_t>(n2, 1));
+        // at most 64x per iteration (a guard against a wild early estimate)
+        want1 = std::min(std::max(t1, n1 + 1), 64 * n1);
+        want2 = std::min(std::max(t2, n2), 64 * std::max(n2, n1));
     }
     out->p_hat = p;
     out->var = V;

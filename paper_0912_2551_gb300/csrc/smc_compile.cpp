@@ -350,13 +350,34 @@ int build_blob(const InstanceModel &M, int n_used, const int32_t *coef_used /*[n
         else if (ra == rb) homo = 1;
         pw[k] = (uint32_t)k | ((uint32_t)ra << 8) | ((uint32_t)rb << 16) | (homo << 24);
     }
+    // rate-law factors: CSR by reaction (in the given order within a reaction)
+    std::vector<uint32_t> f_ptr(R + 1, 0), f_words;
+    std::vector<double> f_d;
+    std::vector<float> f_f;
+    std::vector<std::vector<int>> f_species(R);
+    for (int k = 0; k < R; ++k) {
+        f_ptr[k] = (uint32_t)f_words.size();
+        for (int q = 0; q < M.n_fact; ++q) {
+            if (M.f_reac[q] != k) continue;
+            f_words.push_back((uint32_t)M.f_spec[q] | ((uint32_t)M.f_pow[q] << 8));
+            for (int c = 0; c < 4; ++c) {
+                f_d.push_back(M.f_par[4 * q + c]);
+                f_f.push_back((float)M.f_par[4 * q + c]);
+            }
+            f_species[k].push_back(M.f_spec[q]);
+            pw[k] |= SMC_PW_FACT;
+        }
+    }
+    f_ptr[R] = (uint32_t)f_words.size();
     // dependency graph: k in dep(j) iff a_k reads a species that j changes
     std::vector<uint32_t> dep_ptr(R + 1, 0), dep;
     for (int j = 0; j < R; ++j) {
         dep_ptr[j] = (uint32_t)dep.size();
         for (int k = 0; k < R; ++k) {
             const int ra = M.reactants[2 * k], rb = M.reactants[2 * k + 1];
-            if ((ra >= 0 && changes[j][ra]) || (rb >= 0 && changes[j][rb])) dep.push_back(pw[k]);
+            bool reads = (ra >= 0 && changes[j][ra]) || (rb >= 0 && changes[j][rb]);
+            for (int m : f_species[k]) reads = reads || changes[j][m];
+            if (reads) dep.push_back(pw[k]);
         }
     }
     dep_ptr[R] = (uint32_t)dep.size();
@@ -446,6 +467,23 @@ int build_blob(const InstanceModel &M, int n_used, const int32_t *coef_used /*[n
             blob.push_back((uint32_t)v);
             blob.push_back((uint32_t)(v >> 32));
         }
+    }
+    section(BH_FACT_PTR);
+    blob.insert(blob.end(), f_ptr.begin(), f_ptr.end());
+    section(BH_FACT);
+    blob.insert(blob.end(), f_words.begin(), f_words.end());
+    section(BH_FACT_D);
+    for (double v : f_d) {
+        uint32_t w[2];
+        std::memcpy(w, &v, 8);
+        blob.push_back(w[0]);
+        blob.push_back(w[1]);
+    }
+    section(BH_FACT_F);
+    for (float v : f_f) {
+        uint32_t w;
+        std::memcpy(&w, &v, 4);
+        blob.push_back(w);
     }
     while (blob.size() & 3) blob.push_back(0);
     blob[BH_S] = (uint32_t)S;

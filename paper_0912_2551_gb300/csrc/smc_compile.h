@@ -23,6 +23,10 @@ struct InstanceModel {
     const int32_t *stoich = nullptr;     // [R][S]
     const double *rates = nullptr;       // [R]
     const int32_t *x0 = nullptr;         // [S]
+    // rate-law factors (may be empty): reaction, species, power, params [4]
+    int n_fact = 0;
+    const int32_t *f_reac = nullptr, *f_spec = nullptr, *f_pow = nullptr;
+    const double *f_par = nullptr;
 };
 
 int parse_formula(const smc_node *nodes, int n_nodes, int n_atoms, std::vector<FNode> &tree,

@@ -70,8 +70,19 @@ enum BlobHdr {
     BH_ATOM,      // u32    [NA][6]  atom record (below)
     BH_DENSE,     // u32    [R][2]   small networks only (else offset 0): the
                   //                 net changes of species 0..7 as int8 bytes
-    BH_COUNT = 20
+    BH_FACT_PTR,  // u32    [R+1]    CSR row pointers of the rate-law factors
+    BH_FACT,      // u32    [nf]     species | (power << 8) of factor q
+    BH_FACT_D,    // double [nf][4]  a0, a1, b0, b1 of factor q
+    BH_FACT_F,    // float  [nf][4]  the same, rounded to FP32
+    BH_COUNT = 24
 };
+// Rate-law factors: reaction k's propensity is c_k h_k(x) times, for each of
+// its factors q in order, (a0 + a1 x^n) / (b0 + b1 x^n) with x the count of
+// the factor's species; propensity words of reactions with factors carry
+// bit 25 (SMC_PW_FACT).
+#define SMC_PW_FACT (1u << 25)
+#define SMC_MAX_FACTORS_PER_REACTION 2
+#define SMC_MAX_FACTOR_POWER 4
 // Small networks (S <= 8, R <= 8, |v_ji| <= 127) are stepped with warp-uniform
 // loops: every propensity recomputed per event, selection on the prefix sums
 // kept in registers, stoichiometry from the dense byte rows.
@@ -131,6 +142,8 @@ struct SsaParams {
     double t_snap;
     uint8_t *o_snap;             // [n_inst][out_stride]
     int32_t *o_xsnap;            // [n_inst][out_stride][x_stride]
+    uint32_t *o_esnap;           // [n_inst][out_stride] events up to the snapshot
+                                 // (or to the verdict, if fixed before t_snap); may be null
 };
 
 // Monitor replay (tests): runs the compiled monitor over given paths.
@@ -164,8 +177,8 @@ int smc_launch_log_batch(const double *tab, const double *u, uint64_t n, double 
 int smc_launch_snapshot_features(uint64_t n_rows, uint64_t n_traj, int S, int R, int x_stride,
                                  const int32_t *x_snap, const float *x_scale, float t_feat,
                                  const float *lograte, float *feat, void *stream);
-int smc_launch_cv_sums(uint64_t n, const uint8_t *y, const uint8_t *snap, const float *g, int prefix,
-                       double *sums, void *stream);
+int smc_launch_cv_sums(uint64_t n, const uint8_t *y, const uint8_t *snap, const float *g, const uint32_t *e_pre,
+                       int prefix, double *sums, void *stream);
 // model-specialized kernels (smc_jit.cpp): the same contract as the three
 // above, for a kernel handle returned by smc::jit_compile
 int smc_jit_set_smem_limit(void *kernel, int smem_bytes);

@@ -67,6 +67,29 @@ std::map<std::string, JitKernels> g_cache;  // generated header -> kernels (neve
 
 }  // namespace
 
+namespace {
+// exact hexadecimal literals (C++17)
+std::string hex_double(double v)
+{
+    char b[64];
+    std::snprintf(b, sizeof(b), "%a", v);
+    return b;
+}
+std::string hex_float(double v)
+{
+    char b[64];
+    std::snprintf(b, sizeof(b), "%af", (double)(float)v);
+    return b;
+}
+}  // namespace
+
+void jit_layout(const JitModel &M, int &delta_bytes, int &rate_count)
+{
+    const bool medium = M.S > SMC_JIT_SMALL || M.R > SMC_JIT_SMALL;
+    delta_bytes = medium ? (M.R * ((M.S + 3) / 4) * 4 + 15) / 16 * 16 : 0;
+    rate_count = medium ? M.R : 0;
+}
+
 std::string jit_model_header(const JitModel &M, std::string &why)
 {
     const int S = M.S, R = M.R;
@@ -74,9 +97,42 @@ std::string jit_model_header(const JitModel &M, std::string &why)
         why = "network larger than the specialized kernels' limit";
         return "";
     }
+    const bool medium = S > SMC_JIT_SMALL || R > SMC_JIT_SMALL;
+    for (int k = 0; medium && k < R; ++k)
+        for (int i = 0; i < S; ++i) {
+            const int32_t v = M.stoich[(size_t)k * S + i];
+            if (v > 127 || v < -127) {
+                why = "net change outside the specialized kernels' int8 table";
+                return "";
+            }
+        }
     std::ostringstream o;
     o << "// generated: one network structure as code (see smc_jit_kernel.cuh)\n#pragma once\n";
     o << "#define JS " << S << "\n#define JR " << R << "\n#define JNA " << M.n_atoms << "\n";
+    if (medium) {
+        // net changes of reaction j as int8 bytes, (S + 3) / 4 words per row
+        const int W = (S + 3) / 4;
+        o << "#define JIT_MEDIUM 1\n#define JW " << W << "\n";
+        o << "__device__ const uint32_t kJitDelta[" << R * W << "] = {";
+        for (int k = 0; k < R; ++k)
+            for (int w = 0; w < W; ++w) {
+                uint32_t word = 0;
+                for (int b = 0; b < 4; ++b) {
+                    const int i = 4 * w + b;
+                    if (i < S) word |= (uint32_t)(uint8_t)(int8_t)M.stoich[(size_t)k * S + i] << (8 * b);
+                }
+                o << (k || w ? ", " : "") << word << "u";
+            }
+        o << "};\n";
+        o << "__device__ __forceinline__ void jit_apply_row(const uint32_t *row, int32_t *x)\n{\n";
+        for (int i = 0; i < S; ++i) {
+            bool any = false;
+            for (int k = 0; k < R; ++k) any = any || M.stoich[(size_t)k * S + i] != 0;
+            if (any)
+                o << "    x[" << i << "] += (int32_t)(int8_t)(row[" << i / 4 << "] >> " << 8 * (i % 4) << ");\n";
+        }
+        o << "}\n";
+    }
     // propensities, both precisions, in the generic kernel's arithmetic
     for (int plain = 1; plain >= 0; --plain) {
         const char *T = plain ? "double" : "float";
@@ -102,6 +158,25 @@ std::string jit_model_header(const JitModel &M, std::string &why)
                     o << "    a = __fmul_rn(c[" << k << "], " << h.str() << ");\n";
                 }
             }
+            // rate-law factors of reaction k, in order, as in the generic kernel
+            for (int q = 0; q < M.n_fact; ++q) {
+                if (M.f_reac[q] != k) continue;
+                const double *c = M.f_par + 4 * q;
+                const int m = M.f_spec[q];
+                if (plain) {
+                    o << "    { const double xv = int_to_double((long long)x[" << m << "]); double xn = xv;";
+                    for (int i = 1; i < M.f_pow[q]; ++i) o << " xn = __dmul_rn(xn, xv);";
+                    o << "\n      a = __dmul_rn(a, __ddiv_rn(__dadd_rn(" << hex_double(c[0]) << ", __dmul_rn("
+                      << hex_double(c[1]) << ", xn)), __dadd_rn(" << hex_double(c[2]) << ", __dmul_rn("
+                      << hex_double(c[3]) << ", xn)))); }\n";
+                } else {
+                    o << "    { const float xv = (float)x[" << m << "]; float xn = xv;";
+                    for (int i = 1; i < M.f_pow[q]; ++i) o << " xn = __fmul_rn(xn, xv);";
+                    o << "\n      a = __fmul_rn(a, __fdiv_rn(__fadd_rn(" << hex_float(c[0]) << ", __fmul_rn("
+                      << hex_float(c[1]) << ", xn)), __fadd_rn(" << hex_float(c[2]) << ", __fmul_rn("
+                      << hex_float(c[3]) << ", xn)))); }\n";
+                }
+            }
             o << "    pos |= (uint32_t)(" << (plain ? "__double_as_longlong(a) > 0" : "a > 0.0f") << ") << " << k
               << ";\n";
             if (k == 0) o << "    acc = a;\n";
@@ -110,15 +185,17 @@ std::string jit_model_header(const JitModel &M, std::string &why)
         }
         o << "}\n";
     }
-    // x += v_j as selects (no divergent branch on j)
+    // x += v_j as selects (no divergent branch on j); medium networks use the
+    // table above instead
     o << "__device__ __forceinline__ void jit_apply(int j, int32_t *x)\n{\n";
+    if (medium) o << "    (void)j; (void)x;\n";
     for (int i = 0; i < S; ++i) {
         std::ostringstream d;
         for (int k = 0; k < R; ++k) {
             const int32_t v = M.stoich[(size_t)k * S + i];
             if (v) d << (d.tellp() > 0 ? " + " : "") << "(j == " << k << " ? " << v << " : 0)";
         }
-        if (d.tellp() > 0) o << "    x[" << i << "] += " << d.str() << ";\n";
+        if (d.tellp() > 0 && !medium) o << "    x[" << i << "] += " << d.str() << ";\n";
     }
     o << "}\n";
     // atoms: (lo <= L <= hi) xor neg, L = sum coef x (exact int64)

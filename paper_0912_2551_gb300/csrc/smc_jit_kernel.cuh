@@ -17,14 +17,40 @@
 #include "smc_device.cuh"
 #include "smc_jit_model.h"
 
+// Medium networks (JIT_MEDIUM: more than 8 species or reactions): the fired
+// reaction's net changes come from kJitDelta staged in shared memory (one
+// row of JW words per reaction), the rates from a per-warp shared-memory
+// slice, and the launch keeps 2 blocks of 256 threads per SM (128 registers
+// per thread for the counts and the prefix sums).
+#ifdef JIT_MEDIUM
+#define JIT_DELTA_BYTES ((JR * JW * 4 + 15) / 16 * 16)
+#define JIT_MINB_PLAIN 2
+#define JIT_MINB_MIXED 2
+#else
+#define JIT_DELTA_BYTES 0
+#define JIT_MINB_PLAIN 3
+#define JIT_MINB_MIXED 4
+#endif
+
 namespace {
 
 template <bool PLAIN>
 __device__ __forceinline__ void jit_run_instance(const SsaParams &p, const MonProg &P, const double *ltab,
-                                                 const int m, double *tc, const int lane)
+                                                 const int m, double *tc, typename Prec<PLAIN>::T *crate,
+                                                 const uint32_t *sdelta, const int lane)
 {
     typedef typename Prec<PLAIN>::T T;
     const uint32_t *blob = p.blobs + p.blob_off[m];
+#ifdef JIT_MEDIUM
+    T *c = crate;  // the instance's rates in the warp's shared-memory slice
+    {
+        const T *rg = reinterpret_cast<const T *>(blob + blob[PLAIN ? BH_RATE_D : BH_RATE_F]);
+        for (int k = lane; k < JR; k += 32) c[k] = rg[k];
+        __syncwarp();
+    }
+#else
+    (void)crate;
+    (void)sdelta;
     T c[JR];
     if constexpr (PLAIN) {
         const double *rd = reinterpret_cast<const double *>(blob + blob[BH_RATE_D]);
@@ -35,6 +61,7 @@ __device__ __forceinline__ void jit_run_instance(const SsaParams &p, const MonPr
 #pragma unroll
         for (int k = 0; k < JR; ++k) c[k] = rf[k];
     }
+#endif
     const int32_t *x0 = reinterpret_cast<const int32_t *>(blob + blob[BH_X0]);
     const unsigned long long tend = p.uniform ? p.u_end : p.tend[m];
     const bool always_step = P.has_lower != 0;
@@ -70,7 +97,10 @@ __device__ __forceinline__ void jit_run_instance(const SsaParams &p, const MonPr
                 for (int i = 0; i < JS; ++i) p.o_xfinal[idx * p.x_stride + i] = x[i];
             }
         }
-        if (snap_mode && !snapped) p.o_snap[idx] = 1;  // decided before t_snap
+        if (snap_mode && !snapped) {  // decided before t_snap
+            p.o_snap[idx] = 1;
+            if (p.o_esnap) p.o_esnap[idx] = e;
+        }
         active = false;
     };
 
@@ -137,6 +167,7 @@ __device__ __forceinline__ void jit_run_instance(const SsaParams &p, const MonPr
             snapped = true;
             const uint64_t idx = (uint64_t)m * p.out_stride + ((uint64_t)traj - p.out_base);
             p.o_snap[idx] = 0;
+            if (p.o_esnap) p.o_esnap[idx] = e;
 #pragma unroll
             for (int i = 0; i < JS; ++i) p.o_xsnap[idx * p.x_stride + i] = x[i];
             if (snap_mode == 2) { finish(4); continue; }
@@ -160,7 +191,11 @@ __device__ __forceinline__ void jit_run_instance(const SsaParams &p, const MonPr
         if (j < 0) j = 31 - __clz(pos);  // r reached the full sum: last positive a_k
 
         // step 4: x += v_j, then the monitor at the new state
+#ifdef JIT_MEDIUM
+        jit_apply_row(sdelta + j * JW, x);
+#else
         jit_apply(j, x);
+#endif
         ++e;
         t = tn;
         const uint32_t ab = jit_atoms(x);
@@ -192,15 +227,25 @@ __device__ __forceinline__ void jit_kernel_body(const SsaParams &p)
     const MonProg &P = *reinterpret_cast<const MonProg *>(smem);
     const double *ltab = reinterpret_cast<const double *>(smem + sizeof(MonProg));
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    // warp slice: the nested operators' candidate clocks tc[units][32]
-    double *tc = reinterpret_cast<double *>(smem + sizeof(MonProg) + p.logtab_bytes +
-                                            (size_t)warp * p.warp_bytes) + lane;
+    // block: monitor program | logarithm table (FP64 path) | net-change table
+    // (medium networks) | warp slices
+    uint32_t *sdelta = reinterpret_cast<uint32_t *>(smem + sizeof(MonProg) + p.logtab_bytes);
+#ifdef JIT_MEDIUM
+    for (int i = threadIdx.x; i < JR * JW; i += blockDim.x) sdelta[i] = kJitDelta[i];
+    __syncthreads();
+#endif
+    // warp slice: the nested operators' candidate clocks tc[units][32], then
+    // (medium networks) the current instance's rates
+    unsigned char *ws = smem + sizeof(MonProg) + p.logtab_bytes + JIT_DELTA_BYTES + (size_t)warp * p.warp_bytes;
+    double *tc = reinterpret_cast<double *>(ws) + lane;
+    typedef typename Prec<PLAIN>::T T;
+    T *crate = reinterpret_cast<T *>(ws + p.tc_bytes);
     bool first = true;
     const int gw = blockIdx.x * (blockDim.x >> 5) + warp;
     for (;;) {
         const int m = acquire_instance(p, first, gw, lane);
         if (m < 0) break;
-        jit_run_instance<PLAIN>(p, P, ltab, m, tc, lane);
+        jit_run_instance<PLAIN>(p, P, ltab, m, tc, crate, sdelta, lane);
         __syncwarp();
     }
     wilson_epilogue(p, &s_last);
@@ -208,12 +253,12 @@ __device__ __forceinline__ void jit_kernel_body(const SsaParams &p)
 
 }  // namespace
 
-extern "C" __global__ void __launch_bounds__(256, 3) smc_jit_ssa_plain(const SsaParams p)
+extern "C" __global__ void __launch_bounds__(256, JIT_MINB_PLAIN) smc_jit_ssa_plain(const SsaParams p)
 {
     jit_kernel_body<true>(p);
 }
 
-extern "C" __global__ void __launch_bounds__(256, 4) smc_jit_ssa_mixed(const SsaParams p)
+extern "C" __global__ void __launch_bounds__(256, JIT_MINB_MIXED) smc_jit_ssa_mixed(const SsaParams p)
 {
     jit_kernel_body<false>(p);
 }

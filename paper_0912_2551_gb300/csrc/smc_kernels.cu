@@ -33,24 +33,62 @@
 namespace {
 
 
-// a_k = c_k h_k(x) (Sec. 2.2) from a propensity word (see smc_internal.h).
-// FP64 path: h as an exact integer, rounded once; mixed path: h in FP32.
+// Rate-law factors of reaction k applied to a (in order): a *= (a0 + a1 x^n)
+// / (b0 + b1 x^n), x^n by repeated multiplication, every operation rounded
+// once (FP64 path: FP64; mixed path: FP32).
+template <bool PLAIN>
+__device__ __noinline__ typename Prec<PLAIN>::T apply_factors(typename Prec<PLAIN>::T a, int k,
+                                                              const int32_t *xs, const uint32_t *blob)
+{
+    const uint32_t *fp = blob + blob[BH_FACT_PTR];
+    const uint32_t *fw = blob + blob[BH_FACT];
+    for (uint32_t q = fp[k], qe = fp[k + 1]; q < qe; ++q) {
+        const uint32_t w = fw[q];
+        const int32_t x = xs[(w & 255u) * 32];
+        const int n = (int)(w >> 8);
+        if (PLAIN) {
+            const double *c = reinterpret_cast<const double *>(blob + blob[BH_FACT_D]) + 4 * q;
+            const double xv = int_to_double(x);
+            double xn = xv;
+            for (int i = 1; i < n; ++i) xn = __dmul_rn(xn, xv);
+            const double num = __dadd_rn(c[0], __dmul_rn(c[1], xn));
+            const double den = __dadd_rn(c[2], __dmul_rn(c[3], xn));
+            a = (typename Prec<PLAIN>::T)__dmul_rn((double)a, __ddiv_rn(num, den));
+        } else {
+            const float *c = reinterpret_cast<const float *>(blob + blob[BH_FACT_F]) + 4 * q;
+            const float xv = (float)x;
+            float xn = xv;
+            for (int i = 1; i < n; ++i) xn = __fmul_rn(xn, xv);
+            const float num = __fadd_rn(c[0], __fmul_rn(c[1], xn));
+            const float den = __fadd_rn(c[2], __fmul_rn(c[3], xn));
+            a = (typename Prec<PLAIN>::T)__fmul_rn((float)a, __fdiv_rn(num, den));
+        }
+    }
+    return a;
+}
+
+// a_k = c_k h_k(x) (Sec. 2.2) from a propensity word (see smc_internal.h),
+// times the reaction's rate-law factors if it has any.  FP64 path: h as an
+// exact integer, rounded once; mixed path: h in FP32.
 template <bool PLAIN>
 __device__ __forceinline__ typename Prec<PLAIN>::T propensity(uint32_t pw, const int32_t *xs,
                                                               const double *rate_d,
-                                                              const float *rate_f)
+                                                              const float *rate_f, const uint32_t *blob)
 {
     const int k = pw & 255u, ra = (pw >> 8) & 255u, rb = (pw >> 16) & 255u;
     const int homo = (pw >> 24) & 1u;
     const int32_t xa = xs[ra * 32], xb = xs[rb * 32];
+    typename Prec<PLAIN>::T a;
     if (PLAIN) {
         const long long h = ((long long)xa * (long long)(xb - homo)) >> homo;
-        return __dmul_rn(rate_d[k], int_to_double(h));
+        a = __dmul_rn(rate_d[k], int_to_double(h));
     } else {
         const float s = homo ? 0.5f : 1.0f;
         const float h = __fmul_rn((float)xa, __fmaf_rn((float)xb, s, homo ? -0.5f : 0.0f));
-        return __fmul_rn(rate_f[k], h);
+        a = __fmul_rn(rate_f[k], h);
     }
+    if (pw & SMC_PW_FACT) a = apply_factors<PLAIN>(a, k, xs, blob);
+    return a;
 }
 
 template <bool PLAIN>
@@ -107,7 +145,10 @@ __device__ __forceinline__ void run_instance(const SsaParams &p, const MonProg &
             if (p.o_xfinal)
                 for (int i = 0; i < S; ++i) p.o_xfinal[idx * p.x_stride + i] = xs[i * 32];
         }
-        if (snap_mode && !snapped) p.o_snap[idx] = 1;  // decided before t_snap
+        if (snap_mode && !snapped) {  // decided before t_snap
+            p.o_snap[idx] = 1;
+            if (p.o_esnap) p.o_esnap[idx] = e;
+        }
         active = false;
     };
 
@@ -134,7 +175,7 @@ __device__ __forceinline__ void run_instance(const SsaParams &p, const MonProg &
                         xs[S * 32] = 1;
                         double s = 0.0;
                         for (int k = 0; k < R; ++k) {
-                            const T ak = propensity<PLAIN>(reac[k], xs, rate_d, rate_f);
+                            const T ak = propensity<PLAIN>(reac[k], xs, rate_d, rate_f, blob);
                             as[k * 32] = ak;
                             s = __dadd_rn(s, (double)ak);
                         }
@@ -165,7 +206,7 @@ __device__ __forceinline__ void run_instance(const SsaParams &p, const MonProg &
 #pragma unroll
             for (int k = 0; k < SMC_SMALL_MAX; ++k) {
                 if (k < R) {
-                    const T ak = propensity<PLAIN>(reac[k], xs, rate_d, rate_f);
+                    const T ak = propensity<PLAIN>(reac[k], xs, rate_d, rate_f, blob);
                     const bool positive =
                         PLAIN ? __double_as_longlong((double)ak) > 0 : ak > (T)0;
                     pos |= (uint32_t)positive << k;
@@ -207,6 +248,7 @@ __device__ __forceinline__ void run_instance(const SsaParams &p, const MonProg &
             snapped = true;
             const uint64_t idx = (uint64_t)m * p.out_stride + ((uint64_t)traj - p.out_base);
             p.o_snap[idx] = 0;
+            if (p.o_esnap) p.o_esnap[idx] = e;
             for (int i = 0; i < S; ++i) p.o_xsnap[idx * p.x_stride + i] = xs[i * 32];
             if (snap_mode == 2) { finish(4); continue; }
         }
@@ -272,7 +314,7 @@ __device__ __forceinline__ void run_instance(const SsaParams &p, const MonProg &
             for (uint32_t q = dpp[j], qe = dpp[j + 1]; q < qe; ++q) {
                 const uint32_t pw = dp[q];
                 const int k = pw & 255u;
-                const T ak = propensity<PLAIN>(pw, xs, rate_d, rate_f);
+                const T ak = propensity<PLAIN>(pw, xs, rate_d, rate_f, blob);
                 if (!PLAIN) a0 = a0 + (ak - as[k * 32]);
                 as[k * 32] = ak;
             }
@@ -492,14 +534,15 @@ int smc_launch_snapshot_features(uint64_t n_rows, uint64_t n_traj, int S, int R,
 }
 
 // Control-variate sums over n trajectories: G = g for trajectories alive at
-// the snapshot, G = Y for those decided before it; sums[0..5] += (count,
-// sum Y, sum G, sum Y^2, sum G^2, sum Y G) in FP64 (Y ignored for prefix-only
-// runs, whose verdict is unknown: they contribute count and the G sums, with
-// G = Y only when decided before the snapshot).
-__global__ void cv_sums_kernel(uint64_t n, const uint8_t *y, const uint8_t *snap, const float *g, int prefix,
-                               double *sums)
+// the snapshot, G = Y for those decided before it; sums[0..6] += (count,
+// sum Y, sum G, sum Y^2, sum G^2, sum Y G, sum e_pre) in FP64 (Y ignored for
+// prefix-only runs, whose verdict is unknown: they contribute count and the G
+// sums, with G = Y only when decided before the snapshot; e_pre, the events
+// up to the snapshot or the verdict, may be null).
+__global__ void cv_sums_kernel(uint64_t n, const uint8_t *y, const uint8_t *snap, const float *g,
+                               const uint32_t *e_pre, int prefix, double *sums)
 {
-    double s[6] = {0, 0, 0, 0, 0, 0};
+    double s[7] = {0, 0, 0, 0, 0, 0, 0};
     for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (uint64_t)gridDim.x * blockDim.x) {
         const double Y = y[i];
@@ -510,21 +553,22 @@ __global__ void cv_sums_kernel(uint64_t n, const uint8_t *y, const uint8_t *snap
         s[3] += prefix ? 0.0 : Y * Y;
         s[4] += G * G;
         s[5] += prefix ? 0.0 : Y * G;
+        s[6] += e_pre ? (double)e_pre[i] : 0.0;  // what a prefix-only run of this trajectory costs
     }
 #pragma unroll
-    for (int k = 0; k < 6; ++k) {
+    for (int k = 0; k < 7; ++k) {
         double v = s[k];
         for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL_MASK, v, o);
         if ((threadIdx.x & 31) == 0) atomicAdd(&sums[k], v);
     }
 }
 
-int smc_launch_cv_sums(uint64_t n, const uint8_t *y, const uint8_t *snap, const float *g, int prefix,
-                       double *sums, void *stream)
+int smc_launch_cv_sums(uint64_t n, const uint8_t *y, const uint8_t *snap, const float *g, const uint32_t *e_pre,
+                       int prefix, double *sums, void *stream)
 {
     if (n == 0) return 0;
     const unsigned blocks = (unsigned)std::min<uint64_t>(1024, (n + 255) / 256);
-    cv_sums_kernel<<<blocks, 256, 0, (cudaStream_t)stream>>>(n, y, snap, g, prefix, sums);
+    cv_sums_kernel<<<blocks, 256, 0, (cudaStream_t)stream>>>(n, y, snap, g, e_pre, prefix, sums);
     return to_code(cudaGetLastError());
 }
 

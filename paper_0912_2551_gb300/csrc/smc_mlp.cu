@@ -85,17 +85,15 @@ __device__ __forceinline__ void relu_epilogue(float (&acc)[16][4], const float *
     }
 }
 
-// Forward pass over B rows of x (BF16 [B][16]).  z_out[r] = logit.  With
-// train, the activations h1..h3 are stored for the backward pass.
-__global__ void __launch_bounds__(128) mlp_fwd_kernel(const bf16 *__restrict__ x, int B, const bf16 *w1b,
-                                                      const bf16 *w2b, const bf16 *w3b, const float *master,
-                                                      float *z_out, bf16 *h1, bf16 *h2, bf16 *h3)
+// Weights of the network staged in shared memory (forward direction):
+// W1 [H][IN], W2 [H][H], W3 [H][H] in BF16, then b1 | b2 | b3 | w4 | b4 in FP32.
+__device__ __forceinline__ void stage_forward_weights(unsigned char *sm, const bf16 *w1b, const bf16 *w2b,
+                                                      const bf16 *w3b, const float *master)
 {
-    extern __shared__ __align__(16) unsigned char sm[];
     bf16 *sW1 = reinterpret_cast<bf16 *>(sm);
     bf16 *sW2 = sW1 + H * IN;
     bf16 *sW3 = sW2 + H * H;
-    float *sb = reinterpret_cast<float *>(sW3 + H * H);  // b1 | b2 | b3 | w4 | b4
+    float *sb = reinterpret_cast<float *>(sW3 + H * H);
     stage(sW1, w1b, H * IN * 2);
     stage(sW2, w2b, H * H * 2);
     stage(sW3, w3b, H * H * 2);
@@ -107,15 +105,20 @@ __global__ void __launch_bounds__(128) mlp_fwd_kernel(const bf16 *__restrict__ x
     }
     if (threadIdx.x == 0) sb[4 * H] = master[MLP_OFF_B4];
     __syncthreads();
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-    const int r0 = blockIdx.x * MLP_ROWS_FWD + warp * 16, ra = r0 + g, rb = r0 + g + 8;
-    if (r0 >= B) return;
+}
 
-    uint32_t a[4];
-    a[0] = ra < B ? ld32(x + (size_t)ra * IN + 2 * t) : 0u;
-    a[1] = rb < B ? ld32(x + (size_t)rb * IN + 2 * t) : 0u;
-    a[2] = ra < B ? ld32(x + (size_t)ra * IN + 2 * t + 8) : 0u;
-    a[3] = rb < B ? ld32(x + (size_t)rb * IN + 2 * t + 8) : 0u;
+// The network on one 16-row tile held by a warp: a = the input A fragment of
+// rows ra = r0 + g and rb = r0 + g + 8.  The logits of rows ra / rb end up in
+// za / zb (every lane of the row's quad).  Stores h1..h3 (rows < B) when the
+// pointers are given.
+__device__ __forceinline__ void forward_tile(const uint32_t (&a)[4], const unsigned char *sm, int g, int t, int ra,
+                                             int rb, int B, bf16 *h1, bf16 *h2, bf16 *h3, float &za_out,
+                                             float &zb_out)
+{
+    const bf16 *sW1 = reinterpret_cast<const bf16 *>(sm);
+    const bf16 *sW2 = sW1 + H * IN;
+    const bf16 *sW3 = sW2 + H * H;
+    const float *sb = reinterpret_cast<const float *>(sW3 + H * H);
     float acc[16][4];
     uint32_t af[8][4];
 #pragma unroll
@@ -154,9 +157,64 @@ __global__ void __launch_bounds__(128) mlp_fwd_kernel(const bf16 *__restrict__ x
     za += __shfl_xor_sync(0xffffffffu, za, 2);
     zb += __shfl_xor_sync(0xffffffffu, zb, 1);
     zb += __shfl_xor_sync(0xffffffffu, zb, 2);
+    za_out = za + sb[4 * H];
+    zb_out = zb + sb[4 * H];
+}
+
+// Forward pass over B rows of x (BF16 [B][16]).  z_out[r] = logit.  With
+// train, the activations h1..h3 are stored for the backward pass.
+__global__ void __launch_bounds__(128) mlp_fwd_kernel(const bf16 *__restrict__ x, int B, const bf16 *w1b,
+                                                      const bf16 *w2b, const bf16 *w3b, const float *master,
+                                                      float *z_out, bf16 *h1, bf16 *h2, bf16 *h3)
+{
+    extern __shared__ __align__(16) unsigned char sm[];
+    stage_forward_weights(sm, w1b, w2b, w3b, master);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+    const int r0 = blockIdx.x * MLP_ROWS_FWD + warp * 16, ra = r0 + g, rb = r0 + g + 8;
+    if (r0 >= B) return;
+    uint32_t a[4];
+    a[0] = ra < B ? ld32(x + (size_t)ra * IN + 2 * t) : 0u;
+    a[1] = rb < B ? ld32(x + (size_t)rb * IN + 2 * t) : 0u;
+    a[2] = ra < B ? ld32(x + (size_t)ra * IN + 2 * t + 8) : 0u;
+    a[3] = rb < B ? ld32(x + (size_t)rb * IN + 2 * t + 8) : 0u;
+    float za, zb;
+    forward_tile(a, sm, g, t, ra, rb, B, h1, h2, h3, za, zb);
     if (t == 0) {
-        if (ra < B) z_out[ra] = za + sb[4 * H];
-        if (rb < B) z_out[rb] = zb + sb[4 * H];
+        if (ra < B) z_out[ra] = za;
+        if (rb < B) z_out[rb] = zb;
+    }
+}
+
+// Inference over n rows of FP32 features x [n][n_in] (n_in <= 16): one
+// persistent launch, the weights staged once per CTA, 16-row tiles per warp
+// (grid-stride); features rounded to BF16 as the training input is;
+// g[r] = 1 / (1 + e^-z).  Rows with skip[r] != 0 (may be null) need no
+// output; a tile whose rows all skip is not computed.
+__global__ void __launch_bounds__(128) mlp_infer_kernel(const float *__restrict__ x, uint64_t n, int n_in,
+                                                        const uint8_t *__restrict__ skip, const bf16 *w1b,
+                                                        const bf16 *w2b, const bf16 *w3b, const float *master,
+                                                        float *g_out)
+{
+    extern __shared__ __align__(16) unsigned char sm[];
+    stage_forward_weights(sm, w1b, w2b, w3b, master);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+    const uint64_t tiles = (n + 15) / 16;
+    for (uint64_t tile = (uint64_t)blockIdx.x * 4 + warp; tile < tiles; tile += (uint64_t)gridDim.x * 4) {
+        const uint64_t ra = tile * 16 + g, rb = ra + 8;
+        const bool need = (ra < n && !(skip && skip[ra])) || (rb < n && !(skip && skip[rb]));
+        if (!__any_sync(0xffffffffu, need)) continue;
+        auto feat = [&](uint64_t r, int k) { return (r < n && k < n_in) ? x[r * n_in + k] : 0.0f; };
+        uint32_t a[4];
+        a[0] = pack2(feat(ra, 2 * t), feat(ra, 2 * t + 1));
+        a[1] = pack2(feat(rb, 2 * t), feat(rb, 2 * t + 1));
+        a[2] = pack2(feat(ra, 2 * t + 8), feat(ra, 2 * t + 9));
+        a[3] = pack2(feat(rb, 2 * t + 8), feat(rb, 2 * t + 9));
+        float za, zb;
+        forward_tile(a, sm, g, t, 0, 0, 0, nullptr, nullptr, nullptr, za, zb);
+        if (t == 0) {
+            if (ra < n) g_out[ra] = 1.0f / (1.0f + expf(-za));
+            if (rb < n) g_out[rb] = 1.0f / (1.0f + expf(-zb));
+        }
     }
 }
 
@@ -383,12 +441,6 @@ __global__ void mlp_gather_kernel(const float *x, const float *y, uint64_t n, in
     if (yb) yb[i] = ok ? y[r] : 0.0f;
 }
 
-__global__ void sigmoid_kernel(const float *z, int B, float *g)
-{
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < B) g[i] = 1.0f / (1.0f + expf(-z[i]));
-}
-
 constexpr int kMaxBatch = 8192;
 constexpr int kChunks = kMaxBatch / MLP_CHUNK;
 constexpr int kFwdSmem = (H * IN + 2 * H * H) * 2 + (4 * H + 4) * 4;
@@ -493,9 +545,9 @@ int smc_mlp_create(smc_mlp **out, int device, int n_in, uint64_t seed)
         if (cudaMalloc(p, (size_t)kMaxBatch * 4) != cudaSuccess) return fin(SMC_E_OOM);
     if (cudaMalloc((void **)&m->loss, 4096 * 4) != cudaSuccess) return fin(SMC_E_OOM);
     const void *kern[] = {(const void *)mlp_fwd_kernel, (const void *)mlp_bwd_kernel,
-                          (const void *)mlp_wgrad_kernel};
-    const int smem[] = {kFwdSmem, kBwdSmem, kWgSmem};
-    for (int k = 0; k < 3; ++k)
+                          (const void *)mlp_wgrad_kernel, (const void *)mlp_infer_kernel};
+    const int smem[] = {kFwdSmem, kBwdSmem, kWgSmem, kFwdSmem};
+    for (int k = 0; k < 4; ++k)
         if (cudaFuncSetAttribute(kern[k], cudaFuncAttributeMaxDynamicSharedMemorySize, smem[k]) != cudaSuccess)
             return fin(SMC_E_CUDA);
     // He-uniform initial weights from the seed; zero biases and Adam moments
@@ -620,22 +672,26 @@ int smc_mlp_train(smc_mlp *m, const float *x, const float *y, uint64_t n, int ep
     return SMC_OK;
 }
 
-int smc_mlp_predict(smc_mlp *m, const float *x, uint64_t n, float *g, void *stream)
+int smc_mlp_predict_masked(smc_mlp *m, const float *x, uint64_t n, const uint8_t *skip, float *g, void *stream)
 {
-    if (!m || !x || !g) return SMC_E_INVALID_ARG;
+    if (!m || (n && (!x || !g))) return SMC_E_INVALID_ARG;
+    if (n == 0) return SMC_OK;
     MCK(cudaSetDevice(m->device));
     cudaStream_t s = stream ? (cudaStream_t)stream : m->stream;
-    for (uint64_t base = 0; base < n; base += kMaxBatch) {
-        const int B = (int)std::min<uint64_t>(kMaxBatch, n - base);
-        mlp_gather_kernel<<<(B + 127) / 128, 128, 0, s>>>(x, nullptr, n, m->n_in, B, base, 0, 0, 0, m->xb,
-                                                          nullptr);
-        MCK(cudaGetLastError());
-        int rc = pass(m, B, false, s);
-        if (rc) return rc;
-        sigmoid_kernel<<<(B + 127) / 128, 128, 0, s>>>(m->z, B, g + base);
-        MCK(cudaGetLastError());
-    }
+    int dev_sm = 0, per_sm = 0;
+    MCK(cudaDeviceGetAttribute(&dev_sm, cudaDevAttrMultiProcessorCount, m->device));
+    MCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, mlp_infer_kernel, 128, kFwdSmem));
+    const uint64_t tiles = (n + 15) / 16;
+    const uint64_t want = (tiles + 3) / 4;
+    const int grid = (int)std::max<uint64_t>(1, std::min<uint64_t>(want, (uint64_t)dev_sm * std::max(per_sm, 1)));
+    mlp_infer_kernel<<<grid, 128, kFwdSmem, s>>>(x, n, m->n_in, skip, m->w1b, m->w2b, m->w3b, m->master, g);
+    MCK(cudaGetLastError());
     return SMC_OK;
+}
+
+int smc_mlp_predict(smc_mlp *m, const float *x, uint64_t n, float *g, void *stream)
+{
+    return smc_mlp_predict_masked(m, x, n, nullptr, g, stream);
 }
 
 }  // extern "C"

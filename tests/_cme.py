@@ -26,6 +26,11 @@ def _rate(c, reac, x):
     return c * x[a] * x[b]
 
 
+def _factor(x, m, n, a0, a1, b0, b1):
+    v = float(x[m]) ** n
+    return (a0 + a1 * v) / (b0 + b1 * v)
+
+
 def eventually_probability(model, goal, T, cap=None, inst=0):
     """P(exists t <= T with goal(x(t))) for x(0) = model.x0[inst]; states
     with any count above ``cap`` are made absorbing and counted as failure
@@ -43,6 +48,9 @@ def eventually_probability(model, goal, T, cap=None, inst=0):
             continue
         for j in range(model.n_reactions):
             r = _rate(rates[j], model.reactants[j], x)
+            for f in getattr(model, 'factors', None) or []:
+                if f[0] == j:
+                    r *= _factor(x, *f[1:])
             if r <= 0:
                 continue
             y = tuple(int(v) for v in np.asarray(x) + model.stoich[j])

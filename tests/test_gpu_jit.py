@@ -1,10 +1,15 @@
 """Model-specialized kernels (SMC_OPT_JIT): the run-time compiled kernel of a
 network structure must reproduce the generic kernel bit for bit -- same
-random numbers, same arithmetic in the same order -- on the FP64 and the
-mixed path: per-trajectory verdicts, statuses, event counts, final clocks and
-states, snapshots, and the device-side counts and Wilson interval.  The FP64
-path's agreement with the oracle is covered by the parity tests, which run
-through the specialized kernel by default."""
+random numbers, same arithmetic in the same order -- on the FP64 path, and on
+the mixed path for small networks (S, R <= 8, where both recompute every
+propensity per event): per-trajectory verdicts, statuses, event counts,
+final clocks and states, snapshots, and the device-side counts and Wilson
+interval.  For larger networks the generic mixed kernel updates a_0
+incrementally in FP32 (renormalised in FP64 every 2^k events) while the
+specialized one recomputes it per event, so their FP32 roundings differ and
+trajectories may part at a selection boundary: there the comparison is
+statistical.  The FP64 path's agreement with the oracle is covered by the
+parity tests, which run through the specialized kernel by default."""
 import math
 
 import numpy as np
@@ -52,7 +57,15 @@ MODELS = {
     'pure_decay': lambda: workloads.pure_decay(),
     'nested_lv': _nested_lv,
     'weighted_atom': _weighted_atom,
+    'mm_degradation': lambda: workloads.mm_degradation(),
+    'autorepressor': lambda: workloads.autorepressor(),
+    # medium networks: net changes from the shared-memory table, rates per warp
+    'cascade_literal': lambda: workloads.mapk_cascade(2, seed=5),
+    'cascade_variant': lambda: workloads.mapk_cascade(2, seed=5, variant=True),
+    'factor_chain': lambda: workloads.factor_chain(),
 }
+SIZES = {'lotka_volterra': 1500, 'cascade_literal': 512, 'cascade_variant': 256}
+MEDIUM = {'cascade_literal', 'cascade_variant', 'factor_chain'}
 OUTPUTS = ('verdict', 'status', 'events', 't_final', 'x_final')
 
 
@@ -72,15 +85,24 @@ def _run(smc, model, prop, jit, precision, n, t_max=math.inf):
 @pytest.mark.parametrize('name', sorted(MODELS))
 def test_specialized_kernel_reproduces_generic(smc, name, precision):
     model, prop = MODELS[name]()
-    n = 3000 if name != 'lotka_volterra' else 1500
+    n = SIZES.get(name, 3000)
     spec, s1 = _run(smc, model, prop, 1, precision, n)
     gen, s0 = _run(smc, model, prop, 0, precision, n)
     assert all(s['specialized'] for s in s1), s1
     assert not any(s['specialized'] for s in s0)
+    assert spec['counts'][:, 1].sum() + spec['counts'][:, 3].sum() == model.n_inst * n
+    if precision == 'mixed' and name in MEDIUM:
+        assert (spec['verdict'] == gen['verdict']).mean() >= 0.95
+        p1, p2 = spec['verdict'].mean(), gen['verdict'].mean()
+        pm = 0.5 * (p1 + p2)
+        assert abs(p1 - p2) <= 4 * math.sqrt(max(pm * (1 - pm), 1e-4) / spec['verdict'].size) + 1e-3
+        e1, e2 = spec['events'].astype(float).mean(), gen['events'].astype(float).mean()
+        assert abs(e1 - e2) <= 0.02 * e2, (e1, e2)
+        assert (spec['status'] == gen['status']).mean() >= 0.95
+        return
     for k in OUTPUTS + ('counts',):
         assert np.array_equal(spec[k], gen[k]), (k, np.argwhere(spec[k] != gen[k])[:5])
     assert np.array_equal(spec['wilson'], gen['wilson'])
-    assert spec['counts'][:, 1].sum() + spec['counts'][:, 3].sum() == model.n_inst * n
 
 
 @pytest.mark.parametrize('precision', ['plain', 'mixed'])
@@ -105,8 +127,10 @@ def test_specialized_snapshots_reproduce_generic(smc, precision):
 
 def test_ineligible_models_run_generic(smc):
     import torch
-    # more than 8 species: the cascade
-    m, p = workloads.mapk_cascade(2, seed=5)
+    # more than 32 reactions: one network of the random batch, loaded alone
+    b = workloads.random_networks(64, seed=3)
+    i = next(k for k, mm in enumerate(b.models) if mm.n_reactions > 32)
+    m, p = b.models[i], b.properties[i]
     with smc.Context(0) as ctx:
         ctx.load_model(m)
         ctx.load_property(p)

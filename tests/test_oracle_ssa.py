@@ -146,3 +146,57 @@ def test_absorbing_state_closes_the_path(orc):
     p = workloads.Property([workloads.atom(['A'], 'A', '>=', 5)], ('F', 0.0, 100.0, ('atom', 0)))
     r = orc.run(m, p, seed=0, n_traj=100)
     assert (r['status'] == 0).all() and (r['verdict'] == 0).all() and (r['events'] == 3).all()
+
+
+def birth_death_survival_exact(b, d, A0, T):
+    """P(a linear birth-death lineage from A0 is alive at T) = 1 - P0(T),
+    P0(T) = (d (e^{(b-d)T} - 1) / (b e^{(b-d)T} - d))^A0 (Kendall 1948)."""
+    g = math.exp((b - d) * T)
+    return 1.0 - (d * (g - 1.0) / (b * g - d)) ** A0
+
+
+def test_birth_death_survival_closed_form(orc):
+    # G[0,T](A > 0) on A -> 2A (b), A -> 0 (d A): the verdict is survival to T.
+    m, p = workloads.birth_death_survival(1, b=1.0, d=0.8, A0=5, T=20.0)
+    exact = birth_death_survival_exact(1.0, 0.8, 5, 20.0)
+    r = orc.run(m, p, seed=21, n_traj=4000)
+    y = r['verdict'].astype(float)
+    assert abs(y.mean() - exact) < 4.5 * math.sqrt(exact * (1 - exact) / y.size), (y.mean(), exact)
+    # a shorter horizon, where extinction is still under way
+    m2, p2 = workloads.birth_death_survival(1, b=1.0, d=0.8, A0=2, T=3.0)
+    exact2 = birth_death_survival_exact(1.0, 0.8, 2, 3.0)
+    y2 = orc.run(m2, p2, seed=22, n_traj=8000)['verdict'].astype(float)
+    assert abs(y2.mean() - exact2) < 4.5 * math.sqrt(exact2 * (1 - exact2) / y2.size), (y2.mean(), exact2)
+
+
+@pytest.mark.parametrize('name', ['mm_degradation', 'autorepressor'])
+def test_rate_law_factors_against_cme(orc, name):
+    # Propensities with rational rate-law factors (Michaelis-Menten
+    # degradation vmax A/(K + A); Hill-repressed production k K^2/(K^2 + A^2)):
+    # the oracle's P(F[0,T] goal) against the exact CME solve of the same
+    # chain (tests/_cme.py applies the factors independently).
+    m, p = getattr(workloads, name)()
+    atom = p.atoms[0]
+    T = p.formula[2]
+    if atom.op == '<=':
+        goal = lambda x: x[0] <= atom.bound  # noqa: E731
+    else:
+        goal = lambda x: x[0] >= atom.bound  # noqa: E731
+    exact = _cme.eventually_probability(m, goal, T, cap=300)
+    assert 0.2 < exact < 0.8
+    r = orc.run(m, p, seed=41, n_traj=20000)
+    y = r['verdict'].astype(float)
+    assert abs(y.mean() - exact) < 4.5 * math.sqrt(exact * (1 - exact) / y.size), (y.mean(), exact)
+
+
+def test_rate_law_factor_dropped_is_detected(orc):
+    # the same Hill-repressed gene without its factor is a plain
+    # immigration-death chain with a different answer: the pin above fails
+    # for an oracle that ignores factors
+    m, p = workloads.autorepressor()
+    exact = _cme.eventually_probability(m, lambda x: x[0] >= 48, 40.0, cap=300)
+    plain = workloads.Model(m.name, m.species, m.reactants, m.stoich, m.rates, m.x0)
+    wrong = _cme.eventually_probability(plain, lambda x: x[0] >= 48, 40.0, cap=300)
+    assert abs(exact - wrong) > 0.2
+    y = orc.run(plain, p, seed=41, n_traj=4000)['verdict'].astype(float)
+    assert abs(y.mean() - wrong) < 4.5 * math.sqrt(wrong * (1 - wrong) / y.size)

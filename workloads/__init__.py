@@ -63,6 +63,10 @@ class Model:
     stoich: np.ndarray
     rates: np.ndarray
     x0: np.ndarray
+    # rate-law factors beyond mass action, shared by all instances: tuples
+    # (reaction k, species m, power n, a0, a1, b0, b1) multiplying a_k by
+    # (a0 + a1 x_m^n) / (b0 + b1 x_m^n), applied in the listed order
+    factors: list = dataclasses.field(default_factory=list)
 
     def __post_init__(self):
         self.reactants = np.ascontiguousarray(self.reactants, dtype=np.int32).reshape(-1, 2)
@@ -93,7 +97,7 @@ class Model:
 
     def instance(self, m: int) -> "Model":
         return Model(self.name, list(self.species), self.reactants, self.stoich,
-                     self.rates[m:m + 1], self.x0[m:m + 1])
+                     self.rates[m:m + 1], self.x0[m:m + 1], list(self.factors))
 
 
 @dataclasses.dataclass
@@ -200,6 +204,66 @@ def dimerisation(n_inst: int = 1) -> Tuple[Model, Property]:
     m = Model('dimerisation', sp, reac, st, np.tile([0.002, 0.1, 5.0], (n_inst, 1)),
               np.tile([100, 0], (n_inst, 1)))
     p = Property([atom(sp, 'B', '>=', 40)], ('F', 0.0, 20.0, ('atom', 0)), 'F[0,20](B>=40)')
+    return m, p
+
+
+def birth_death_survival(n_inst: int = 1, b: float = 1.0, d: float = 0.8, A0: int = 5,
+                         T: float = 20.0) -> Tuple[Model, Property]:
+    """Linear birth-death process A -> 2A (c=b), A -> 0 (c=d) from A0;
+    property G[0,T](A > 0) (the lineage survives to T).  Survivors grow like
+    e^{(b-d)t}, so most of a surviving trajectory's events come late, while
+    its fate is largely settled early: the setting in which a checkpoint
+    predictor pays as a control variate."""
+    sp = ['A']
+    reac, st = _net(sp, [(['A'], ['A', 'A']), (['A'], [])])
+    m = Model('birth_death_survival', sp, reac, st, np.tile([b, d], (n_inst, 1)),
+              np.full((n_inst, 1), A0))
+    p = Property([atom(sp, 'A', '>', 0)], ('G', 0.0, T, ('atom', 0)), f'G[0,{T}](A>0)')
+    return m, p
+
+
+def mm_degradation(A0: int = 40, vmax: float = 4.0, K: float = 10.0, T: float = 12.0,
+                   theta: int = 8) -> Tuple[Model, Property]:
+    """Michaelis-Menten degradation A -> 0 with propensity vmax A / (K + A)
+    (a zeroth-order mass-action part times the factor A / (K + A));
+    property F[0,T](A <= theta)."""
+    sp = ['A']
+    m = Model('mm_degradation', sp, [[-1, -1]], [[-1]], [[vmax]], [[A0]],
+              [(0, 0, 1, 0.0, 1.0, float(K), 1.0)])
+    p = Property([atom(sp, 'A', '<=', theta)], ('F', 0.0, T, ('atom', 0)), f'F[0,{T}](A<={theta})')
+    return m, p
+
+
+def autorepressor(n_inst: int = 1, k: float = 20.0, K: float = 30.0, n: int = 2, d: float = 0.2,
+                  T: float = 40.0, theta: int = 48) -> Tuple[Model, Property]:
+    """A gene repressing its own production: 0 -> A with propensity
+    k K^n / (K^n + A^n) (Hill repression), A -> 0 (d A); A0 = 0; property
+    F[0,T](A >= theta)."""
+    sp = ['A']
+    reac, st = _net(sp, [([], ['A']), (['A'], [])])
+    Kn = float(K) ** n
+    m = Model('autorepressor', sp, reac, st, np.tile([k, d], (n_inst, 1)), np.zeros((n_inst, 1)),
+              [(0, 0, n, Kn, 0.0, Kn, 1.0)])
+    p = Property([atom(sp, 'A', '>=', theta)], ('F', 0.0, T, ('atom', 0)), f'F[0,{T}](A>={theta})')
+    return m, p
+
+
+def factor_chain(n: int = 10, T: float = 25.0, theta: int = 10) -> Tuple[Model, Property]:
+    """A conversion chain A_0 -> A_1 -> ... -> A_{n-1} (c = 1, mass action
+    in A_j) whose step j is activated by A_{j+2 mod n}, factor
+    (0.5 + x) / (5 + x), fed by 0 -> A_0 (c = 3) under Hill repression by
+    A_{n-1}, factor 100 / (100 + x^2); A_0 = 30, property
+    F[0,T](A_{n-1} >= theta).  More than 8 species: the generic kernel with
+    dependency-graph updates, where a factor's species enlarges dep(j)."""
+    sp = [f'A{i}' for i in range(n)]
+    reactions = [([sp[j]], [sp[j + 1]]) for j in range(n - 1)] + [([], [sp[0]])]
+    reac, st = _net(sp, reactions)
+    rates = [1.0] * (n - 1) + [3.0]
+    x0 = [30] + [0] * (n - 1)
+    factors = [(j, (j + 2) % n, 1, 0.5, 1.0, 5.0, 1.0) for j in range(n - 1)]
+    factors.append((n - 1, n - 1, 2, 100.0, 0.0, 100.0, 1.0))
+    m = Model('factor_chain', sp, reac, st, [rates], [x0], factors)
+    p = Property([atom(sp, sp[-1], '>=', theta)], ('F', 0.0, T, ('atom', 0)), f'F[0,{T}]({sp[-1]}>={theta})')
     return m, p
 
 
