@@ -89,6 +89,9 @@ def immigration_death(args):
         ms, c, wil, clk = _timed_simulate(ctx, 'plain', n, args.steps, args.warmup, seed=0)
         kname = bench.kernel_name(ctx, 'plain')
         it = ctx.estimate(0.95, 0.005, seed=0, precision='plain', sampling='iterative')[0]
+        t0 = time.perf_counter()
+        ex = ctx.cme_reach(cap=1000)  # the exact side of Fig. 4 (uniformisation on the GPU)
+        t_ex = time.perf_counter() - t0
     t0 = time.perf_counter()
     r = oracle.run(m, p, seed=0, n_traj=n)
     cpu = time.perf_counter() - t0
@@ -96,6 +99,8 @@ def immigration_death(args):
     _line(n / (ms / 1e3), 'trajectories/s', args.steps, args.warmup, ms, 'f64',
           'immigration-death, F[0,100](A>=130), 10,000 trajectories, Philox seed 0, Wilson 95%',
           {'events_per_s': ev / (ms / 1e3), 'clocks': clk,
+           'exact_uniformisation': {'p': ex['p'], 'n_states': ex['n_states'], 'iterations': ex['iterations'],
+                                    'truncated': ex['truncated'], 'seconds': t_ex},
            'result': {'p_hat': wil[0, 0], 'lo': wil[0, 1], 'hi': wil[0, 2], 'exact': 0.0912186,
                       'oracle_p_hat': float(r['verdict'].mean()),
                       'iterative_eps_0.005': {'n': it['launched'], 'p_hat': it['p_hat'], 'lo': it['lo'],
@@ -320,6 +325,7 @@ def cascade(args):
             ctx.load_model(m)
             ctx.load_property(p)
             ms, c, wil, clk = _timed_simulate(ctx, 'mixed', n, max(1, min(args.steps, 3)), 1, seed=0, label=name)
+            kname = bench.kernel_name(ctx, 'mixed')
             msp, cp, _, _ = _timed_simulate(ctx, 'plain', min(n, 200), 1, 1, seed=0, label=name)
         ev = float(c[:, 2].sum())
         out[name] = dict(
@@ -336,7 +342,7 @@ def cascade(args):
           f'three-tier cascade, 22 species, 30 reactions, 256 rate-perturbed instances x {n:,} trajectories, '
           '(KPP<500) U[0,200] (KPP>=2000 & F[0,50] KPP<500) and the KPP<2000 variant',
           {'events_per_s': lit['events_per_s'], 'configs': out,
-           'roofline': _issue_roofline(lit['events_per_s'], ops, 'ssa_kernel<mixed>'),
+           'roofline': _issue_roofline(lit['events_per_s'], ops, kname),
            'cpu_baseline': {'value': 64 / cpu, 'unit': 'trajectories/s', 'cores': os.cpu_count(),
                             'kind': 'oracle', 'sample': f'64 trajectories of instance 0 (literal), {cpu:.1f} s'}})
 

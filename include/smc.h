@@ -203,6 +203,29 @@ int smc_load_property(smc_ctx *ctx, int n_atoms, const int32_t *atom_coef,
 int smc_load_rate_factors(smc_ctx *ctx, int n_factors, const int32_t *reaction, const int32_t *species,
                           const int32_t *power, const double *params);
 
+/* Exact time-bounded reachability for the loaded property on one instance,
+ * by uniformisation of the CTMC (Sec. 2.2's chain solved numerically): the
+ * exact side of the comparison of Sec. 5 / Fig. 4 (there done with PRISM),
+ * as a validator of smc_estimate.  No counterpart in the paper's own method.
+ * The property must compile to one L U[0,b] P, F[0,b] P or G[0,b] P over
+ * state formulas (b finite).  The states reachable from x0 are enumerated on
+ * the host (at most max_states; states with a count above cap are absorbing
+ * and their mass by b is reported as `truncated`, which bounds the error
+ * from above); the uniformised chain's iterations run on the GPU in FP64.
+ * Synchronous.  Errors: SMC_E_STATE (no model or property), SMC_E_UNSUPPORTED
+ * (formula shape, or more reachable states than max_states),
+ * SMC_E_INVALID_ARG (instance, cap, a count driven negative), SMC_E_CUDA,
+ * SMC_E_OOM. */
+typedef struct {
+    double p;            /* P(phi) up to the truncation below            */
+    double truncated;    /* probability mass in capped states by b       */
+    double poisson_tail; /* Poisson weight left out (about 1e-14)        */
+    int64_t n_states;    /* reachable states enumerated                  */
+    int64_t iterations;  /* uniformisation steps                         */
+    double lambda_t;     /* uniformisation rate x b                      */
+} smc_cme_result;
+int smc_cme_reach(smc_ctx *ctx, int instance, int32_t cap, int64_t max_states, smc_cme_result *out);
+
 /* Sets an SMC_OPT_* option.  Errors: SMC_E_INVALID_ARG. */
 int smc_set_option(smc_ctx *ctx, int option, double value);
 
@@ -359,8 +382,8 @@ int smc_mlp_predict_masked(smc_mlp *mlp, const float *x, uint64_t n, const uint8
  * (host), t_scale: feature scaling as in smc_snapshot_features; pilot: the
  * least first sample of full runs (>= 2; at least Fig. 2's first batch,
  * Wilson_sample(1, half_width)); later iterations go straight to the
- * cost-optimal sizes (at most 64x growth).  Device buffers are kept in the
- * context for later calls. */
+ * cost-optimal sizes (at most 1024x growth).  Device buffers are kept in
+ * the context for later calls. */
 typedef struct {
     double p_hat, lo, hi;
     double n_eff;      /* p_hat (1 - p_hat) / var */

@@ -179,6 +179,14 @@ class Context:
     def set_option(self, name: str, value: float):
         self._check(N.smc_set_option(self.h, N.OPT[name], float(value)), f'smc_set_option({name})')
 
+    def cme_reach(self, instance: int = 0, cap: int = 1000, max_states: int = 2_000_000):
+        """Exact P(property) by uniformisation (smc_cme_reach): dict p,
+        truncated, poisson_tail, n_states, iterations, lambda_t."""
+        r = N.smc_cme_result()
+        self._check(N.smc_cme_reach(self.h, int(instance), int(cap), int(max_states), ctypes.byref(r)),
+                    'smc_cme_reach')
+        return r.as_dict()
+
     def launch_shapes(self, precision: str = 'mixed'):
         """The launches serving the loaded model (after an estimate or a
         simulation): list of dicts warps_per_block, blocks_per_sm, refill,

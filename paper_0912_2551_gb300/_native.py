@@ -68,6 +68,14 @@ class smc_cv_result(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class smc_cme_result(ctypes.Structure):
+    _fields_ = [('p', ctypes.c_double), ('truncated', ctypes.c_double), ('poisson_tail', ctypes.c_double),
+                ('n_states', ctypes.c_int64), ('iterations', ctypes.c_int64), ('lambda_t', ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 SMC_MLP_NPARAM = 35329
 SMC_MLP_MAX_BATCH = 8192
 c_f32p = ctypes.POINTER(ctypes.c_float)
@@ -88,6 +96,8 @@ SIGNATURES = {
                                          ctypes.c_int, ctypes.POINTER(smc_node), ctypes.c_int,
                                          ctypes.c_double]),
     'smc_set_option': (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_double]),
+    'smc_cme_reach': (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int32, ctypes.c_int64,
+                                     ctypes.POINTER(smc_cme_result)]),
     'smc_load_rate_factors': (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, c_i32p, c_i32p, c_i32p, c_f64p]),
     'smc_get_launch_shape': (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, c_i32p, c_i32p, c_i32p,
                                             c_i32p, c_i32p, c_i32p]),

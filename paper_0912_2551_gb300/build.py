@@ -11,9 +11,9 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, 'csrc')
 BUILD = os.path.join(HERE, '_build')
 LIB = os.path.join(BUILD, 'libsmc.so')
-SOURCES = ['smc_kernels.cu', 'smc_api.cu', 'smc_compile.cpp', 'smc_mlp.cu', 'smc_jit.cpp']
+SOURCES = ['smc_kernels.cu', 'smc_api.cu', 'smc_compile.cpp', 'smc_mlp.cu', 'smc_jit.cpp', 'smc_cme.cu']
 HEADERS = ['smc_internal.h', 'smc_compile.h', 'smc_mlp.h', 'smc_device.cuh', 'smc_jit.h',
-           'smc_jit_kernel.cuh', 'nvrtc_stdint.h']
+           'smc_jit_kernel.cuh', 'nvrtc_stdint.h', 'smc_cme.h']
 # sources of the run-time compiled kernels, embedded into the library as
 # (include name, file) pairs
 JIT_EMBED = [('stdint.h', 'nvrtc_stdint.h'), ('smc_internal.h', 'smc_internal.h'),

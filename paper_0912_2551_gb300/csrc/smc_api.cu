@@ -16,6 +16,7 @@
 #include "smc_compile.h"
 #include "smc_internal.h"
 #include "smc_jit.h"
+#include "smc_cme.h"
 
 namespace {
 
@@ -506,11 +507,13 @@ int tc_bytes_of(const MonProg &prog)
     return 0;
 }
 
-// warp slice: table | x[(s_max + 1)][32] | tc | a[r_max][32]
+// warp slice: table | x[(s_max + 1)][32] | tc | a[r_max][32] | (mixed path)
+// group sums g[ceil(r_max / 8)][32]
 int warp_bytes_of(const SizeClass &c, int plain, int tc_bytes)
 {
     const int blob_words = (c.blob_words + 3) & ~3;
-    const int b = blob_words * 4 + (c.s_max + 1) * 128 + tc_bytes + c.r_max * 32 * (plain ? 8 : 4);
+    const int groups = plain ? 0 : (c.r_max + 7) / 8;
+    const int b = blob_words * 4 + (c.s_max + 1) * 128 + tc_bytes + c.r_max * 32 * (plain ? 8 : 4) + groups * 128;
     return (b + 15) & ~15;
 }
 
@@ -910,6 +913,70 @@ int smc_load_rate_factors(smc_ctx *ctx, int n_factors, const int32_t *reaction, 
     ctx->f_pow.assign(power, power + n_factors);
     ctx->f_par.assign(params, params + 4 * (size_t)n_factors);
     ctx->dirty = true;
+    return SMC_OK;
+}
+
+int smc_cme_reach(smc_ctx *ctx, int instance, int32_t cap, int64_t max_states, smc_cme_result *out)
+{
+    if (!ctx) return SMC_E_INVALID_ARG;
+    if (!out) return fail(ctx, SMC_E_INVALID_ARG, "null result");
+    if (!ctx->have_model || !ctx->have_prop) return fail(ctx, SMC_E_STATE, "load a model and a property first");
+    if (instance < 0 || instance >= ctx->n_inst) return fail(ctx, SMC_E_INVALID_ARG, "instance out of range");
+    if (cap < 0 || max_states < 1) return fail(ctx, SMC_E_INVALID_ARG, "bad cap or max_states");
+    // the property must be one until / eventually / always anchored at 0 over
+    // state formulas (time-bounded reachability)
+    const MonProg &P = ctx->prog;
+    if (P.n_units != 1 || P.u[0].nest != 0 || P.u[0].a != 0.0 || !std::isfinite(P.u[0].b) || P.unbounded)
+        return fail(ctx, SMC_E_UNSUPPORTED, "exact solve needs one U / F / G anchored at 0 over state formulas");
+    const int val_true = P.table[2], val_false = P.table[1];
+    if (!((val_true == 2 && val_false == 1) || (val_true == 1 && val_false == 2)))
+        return fail(ctx, SMC_E_UNSUPPORTED, "exact solve needs the unit or its negation at the top level");
+    const int m = instance, S = ctx->S[m], nu = (int)ctx->used_atoms.size();
+    std::vector<int32_t> coef((size_t)nu * S);
+    std::vector<int64_t> lo(nu), hi(nu);
+    std::vector<uint8_t> neg(nu);
+    for (int b = 0; b < nu; ++b) {
+        const int a = ctx->used_atoms[b];
+        std::memcpy(&coef[(size_t)b * S], ctx->atom_coef.data() + ctx->coef_off[m] + (size_t)a * S, sizeof(int32_t) * S);
+        const double bnd = ctx->per_instance_bound ? ctx->atom_bound[(size_t)m * ctx->n_atoms + a] : ctx->atom_bound[a];
+        bool nb;
+        smc::atom_threshold(ctx->atom_op[a], bnd, lo[b], hi[b], nb);
+        neg[b] = nb;
+    }
+    smc::CmeModel M;
+    M.S = S;
+    M.R = ctx->R[m];
+    M.reactants = ctx->reactants.data() + ctx->reac_off[m];
+    M.stoich = ctx->stoich.data() + ctx->st_off[m];
+    M.rates = ctx->rates.data() + ctx->rate_off[m];
+    M.x0 = ctx->x0.data() + ctx->x0_off[m];
+    M.n_fact = (int)ctx->f_reac.size();
+    M.f_reac = ctx->f_reac.data();
+    M.f_spec = ctx->f_spec.data();
+    M.f_pow = ctx->f_pow.data();
+    M.f_par = ctx->f_par.data();
+    smc::CmePredicate pred;
+    pred.n_atoms = nu;
+    pred.coef = coef.data();
+    pred.lo = lo.data();
+    pred.hi = hi.data();
+    pred.neg = neg.data();
+    pred.goal = P.u[0].P;
+    pred.stay = P.u[0].L;
+    CK(cudaSetDevice(ctx->device));
+    smc::CmeResult r;
+    const int rc = smc::cme_reach(M, pred, P.u[0].b, cap, max_states, r, ctx->err, ctx->stream);
+    if (rc == -1) return SMC_E_INVALID_ARG;
+    if (rc == -2) return SMC_E_OOM;
+    if (rc == -3) return SMC_E_CUDA;
+    if (rc == -4) return SMC_E_UNSUPPORTED;
+    // the unit's probability, or its complement for a negated unit (G)
+    out->p = val_true == 2 ? r.p : 1.0 - r.p;
+    out->truncated = r.truncated;
+    out->poisson_tail = r.poisson_tail;
+    out->n_states = r.n_states;
+    out->iterations = r.iterations;
+    out->lambda_t = r.lambda_t;
     return SMC_OK;
 }
 
@@ -1548,21 +1615,25 @@ int smc_estimate_cv(smc_ctx *ctx, smc_mlp *mlp, double confidence, double half_w
         // cost-optimal sizes for the target variance (events per run measured)
         const double c_full = std::max(1.0, (double)hc[2] / c1n), c_pre = std::max(1.0, sE1 / c1n);
         const double dcost = std::max(c_full - c_pre, 1e-3 * c_full);
+        // sizes aimed 5% above the target, so that the estimates' drift
+        // between iterations rarely costs another (latency-bound) iteration
+        const double aim = 1.05 * target;
         uint64_t t1, t2;
         if (!interior) {  // no variance information yet: grow the full sample as Fig. 2 does
-            t1 = (uint64_t)std::ceil(target);
+            t1 = (uint64_t)std::ceil(aim);
             t2 = n2;
         } else {
-            const double Vt = p * (1.0 - p) / target;
+            const double Vt = p * (1.0 - p) / aim;
             const double k = std::sqrt(a * dcost) + std::sqrt(bb * c_pre);
             double o1 = std::sqrt(a / dcost) * k / Vt, on = bb > 0.0 ? std::sqrt(bb / c_pre) * k / Vt : 0.0;
             if (on < o1) { o1 = (a + bb) / Vt; on = o1; }
             t1 = (uint64_t)std::ceil(o1);
             t2 = (uint64_t)std::ceil(std::max(0.0, on - o1));
         }
-        // at most 64x per iteration (a guard against a wild early estimate)
-        want1 = std::min(std::max(t1, n1 + 1), 64 * n1);
-        want2 = std::min(std::max(t2, n2), 64 * std::max(n2, n1));
+        // at most 1024x per iteration (a guard against a wild early estimate;
+        // the pilot is already Fig. 2's first batch)
+        want1 = std::min(std::max(t1, n1 + 1), 1024 * n1);
+        want2 = std::min(std::max(t2, n2), 1024 * std::max(n2, n1));
     }
     out->p_hat = p;
     out->var = V;

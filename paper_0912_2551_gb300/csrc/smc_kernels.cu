@@ -91,10 +91,28 @@ __device__ __forceinline__ typename Prec<PLAIN>::T propensity(uint32_t pw, const
     return a;
 }
 
+// Mixed path, networks above 8 reactions: per-lane FP32 sums of the
+// propensities in groups of SMC_SEL_GROUP reactions (lane-minor, gs[q * 32]),
+// kept incrementally with a_0 and recomputed with it, so that the selection
+// (Eq. 2b) skips whole groups: ~R / 16 + 4 steps instead of ~R / 2.
+#define SMC_SEL_GROUP 8
+__device__ __forceinline__ float renorm_groups(const float *as, float *gs, int R)
+{
+    double s = 0.0;
+    for (int q = 0; q * SMC_SEL_GROUP < R; ++q) {
+        double g = 0.0;
+        const int ke = min(R, (q + 1) * SMC_SEL_GROUP);
+        for (int k = q * SMC_SEL_GROUP; k < ke; ++k) g = __dadd_rn(g, (double)as[k * 32]);
+        gs[q * 32] = (float)g;
+        s = __dadd_rn(s, g);
+    }
+    return (float)s;
+}
+
 template <bool PLAIN>
 __device__ __forceinline__ void run_instance(const SsaParams &p, const MonProg &P, const double *ltab,
                                              const int m, const uint32_t *blob, int32_t *xs, double *tc,
-                                             typename Prec<PLAIN>::T *as, const int lane)
+                                             typename Prec<PLAIN>::T *as, float *gs, const int lane)
 {
     typedef typename Prec<PLAIN>::T T;
     const int S = (int)blob[BH_S], R = (int)blob[BH_R], NA = (int)blob[BH_NA];
@@ -180,6 +198,7 @@ __device__ __forceinline__ void run_instance(const SsaParams &p, const MonProg &
                             s = __dadd_rn(s, (double)ak);
                         }
                         a0 = (T)s;
+                        if (!PLAIN && !small) a0 = (T)renorm_groups((const float *)as, gs, R);
                         uint32_t ab = 0;
                         for (int a = 0; a < NA; ++a) ab |= atom_bit(atoms, tptr, terms, xs, a);
                         ml.ab = ab;
@@ -220,9 +239,7 @@ __device__ __forceinline__ void run_instance(const SsaParams &p, const MonProg &
             for (int k = 0; k < R; ++k) s = __dadd_rn(s, (double)as[k * 32]);
             a0 = (T)s;
         } else if (!(a0 > (T)0)) {  // drifted running sum: renormalise in FP64
-            double s = 0.0;
-            for (int k = 0; k < R; ++k) s = __dadd_rn(s, (double)as[k * 32]);
-            a0 = (T)s;
+            a0 = (T)renorm_groups((const float *)as, gs, R);
         }
         if (PLAIN ? __double_as_longlong((double)a0) <= 0 : !(a0 > (T)0)) {
             finish(mon_close(ml, P));  // absorbing state: no further position
@@ -280,14 +297,21 @@ __device__ __forceinline__ void run_instance(const SsaParams &p, const MonProg &
                 if (__double_as_longlong(ak) > 0) last = k;
                 if (__double_as_longlong(cum) > rb) { j = k; break; }
             }
-        } else {
+        } else {  // whole groups first, then the reactions of the group that crosses r
+            const float rf = (float)r;
             float cum = 0.0f;
-            for (int k = 0; k < R; ++k) {
-                const float ak = (float)as[k * 32];
-                cum += ak;
-                if (ak > 0.0f) last = k;
-                if (cum > (float)r) { j = k; break; }
+            for (int q = 0; q * SMC_SEL_GROUP < R && j < 0; ++q) {
+                const float g = gs[q * 32];
+                if (!(cum + g > rf)) { cum += g; continue; }
+                const int ke = min(R, (q + 1) * SMC_SEL_GROUP);
+                for (int k = q * SMC_SEL_GROUP; k < ke; ++k) {
+                    cum += (float)as[k * 32];
+                    if (cum > rf) { j = k; break; }
+                }
             }
+            if (j < 0)  // r reached the full sum (rounding, or drifted sums)
+                for (int k = R - 1; k >= 0 && last < 0; --k)
+                    if ((float)as[k * 32] > 0.0f) last = k;
         }
         if (j < 0) j = last;  // r reached the full sum (rounding, or a drifted a0)
         if (j < 0) {          // every a_k is 0 (only a drifted FP32 a0 gets here)
@@ -315,16 +339,17 @@ __device__ __forceinline__ void run_instance(const SsaParams &p, const MonProg &
                 const uint32_t pw = dp[q];
                 const int k = pw & 255u;
                 const T ak = propensity<PLAIN>(pw, xs, rate_d, rate_f, blob);
-                if (!PLAIN) a0 = a0 + (ak - as[k * 32]);
+                if (!PLAIN) {
+                    const T d = ak - as[k * 32];
+                    a0 = a0 + d;
+                    gs[(k / SMC_SEL_GROUP) * 32] += (float)d;
+                }
                 as[k * 32] = ak;
             }
             ++e;
             t = tn;
-            if (!PLAIN && (e & renorm_mask) == 0u) {  // FP64 renormalisation of a0
-                double s = 0.0;
-                for (int k = 0; k < R; ++k) s = __dadd_rn(s, (double)as[k * 32]);
-                a0 = (T)s;
-            }
+            if (!PLAIN && (e & renorm_mask) == 0u)  // FP64 renormalisation of a0 and the group sums
+                a0 = (T)renorm_groups((const float *)as, gs, R);
             // monitor at the new state: re-evaluate the atoms that j moves
             uint32_t am = amask[j];
             while (am) {
@@ -374,6 +399,8 @@ __global__ void __launch_bounds__(256, PLAIN ? 3 : 4) ssa_kernel(const SsaParams
     double *tc = reinterpret_cast<double *>(lanes) + lane;
     lanes += (size_t)p.tc_bytes;
     T *as = reinterpret_cast<T *>(lanes) + lane;
+    // mixed path: the group sums after the propensities
+    float *gs = reinterpret_cast<float *>(reinterpret_cast<T *>(lanes) + (size_t)p.r_max * 32) + lane;
 
     bool first = true;
     int cur = -1;
@@ -388,7 +415,7 @@ __global__ void __launch_bounds__(256, PLAIN ? 3 : 4) ssa_kernel(const SsaParams
             __syncwarp();
             cur = m;
         }
-        run_instance<PLAIN>(p, P, ltab, m, blob, xs, tc, as, lane);
+        run_instance<PLAIN>(p, P, ltab, m, blob, xs, tc, as, gs, lane);
         __syncwarp();
     }
 

@@ -66,3 +66,40 @@ def eventually_probability(model, goal, T, cap=None, inst=0):
         Q[i, i] -= r
     P = expm(Q * T)[0]
     return float(sum(P[index[s]] for s in states if goal(s)))
+
+
+def until_probability(model, stay, goal, T, cap=None, inst=0):
+    """P(stay U[0,T] goal): goal states absorbing (success), states where
+    neither holds absorbing (failure), states above ``cap`` absorbing
+    (failure, truncation)."""
+    x0 = tuple(int(v) for v in model.x0[inst])
+    rates = model.rates[inst]
+    index = {x0: 0}
+    states = [x0]
+    q = deque([x0])
+    edges = []
+    while q:
+        x = q.popleft()
+        i = index[x]
+        if goal(x) or not stay(x) or (cap is not None and max(x) > cap):
+            continue
+        for j in range(model.n_reactions):
+            r = _rate(rates[j], model.reactants[j], x)
+            for f in getattr(model, 'factors', None) or []:
+                if f[0] == j:
+                    r *= _factor(x, *f[1:])
+            if r <= 0:
+                continue
+            y = tuple(int(v) for v in np.asarray(x) + model.stoich[j])
+            if y not in index:
+                index[y] = len(states)
+                states.append(y)
+                q.append(y)
+            edges.append((i, index[y], r))
+    n = len(states)
+    Q = np.zeros((n, n))
+    for i, k, r in edges:
+        Q[i, k] += r
+        Q[i, i] -= r
+    P = expm(Q * T)[0]
+    return float(sum(P[index[s]] for s in states if goal(s)))
