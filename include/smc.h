@@ -226,6 +226,43 @@ typedef struct {
 } smc_cme_result;
 int smc_cme_reach(smc_ctx *ctx, int instance, int32_t cap, int64_t max_states, smc_cme_result *out);
 
+/* Arithmetic atoms (Sec. 3.1's grammar: val <| val with val built from
+ * counts, constants, + - * / and functions such as sqrt and pow).  Atom
+ * `atom` of the loaded property becomes  lhs <op> rhs,  each side a postfix
+ * program of tokens evaluated in FP64, every operation rounded once
+ * (IEEE: x / 0 is +-inf, sqrt of a negative is NaN, and every comparison
+ * with NaN is false except !=):
+ *   SMC_TOK_SPECIES  push (double) x[arg]      SMC_TOK_CONST  push value
+ *   SMC_TOK_ADD / SUB / MUL / DIV  pop b, pop a, push a <op> b
+ *   SMC_TOK_SQRT     pop a, push sqrt(a) (correctly rounded)
+ *   SMC_TOK_POWI     pop a, push a^arg, arg in 0..16, by repeated
+ *                    multiplication left to right (a^0 = 1)
+ * A program must leave exactly one value, with a stack of at most
+ * SMC_EXPR_MAX_DEPTH and at most SMC_EXPR_MAX_TOKENS tokens per side.  The
+ * atom's coefficients and bound given to smc_load_property are then
+ * ignored; the expression applies to every instance (batched networks: to
+ * species indices valid in every instance).  Call after smc_load_property
+ * (which clears expressions).  Errors: SMC_E_STATE before a property is
+ * loaded, SMC_E_INVALID_ARG for a bad atom index, operator, token, species or
+ * program shape. */
+#define SMC_TOK_SPECIES 0
+#define SMC_TOK_CONST 1
+#define SMC_TOK_ADD 2
+#define SMC_TOK_SUB 3
+#define SMC_TOK_MUL 4
+#define SMC_TOK_DIV 5
+#define SMC_TOK_SQRT 6
+#define SMC_TOK_POWI 7
+#define SMC_EXPR_MAX_DEPTH 8
+#define SMC_EXPR_MAX_TOKENS 32
+typedef struct {
+    int32_t kind;  /* SMC_TOK_*                                   */
+    int32_t arg;   /* species index (SPECIES) or exponent (POWI)  */
+    double value;  /* constant (CONST)                            */
+} smc_token;
+int smc_set_atom_expression(smc_ctx *ctx, int atom, int op, const smc_token *lhs, int n_lhs,
+                            const smc_token *rhs, int n_rhs);
+
 /* Sets an SMC_OPT_* option.  Errors: SMC_E_INVALID_ARG. */
 int smc_set_option(smc_ctx *ctx, int option, double value);
 

@@ -120,6 +120,31 @@ def flatten_formula(formula):
     return arr, root
 
 
+class _Token(ctypes.Structure):
+    _fields_ = [('kind', ctypes.c_int32), ('arg', ctypes.c_int32), ('value', ctypes.c_double)]
+
+
+TOKEN_KIND = {'x': 0, 'c': 1, '+': 2, '-': 3, '*': 4, '/': 5, 'sqrt': 6, 'pow': 7}
+
+
+def _expr_arrays(prop):
+    """Arithmetic atoms as (expr_ptr [n+1], n_lhs [n], tokens) or Nones."""
+    if not any(a.lhs is not None for a in prop.atoms):
+        return None, None, None
+    ptr, nl, toks = [0], [], []
+    for a in prop.atoms:
+        if a.lhs is None:
+            nl.append(0)
+        else:
+            nl.append(len(a.lhs))
+            for t in list(a.lhs) + list(a.rhs):
+                k = TOKEN_KIND[t[0]]
+                toks.append((k, int(t[1]) if k in (0, 7) else 0, float(t[1]) if k == 1 else 0.0))
+        ptr.append(len(toks))
+    arr = (_Token * max(1, len(toks)))(*[_Token(*t) for t in toks])
+    return np.asarray(ptr, np.int32), np.asarray(nl, np.int32), arr
+
+
 def _atom_arrays(prop, S):
     n = len(prop.atoms)
     coef = np.zeros((max(n, 1), S), np.int32)
@@ -141,14 +166,18 @@ def eval_prefix(prop, S: int, x: np.ndarray, t: np.ndarray, tmin: float, closed:
     nodes, root = flatten_formula(prop.formula)
     n_at, coef, op, bound = _atom_arrays(prop, S)
 
+    eptr, enl, etok = _expr_arrays(prop)
+
     class F(ctypes.Structure):
         _fields_ = [('n_nodes', ctypes.c_int), ('root', ctypes.c_int),
                     ('nodes', ctypes.POINTER(_Node)), ('n_atoms', ctypes.c_int), ('S', ctypes.c_int),
                     ('coef', ctypes.POINTER(ctypes.c_int32)), ('op', ctypes.POINTER(ctypes.c_int32)),
-                    ('bound', ctypes.POINTER(ctypes.c_double))]
+                    ('bound', ctypes.POINTER(ctypes.c_double)), ('expr_ptr', ctypes.POINTER(ctypes.c_int32)),
+                    ('n_lhs', ctypes.POINTER(ctypes.c_int32)), ('tokens', ctypes.POINTER(_Token))]
 
     f = F(len(nodes), root, nodes, n_at, S, _ptr(coef, ctypes.c_int32), _ptr(op, ctypes.c_int32),
-          _ptr(bound, ctypes.c_double))
+          _ptr(bound, ctypes.c_double), _ptr(eptr, ctypes.c_int32) if eptr is not None else None,
+          _ptr(enl, ctypes.c_int32) if enl is not None else None, etok)
     L = lib()
     L.orc_eval_prefix.argtypes = [ctypes.POINTER(F), ctypes.c_int64, ctypes.POINTER(ctypes.c_double),
                                   ctypes.POINTER(ctypes.c_int32), ctypes.c_double, ctypes.c_int]
@@ -187,6 +216,7 @@ def run(model, prop, seed: int, instance: int = 0, traj_begin: int = 0, n_traj: 
     st = np.ascontiguousarray(model.stoich, np.int32)
     nodes, root = flatten_formula(prop.formula)
     n_at, coef, op, bound = _atom_arrays(prop, S)
+    eptr, enl, etok = _expr_arrays(prop)
     fr, fs, fn, fp = _factor_arrays(model)
     n = int(n_traj)
     out = dict(verdict=np.zeros(n, np.uint8), status=np.zeros(n, np.uint8),
@@ -201,7 +231,7 @@ def run(model, prop, seed: int, instance: int = 0, traj_begin: int = 0, n_traj: 
                           P(ctypes.c_double), P(ctypes.c_int32), ctypes.c_int, P(ctypes.c_int32),
                           P(ctypes.c_int32), P(ctypes.c_int32), P(ctypes.c_double), ctypes.c_int, ctypes.c_int,
                           P(_Node), ctypes.c_int, P(ctypes.c_int32), P(ctypes.c_int32),
-                          P(ctypes.c_double), ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint64,
+                          P(ctypes.c_double), P(ctypes.c_int32), P(ctypes.c_int32), P(_Token), ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint64,
                           ctypes.c_uint64, ctypes.c_uint64, ctypes.c_double, ctypes.c_int,
                           P(ctypes.c_uint8), P(ctypes.c_uint8), P(ctypes.c_uint64),
                           P(ctypes.c_double), P(ctypes.c_int32)]
@@ -210,7 +240,9 @@ def run(model, prop, seed: int, instance: int = 0, traj_begin: int = 0, n_traj: 
                    _ptr(fr, ctypes.c_int32), _ptr(fs, ctypes.c_int32), _ptr(fn, ctypes.c_int32),
                    _ptr(fp, ctypes.c_double), len(nodes), root, nodes,
                    n_at, _ptr(coef, ctypes.c_int32), _ptr(op, ctypes.c_int32),
-                   _ptr(bound, ctypes.c_double), int(seed) & ((1 << 64) - 1), int(instance),
+                   _ptr(bound, ctypes.c_double), _ptr(eptr, ctypes.c_int32) if eptr is not None else None,
+                   _ptr(enl, ctypes.c_int32) if enl is not None else None, etok,
+                   int(seed) & ((1 << 64) - 1), int(instance),
                    int(traj_begin), n, int(budget), float(t_max), int(threads),
                    _ptr(out['verdict'], ctypes.c_uint8), _ptr(out['status'], ctypes.c_uint8),
                    _ptr(out['events'], ctypes.c_uint64), _ptr(out['t_final'], ctypes.c_double),

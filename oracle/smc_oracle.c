@@ -98,12 +98,22 @@ typedef struct {
 } orc_node;
 
 typedef struct {
+    int32_t kind, arg; /* 0 species, 1 constant, 2 +, 3 -, 4 *, 5 /, 6 sqrt, 7 ^arg */
+    double value;
+} orc_token;
+
+typedef struct {
     int n_nodes, root;
     const orc_node *nodes;
     int n_atoms, S;
     const int32_t *coef;  /* [n_atoms][S]                                   */
     const int32_t *op;    /* [n_atoms]                                      */
     const double *bound;  /* [n_atoms]                                      */
+    /* arithmetic atoms (may be NULL): atom a is lhs <op> rhs when
+     * expr_ptr[a + 1] > expr_ptr[a]; its tokens are tokens[expr_ptr[a] ..
+     * expr_ptr[a + 1]), the first n_lhs[a] of them the left side           */
+    const int32_t *expr_ptr, *n_lhs;
+    const orc_token *tokens;
 } orc_formula;
 
 /* what is known about a path: positions 0..n-1 with entry times t[] and
@@ -132,12 +142,41 @@ static int or3(int a, int b)
 }
 
 /* Sec. 3.1: sigma |= (val' <| val'') iff Eval(sigma[0], val') <| Eval(..). */
-static int atom_holds(const orc_formula *f, int a, const int32_t *x)
+/* Sec. 3.1's Eval of an arithmetic value: a postfix program over the state,
+ * every operation in double precision, rounded once; powers by repeated
+ * multiplication. */
+static double eval_value(const orc_token *tk, int n, const int32_t *x)
 {
-    int64_t L = 0;
-    for (int i = 0; i < f->S; ++i) L += (int64_t)f->coef[(int64_t)a * f->S + i] * (int64_t)x[i];
-    double v = (double)L, b = f->bound[a];
-    switch (f->op[a]) {
+    double st[16];
+    int d = 0;
+    for (int i = 0; i < n; ++i) {
+        const orc_token *t = tk + i;
+        double b;
+        switch (t->kind) {
+        case 0: st[d++] = (double)x[t->arg]; break;
+        case 1: st[d++] = t->value; break;
+        case 2: b = st[--d]; st[d - 1] = st[d - 1] + b; break;
+        case 3: b = st[--d]; st[d - 1] = st[d - 1] - b; break;
+        case 4: b = st[--d]; st[d - 1] = st[d - 1] * b; break;
+        case 5: b = st[--d]; st[d - 1] = st[d - 1] / b; break;
+        case 6: st[d - 1] = sqrt(st[d - 1]); break;
+        default: {
+            const double a = st[d - 1];
+            double r = 1.0;
+            if (t->arg > 0) {
+                r = a;
+                for (int k = 1; k < t->arg; ++k) r = r * a;
+            }
+            st[d - 1] = r;
+        }
+        }
+    }
+    return st[0];
+}
+
+static int compare(int op, double v, double b)
+{
+    switch (op) {
     case OP_LT: return v < b;
     case OP_LE: return v <= b;
     case OP_GE: return v >= b;
@@ -145,6 +184,18 @@ static int atom_holds(const orc_formula *f, int a, const int32_t *x)
     case OP_EQ: return v == b;
     default: return v != b;
     }
+}
+
+static int atom_holds(const orc_formula *f, int a, const int32_t *x)
+{
+    if (f->expr_ptr && f->expr_ptr[a + 1] > f->expr_ptr[a]) {
+        const orc_token *tk = f->tokens + f->expr_ptr[a];
+        const int nl = f->n_lhs[a], nr = f->expr_ptr[a + 1] - f->expr_ptr[a] - nl;
+        return compare(f->op[a], eval_value(tk, nl, x), eval_value(tk + nl, nr, x));
+    }
+    int64_t L = 0;
+    for (int i = 0; i < f->S; ++i) L += (int64_t)f->coef[(int64_t)a * f->S + i] * (int64_t)x[i];
+    return compare(f->op[a], (double)L, f->bound[a]);
 }
 
 static int ev3(const orc_formula *f, int node, int64_t i, const orc_know *K);
@@ -475,13 +526,14 @@ int orc_run(int S, int R, const int32_t *reactants, const int32_t *stoich, const
             const int32_t *x0, int n_fact, const int32_t *fact_reaction, const int32_t *fact_species,
             const int32_t *fact_power, const double *fact_param, int n_nodes, int root,
             const orc_node *nodes, int n_atoms, const int32_t *coef, const int32_t *op,
-            const double *bound, uint64_t seed, uint32_t instance, uint64_t traj_begin, uint64_t n_traj,
+            const double *bound, const int32_t *expr_ptr, const int32_t *expr_n_lhs,
+            const orc_token *expr_tokens, uint64_t seed, uint32_t instance, uint64_t traj_begin, uint64_t n_traj,
             uint64_t budget, double t_max, int n_threads, uint8_t *verdict, uint8_t *status,
             uint64_t *events, double *t_final, int32_t *x_final)
 {
     orc_model M = {S, R, reactants, stoich, rates, x0, n_fact, fact_reaction, fact_species, fact_power,
                    fact_param};
-    orc_formula f = {n_nodes, root, nodes, n_atoms, S, coef, op, bound};
+    orc_formula f = {n_nodes, root, nodes, n_atoms, S, coef, op, bound, expr_ptr, expr_n_lhs, expr_tokens};
     orc_job J;
     memset(&J, 0, sizeof(J));
     J.M = &M; J.f = &f; J.seed = seed; J.traj_begin = traj_begin; J.n_traj = n_traj;

@@ -175,6 +175,26 @@ class Context:
         self._check(N.smc_load_property(self.h, n_atoms, _p(coef, ctypes.c_int32), _p(op, ctypes.c_int32),
                                         _p(bound, ctypes.c_double), per, arr, len(nodes),
                                         float(t_max)), 'smc_load_property')
+        atoms = props[0].atoms if isinstance(prop, (list, tuple)) else prop.atoms
+        for a, at in enumerate(atoms):
+            if at.lhs is not None:
+                self.set_atom_expression(a, at.op, at.lhs, at.rhs)
+
+    @staticmethod
+    def _tokens(side):
+        toks = []
+        for t in side:
+            k = N.TOK[t[0]]
+            toks.append(N.smc_token(k, int(t[1]) if k in (0, 7) else 0, float(t[1]) if k == 1 else 0.0))
+        return (N.smc_token * max(1, len(toks)))(*toks), len(toks)
+
+    def set_atom_expression(self, atom: int, op: str, lhs, rhs):
+        """Atom ``atom`` becomes the arithmetic atom lhs <op> rhs (token lists
+        as in workloads.Atom; smc_set_atom_expression)."""
+        la, ln = self._tokens(lhs)
+        ra, rn = self._tokens(rhs)
+        self._check(N.smc_set_atom_expression(self.h, int(atom), N.OP[op], la, ln, ra, rn),
+                    'smc_set_atom_expression')
 
     def set_option(self, name: str, value: float):
         self._check(N.smc_set_option(self.h, N.OPT[name], float(value)), f'smc_set_option({name})')

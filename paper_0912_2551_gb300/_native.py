@@ -68,6 +68,13 @@ class smc_cv_result(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class smc_token(ctypes.Structure):
+    _fields_ = [('kind', ctypes.c_int32), ('arg', ctypes.c_int32), ('value', ctypes.c_double)]
+
+
+TOK = {'x': 0, 'c': 1, '+': 2, '-': 3, '*': 4, '/': 5, 'sqrt': 6, 'pow': 7}
+
+
 class smc_cme_result(ctypes.Structure):
     _fields_ = [('p', ctypes.c_double), ('truncated', ctypes.c_double), ('poisson_tail', ctypes.c_double),
                 ('n_states', ctypes.c_int64), ('iterations', ctypes.c_int64), ('lambda_t', ctypes.c_double)]
@@ -98,6 +105,9 @@ SIGNATURES = {
     'smc_set_option': (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_double]),
     'smc_cme_reach': (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int32, ctypes.c_int64,
                                      ctypes.POINTER(smc_cme_result)]),
+    'smc_set_atom_expression': (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
+                                               ctypes.POINTER(smc_token), ctypes.c_int,
+                                               ctypes.POINTER(smc_token), ctypes.c_int]),
     'smc_load_rate_factors': (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, c_i32p, c_i32p, c_i32p, c_f64p]),
     'smc_get_launch_shape': (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, c_i32p, c_i32p, c_i32p,
                                             c_i32p, c_i32p, c_i32p]),

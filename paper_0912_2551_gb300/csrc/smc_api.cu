@@ -66,6 +66,12 @@ struct smc_ctx {
     std::vector<int32_t> atom_op;
     std::vector<double> atom_bound;   // [n_atoms] or [n_inst][n_atoms]
     std::vector<int32_t> atom_coef;   // concatenated per instance [n_atoms][S_m]
+    // arithmetic atoms (smc_set_atom_expression), [n_atoms]; op < 0: linear
+    struct AtomExpr {
+        int op = -1;
+        std::vector<smc_token> lhs, rhs;
+    };
+    std::vector<AtomExpr> atom_expr;
     std::vector<size_t> coef_off;
 
     // device state
@@ -132,6 +138,7 @@ struct smc_ctx {
     // specialized kernels of the loaded structure (null: the generic ones run)
     smc::JitKernels jit_k;
     bool jit_ready = false;
+    bool ext = false;             // rate-law factors or arithmetic atoms in use (generic kernel variant)
     std::string jit_why;          // why they are not in use
 };
 
@@ -340,6 +347,26 @@ int validate_params(smc_ctx *ctx, int S, int R, const double *rates, const int32
     return SMC_OK;
 }
 
+// The arithmetic atoms among the used atoms (views in used-atom order), and
+// whether there is any.
+std::vector<smc::AtomExprView> used_expr(const smc_ctx *ctx, bool &any)
+{
+    std::vector<smc::AtomExprView> v(ctx->used_atoms.size());
+    any = false;
+    for (size_t b = 0; b < v.size(); ++b) {
+        const int a = ctx->used_atoms[b];
+        if (a >= (int)ctx->atom_expr.size() || ctx->atom_expr[a].op < 0) continue;
+        const auto &e = ctx->atom_expr[a];
+        v[b].op = e.op;
+        v[b].lhs = e.lhs.data();
+        v[b].n_lhs = (int)e.lhs.size();
+        v[b].rhs = e.rhs.data();
+        v[b].n_rhs = (int)e.rhs.size();
+        any = true;
+    }
+    return v;
+}
+
 // Model-specialized kernels: when every instance shares one structure
 // (species, reactions, reactants, stoichiometry, monitored atoms and their
 // thresholds), the structure is compiled into the kernel; rates and x0 stay
@@ -364,6 +391,7 @@ void try_specialize(smc_ctx *ctx)
         }
         for (int b = 0; b < nu; ++b) {
             const int a = ctx->used_atoms[b];
+            if (a < (int)ctx->atom_expr.size() && ctx->atom_expr[a].op >= 0) continue;  // same for all
             const int32_t *c = ctx->atom_coef.data() + ctx->coef_off[m] + (size_t)a * S;
             const double bnd = ctx->per_instance_bound ? ctx->atom_bound[(size_t)m * ctx->n_atoms + a] : ctx->atom_bound[a];
             int64_t lo, hi;
@@ -396,6 +424,9 @@ void try_specialize(smc_ctx *ctx)
     M.f_spec = ctx->f_spec.data();
     M.f_pow = ctx->f_pow.data();
     M.f_par = ctx->f_par.data();
+    bool any_expr = false;
+    const std::vector<smc::AtomExprView> ev = used_expr(ctx, any_expr);
+    M.expr = any_expr ? ev.data() : nullptr;
     const std::string header = smc::jit_model_header(M, ctx->jit_why);
     if (header.empty()) return;
     std::string err;
@@ -439,7 +470,10 @@ int prepare(smc_ctx *ctx)
             bnd[b] = ctx->per_instance_bound ? ctx->atom_bound[(size_t)m * ctx->n_atoms + a]
                                              : ctx->atom_bound[a];
         }
-        int rc = smc::build_blob(M, nu, coef.data(), op.data(), bnd.data(), blob, ctx->err);
+        bool any_expr = false;
+        const std::vector<smc::AtomExprView> ev = used_expr(ctx, any_expr);
+        int rc = smc::build_blob(M, nu, coef.data(), op.data(), bnd.data(), any_expr ? ev.data() : nullptr, blob,
+                                 ctx->err);
         if (rc) return rc;
         off[m] = all.size();
         words[m] = (int)blob.size();
@@ -494,6 +528,11 @@ int prepare(smc_ctx *ctx)
     CK(cudaMallocHost(&ctx->h_range, (size_t)n * 2 * 8));
     CK(cudaMallocHost(&ctx->h_counts, (size_t)n * 4 * 8));
     CK(cudaMallocHost(&ctx->h_wilson, (size_t)n * 3 * 8));
+    {
+        bool any_expr = false;
+        used_expr(ctx, any_expr);
+        ctx->ext = any_expr || !ctx->f_reac.empty();
+    }
     try_specialize(ctx);
     ctx->dirty = false;
     return SMC_OK;
@@ -553,11 +592,12 @@ int plan_class(smc_ctx *ctx, int plain, const SizeClass &c, const Shape &sh, Lau
     L.refill = sh.refill;
     if ((size_t)L.smem > ctx->smem_optin)
         return fail(ctx, SMC_E_UNSUPPORTED, "model tables do not fit in shared memory");
-    const int set_rc = L.kernel ? smc_jit_set_smem_limit(L.kernel, L.smem) : smc_ssa_set_smem_limit(plain, L.smem);
+    const int set_rc =
+        L.kernel ? smc_jit_set_smem_limit(L.kernel, L.smem) : smc_ssa_set_smem_limit(plain, ctx->ext, L.smem);
     if (set_rc) return fail(ctx, SMC_E_CUDA, "cudaFuncSetAttribute failed");
     int per_sm = 0;
     const int occ_rc = L.kernel ? smc_jit_max_blocks_per_sm(L.kernel, L.block, L.smem, &per_sm)
-                                : smc_ssa_max_blocks_per_sm(plain, L.block, L.smem, &per_sm);
+                                : smc_ssa_max_blocks_per_sm(plain, ctx->ext, L.block, L.smem, &per_sm);
     if (occ_rc || per_sm < 1) return fail(ctx, SMC_E_UNSUPPORTED, "no block of this shape fits on an SM");
     if (sh.blocks_sm > 0) per_sm = std::min(per_sm, sh.blocks_sm);
     L.grid = ctx->n_sm * per_sm;
@@ -582,7 +622,7 @@ int issue_class(smc_ctx *ctx, int plain, const SsaParams &common, const Launch &
     if (smc_launch_queue_init(p, s))
         return fail(ctx, SMC_E_CUDA, std::string("queue init: ") + cudaGetErrorString(cudaGetLastError()));
     const int lrc = L.kernel ? smc_jit_launch(L.kernel, p, L.grid, L.block, L.smem, s)
-                             : smc_launch_ssa(plain, p, L.grid, L.block, L.smem, s);
+                             : smc_launch_ssa(plain, ctx->ext, p, L.grid, L.block, L.smem, s);
     if (lrc) return fail(ctx, SMC_E_CUDA, std::string("ssa launch: ") + cudaGetErrorString(cudaGetLastError()));
     return SMC_OK;
 }
@@ -963,6 +1003,9 @@ int smc_cme_reach(smc_ctx *ctx, int instance, int32_t cap, int64_t max_states, s
     pred.neg = neg.data();
     pred.goal = P.u[0].P;
     pred.stay = P.u[0].L;
+    bool any_expr = false;
+    const std::vector<smc::AtomExprView> ev = used_expr(ctx, any_expr);
+    pred.expr = any_expr ? ev.data() : nullptr;
     CK(cudaSetDevice(ctx->device));
     smc::CmeResult r;
     const int rc = smc::cme_reach(M, pred, P.u[0].b, cap, max_states, r, ctx->err, ctx->stream);
@@ -977,6 +1020,28 @@ int smc_cme_reach(smc_ctx *ctx, int instance, int32_t cap, int64_t max_states, s
     out->n_states = r.n_states;
     out->iterations = r.iterations;
     out->lambda_t = r.lambda_t;
+    return SMC_OK;
+}
+
+int smc_set_atom_expression(smc_ctx *ctx, int atom, int op, const smc_token *lhs, int n_lhs,
+                            const smc_token *rhs, int n_rhs)
+{
+    if (!ctx) return SMC_E_INVALID_ARG;
+    if (!ctx->have_prop) return fail(ctx, SMC_E_STATE, "load a property first");
+    if (atom < 0 || atom >= ctx->n_atoms) return fail(ctx, SMC_E_INVALID_ARG, "atom index out of range");
+    if (op < SMC_OP_LT || op > SMC_OP_NE) return fail(ctx, SMC_E_INVALID_ARG, "unknown atom operator");
+    if (!lhs || !rhs) return fail(ctx, SMC_E_INVALID_ARG, "null program");
+    int s_min = ctx->S[0];
+    for (int m = 0; m < ctx->n_inst; ++m) s_min = std::min(s_min, ctx->S[m]);
+    int rc = smc::validate_tokens(lhs, n_lhs, s_min, ctx->err);
+    if (rc) return rc;
+    rc = smc::validate_tokens(rhs, n_rhs, s_min, ctx->err);
+    if (rc) return rc;
+    auto &e = ctx->atom_expr[atom];
+    e.op = op;
+    e.lhs.assign(lhs, lhs + n_lhs);
+    e.rhs.assign(rhs, rhs + n_rhs);
+    ctx->dirty = true;
     return SMC_OK;
 }
 
@@ -1026,6 +1091,7 @@ int smc_load_property(smc_ctx *ctx, int n_atoms, const int32_t *atom_coef, const
     ctx->atom_bound.assign(atom_bound, atom_bound + nb);
     ctx->atom_coef.assign(atom_coef, atom_coef + total);
     ctx->coef_off = coff;
+    ctx->atom_expr.assign(n_atoms, smc_ctx::AtomExpr());
     ctx->have_prop = true;
     ctx->dirty = true;
     return SMC_OK;
@@ -1356,6 +1422,11 @@ int smc_monitor_replay(smc_ctx *ctx, int n_paths, const int32_t *len, const int3
     if (!ctx) return SMC_E_INVALID_ARG;
     if (!ctx->have_model || !ctx->have_prop) return fail(ctx, SMC_E_STATE, "load a model and a property first");
     if (ctx->batch) return fail(ctx, SMC_E_UNSUPPORTED, "replay needs a single network");
+    {
+        bool any_expr = false;
+        used_expr(ctx, any_expr);
+        if (any_expr) return fail(ctx, SMC_E_UNSUPPORTED, "replay supports linear atoms only");
+    }
     if (n_paths < 1 || !len || !x || !t || !tmin || !closed || !verdict || !decided_at)
         return fail(ctx, SMC_E_INVALID_ARG, "bad replay arrays");
     CK(cudaSetDevice(ctx->device));

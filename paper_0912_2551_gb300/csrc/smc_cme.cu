@@ -96,6 +96,10 @@ int cme_reach(const CmeModel &M, const CmePredicate &pred, double t_end, int32_t
     auto bits = [&](const int32_t *x) {
         uint32_t ab = 0;
         for (int a = 0; a < pred.n_atoms; ++a) {
+            if (pred.expr && pred.expr[a].op >= 0) {
+                ab |= (uint32_t)expr_atom_holds(pred.expr[a], x) << a;
+                continue;
+            }
             int64_t L = 0;
             for (int i = 0; i < S; ++i) L += (int64_t)pred.coef[(size_t)a * S + i] * x[i];
             const uint32_t in = (L >= pred.lo[a]) & (L <= pred.hi[a]);

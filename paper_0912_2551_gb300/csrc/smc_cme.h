@@ -6,6 +6,8 @@
 
 #include <string>
 
+#include "smc_compile.h"
+
 namespace smc {
 
 // One network instance (host arrays), with optional rate-law factors.
@@ -28,6 +30,7 @@ struct CmePredicate {
     const int64_t *lo = nullptr, *hi = nullptr;
     const uint8_t *neg = nullptr;
     uint64_t goal = 0, stay = ~0ull;
+    const AtomExprView *expr = nullptr;  // [n_atoms] arithmetic atoms, or null
 };
 
 struct CmeResult {

@@ -319,9 +319,82 @@ void atom_threshold(int op, double b, int64_t &lo, int64_t &hi, bool &neg)
     }
 }
 
+int validate_tokens(const smc_token *t, int n, int S, std::string &err)
+{
+    if (n < 1 || n > SMC_EXPR_MAX_TOKENS) { err = "an atom program needs 1..32 tokens"; return SMC_E_INVALID_ARG; }
+    int d = 0;
+    for (int i = 0; i < n; ++i) {
+        switch (t[i].kind) {
+        case SMC_TOK_SPECIES:
+            if (t[i].arg < 0 || t[i].arg >= S) { err = "atom program: species out of range"; return SMC_E_INVALID_ARG; }
+            ++d;
+            break;
+        case SMC_TOK_CONST:
+            if (!std::isfinite(t[i].value)) { err = "atom program: constants must be finite"; return SMC_E_INVALID_ARG; }
+            ++d;
+            break;
+        case SMC_TOK_ADD: case SMC_TOK_SUB: case SMC_TOK_MUL: case SMC_TOK_DIV:
+            if (d < 2) { err = "atom program: operator without two operands"; return SMC_E_INVALID_ARG; }
+            --d;
+            break;
+        case SMC_TOK_SQRT:
+            if (d < 1) { err = "atom program: sqrt without an operand"; return SMC_E_INVALID_ARG; }
+            break;
+        case SMC_TOK_POWI:
+            if (d < 1 || t[i].arg < 0 || t[i].arg > 16) { err = "atom program: bad power"; return SMC_E_INVALID_ARG; }
+            break;
+        default: err = "atom program: unknown token"; return SMC_E_INVALID_ARG;
+        }
+        if (d > SMC_EXPR_MAX_DEPTH) { err = "atom program deeper than 8"; return SMC_E_INVALID_ARG; }
+    }
+    if (d != 1) { err = "an atom program must leave one value"; return SMC_E_INVALID_ARG; }
+    return SMC_OK;
+}
+
+double eval_tokens(const smc_token *t, int n, const int32_t *x)
+{
+    double st[SMC_EXPR_MAX_DEPTH + 1];
+    int d = 0;
+    for (int i = 0; i < n; ++i) {
+        double b;
+        switch (t[i].kind) {
+        case SMC_TOK_SPECIES: st[d++] = (double)x[t[i].arg]; break;
+        case SMC_TOK_CONST: st[d++] = t[i].value; break;
+        case SMC_TOK_ADD: b = st[--d]; st[d - 1] = st[d - 1] + b; break;
+        case SMC_TOK_SUB: b = st[--d]; st[d - 1] = st[d - 1] - b; break;
+        case SMC_TOK_MUL: b = st[--d]; st[d - 1] = st[d - 1] * b; break;
+        case SMC_TOK_DIV: b = st[--d]; st[d - 1] = st[d - 1] / b; break;
+        case SMC_TOK_SQRT: st[d - 1] = std::sqrt(st[d - 1]); break;
+        default: {
+            const double a = st[d - 1];
+            double r = 1.0;
+            if (t[i].arg > 0) {
+                r = a;
+                for (int k = 1; k < t[i].arg; ++k) r = r * a;
+            }
+            st[d - 1] = r;
+        }
+        }
+    }
+    return st[0];
+}
+
+bool expr_atom_holds(const AtomExprView &e, const int32_t *x)
+{
+    const double l = eval_tokens(e.lhs, e.n_lhs, x), r = eval_tokens(e.rhs, e.n_rhs, x);
+    switch (e.op) {
+    case SMC_OP_LT: return l < r;
+    case SMC_OP_LE: return l <= r;
+    case SMC_OP_GE: return l >= r;
+    case SMC_OP_GT: return l > r;
+    case SMC_OP_EQ: return l == r;
+    default: return l != r;
+    }
+}
+
 int build_blob(const InstanceModel &M, int n_used, const int32_t *coef_used /*[n_used][S]*/,
-               const int32_t *op_used, const double *bound_used, std::vector<uint32_t> &blob,
-               std::string &err)
+               const int32_t *op_used, const double *bound_used, const AtomExprView *expr_used,
+               std::vector<uint32_t> &blob, std::string &err)
 {
     const int S = M.S, R = M.R;
     // stoichiometry CSR and changed-species sets
@@ -400,6 +473,17 @@ int build_blob(const InstanceModel &M, int n_used, const int32_t *coef_used /*[n
             for (int i = 0; i < S; ++i) d += (int64_t)c[i] * M.stoich[(size_t)j * S + i];
             if (d != 0) amask[j] |= 1u << a;
         }
+        if (expr_used && expr_used[a].op >= 0) {  // arithmetic atom: moved by any change of its species
+            const AtomExprView &e = expr_used[a];
+            for (int j = 0; j < R; ++j)
+                for (int side = 0; side < 2; ++side) {
+                    const smc_token *t = side ? e.rhs : e.lhs;
+                    const int n = side ? e.n_rhs : e.n_lhs;
+                    for (int i = 0; i < n; ++i)
+                        if (t[i].kind == SMC_TOK_SPECIES && M.stoich[(size_t)j * S + t[i].arg] != 0)
+                            amask[j] |= 1u << a;
+                }
+        }
         if (!std::isfinite(bound_used[a])) { err = "atom bounds must be finite"; return SMC_E_INVALID_ARG; }
         bool neg;
         atom_threshold(op_used[a], bound_used[a], athr[2 * a], athr[2 * a + 1], neg);
@@ -457,8 +541,37 @@ int build_blob(const InstanceModel &M, int n_used, const int32_t *coef_used /*[n
     }
     section(BH_X0);
     for (int i = 0; i < S; ++i) blob.push_back((uint32_t)M.x0[i]);
+    // arithmetic atoms' tokens (4 words each)
+    std::vector<uint32_t> ex;
+    std::vector<uint32_t> ex_off(n_used, 0);
+    for (int a = 0; a < n_used; ++a) {
+        if (!expr_used || expr_used[a].op < 0) continue;
+        const AtomExprView &e = expr_used[a];
+        ex_off[a] = (uint32_t)ex.size();
+        for (int side = 0; side < 2; ++side) {
+            const smc_token *t = side ? e.rhs : e.lhs;
+            const int n = side ? e.n_rhs : e.n_lhs;
+            for (int i = 0; i < n; ++i) {
+                uint32_t w[2];
+                std::memcpy(w, &t[i].value, 8);
+                ex.push_back((uint32_t)t[i].kind | ((uint32_t)t[i].arg << 8));
+                ex.push_back(0);
+                ex.push_back(w[0]);
+                ex.push_back(w[1]);
+            }
+        }
+    }
     section(BH_ATOM);
     for (int a = 0; a < n_used; ++a) {
+        if (expr_used && expr_used[a].op >= 0) {
+            blob.push_back(SMC_ATOM_EXPR);
+            blob.push_back((uint32_t)expr_used[a].op);
+            blob.push_back(ex_off[a]);
+            blob.push_back((uint32_t)expr_used[a].n_lhs);
+            blob.push_back((uint32_t)expr_used[a].n_rhs);
+            blob.push_back(0);
+            continue;
+        }
         const uint32_t nt = aterm_ptr[a + 1] - aterm_ptr[a];
         blob.push_back(nt == 1 ? aterm[aterm_ptr[a]] : 0xFFFFFFFFu);
         blob.push_back((aneg >> a) & 1u);
@@ -468,6 +581,8 @@ int build_blob(const InstanceModel &M, int n_used, const int32_t *coef_used /*[n
             blob.push_back((uint32_t)(v >> 32));
         }
     }
+    section(BH_EXPR);
+    blob.insert(blob.end(), ex.begin(), ex.end());
     section(BH_FACT_PTR);
     blob.insert(blob.end(), f_ptr.begin(), f_ptr.end());
     section(BH_FACT);

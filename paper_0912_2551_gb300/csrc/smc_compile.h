@@ -39,8 +39,28 @@ int compile_formula(const std::vector<FNode> &tree, int root, int n_atoms, doubl
 // atom  L <op> b  (L an integer)  as  lo <= L <= hi, negated when neg.
 void atom_threshold(int op, double b, int64_t &lo, int64_t &hi, bool &neg);
 
+// An arithmetic atom lhs <op> rhs (smc_set_atom_expression); op < 0: none.
+struct AtomExprView {
+    int op = -1;
+    const smc_token *lhs = nullptr, *rhs = nullptr;
+    int n_lhs = 0, n_rhs = 0;
+};
+
+// Checks a postfix program: known tokens, species < S, exponents 0..16,
+// stack never empty when popped, at most SMC_EXPR_MAX_DEPTH deep, one value
+// left.  0 or SMC_E_INVALID_ARG with the reason in err.
+int validate_tokens(const smc_token *t, int n, int S, std::string &err);
+
+// Evaluates a program on a state (FP64, each operation rounded once).
+double eval_tokens(const smc_token *t, int n, const int32_t *x);
+
+// lhs <op> rhs on a state.
+bool expr_atom_holds(const AtomExprView &e, const int32_t *x);
+
 // Builds the shared-memory table of one instance (layout: BlobHdr).
+// expr_used (may be null): the arithmetic atoms among the used ones.
 int build_blob(const InstanceModel &M, int n_used, const int32_t *coef_used, const int32_t *op_used,
-               const double *bound_used, std::vector<uint32_t> &blob, std::string &err);
+               const double *bound_used, const AtomExprView *expr_used, std::vector<uint32_t> &blob,
+               std::string &err);
 
 }  // namespace smc

@@ -266,13 +266,66 @@ __device__ __forceinline__ void mon_start(MonLane &ml, const MonProg &P)
     mon_horizon(ml, P);
 }
 
+// One side of an arithmetic atom: a postfix program over the lane's counts
+// (x[i] at xs[i * 32]), FP64, each operation rounded once.
+__device__ __forceinline__ double eval_expr(const uint32_t *tk, int n, const int32_t *xs)
+{
+    double st[SMC_EXPR_MAX_DEPTH + 1];
+    int d = 0;
+    for (int i = 0; i < n; ++i) {
+        const uint32_t w = tk[4 * i];
+        const int kind = (int)(w & 255u), arg = (int)(w >> 8);
+        double b;
+        switch (kind) {
+        case SMC_TOK_SPECIES: st[d++] = int_to_double(xs[arg * 32]); break;
+        case SMC_TOK_CONST:
+            st[d++] = __hiloint2double((int)tk[4 * i + 3], (int)tk[4 * i + 2]);
+            break;
+        case SMC_TOK_ADD: b = st[--d]; st[d - 1] = __dadd_rn(st[d - 1], b); break;
+        case SMC_TOK_SUB: b = st[--d]; st[d - 1] = __dsub_rn(st[d - 1], b); break;
+        case SMC_TOK_MUL: b = st[--d]; st[d - 1] = __dmul_rn(st[d - 1], b); break;
+        case SMC_TOK_DIV: b = st[--d]; st[d - 1] = __ddiv_rn(st[d - 1], b); break;
+        case SMC_TOK_SQRT: st[d - 1] = __dsqrt_rn(st[d - 1]); break;
+        default: {
+            const double a = st[d - 1];
+            double r = 1.0;
+            if (arg > 0) {
+                r = a;
+                for (int k = 1; k < arg; ++k) r = __dmul_rn(r, a);
+            }
+            st[d - 1] = r;
+        }
+        }
+    }
+    return st[0];
+}
+
+// An arithmetic atom (record: SMC_ATOM_EXPR, op, token offset, n_lhs, n_rhs).
+__device__ __noinline__ uint32_t expr_atom_bit(const uint32_t *A, const uint32_t *ex, const int32_t *xs)
+{
+    const uint32_t *tk = ex + A[2];
+    const int nl = (int)A[3], nr = (int)A[4];
+    const double l = eval_expr(tk, nl, xs), r = eval_expr(tk + 4 * nl, nr, xs);
+    switch ((int)A[1]) {
+    case SMC_OP_LT: return l < r;
+    case SMC_OP_LE: return l <= r;
+    case SMC_OP_GE: return l >= r;
+    case SMC_OP_GT: return l > r;
+    case SMC_OP_EQ: return l == r;
+    default: return l != r;
+    }
+}
+
 // Atom a at the lane's current state: L = sum of coef * x over the atom's
-// terms (exact int64), bit = (lo <= L <= hi) xor neg, placed at bit a.
+// terms (exact int64), bit = (lo <= L <= hi) xor neg, placed at bit a; or
+// an arithmetic atom.
+template <bool EXT>
 __device__ __forceinline__ uint32_t atom_bit(const uint32_t *atoms, const uint32_t *tptr,
-                                             const uint32_t *terms, const int32_t *xs, int a)
+                                             const uint32_t *terms, const uint32_t *ex, const int32_t *xs, int a)
 {
     const uint32_t *A = atoms + 6 * a;
     const uint32_t w1 = A[0];
+    if (EXT && w1 == SMC_ATOM_EXPR) return expr_atom_bit(A, ex, xs) << a;
     long long L;
     if (w1 != 0xFFFFFFFFu) {  // single term
         L = (long long)xs[(w1 & 255u) * 32] * (long long)(((int32_t)w1) >> 8);

@@ -74,8 +74,31 @@ enum BlobHdr {
     BH_FACT,      // u32    [nf]     species | (power << 8) of factor q
     BH_FACT_D,    // double [nf][4]  a0, a1, b0, b1 of factor q
     BH_FACT_F,    // float  [nf][4]  the same, rounded to FP32
-    BH_COUNT = 24
+    BH_EXPR,      // u32    [nt][4]  arithmetic atoms' tokens: kind | arg << 8, 0, value (double)
+    BH_COUNT = 26
 };
+// The atom operators and arithmetic-atom tokens of include/smc.h, repeated
+// (identical definitions) for the run-time compiled kernels, which cannot
+// include that host header.
+#define SMC_OP_LT 0
+#define SMC_OP_LE 1
+#define SMC_OP_GE 2
+#define SMC_OP_GT 3
+#define SMC_OP_EQ 4
+#define SMC_OP_NE 5
+#define SMC_TOK_SPECIES 0
+#define SMC_TOK_CONST 1
+#define SMC_TOK_ADD 2
+#define SMC_TOK_SUB 3
+#define SMC_TOK_MUL 4
+#define SMC_TOK_DIV 5
+#define SMC_TOK_SQRT 6
+#define SMC_TOK_POWI 7
+#define SMC_EXPR_MAX_DEPTH 8
+// An arithmetic atom's record has word 0 = SMC_ATOM_EXPR, then op, the
+// word offset of its tokens within BH_EXPR, the token counts of the left
+// and right programs, 0.
+#define SMC_ATOM_EXPR 0xFFFFFFFEu
 // Rate-law factors: reaction k's propensity is c_k h_k(x) times, for each of
 // its factors q in order, (a0 + a1 x^n) / (b0 + b1 x^n) with x the count of
 // the factor's species; propensity words of reactions with factors carry
@@ -167,10 +190,11 @@ struct ReplayParams {
 #if defined(__cplusplus) && !defined(__CUDACC_RTC__)  // host code only (not in run-time compilation)
 extern "C++" {
 // host launch wrappers (smc_kernels.cu)
-int smc_launch_ssa(int plain, const SsaParams &p, int grid, int block, int smem_bytes,
+// ext: the model uses rate-law factors or arithmetic atoms (kernel variant)
+int smc_launch_ssa(int plain, int ext, const SsaParams &p, int grid, int block, int smem_bytes,
                    void *stream);
-int smc_ssa_max_blocks_per_sm(int plain, int block, int smem_bytes, int *out);
-int smc_ssa_set_smem_limit(int plain, int smem_bytes);
+int smc_ssa_max_blocks_per_sm(int plain, int ext, int block, int smem_bytes, int *out);
+int smc_ssa_set_smem_limit(int plain, int ext, int smem_bytes);
 int smc_launch_queue_init(const SsaParams &p, void *stream);
 int smc_launch_replay(const ReplayParams &p, void *stream);
 int smc_launch_log_batch(const double *tab, const double *u, uint64_t n, double *out, void *stream);

@@ -201,7 +201,51 @@ std::string jit_model_header(const JitModel &M, std::string &why)
     // atoms: (lo <= L <= hi) xor neg, L = sum coef x (exact int64)
     o << "__device__ __forceinline__ uint32_t jit_atoms(const int32_t *x)\n{\n    uint32_t ab = 0;\n";
     const int64_t MIN64 = std::numeric_limits<int64_t>::min(), MAX64 = std::numeric_limits<int64_t>::max();
+    int tmp = 0;
     for (int a = 0; a < M.n_atoms; ++a) {
+        if (M.expr && M.expr[a].op >= 0) {  // arithmetic atom: one temporary per token, in program order
+            const AtomExprView &e = M.expr[a];
+            std::string side[2];
+            for (int sd = 0; sd < 2; ++sd) {
+                const smc_token *t = sd ? e.rhs : e.lhs;
+                const int n = sd ? e.n_rhs : e.n_lhs;
+                std::vector<std::string> st;
+                for (int i = 0; i < n; ++i) {
+                    const std::string v = "e" + std::to_string(tmp++);
+                    std::string rhs;
+                    switch (t[i].kind) {
+                    case SMC_TOK_SPECIES: rhs = "int_to_double((long long)x[" + std::to_string(t[i].arg) + "])"; break;
+                    case SMC_TOK_CONST: rhs = hex_double(t[i].value); break;
+                    case SMC_TOK_SQRT: rhs = "__dsqrt_rn(" + st.back() + ")"; st.pop_back(); break;
+                    case SMC_TOK_POWI: {
+                        const std::string base = st.back();
+                        st.pop_back();
+                        if (t[i].arg == 0) rhs = "1.0";
+                        else {
+                            rhs = base;
+                            for (int k = 1; k < t[i].arg; ++k) rhs = "__dmul_rn(" + rhs + ", " + base + ")";
+                        }
+                        break;
+                    }
+                    default: {
+                        const std::string b = st.back();
+                        st.pop_back();
+                        const std::string x = st.back();
+                        st.pop_back();
+                        const char *fn = t[i].kind == SMC_TOK_ADD ? "__dadd_rn" : t[i].kind == SMC_TOK_SUB ? "__dsub_rn"
+                                       : t[i].kind == SMC_TOK_MUL ? "__dmul_rn" : "__ddiv_rn";
+                        rhs = std::string(fn) + "(" + x + ", " + b + ")";
+                    }
+                    }
+                    o << "    const double " << v << " = " << rhs << ";\n";
+                    st.push_back(v);
+                }
+                side[sd] = st.back();
+            }
+            static const char *cmp[] = {"<", "<=", ">=", ">", "==", "!="};
+            o << "    ab |= ((uint32_t)(" << side[0] << " " << cmp[e.op] << " " << side[1] << ")) << " << a << ";\n";
+            continue;
+        }
         std::ostringstream L;
         int nterm = 0, single = -1;
         for (int i = 0; i < S; ++i) {

@@ -12,6 +12,8 @@
 
 #include <string>
 
+#include "smc_compile.h"
+
 namespace smc {
 
 #define SMC_JIT_MAX_S 32
@@ -32,6 +34,7 @@ struct JitModel {
     const int32_t *coef = nullptr;       // [n_atoms][S]
     const int64_t *lo = nullptr, *hi = nullptr;
     const uint8_t *neg = nullptr;
+    const AtomExprView *expr = nullptr;  // [n_atoms] arithmetic atoms, or null
     // rate-law factors (reaction, species, power, params [4]); may be empty
     int n_fact = 0;
     const int32_t *f_reac = nullptr, *f_spec = nullptr, *f_pow = nullptr;

@@ -70,7 +70,7 @@ __device__ __noinline__ typename Prec<PLAIN>::T apply_factors(typename Prec<PLAI
 // a_k = c_k h_k(x) (Sec. 2.2) from a propensity word (see smc_internal.h),
 // times the reaction's rate-law factors if it has any.  FP64 path: h as an
 // exact integer, rounded once; mixed path: h in FP32.
-template <bool PLAIN>
+template <bool PLAIN, bool EXT>
 __device__ __forceinline__ typename Prec<PLAIN>::T propensity(uint32_t pw, const int32_t *xs,
                                                               const double *rate_d,
                                                               const float *rate_f, const uint32_t *blob)
@@ -87,7 +87,7 @@ __device__ __forceinline__ typename Prec<PLAIN>::T propensity(uint32_t pw, const
         const float h = __fmul_rn((float)xa, __fmaf_rn((float)xb, s, homo ? -0.5f : 0.0f));
         a = __fmul_rn(rate_f[k], h);
     }
-    if (pw & SMC_PW_FACT) a = apply_factors<PLAIN>(a, k, xs, blob);
+    if (EXT && (pw & SMC_PW_FACT)) a = apply_factors<PLAIN>(a, k, xs, blob);
     return a;
 }
 
@@ -109,7 +109,7 @@ __device__ __forceinline__ float renorm_groups(const float *as, float *gs, int R
     return (float)s;
 }
 
-template <bool PLAIN>
+template <bool PLAIN, bool EXT>
 __device__ __forceinline__ void run_instance(const SsaParams &p, const MonProg &P, const double *ltab,
                                              const int m, const uint32_t *blob, int32_t *xs, double *tc,
                                              typename Prec<PLAIN>::T *as, float *gs, const int lane)
@@ -128,6 +128,7 @@ __device__ __forceinline__ void run_instance(const SsaParams &p, const MonProg &
     const uint32_t *terms = blob + blob[BH_ATERM];
     const int32_t *x0 = reinterpret_cast<const int32_t *>(blob + blob[BH_X0]);
     const uint32_t *atoms = blob + blob[BH_ATOM];
+    const uint32_t *ex = blob + blob[BH_EXPR];
     const uint32_t *dense = blob + blob[BH_DENSE];
     const bool small = blob[BH_DENSE] != 0;
     const unsigned long long tend = p.uniform ? p.u_end : p.tend[m];
@@ -193,14 +194,14 @@ __device__ __forceinline__ void run_instance(const SsaParams &p, const MonProg &
                         xs[S * 32] = 1;
                         double s = 0.0;
                         for (int k = 0; k < R; ++k) {
-                            const T ak = propensity<PLAIN>(reac[k], xs, rate_d, rate_f, blob);
+                            const T ak = propensity<PLAIN, EXT>(reac[k], xs, rate_d, rate_f, blob);
                             as[k * 32] = ak;
                             s = __dadd_rn(s, (double)ak);
                         }
                         a0 = (T)s;
                         if (!PLAIN && !small) a0 = (T)renorm_groups((const float *)as, gs, R);
                         uint32_t ab = 0;
-                        for (int a = 0; a < NA; ++a) ab |= atom_bit(atoms, tptr, terms, xs, a);
+                        for (int a = 0; a < NA; ++a) ab |= atom_bit<EXT>(atoms, tptr, terms, ex, xs, a);
                         ml.ab = ab;
                         mon_start(ml, P);
                         active = true;
@@ -225,7 +226,7 @@ __device__ __forceinline__ void run_instance(const SsaParams &p, const MonProg &
 #pragma unroll
             for (int k = 0; k < SMC_SMALL_MAX; ++k) {
                 if (k < R) {
-                    const T ak = propensity<PLAIN>(reac[k], xs, rate_d, rate_f, blob);
+                    const T ak = propensity<PLAIN, EXT>(reac[k], xs, rate_d, rate_f, blob);
                     const bool positive =
                         PLAIN ? __double_as_longlong((double)ak) > 0 : ak > (T)0;
                     pos |= (uint32_t)positive << k;
@@ -329,7 +330,7 @@ __device__ __forceinline__ void run_instance(const SsaParams &p, const MonProg &
             ++e;
             t = tn;
             ab = 0;
-            for (int a = 0; a < NA; ++a) ab |= atom_bit(atoms, tptr, terms, xs, a);
+            for (int a = 0; a < NA; ++a) ab |= atom_bit<EXT>(atoms, tptr, terms, ex, xs, a);
         } else {
             for (uint32_t q = stp[j], qe = stp[j + 1]; q < qe; ++q) {
                 const uint32_t w = st[q];
@@ -338,7 +339,7 @@ __device__ __forceinline__ void run_instance(const SsaParams &p, const MonProg &
             for (uint32_t q = dpp[j], qe = dpp[j + 1]; q < qe; ++q) {
                 const uint32_t pw = dp[q];
                 const int k = pw & 255u;
-                const T ak = propensity<PLAIN>(pw, xs, rate_d, rate_f, blob);
+                const T ak = propensity<PLAIN, EXT>(pw, xs, rate_d, rate_f, blob);
                 if (!PLAIN) {
                     const T d = ak - as[k * 32];
                     a0 = a0 + d;
@@ -355,7 +356,7 @@ __device__ __forceinline__ void run_instance(const SsaParams &p, const MonProg &
             while (am) {
                 const int a = __ffs(am) - 1;
                 am &= am - 1u;
-                ab = (ab & ~(1u << a)) | atom_bit(atoms, tptr, terms, xs, a);
+                ab = (ab & ~(1u << a)) | atom_bit<EXT>(atoms, tptr, terms, ex, xs, a);
             }
         }
         if (always_step || ab != mh.ab || mh.pend) {
@@ -380,7 +381,9 @@ __device__ __forceinline__ void run_instance(const SsaParams &p, const MonProg &
 
 // Register budget: 64 per thread for the mixed path (32 resident warps per
 // SM), 80 for the FP64 path (24 warps; its FP64 pipe saturates before issue).
-template <bool PLAIN>
+// EXT: the model uses rate-law factors or arithmetic atoms; without them the
+// kernel carries none of their code (and none of its register pressure).
+template <bool PLAIN, bool EXT>
 __global__ void __launch_bounds__(256, PLAIN ? 3 : 4) ssa_kernel(const SsaParams p)
 {
     typedef typename Prec<PLAIN>::T T;
@@ -415,7 +418,7 @@ __global__ void __launch_bounds__(256, PLAIN ? 3 : 4) ssa_kernel(const SsaParams
             __syncwarp();
             cur = m;
         }
-        run_instance<PLAIN>(p, P, ltab, m, blob, xs, tc, as, gs, lane);
+        run_instance<PLAIN, EXT>(p, P, ltab, m, blob, xs, tc, as, gs, lane);
         __syncwarp();
     }
 
@@ -479,23 +482,33 @@ __global__ void replay_kernel(const ReplayParams rp)
 
 static int to_code(cudaError_t e) { return e == cudaSuccess ? 0 : -3; }
 
-int smc_ssa_set_smem_limit(int plain, int smem_bytes)
+static const void *ssa_kernel_ptr(int plain, int ext)
 {
-    const void *f = plain ? (const void *)ssa_kernel<true> : (const void *)ssa_kernel<false>;
-    return to_code(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes));
+    if (plain) return ext ? (const void *)ssa_kernel<true, true> : (const void *)ssa_kernel<true, false>;
+    return ext ? (const void *)ssa_kernel<false, true> : (const void *)ssa_kernel<false, false>;
 }
 
-int smc_ssa_max_blocks_per_sm(int plain, int block, int smem_bytes, int *out)
+int smc_ssa_set_smem_limit(int plain, int ext, int smem_bytes)
 {
-    const void *f = plain ? (const void *)ssa_kernel<true> : (const void *)ssa_kernel<false>;
-    return to_code(cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, f, block, smem_bytes));
+    return to_code(cudaFuncSetAttribute(ssa_kernel_ptr(plain, ext), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        smem_bytes));
 }
 
-int smc_launch_ssa(int plain, const SsaParams &p, int grid, int block, int smem_bytes, void *stream)
+int smc_ssa_max_blocks_per_sm(int plain, int ext, int block, int smem_bytes, int *out)
+{
+    return to_code(cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, ssa_kernel_ptr(plain, ext), block, smem_bytes));
+}
+
+int smc_launch_ssa(int plain, int ext, const SsaParams &p, int grid, int block, int smem_bytes, void *stream)
 {
     cudaStream_t s = (cudaStream_t)stream;
-    if (plain) ssa_kernel<true><<<grid, block, smem_bytes, s>>>(p);
-    else ssa_kernel<false><<<grid, block, smem_bytes, s>>>(p);
+    if (plain) {
+        if (ext) ssa_kernel<true, true><<<grid, block, smem_bytes, s>>>(p);
+        else ssa_kernel<true, false><<<grid, block, smem_bytes, s>>>(p);
+    } else {
+        if (ext) ssa_kernel<false, true><<<grid, block, smem_bytes, s>>>(p);
+        else ssa_kernel<false, false><<<grid, block, smem_bytes, s>>>(p);
+    }
     return to_code(cudaGetLastError());
 }
 

@@ -63,6 +63,7 @@ MODELS = {
     'cascade_literal': lambda: workloads.mapk_cascade(2, seed=5),
     'cascade_variant': lambda: workloads.mapk_cascade(2, seed=5, variant=True),
     'factor_chain': lambda: workloads.factor_chain(),
+    'sqrt_race': lambda: workloads.sqrt_race(),  # arithmetic atoms (the paper's example formula)
 }
 SIZES = {'lotka_volterra': 1500, 'cascade_literal': 512, 'cascade_variant': 256}
 MEDIUM = {'cascade_literal', 'cascade_variant', 'factor_chain'}

@@ -34,17 +34,30 @@ import numpy as np
 OPS = ('<', '<=', '>=', '>', '==', '!=')
 
 
+TOKENS = ('x', 'c', '+', '-', '*', '/', 'sqrt', 'pow')
+
+
 @dataclasses.dataclass
 class Atom:
+    """``sum_i coef[i] x_i <op> bound``, or, when ``lhs`` is given, the
+    arithmetic atom ``lhs <op> rhs`` (Sec. 3.1's val <| val): each side a
+    postfix program of tokens ('x', species index), ('c', constant), ('+',),
+    ('-',), ('*',), ('/',), ('sqrt',), ('pow', n)."""
     coef: np.ndarray  # int32 [S]
     op: str
     bound: float
+    lhs: list = None
+    rhs: list = None
 
     def __post_init__(self):
         self.coef = np.ascontiguousarray(self.coef, dtype=np.int32)
         if self.op not in OPS:
             raise ValueError(f"unknown comparison {self.op!r}")
         self.bound = float(self.bound)
+        for side in (self.lhs, self.rhs):
+            for t in side or []:
+                if t[0] not in TOKENS:
+                    raise ValueError(f"unknown token {t!r}")
 
 
 @dataclasses.dataclass
@@ -129,6 +142,15 @@ def _net(species: Sequence[str], reactions: Sequence[Tuple[Sequence[str], Sequen
         for s in rhs:
             st[j, idx[s]] += 1
     return reac, st
+
+
+def expr_atom(species: Sequence[str], lhs, op: str, rhs) -> Atom:
+    """Arithmetic atom ``lhs <op> rhs``; tokens ('x', name) name species."""
+    idx = {s: i for i, s in enumerate(species)}
+
+    def res(side):
+        return [('x', idx[t[1]]) if t[0] == 'x' else tuple(t) for t in side]
+    return Atom(np.zeros(len(species), np.int32), op, 0.0, res(lhs), res(rhs))
 
 
 def atom(species: Sequence[str], terms, op: str, bound: float) -> Atom:
@@ -264,6 +286,21 @@ def factor_chain(n: int = 10, T: float = 25.0, theta: int = 10) -> Tuple[Model, 
     factors.append((n - 1, n - 1, 2, 100.0, 0.0, 100.0, 1.0))
     m = Model('factor_chain', sp, reac, st, [rates], [x0], factors)
     p = Property([atom(sp, sp[-1], '>=', theta)], ('F', 0.0, T, ('atom', 0)), f'F[0,{T}]({sp[-1]}>={theta})')
+    return m, p
+
+
+def sqrt_race(T: float = 15.0) -> Tuple[Model, Property]:
+    """The paper's example formula (Sec. 3.1), (X1 < sqrt(X2)) U[0,T]
+    (X2 >= 10 + X3), on a small network: X1 and X2 produced and degraded,
+    X2 converted into X3.  0 -> X1 (1.0), X1 -> 0 (0.2 X1), 0 -> X2 (4.0),
+    X2 -> X3 (0.1 X2), X3 -> 0 (0.2 X3); X1 = 2, X2 = 9, X3 = 0."""
+    sp = ['X1', 'X2', 'X3']
+    reac, st = _net(sp, [([], ['X1']), (['X1'], []), ([], ['X2']), (['X2'], ['X3']), (['X3'], [])])
+    m = Model('sqrt_race', sp, reac, st, [[1.0, 0.2, 4.0, 0.1, 0.2]], [[2, 9, 0]])
+    left = expr_atom(sp, [('x', 'X1')], '<', [('x', 'X2'), ('sqrt',)])
+    right = expr_atom(sp, [('x', 'X2')], '>=', [('c', 10.0), ('x', 'X3'), ('+',)])
+    p = Property([left, right], ('U', 0.0, T, ('atom', 0), ('atom', 1)),
+                 f'(X1 < sqrt(X2)) U[0,{T}] (X2 >= 10 + X3)')
     return m, p
 
 
