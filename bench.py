@@ -34,6 +34,9 @@ CONFIDENCE = 0.99
 HALF_WIDTH = 0.001
 SEED = 0
 METRIC = 'verified trajectories/s & SSA events/s at fixed 95% Wilson width, plain vs chosen'
+# DRAM bytes (read + write) of one launch of the FP64 kernel on this workload,
+# from an ncu capture of the current kernel; None when not yet taken.
+TRAFFIC_PLAIN = None
 WORKLOAD = ('Lotka-Volterra X->2X 1.0, X+Y->2Y 0.005, Y->0 0.6, X0=Y0=1000; G[0,30](X>0 & Y>0); '
             '1,000,000 trajectories per step; 99% Wilson half-width 0.001')
 
@@ -350,13 +353,16 @@ def main():
     w_mixed = algorithmic_ops_per_event(model, 2, False)
     ach_plain = w_plain * res['plain']['events_s'] / max(world, 1)
     ach_mixed = w_mixed * res['mixed']['events_s'] / max(world, 1)
-    # The FP64 path's tighter bound: GB300 issues 2 FP64 operations per clock
-    # per SM.  Per event it runs R products and R - 1 sums (Eq. 1), 15 for the
-    # logarithm, the correctly rounded division (9.75 as counted by ncu on
-    # this kernel), the clock add and u_sel * a_0 (ncu total for this
-    # workload: 31.75 = 9.75 DADD + 16 DFMA + 6 DMUL).
+    # FP64 pipe: GB300 issues 2 FP64 operations per clock per SM (1/64 of
+    # FP32).  Per event the kernel leaves R products and R - 1 sums (Eq. 1),
+    # the clock add and u_sel * a_0 on it; ln u and the division by a_0 run
+    # on the integer pipes.  Had they stayed FP64 (15 operations for the
+    # table-driven logarithm, 9.75 for the correctly rounded division, as
+    # counted by ncu), the FP64 pipe alone would cap the path at
+    # fp64_only_bound_events_per_s.
     R = model.n_reactions
-    fp64_per_event = 2 * R - 1 + 15 + 9.75 + 2
+    fp64_per_event = 2 * R - 1 + 2
+    fp64_naive = fp64_per_event + 15 + 9.75
     fp64_peak = n_sm * 2 * f_clk
     fp64_ach = fp64_per_event * res['plain']['events_s'] / max(world, 1)
 
@@ -391,14 +397,15 @@ def main():
                                         'n': it['launched'], 'p_hat': it['p_hat'], 'lo': it['lo'],
                                         'hi': it['hi'], 'iterations': it['iterations']}},
         'roofline': {'bound': 'alu', 'kernel': kernel_name(ctx, 'plain'),
-                     'achieved': ach_plain / 1e9, 'peak': peak_ops / 1e9, 'unit': 'Gop/s',
-                     'frac': ach_plain / peak_ops, 'traffic': None,
+                     'achieved': ach_plain / 1e9, 'peak': peak_ops / 1e9, 'unit': 'G thread-op/s',
+                     'frac': ach_plain / peak_ops, 'traffic': TRAFFIC_PLAIN,
                      'ops_per_event': w_plain,
                      'peak_source': f'{n_sm} SMs x 4 issue slots x 32 lanes x {f_clk / 1e6:.0f} MHz '
                                     f'({pk_src} max SM clock)'},
         'fp64_pipe': {'kernel': kernel_name(ctx, 'plain'), 'fp64_ops_per_event': fp64_per_event,
-                      'achieved': fp64_ach / 1e9, 'peak': fp64_peak / 1e9, 'unit': 'G FP64 ops/s',
+                      'achieved': fp64_ach / 1e9, 'peak': fp64_peak / 1e9, 'unit': 'G FP64 op/s',
                       'frac': fp64_ach / fp64_peak,
+                      'fp64_only_bound_events_per_s': fp64_peak / fp64_naive,
                       'peak_source': f'{n_sm} SMs x 2 FP64 ops/clk x {f_clk / 1e6:.0f} MHz'},
         'e2e': {'value': e2e_value, 'unit': 'trajectories/s', 'h2d_bytes_per_step': h2d,
                 'd2h_bytes_per_step': d2h},

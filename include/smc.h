@@ -69,6 +69,9 @@ extern "C" {
 #define SMC_NODE_UNTIL 7      /* phi U[lo,hi] psi: 2 operands (phi first)  */
 #define SMC_NODE_EVENTUALLY 8 /* F[lo,hi] psi = tt U[lo,hi] psi            */
 #define SMC_NODE_ALWAYS 9     /* G[lo,hi] psi = not F[lo,hi] not psi       */
+#define SMC_NODE_NEXT 10      /* X[lo,hi] psi: the next state is entered at
+                                 a time in [lo, hi] and satisfies psi (Sec.
+                                 3.1); psi a state formula, at the top level */
 
 /* ---- atom comparison operators ------------------------------------------ */
 #define SMC_OP_LT 0
@@ -435,14 +438,25 @@ int smc_estimate_cv(smc_ctx *ctx, smc_mlp *mlp, double confidence, double half_w
                     uint64_t pilot, smc_cv_result *out);
 
 /* The natural logarithm used by the FP64 path for tau = -ln(u) / a_0
- * (Eq. 2a): a table-driven method after Tang (ACM TOMS 16, 1990) with an
- * exact argument reduction, 15 FP64 operations (GB300 runs FP64 at 1/64 of
- * FP32), within about half an ulp (correctly rounded but for values within
- * ~2^-6 ulp of a rounding midpoint).  Diagnostic entry point (tests).
+ * (Eq. 2a), evaluated on the integer pipes (GB300 runs FP64 arithmetic at
+ * 1/64 of the FP32 rate): a table-driven method after Tang (ACM TOMS 16,
+ * 1990) with an exact argument reduction and a 128-bit fixed-point sum,
+ * within 0.502 ulp (correctly rounded but for values within ~2^-9 ulp of a
+ * rounding midpoint); zero, negative, subnormal and non-finite arguments go
+ * to the FP64 library logarithm.  Diagnostic entry point (tests).
  * u, out: device arrays of n doubles, caller-owned; out[i] = ln(u[i]),
  * enqueued on `stream` (0: the context's stream).  Errors: INVALID_ARG for
  * null pointers with n > 0, CUDA for a failed launch. */
 int smc_log_fp64(smc_ctx *ctx, const double *u, uint64_t n, double *out, void *stream);
+
+/* The division of the same step, tau = (-ln u) / a_0, on the integer pipes:
+ * out[i] = num[i] / den[i] rounded to nearest-even, bit for bit the IEEE-754
+ * binary64 quotient for every input (positive normal operands with a normal
+ * quotient take the integer path, the rest the FP64 division).  Diagnostic
+ * entry point (tests).  num, den, out: device arrays of n doubles, caller-
+ * owned, enqueued on `stream` (0: the context's stream).  Errors:
+ * INVALID_ARG for null pointers with n > 0, CUDA for a failed launch. */
+int smc_div_fp64(smc_ctx *ctx, const double *num, const double *den, uint64_t n, double *out, void *stream);
 
 /* Host utilities (no GPU needed). */
 double smc_normal_quantile(double p);                           /* Phi^{-1}(p) */

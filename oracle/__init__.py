@@ -28,7 +28,7 @@ _lock = threading.Lock()
 _lib = None
 
 KINDS = {'true': 0, 'false': 1, 'atom': 2, 'not': 3, 'and': 4, 'or': 5, 'implies': 6,
-         'U': 7, 'F': 8, 'G': 9}
+         'U': 7, 'F': 8, 'G': 9, 'X': 10}
 OPS = {'<': 0, '<=': 1, '>=': 2, '>': 3, '==': 4, '!=': 5}
 V_F, V_T, V_U = 0, 1, 2
 
@@ -107,7 +107,7 @@ def flatten_formula(formula):
         elif k == 'U':
             lo, hi = float(f[1]), float(f[2])
             c0 = rec(f[3]); c1 = rec(f[4])
-        elif k in ('F', 'G'):
+        elif k in ('F', 'G', 'X'):
             lo, hi = float(f[1]), float(f[2])
             c0 = rec(f[3])
         elif k not in ('true', 'false'):
@@ -157,10 +157,12 @@ def _atom_arrays(prop, S):
     return n, coef, op, bound
 
 
-def eval_prefix(prop, S: int, x: np.ndarray, t: np.ndarray, tmin: float, closed: bool) -> int:
+def eval_prefix(prop, S: int, x: np.ndarray, t: np.ndarray, tmin: float, closed: bool,
+                tmin_exact: bool = False) -> int:
     """Kleene value (0 false, 1 true, 2 undetermined) of ``prop`` at position 0
     of a prefix with states x[n,S] and entry times t[n]; later positions have
-    entry time >= tmin, or do not exist when ``closed``."""
+    entry time >= tmin (the next one exactly tmin when ``tmin_exact``), or do
+    not exist when ``closed``."""
     x = np.ascontiguousarray(x, np.int32).reshape(-1, S)
     t = np.ascontiguousarray(t, np.float64)
     nodes, root = flatten_formula(prop.formula)
@@ -180,9 +182,9 @@ def eval_prefix(prop, S: int, x: np.ndarray, t: np.ndarray, tmin: float, closed:
           _ptr(enl, ctypes.c_int32) if enl is not None else None, etok)
     L = lib()
     L.orc_eval_prefix.argtypes = [ctypes.POINTER(F), ctypes.c_int64, ctypes.POINTER(ctypes.c_double),
-                                  ctypes.POINTER(ctypes.c_int32), ctypes.c_double, ctypes.c_int]
+                                  ctypes.POINTER(ctypes.c_int32), ctypes.c_double, ctypes.c_int, ctypes.c_int]
     return L.orc_eval_prefix(ctypes.byref(f), t.shape[0], _ptr(t, ctypes.c_double),
-                             _ptr(x, ctypes.c_int32), float(tmin), int(bool(closed)))
+                             _ptr(x, ctypes.c_int32), float(tmin), int(bool(closed)), int(bool(tmin_exact)))
 
 
 def _factor_arrays(model):

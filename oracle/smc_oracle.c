@@ -88,7 +88,7 @@ typedef struct {
     const double *fp;
 } orc_model;
 
-enum { K_TRUE = 0, K_FALSE, K_ATOM, K_NOT, K_AND, K_OR, K_IMPLIES, K_UNTIL, K_EVENTUALLY, K_ALWAYS };
+enum { K_TRUE = 0, K_FALSE, K_ATOM, K_NOT, K_AND, K_OR, K_IMPLIES, K_UNTIL, K_EVENTUALLY, K_ALWAYS, K_NEXT };
 enum { OP_LT = 0, OP_LE, OP_GE, OP_GT, OP_EQ, OP_NE };
 enum { V_F = 0, V_T = 1, V_U = 2 }; /* Kleene truth values */
 
@@ -118,13 +118,16 @@ typedef struct {
 
 /* what is known about a path: positions 0..n-1 with entry times t[] and
  * states x[], and every later position (if any) has entry time >= tmin;
- * closed=1 means the path has no position beyond n-1 (absorbing state).  */
+ * closed=1 means the path has no position beyond n-1 (absorbing state);
+ * tmin_exact=1 means position n, if any, is entered exactly at tmin (its
+ * entry time has been drawn).                                              */
 typedef struct {
     int64_t n;
     const double *t;
     const int32_t *x;
     double tmin;
     int closed;
+    int tmin_exact;
 } orc_know;
 
 static int not3(int a) { return a == V_U ? V_U : (a == V_T ? V_F : V_T); }
@@ -253,15 +256,27 @@ static int ev3(const orc_formula *f, int node, int64_t i, const orc_know *K)
     case K_UNTIL: return until3(f, nd->c0, nd->c1, 0, nd->lo, nd->hi, i, K);
     case K_EVENTUALLY: return until3(f, -1, nd->c0, 0, nd->lo, nd->hi, i, K);
     case K_ALWAYS: return not3(until3(f, -1, nd->c0, 1, nd->lo, nd->hi, i, K));
+    case K_NEXT: {  /* sigma^i |= X^I psi iff sigma^{i+1} |= psi and delta(sigma, i) in I */
+        if (i + 1 < K->n) {
+            const double d = K->t[i + 1] - K->t[i];
+            if (d < nd->lo || d > nd->hi) return V_F;
+            return ev3(f, nd->c0, i + 1, K);
+        }
+        if (K->closed) return V_F;
+        const double d = K->tmin - K->t[i];
+        if (d > nd->hi) return V_F;
+        if (K->tmin_exact && d < nd->lo) return V_F;
+        return V_U;
+    }
     default: return V_U;
     }
 }
 
 /* Three-valued truth of the formula on a prefix (exported for tests). */
 int orc_eval_prefix(const orc_formula *f, int64_t n, const double *t, const int32_t *x,
-                    double tmin, int closed)
+                    double tmin, int closed, int tmin_exact)
 {
-    orc_know K = {n, t, x, tmin, closed};
+    orc_know K = {n, t, x, tmin, closed, tmin_exact};
     return ev3(f, f->root, 0, &K);
 }
 
@@ -365,6 +380,7 @@ static int eval_at(const orc_path *P, int64_t q)
     K.t = P->t;
     K.x = P->x;
     K.closed = 0;
+    K.tmin_exact = (int)(q & 1);  /* after a draw the next entry time is known */
     if ((q & 1) == 0) {
         K.tmin = P->t[k];
     } else if (k < P->E) {

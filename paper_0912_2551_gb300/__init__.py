@@ -56,7 +56,7 @@ def postfix(formula) -> list:
             rec(f[1]); rec(f[2]); out.append((N.NODE[k], 0, 0.0, 0.0))
         elif k == 'U':
             rec(f[3]); rec(f[4]); out.append((N.NODE['U'], 0, float(f[1]), float(f[2])))
-        elif k in ('F', 'G'):
+        elif k in ('F', 'G', 'X'):
             rec(f[3]); out.append((N.NODE[k], 0, float(f[1]), float(f[2])))
         else:
             raise ValueError(f'unknown formula node {k!r}')

@@ -25,7 +25,7 @@ SMC_MIXED = 1
 SMC_FIXED_N = 0 << 4
 SMC_ITERATIVE = 1 << 4
 SMC_CONSERVATIVE = 2 << 4
-NODE = dict(true=0, false=1, atom=2, **{'not': 3, 'and': 4, 'or': 5, 'implies': 6}, U=7, F=8, G=9)
+NODE = dict(true=0, false=1, atom=2, **{'not': 3, 'and': 4, 'or': 5, 'implies': 6}, U=7, F=8, G=9, X=10)
 OP = {'<': 0, '<=': 1, '>=': 2, '>': 3, '==': 4, '!=': 5}
 OPT = dict(event_budget=0, renorm_log2=1, autotune=2, warps_per_block=3, blocks_per_sm=4,
            refill=5, record=6, jit=7)
@@ -149,6 +149,8 @@ SIGNATURES = {
                                        ctypes.POINTER(smc_cv_result)]),
     'smc_log_fp64': (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p,
                                     ctypes.c_void_p]),
+    'smc_div_fp64': (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64,
+                                    ctypes.c_void_p, ctypes.c_void_p]),
     'smc_normal_quantile': (ctypes.c_double, [ctypes.c_double]),
     'smc_wilson_interval': (ctypes.c_int, [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_double, c_f64p,
                                            c_f64p]),

@@ -13,10 +13,10 @@ BUILD = os.path.join(HERE, '_build')
 LIB = os.path.join(BUILD, 'libsmc.so')
 SOURCES = ['smc_kernels.cu', 'smc_api.cu', 'smc_compile.cpp', 'smc_mlp.cu', 'smc_jit.cpp', 'smc_cme.cu']
 HEADERS = ['smc_internal.h', 'smc_compile.h', 'smc_mlp.h', 'smc_device.cuh', 'smc_jit.h',
-           'smc_jit_kernel.cuh', 'nvrtc_stdint.h', 'smc_cme.h']
+           'smc_jit_kernel.cuh', 'nvrtc_stdint.h', 'smc_cme.h', 'smc_fp64i.h']
 # sources of the run-time compiled kernels, embedded into the library as
 # (include name, file) pairs
-JIT_EMBED = [('stdint.h', 'nvrtc_stdint.h'), ('smc_internal.h', 'smc_internal.h'),
+JIT_EMBED = [('stdint.h', 'nvrtc_stdint.h'), ('smc_fp64i.h', 'smc_fp64i.h'), ('smc_internal.h', 'smc_internal.h'),
              ('smc_device.cuh', 'smc_device.cuh'), ('smc_jit_kernel.cuh', 'smc_jit_kernel.cuh')]
 ARCH = ['-gencode', 'arch=compute_103a,code=sm_103a']
 

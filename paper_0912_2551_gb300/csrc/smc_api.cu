@@ -105,7 +105,7 @@ struct smc_ctx {
     uint64_t record_n = 0, record_valid = 0;
     float *d_feat_aux = nullptr;  // feature scales and centred log rates
     size_t feat_aux_n = 0;
-    double *d_logtab = nullptr;   // table of the FP64 path's logarithm (lives with the context)
+    uint64_t *d_logtab = nullptr;  // table of the FP64 path's logarithm (lives with the context)
     // control-variate estimator's buffers, grown on demand and kept (a
     // cudaFree per call would synchronise the device)
     struct CvBuf {
@@ -243,41 +243,6 @@ double as241(double p)
 }
 
 double z_of(double confidence) { return as241(1.0 - (1.0 - confidence) / 2.0); }
-
-// Table of the FP64 path's logarithm (Tang 1990, exact-reduction form): for
-// the bucket of m around F_j = 0.75 + j/256, a 9-bit G_j ~ 1/F_j and
-// ln(1/G_j) split into a high double and the low remainder (long double);
-// then ln 2 the same way.  Empty if some bucket's reduction is not exact.
-std::vector<double> log_table_host()
-{
-    std::vector<double> t(SMC_LOGTAB_BYTES / 8, 0.0);
-    // high part: the nearest multiple of 2^-42; low part: the remainder
-    auto split = [](long double L, double &hi, double &lo) {
-        hi = (double)(roundl(L * 0x1p42L) * 0x1p-42L);
-        lo = (double)(L - (long double)hi);
-    };
-    for (int j = 0; j < SMC_LOGTAB_N; ++j) {
-        // bucket of m: [F - 1/512, F + 1/512] within [0.75, 1.5)
-        const double F = 0.75 + j / 256.0;
-        const long double m_lo = std::max(F - 1.0 / 512, 0.75), m_hi = std::min(F + 1.0 / 512, 1.5);
-        // G = n / q with 9 significant bits (q = 256 above 1, 512 below),
-        // the one with the smallest max |m G - 1| over the bucket
-        const long double inv = 1.0L / F;
-        const int q = inv > 1 ? 256 : 512;
-        long double best = 1, G = 1;
-        for (long n = (long)floorl(inv * q) - 2; n <= (long)floorl(inv * q) + 3; ++n) {
-            const long double g = (long double)n / q;
-            if ((g > 1 && q != 256) || (g < 1 && q != 512)) continue;
-            const long double e = std::max(fabsl(m_lo * g - 1), fabsl(m_hi * g - 1));
-            if (e < best) { best = e; G = g; }
-        }
-        if (!(best < 1.0L / 256)) return {};  // the reduction would not be exact
-        t[j] = (double)G;
-        split(-logl(G), t[SMC_LOGTAB_N + j], t[2 * SMC_LOGTAB_N + j]);
-    }
-    split(logl(2.0L), t[3 * SMC_LOGTAB_N], t[3 * SMC_LOGTAB_N + 1]);
-    return t;
-}
 
 // Eq. 5
 double wilson_sample_real(double p, double eps, double z)
@@ -546,13 +511,11 @@ int tc_bytes_of(const MonProg &prog)
     return 0;
 }
 
-// warp slice: table | x[(s_max + 1)][32] | tc | a[r_max][32] | (mixed path)
-// group sums g[ceil(r_max / 8)][32]
+// warp slice: table | x[(s_max + 1)][32] | tc | a[r_max][32]
 int warp_bytes_of(const SizeClass &c, int plain, int tc_bytes)
 {
     const int blob_words = (c.blob_words + 3) & ~3;
-    const int groups = plain ? 0 : (c.r_max + 7) / 8;
-    const int b = blob_words * 4 + (c.s_max + 1) * 128 + tc_bytes + c.r_max * 32 * (plain ? 8 : 4) + groups * 128;
+    const int b = blob_words * 4 + (c.s_max + 1) * 128 + tc_bytes + c.r_max * 32 * (plain ? 8 : 4);
     return (b + 15) & ~15;
 }
 
@@ -829,8 +792,8 @@ int smc_create(smc_ctx **out, int device)
         delete ctx;
         return SMC_E_CUDA;
     }
-    const std::vector<double> tab = log_table_host();
-    if (tab.empty()) {
+    std::vector<uint64_t> tab(SMC_LOGTAB_BYTES / 8, 0);
+    if (fp64i_log_table(tab.data())) {
         smc_destroy(ctx);
         return SMC_E_UNSUPPORTED;
     }
@@ -862,6 +825,16 @@ int smc_log_fp64(smc_ctx *ctx, const double *u, uint64_t n, double *out, void *s
     CK(cudaSetDevice(ctx->device));
     cudaStream_t s = stream ? (cudaStream_t)stream : ctx->stream;
     if (smc_launch_log_batch(ctx->d_logtab, u, n, out, s)) return fail(ctx, SMC_E_CUDA, "log kernel launch failed");
+    return SMC_OK;
+}
+
+int smc_div_fp64(smc_ctx *ctx, const double *num, const double *den, uint64_t n, double *out, void *stream)
+{
+    if (!ctx) return SMC_E_INVALID_ARG;
+    if (n > 0 && (!num || !den || !out)) return fail(ctx, SMC_E_INVALID_ARG, "null array");
+    CK(cudaSetDevice(ctx->device));
+    cudaStream_t s = stream ? (cudaStream_t)stream : ctx->stream;
+    if (smc_launch_div_batch(num, den, n, out, s)) return fail(ctx, SMC_E_CUDA, "division kernel launch failed");
     return SMC_OK;
 }
 

@@ -28,7 +28,8 @@ int kleene_or(int a, int b)
 
 bool is_temporal(int kind)
 {
-    return kind == SMC_NODE_UNTIL || kind == SMC_NODE_EVENTUALLY || kind == SMC_NODE_ALWAYS;
+    return kind == SMC_NODE_UNTIL || kind == SMC_NODE_EVENTUALLY || kind == SMC_NODE_ALWAYS ||
+           kind == SMC_NODE_NEXT;
 }
 
 struct Compiler {
@@ -124,6 +125,15 @@ struct Compiler {
             }
             u.a = f.lo;
             u.b = f.hi;
+            if (f.kind == SMC_NODE_NEXT) {  // X[a,b] psi: decided by the next state (nest 3)
+                if (!is_state(f.c0)) { err = "the operand of X must be a state formula"; return false; }
+                u.nest = 3;
+                u.P = table_of(f.c0, false);
+                leaf.unit = (int)units.size();
+                leaf.neg = false;
+                units.push_back(u);
+                return true;
+            }
             if (f.kind == SMC_NODE_UNTIL) {
                 if (!is_state(f.c0)) { err = "left operand of U must be a state formula"; return false; }
                 u.L = table_of(f.c0, false);
@@ -220,7 +230,7 @@ int parse_formula(const smc_node *nodes, int n_nodes, int n_atoms, std::vector<F
             arity = 0;
             if (f.arg < 0 || f.arg >= n_atoms) { err = "atom index out of range"; return SMC_E_INVALID_ARG; }
             break;
-        case SMC_NODE_NOT: case SMC_NODE_EVENTUALLY: case SMC_NODE_ALWAYS: arity = 1; break;
+        case SMC_NODE_NOT: case SMC_NODE_EVENTUALLY: case SMC_NODE_ALWAYS: case SMC_NODE_NEXT: arity = 1; break;
         case SMC_NODE_AND: case SMC_NODE_OR: case SMC_NODE_IMPLIES: case SMC_NODE_UNTIL: arity = 2; break;
         default: err = "unknown node kind"; return SMC_E_INVALID_ARG;
         }
@@ -259,8 +269,9 @@ int compile_formula(const std::vector<FNode> &tree, int root, int n_atoms, doubl
     prog.n_atoms = (int)used_atoms.size();
     for (int u = 0; u < nu; ++u) {
         prog.u[u] = C.units[u];
-        if (std::isinf(prog.u[u].b) || (prog.u[u].nest && std::isinf(prog.u[u].d))) prog.unbounded = 1;
-        if (prog.u[u].a > 0.0) prog.has_lower = 1;
+        const bool next = prog.u[u].nest == 3;  // decided by the first event, whatever its window
+        if (!next && (std::isinf(prog.u[u].b) || (prog.u[u].nest && std::isinf(prog.u[u].d)))) prog.unbounded = 1;
+        if (!next && prog.u[u].a > 0.0) prog.has_lower = 1;
     }
     if (prog.unbounded) {
         if (!(t_max > 0.0) || std::isinf(t_max)) {
@@ -581,24 +592,28 @@ int build_blob(const InstanceModel &M, int n_used, const int32_t *coef_used /*[n
             blob.push_back((uint32_t)(v >> 32));
         }
     }
-    section(BH_EXPR);
-    blob.insert(blob.end(), ex.begin(), ex.end());
-    section(BH_FACT_PTR);
-    blob.insert(blob.end(), f_ptr.begin(), f_ptr.end());
-    section(BH_FACT);
-    blob.insert(blob.end(), f_words.begin(), f_words.end());
-    section(BH_FACT_D);
-    for (double v : f_d) {
-        uint32_t w[2];
-        std::memcpy(w, &v, 8);
-        blob.push_back(w[0]);
-        blob.push_back(w[1]);
+    if (!ex.empty()) {  // only read through arithmetic atoms' records
+        section(BH_EXPR);
+        blob.insert(blob.end(), ex.begin(), ex.end());
     }
-    section(BH_FACT_F);
-    for (float v : f_f) {
-        uint32_t w;
-        std::memcpy(&w, &v, 4);
-        blob.push_back(w);
+    if (!f_words.empty()) {  // only read for reactions flagged SMC_PW_FACT
+        section(BH_FACT_PTR);
+        blob.insert(blob.end(), f_ptr.begin(), f_ptr.end());
+        section(BH_FACT);
+        blob.insert(blob.end(), f_words.begin(), f_words.end());
+        section(BH_FACT_D);
+        for (double v : f_d) {
+            uint32_t w[2];
+            std::memcpy(w, &v, 8);
+            blob.push_back(w[0]);
+            blob.push_back(w[1]);
+        }
+        section(BH_FACT_F);
+        for (float v : f_f) {
+            uint32_t w;
+            std::memcpy(&w, &v, 4);
+            blob.push_back(w);
+        }
     }
     while (blob.size() & 3) blob.push_back(0);
     blob[BH_S] = (uint32_t)S;

@@ -78,49 +78,11 @@ __device__ __forceinline__ double int_to_double(long long h)
     return __ll2double_rn(h);
 }
 
-// Natural logarithm for the FP64 path, table-driven (Tang, ACM TOMS 16,
-// 1990), with a reduction that is exact: u = 2^k m, m in [0.75, 1.5) taken
-// from the bit pattern; j = the multiple of 1/256 nearest m (j = 0..192);
-// G_j ~ 1/F_j, F_j = 0.75 + j/256, has 9 significant bits and is chosen so
-// that |m G_j - 1| < 2^-8 over the whole bucket, which makes
-// r = fma(m, G_j, -1) exact (m G_j has no bit below 2^-61).  Then
-//   ln u = k ln 2 + ln(1/G_j) + ln(1 + r),
-// ln(1 + r) = r + r^2 s(r), s the Taylor series of (ln(1+r) - r)/r^2 to r^5;
-// H = k ln2_hi + ln(1/G_j)_hi is exact (both multiples of 2^-42), H + r is
-// split into sum and error by Fast2Sum (|H| >= |r| or H = 0), and the small
-// terms join the error: at most about half an ulp plus 2^-6 ulp.  Fifteen
-// FP64 operations.  tab: G_j | ln(1/G_j) high | low | ln 2 high | low.
-__device__ __forceinline__ double exact_scaled(uint64_t m, int e0);
-__device__ __forceinline__ double log_table(double u, const double *tab)
+// -ln u for the FP64 path (u from u01_52): the integer-pipe logarithm of
+// smc_fp64i.h (table-driven, below 0.502 ulp), negated by its sign bit.
+__device__ __forceinline__ double neg_log(double u, const uint64_t *tab)
 {
-    const unsigned long long b = (unsigned long long)__double_as_longlong(u);
-    const int e = (int)((b >> 52) & 0x7FF);
-    if (e == 0 || e == 0x7FF || (b >> 63)) return log(u);  // zero, subnormal, inf, nan, negative
-    const unsigned long long mant = b & 0x000FFFFFFFFFFFFFull;
-    int k = e - 1023, j;
-    unsigned long long mb;
-    if (mant >= (1ull << 51)) {  // m in [1.5, 2): use m / 2 in [0.75, 1)
-        k += 1;
-        j = (int)(((mant - (1ull << 51)) + (1ull << 44)) >> 45);
-        mb = (1022ull << 52) | mant;
-    } else {
-        j = 64 + (int)((mant + (1ull << 43)) >> 44);
-        mb = (1023ull << 52) | mant;
-    }
-    const double m = __longlong_as_double((long long)mb);
-    const double r = __fma_rn(m, tab[j], -1.0);  // exact
-    double s = __fma_rn(r, 1.0 / 7.0, -1.0 / 6.0);
-    s = __fma_rn(r, s, 1.0 / 5.0);
-    s = __fma_rn(r, s, -0.25);
-    s = __fma_rn(r, s, 1.0 / 3.0);
-    s = __fma_rn(r, s, -0.5);
-    const double kd = k > 0 ? exact_scaled((uint64_t)k, 0) : (k < 0 ? -exact_scaled((uint64_t)(-k), 0) : 0.0);
-    const double H = __fma_rn(kd, tab[3 * SMC_LOGTAB_N], tab[SMC_LOGTAB_N + j]);            // exact
-    const double lo = __fma_rn(kd, tab[3 * SMC_LOGTAB_N + 1], tab[2 * SMC_LOGTAB_N + j]);
-    const double S = __dadd_rn(H, r);
-    const double err = __dsub_rn(r, __dsub_rn(S, H));                                      // H + r = S + err
-    const double small = __fma_rn(__dmul_rn(r, r), s, lo);
-    return __dadd_rn(S, __dadd_rn(err, small));
+    return __longlong_as_double(__double_as_longlong(fp64i_log(u, tab)) ^ (long long)0x8000000000000000ull);
 }
 
 // x > y for x, y >= 0 (including +inf): ordered like their bit patterns,
@@ -163,17 +125,24 @@ struct MonHot {
 
 __device__ __constant__ int kPow3[SMC_MAX_UNITS] = {1, 3, 9, 27};
 
+// hb: the draws after which the monitor must be consulted are those whose
+// entry time's bit pattern exceeds hb (entry times are >= 0, so hb = -1 means
+// every draw): the smallest window end of the alive undecided units, -1 for
+// an undecided X unit (its first draw decides or arms it, even at time 0),
+// and -1 when no unit is alive.
 __device__ __forceinline__ void mon_horizon(MonLane &ml, const MonProg &P)
 {
-    long long h = -1;
+    long long h = 0x7FFFFFFFFFFFFFFFll;
+    bool any = false;
 #pragma unroll
     for (int u = 0; u < SMC_MAX_UNITS; ++u) {
         if (u < P.n_units && !((ml.done >> u) & 1u) && ((ml.alive >> u) & 1u)) {
-            const long long b = __double_as_longlong(P.u[u].b);
-            h = (h < 0 || b < h) ? b : h;
+            const long long b = P.u[u].nest == 3 ? -1ll : __double_as_longlong(P.u[u].b);
+            h = b < h ? b : h;
+            any = true;
         }
     }
-    ml.hb = h;
+    ml.hb = any ? h : -1ll;
 }
 
 __device__ __forceinline__ void mon_set(MonLane &ml, int u, int val)
@@ -193,6 +162,10 @@ __device__ __noinline__ int mon_state(MonLane &ml, const MonProg &P, double t, d
         const uint32_t ab = ml.ab;
         const bool l = (U.L >> ab) & 1ull, p = (U.P >> ab) & 1ull, q = (U.Q >> ab) & 1ull;
         bool al = (ml.alive >> u) & 1u, pe = (ml.pend >> u) & 1u;
+        if (U.nest == 3) {  // X: pending after a draw within the window, so this is state 1
+            if (pe) { mon_set(ml, u, p ? 2 : 1); changed = true; }
+            continue;
+        }
         const bool inwin = al && !dgt(U.a, t) && !dgt(t, U.b);
         int val = 0;
         if (U.nest == 0) {
@@ -222,7 +195,10 @@ __device__ __noinline__ int mon_state(MonLane &ml, const MonProg &P, double t, d
     return P.table[ml.vidx];
 }
 
-// The next state's entry time tn has been drawn (not yet applied).
+// The next state's entry time tn has been drawn (not yet applied).  EXACT =
+// false: tn is only a lower bound of that time (a path known up to tmin), so
+// an X unit can only be refuted by tn beyond its window.
+template <bool EXACT = true>
 __device__ __noinline__ int mon_draw(MonLane &ml, const MonProg &P, double tn, const double *tc)
 {
     bool changed = false;
@@ -232,6 +208,13 @@ __device__ __noinline__ int mon_draw(MonLane &ml, const MonProg &P, double tn, c
         const MonUnit &U = P.u[u];
         const bool al = (ml.alive >> u) & 1u;
         bool pe = (ml.pend >> u) & 1u;
+        if (U.nest == 3) {  // X: the first draw is the next state's entry time
+            if (!pe) {
+                if ((EXACT && dgt(U.a, tn)) || dgt(tn, U.b)) { mon_set(ml, u, 1); changed = true; }
+                else if (EXACT) ml.pend |= 1u << u;
+            }
+            continue;
+        }
         int val = 0;
         if (pe && dgt(__dsub_rn(tn, tc[u * 32]), U.d)) {
             if (U.nest == 2) val = 2;

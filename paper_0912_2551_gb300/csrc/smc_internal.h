@@ -9,8 +9,8 @@
 // approximations of 1/F_j) | ln(1/G_j) high [193] | ln(1/G_j) low [193] |
 // ln 2 high | ln 2 low | pad.  The high parts are multiples of 2^-42, so
 // k ln2_high + ln(1/G_j) high is exact for |k| <= 1075.
-#define SMC_LOGTAB_N 193
-#define SMC_LOGTAB_BYTES ((SMC_LOGTAB_N * 3 + 3) * 8)  // a multiple of 16 bytes
+#include "smc_fp64i.h"
+#define SMC_LOGTAB_BYTES FP64I_LOG_BYTES  // the FP64 path's log table (a multiple of 16 bytes)
 #define SMC_MAX_UNITS 4   // temporal operators (monitor units) per formula
 #define SMC_MAX_ATOMS 6   // distinct atoms (truth tables are 64-bit)
 #define SMC_MAX_SPECIES 255
@@ -23,7 +23,9 @@
 //     L  U[a,b]  ( P  and  N )
 // anchored at time 0, where L, P, Q are state formulas over the atoms (held
 // as 64-entry truth tables indexed by the atom bit vector) and N is either
-// tt (nest = 0), F[0,d] Q (nest = 1) or G[0,d] Q (nest = 2).  F[a,b] psi is
+// tt (nest = 0), F[0,d] Q (nest = 1) or G[0,d] Q (nest = 2); nest = 3 is the
+// unit X[a,b] P (the next state is entered within [a, b] and satisfies P).
+// F[a,b] psi is
 // tt U[a,b] psi; G[a,b] psi is compiled as the unit F[a,b] (not psi) whose
 // value the top-level table negates.  A bare state formula at the top level
 // is the unit ff U[0,0] P (decided at the initial state).
@@ -35,7 +37,7 @@ struct MonUnit {
     uint64_t L, P, Q;  // truth tables over the atom bit vector
     double a, b;       // window of the unit (entry time of a witness)
     double d;          // window [0, d] of the nested operator
-    int32_t nest;      // 0 none, 1 F-nested, 2 G-nested
+    int32_t nest;      // 0 none, 1 F-nested, 2 G-nested, 3 next
     int32_t pad;
 };
 
@@ -135,7 +137,7 @@ struct SsaParams {
     unsigned int *cursor;        // instance cursor (starts at 0)
     unsigned int *ticket;        // blocks finished (starts at 0)
     const MonProg *prog;
-    const double *logtab;        // FP64 path: ln table (SMC_LOGTAB_BYTES, layout above)
+    const uint64_t *logtab;      // FP64 path: ln table (SMC_LOGTAB_BYTES, layout of smc_fp64i.h)
     int32_t logtab_bytes;        // its shared-memory footprint (0: mixed path)
     uint32_t rk0[10], rk1[10];   // Philox round keys
     uint64_t budget;             // max reactions per trajectory
@@ -197,7 +199,8 @@ int smc_ssa_max_blocks_per_sm(int plain, int ext, int block, int smem_bytes, int
 int smc_ssa_set_smem_limit(int plain, int ext, int smem_bytes);
 int smc_launch_queue_init(const SsaParams &p, void *stream);
 int smc_launch_replay(const ReplayParams &p, void *stream);
-int smc_launch_log_batch(const double *tab, const double *u, uint64_t n, double *out, void *stream);
+int smc_launch_log_batch(const uint64_t *tab, const double *u, uint64_t n, double *out, void *stream);
+int smc_launch_div_batch(const double *num, const double *den, uint64_t n, double *out, void *stream);
 int smc_launch_snapshot_features(uint64_t n_rows, uint64_t n_traj, int S, int R, int x_stride,
                                  const int32_t *x_snap, const float *x_scale, float t_feat,
                                  const float *lograte, float *feat, void *stream);

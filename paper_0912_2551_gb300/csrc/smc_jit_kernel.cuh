@@ -35,7 +35,7 @@
 namespace {
 
 template <bool PLAIN>
-__device__ __forceinline__ void jit_run_instance(const SsaParams &p, const MonProg &P, const double *ltab,
+__device__ __forceinline__ void jit_run_instance(const SsaParams &p, const MonProg &P, const uint64_t *ltab,
                                                  const int m, double *tc, typename Prec<PLAIN>::T *crate,
                                                  const uint32_t *sdelta, const int lane)
 {
@@ -155,7 +155,7 @@ __device__ __forceinline__ void jit_run_instance(const SsaParams &p, const MonPr
         T r;
         if (PLAIN) {
             const double ut = u01_52(w0, w1), us = u01_52(w2, w3);
-            tn = __dadd_rn(t, __ddiv_rn(-log_table(ut, ltab), (double)a0));
+            tn = __dadd_rn(t, fp64i_div(neg_log(ut, ltab), (double)a0));
             r = (T)__dmul_rn(us, (double)a0);
         } else {
             const float ut = u01_23(w0), us = u01_23(w2);
@@ -225,7 +225,7 @@ __device__ __forceinline__ void jit_kernel_body(const SsaParams &p)
     __shared__ int s_last;
     stage_block_tables(p, smem, PLAIN);
     const MonProg &P = *reinterpret_cast<const MonProg *>(smem);
-    const double *ltab = reinterpret_cast<const double *>(smem + sizeof(MonProg));
+    const uint64_t *ltab = reinterpret_cast<const uint64_t *>(smem + sizeof(MonProg));
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     // block: monitor program | logarithm table (FP64 path) | net-change table
     // (medium networks) | warp slices

@@ -91,28 +91,10 @@ __device__ __forceinline__ typename Prec<PLAIN>::T propensity(uint32_t pw, const
     return a;
 }
 
-// Mixed path, networks above 8 reactions: per-lane FP32 sums of the
-// propensities in groups of SMC_SEL_GROUP reactions (lane-minor, gs[q * 32]),
-// kept incrementally with a_0 and recomputed with it, so that the selection
-// (Eq. 2b) skips whole groups: ~R / 16 + 4 steps instead of ~R / 2.
-#define SMC_SEL_GROUP 8
-__device__ __forceinline__ float renorm_groups(const float *as, float *gs, int R)
-{
-    double s = 0.0;
-    for (int q = 0; q * SMC_SEL_GROUP < R; ++q) {
-        double g = 0.0;
-        const int ke = min(R, (q + 1) * SMC_SEL_GROUP);
-        for (int k = q * SMC_SEL_GROUP; k < ke; ++k) g = __dadd_rn(g, (double)as[k * 32]);
-        gs[q * 32] = (float)g;
-        s = __dadd_rn(s, g);
-    }
-    return (float)s;
-}
-
 template <bool PLAIN, bool EXT>
-__device__ __forceinline__ void run_instance(const SsaParams &p, const MonProg &P, const double *ltab,
+__device__ __forceinline__ void run_instance(const SsaParams &p, const MonProg &P, const uint64_t *ltab,
                                              const int m, const uint32_t *blob, int32_t *xs, double *tc,
-                                             typename Prec<PLAIN>::T *as, float *gs, const int lane)
+                                             typename Prec<PLAIN>::T *as, const int lane)
 {
     typedef typename Prec<PLAIN>::T T;
     const int S = (int)blob[BH_S], R = (int)blob[BH_R], NA = (int)blob[BH_NA];
@@ -199,7 +181,6 @@ __device__ __forceinline__ void run_instance(const SsaParams &p, const MonProg &
                             s = __dadd_rn(s, (double)ak);
                         }
                         a0 = (T)s;
-                        if (!PLAIN && !small) a0 = (T)renorm_groups((const float *)as, gs, R);
                         uint32_t ab = 0;
                         for (int a = 0; a < NA; ++a) ab |= atom_bit<EXT>(atoms, tptr, terms, ex, xs, a);
                         ml.ab = ab;
@@ -240,7 +221,9 @@ __device__ __forceinline__ void run_instance(const SsaParams &p, const MonProg &
             for (int k = 0; k < R; ++k) s = __dadd_rn(s, (double)as[k * 32]);
             a0 = (T)s;
         } else if (!(a0 > (T)0)) {  // drifted running sum: renormalise in FP64
-            a0 = (T)renorm_groups((const float *)as, gs, R);
+            double s = 0.0;
+            for (int k = 0; k < R; ++k) s = __dadd_rn(s, (double)as[k * 32]);
+            a0 = (T)s;
         }
         if (PLAIN ? __double_as_longlong((double)a0) <= 0 : !(a0 > (T)0)) {
             finish(mon_close(ml, P));  // absorbing state: no further position
@@ -252,7 +235,7 @@ __device__ __forceinline__ void run_instance(const SsaParams &p, const MonProg &
         T r;
         if (PLAIN) {
             const double ut = u01_52(w0, w1), us = u01_52(w2, w3);
-            tn = __dadd_rn(t, __ddiv_rn(-log_table(ut, ltab), (double)a0));
+            tn = __dadd_rn(t, fp64i_div(neg_log(ut, ltab), (double)a0));
             r = (T)__dmul_rn(us, (double)a0);
         } else {
             const float ut = u01_23(w0), us = u01_23(w2);
@@ -298,21 +281,14 @@ __device__ __forceinline__ void run_instance(const SsaParams &p, const MonProg &
                 if (__double_as_longlong(ak) > 0) last = k;
                 if (__double_as_longlong(cum) > rb) { j = k; break; }
             }
-        } else {  // whole groups first, then the reactions of the group that crosses r
-            const float rf = (float)r;
+        } else {
             float cum = 0.0f;
-            for (int q = 0; q * SMC_SEL_GROUP < R && j < 0; ++q) {
-                const float g = gs[q * 32];
-                if (!(cum + g > rf)) { cum += g; continue; }
-                const int ke = min(R, (q + 1) * SMC_SEL_GROUP);
-                for (int k = q * SMC_SEL_GROUP; k < ke; ++k) {
-                    cum += (float)as[k * 32];
-                    if (cum > rf) { j = k; break; }
-                }
+            for (int k = 0; k < R; ++k) {
+                const float ak = (float)as[k * 32];
+                cum += ak;
+                if (ak > 0.0f) last = k;
+                if (cum > (float)r) { j = k; break; }
             }
-            if (j < 0)  // r reached the full sum (rounding, or drifted sums)
-                for (int k = R - 1; k >= 0 && last < 0; --k)
-                    if ((float)as[k * 32] > 0.0f) last = k;
         }
         if (j < 0) j = last;  // r reached the full sum (rounding, or a drifted a0)
         if (j < 0) {          // every a_k is 0 (only a drifted FP32 a0 gets here)
@@ -340,17 +316,16 @@ __device__ __forceinline__ void run_instance(const SsaParams &p, const MonProg &
                 const uint32_t pw = dp[q];
                 const int k = pw & 255u;
                 const T ak = propensity<PLAIN, EXT>(pw, xs, rate_d, rate_f, blob);
-                if (!PLAIN) {
-                    const T d = ak - as[k * 32];
-                    a0 = a0 + d;
-                    gs[(k / SMC_SEL_GROUP) * 32] += (float)d;
-                }
+                if (!PLAIN) a0 = a0 + (ak - as[k * 32]);
                 as[k * 32] = ak;
             }
             ++e;
             t = tn;
-            if (!PLAIN && (e & renorm_mask) == 0u)  // FP64 renormalisation of a0 and the group sums
-                a0 = (T)renorm_groups((const float *)as, gs, R);
+            if (!PLAIN && (e & renorm_mask) == 0u) {  // FP64 renormalisation of a0
+                double s = 0.0;
+                for (int k = 0; k < R; ++k) s = __dadd_rn(s, (double)as[k * 32]);
+                a0 = (T)s;
+            }
             // monitor at the new state: re-evaluate the atoms that j moves
             uint32_t am = amask[j];
             while (am) {
@@ -391,7 +366,7 @@ __global__ void __launch_bounds__(256, PLAIN ? 3 : 4) ssa_kernel(const SsaParams
     __shared__ int s_last;
     stage_block_tables(p, smem, PLAIN);  // monitor program, then the logarithm's table
     const MonProg &P = *reinterpret_cast<const MonProg *>(smem);
-    const double *ltab = reinterpret_cast<const double *>(smem + sizeof(MonProg));
+    const uint64_t *ltab = reinterpret_cast<const uint64_t *>(smem + sizeof(MonProg));
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     // warp slice: table | x[(s_max + 1)][32] | tc[units][32] | a[r_max][32]
     unsigned char *wb = smem + sizeof(MonProg) + p.logtab_bytes + (size_t)warp * p.warp_bytes;
@@ -402,8 +377,6 @@ __global__ void __launch_bounds__(256, PLAIN ? 3 : 4) ssa_kernel(const SsaParams
     double *tc = reinterpret_cast<double *>(lanes) + lane;
     lanes += (size_t)p.tc_bytes;
     T *as = reinterpret_cast<T *>(lanes) + lane;
-    // mixed path: the group sums after the propensities
-    float *gs = reinterpret_cast<float *>(reinterpret_cast<T *>(lanes) + (size_t)p.r_max * 32) + lane;
 
     bool first = true;
     int cur = -1;
@@ -418,7 +391,7 @@ __global__ void __launch_bounds__(256, PLAIN ? 3 : 4) ssa_kernel(const SsaParams
             __syncwarp();
             cur = m;
         }
-        run_instance<PLAIN, EXT>(p, P, ltab, m, blob, xs, tc, as, gs, lane);
+        run_instance<PLAIN, EXT>(p, P, ltab, m, blob, xs, tc, as, lane);
         __syncwarp();
     }
 
@@ -468,7 +441,7 @@ __global__ void replay_kernel(const ReplayParams rp)
     }
     if (!v && n > 0) {
         if (rp.closed[i]) v = mon_close(ml, P);
-        else v = mon_draw(ml, P, rp.tmin[i], tc);
+        else v = mon_draw<false>(ml, P, rp.tmin[i], tc);  // tmin bounds the next entry time
         if (v) q = 2 * (long long)n - 1;
     }
     rp.verdict[i] = v;
@@ -527,22 +500,36 @@ int smc_launch_replay(const ReplayParams &rp, void *stream)
 }
 
 // ---------------------------------------------------------------------------
-// The FP64 path's logarithm on an array (tests and callers that want the
-// same function).
-__global__ void log_batch_kernel(const double *tab_g, const double *u, uint64_t n, double *out)
+// The FP64 path's logarithm and division on arrays (tests and callers that
+// want the same functions).
+__global__ void log_batch_kernel(const uint64_t *tab_g, const double *u, uint64_t n, double *out)
 {
-    __shared__ double tab[SMC_LOGTAB_BYTES / 8];
+    __shared__ uint64_t tab[SMC_LOGTAB_BYTES / 8];
     for (int i = threadIdx.x; i < SMC_LOGTAB_BYTES / 8; i += blockDim.x) tab[i] = tab_g[i];
     __syncthreads();
     for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x)
-        out[i] = log_table(u[i], tab);
+        out[i] = fp64i_log(u[i], tab);
 }
 
-int smc_launch_log_batch(const double *tab, const double *u, uint64_t n, double *out, void *stream)
+int smc_launch_log_batch(const uint64_t *tab, const double *u, uint64_t n, double *out, void *stream)
 {
     if (n == 0) return 0;
     const unsigned blocks = (unsigned)std::min<uint64_t>(4096, (n + 255) / 256);
     log_batch_kernel<<<blocks, 256, 0, (cudaStream_t)stream>>>(tab, u, n, out);
+    return to_code(cudaGetLastError());
+}
+
+__global__ void div_batch_kernel(const double *num, const double *den, uint64_t n, double *out)
+{
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x)
+        out[i] = fp64i_div(num[i], den[i]);
+}
+
+int smc_launch_div_batch(const double *num, const double *den, uint64_t n, double *out, void *stream)
+{
+    if (n == 0) return 0;
+    const unsigned blocks = (unsigned)std::min<uint64_t>(4096, (n + 255) / 256);
+    div_batch_kernel<<<blocks, 256, 0, (cudaStream_t)stream>>>(num, den, n, out);
     return to_code(cudaGetLastError());
 }
 

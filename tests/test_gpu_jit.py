@@ -64,6 +64,9 @@ MODELS = {
     'cascade_variant': lambda: workloads.mapk_cascade(2, seed=5, variant=True),
     'factor_chain': lambda: workloads.factor_chain(),
     'sqrt_race': lambda: workloads.sqrt_race(),  # arithmetic atoms (the paper's example formula)
+    'next': lambda: (workloads.immigration_death()[0],  # the Next operator with F
+                     workloads.Property([workloads.atom(['A'], 'A', '>=', 1), workloads.atom(['A'], 'A', '>=', 130)],
+                                        ('and', ('X', 0.05, 0.2, ('atom', 0)), ('F', 0.0, 100.0, ('atom', 1))))),
 }
 SIZES = {'lotka_volterra': 1500, 'cascade_literal': 512, 'cascade_variant': 256}
 MEDIUM = {'cascade_literal', 'cascade_variant', 'factor_chain'}

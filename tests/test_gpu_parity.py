@@ -200,7 +200,8 @@ def _oracle_decision_point(orc, prop, S, x, t, tmin, closed):
         if q % 2 == 0:
             v = orc.eval_prefix(prop, S, x[:k + 1], t[:k + 1], t[k], False)
         elif k + 1 < n:
-            v = orc.eval_prefix(prop, S, x[:k + 1], t[:k + 1], t[k + 1], False)
+            # after the draw the next entry time is known exactly
+            v = orc.eval_prefix(prop, S, x[:k + 1], t[:k + 1], t[k + 1], False, tmin_exact=True)
         else:
             v = orc.eval_prefix(prop, S, x, t, tmin, closed)
         if v != 2:

@@ -42,8 +42,12 @@ FORMULAS = [
     ('or', ('F', 0.0, 1.0, A(2)), ('not', ('F', 0.0, 2.0, A(1)))),
     ('or', A(2), ('U', 0.0, 1.0, A(5), A(0))),
     ('implies', A(0), ('G', 0.0, 1.0, A(0))),
+    ('X', 0.0, 1.0, A(0)),
+    ('X', 0.5, 1.5, ('not', A(1))),
+    ('and', ('X', 0.0, 2.0, A(2)), ('F', 0.0, 2.0, A(0))),
+    ('or', ('X', 0.25, 1.0, A(5)), A(2)),
 ]
-SINGLE = {0, 1, 2, 3, 4, 5}  # single-operator formulas: Kleene is complete
+SINGLE = {0, 1, 2, 3, 4, 5, 14, 15}  # single-operator formulas: Kleene is complete
 
 
 def _atom_val(a, x):
@@ -78,6 +82,9 @@ def sat(f, xs, ts, i, atoms):
         return sat(('U', f[1], f[2], ('true',), f[3]), xs, ts, i, atoms)
     if k == 'G':
         return not sat(('F', f[1], f[2], ('not', f[3])), xs, ts, i, atoms)
+    if k == 'X':
+        _, a, b, g = f
+        return i + 1 < len(xs) and a <= ts[i + 1] - ts[i] <= b and sat(g, xs, ts, i + 1, atoms)
     raise ValueError(k)
 
 
@@ -156,3 +163,25 @@ def test_nested_until_on_a_handmade_path(orc):
     assert orc.eval_prefix(prop, 1, np.asarray(xs[:4]), np.asarray(ts[:4]), 59.0, False) == 2
     assert orc.eval_prefix(prop, 1, np.asarray(xs[:4]), np.asarray(ts[:4]), 60.0, False) == 2
     assert orc.eval_prefix(prop, 1, np.asarray(xs[:4]), np.asarray(ts[:4]), 60.01, False) == 0
+
+
+@pytest.mark.parametrize('fi', range(len(FORMULAS)))
+def test_prefix_verdicts_with_a_drawn_next_time_are_sound(orc, fi):
+    # after the next entry time is drawn (tmin exact), a defined verdict must
+    # agree with every extension whose next state is entered exactly then
+    rng = random.Random(300 + fi)
+    f = FORMULAS[fi]
+    prop = workloads.Property(_atoms(), f)
+    for xs, ts in _paths(rng, 160):
+        t1 = ts[-1] + rng.choice([0.0, 0.25, 0.5, 1.0, 1.5])
+        got = orc.eval_prefix(prop, 1, np.asarray(xs), np.asarray(ts), t1, False, tmin_exact=True)
+        if got == 2:
+            continue
+        grid = [g for g in (t1, t1 + 0.25, t1 + 0.5, 1.0, 2.0, 3.0, 5.0) if g >= t1]
+        verdicts = set()
+        for y in range(4):
+            verdicts.add(sat(f, xs + [y], ts + [t1], 0, prop.atoms))
+            for y2 in range(4):
+                for t2 in grid:
+                    verdicts.add(sat(f, xs + [y, y2], ts + [t1, t2], 0, prop.atoms))
+        assert verdicts == {bool(got)}, (f, xs, ts, t1, got, verdicts)

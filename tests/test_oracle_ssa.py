@@ -200,3 +200,17 @@ def test_rate_law_factor_dropped_is_detected(orc):
     assert abs(exact - wrong) > 0.2
     y = orc.run(plain, p, seed=41, n_traj=4000)['verdict'].astype(float)
     assert abs(y.mean() - wrong) < 4.5 * math.sqrt(wrong * (1 - wrong) / y.size)
+
+
+def test_next_operator_closed_form(orc):
+    # immigration-death from A = 0: the first event is an immigration at an
+    # Exp(10) time, so X[0.05,0.2](A >= 1) holds with e^-0.5 - e^-2
+    m, _ = workloads.immigration_death()
+    p = workloads.Property([workloads.atom(['A'], 'A', '>=', 1)], ('X', 0.05, 0.2, ('atom', 0)))
+    exact = math.exp(-0.5) - math.exp(-2.0)
+    r = orc.run(m, p, seed=17, n_traj=20000)
+    y = r['verdict'].astype(float)
+    assert abs(y.mean() - exact) < 4.5 * math.sqrt(exact * (1 - exact) / y.size), (y.mean(), exact)
+    # decided by the first event: when its time falls outside the window, at
+    # the draw (no reaction applied); otherwise at the first state
+    assert set(np.unique(r['events'])) <= {0, 1}

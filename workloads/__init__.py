@@ -18,7 +18,7 @@ constraint ``sum_i coef[i] * x_i  <op>  bound`` with integer coefficients and
 ``formula`` is a tree of tuples:
 
   ('true',) ('false',) ('atom', k) ('not', f) ('and', f, g) ('or', f, g)
-  ('implies', f, g) ('U', a, b, f, g) ('F', a, b, f) ('G', a, b, f)
+  ('implies', f, g) ('U', a, b, f, g) ('F', a, b, f) ('G', a, b, f) ('X', a, b, f)
 
 which is the BLTLc grammar of Sec. 3.1 restricted to linear atoms over counts,
 with closed time intervals [a, b].
