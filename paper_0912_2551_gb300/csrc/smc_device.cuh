@@ -38,21 +38,14 @@ __device__ __forceinline__ void philox10(uint32_t c0, uint32_t c1, uint32_t c2, 
     w0 = c0; w1 = c1; w2 = c2; w3 = c3;
 }
 
-// The double holding m * 2^e0 for an integer 0 < m < 2^53, assembled on the
-// integer pipe (exact: no rounding is needed below 2^53).
-__device__ __forceinline__ double exact_scaled(uint64_t m, int e0)
-{
-    const int p = 63 - __clzll((long long)m);  // position of the leading one
-    const uint64_t mant = (m << (52 - p)) & 0x000FFFFFFFFFFFFFull;
-    return __longlong_as_double((long long)(((uint64_t)(1023 + p + e0) << 52) | mant));
-}
-
 // (0,1) from 52 bits: ((hi:lo) >> 12 + 1/2) 2^-52 = (2v + 1) 2^-53, exact, in
-// [2^-53, 1 - 2^-53].
+// [2^-53, 1 - 2^-53]: the odd integer 2v + 1 < 2^53 converted exactly (one
+// conversion on the FP64 pipe, which has room on the FP64 path; the integer
+// assembly costs 18 more issue slots), then 2^-53 applied to the exponent.
 __device__ __forceinline__ double u01_52(uint32_t hi, uint32_t lo)
 {
-    const uint64_t v = ((((uint64_t)hi) << 32) | (uint64_t)lo) >> 12;
-    return exact_scaled((v << 1) | 1ull, -53);
+    const uint64_t n = ((((((uint64_t)hi) << 32) | (uint64_t)lo) >> 12) << 1) | 1ull;
+    return __longlong_as_double(__double_as_longlong(__ull2double_rn(n)) - (53ll << 52));
 }
 
 // A positive normal float as a double, built on the integer pipe (exact:
@@ -71,18 +64,15 @@ __device__ __forceinline__ float u01_23(uint32_t w)
     return __fmaf_rn((float)(w >> 9), 0x1p-23f, 0x1p-24f);
 }
 
-// An integer h (exact for 0 <= h < 2^53, rounded once otherwise) as a double.
-__device__ __forceinline__ double int_to_double(long long h)
-{
-    if ((unsigned long long)h < (1ull << 53)) return h ? exact_scaled((uint64_t)h, 0) : 0.0;
-    return __ll2double_rn(h);
-}
+// An integer h as a double (exact for |h| < 2^53, rounded to nearest
+// otherwise): the conversion instruction.
+__device__ __forceinline__ double int_to_double(long long h) { return __ll2double_rn(h); }
 
-// -ln u for the FP64 path (u from u01_52): the integer-pipe logarithm of
-// smc_fp64i.h (table-driven, below 0.502 ulp), negated by its sign bit.
-__device__ __forceinline__ double neg_log(double u, const uint64_t *tab)
+// The odd integer n = 2v + 1 < 2^53 of the uniform (2v + 1) 2^-53 that
+// u01_52(hi, lo) returns (v = the top 52 bits of hi:lo).
+__device__ __forceinline__ uint64_t odd53(uint32_t hi, uint32_t lo)
 {
-    return __longlong_as_double(__double_as_longlong(fp64i_log(u, tab)) ^ (long long)0x8000000000000000ull);
+    return ((((((uint64_t)hi) << 32) | (uint64_t)lo) >> 12) << 1) | 1ull;
 }
 
 // x > y for x, y >= 0 (including +inf): ordered like their bit patterns,

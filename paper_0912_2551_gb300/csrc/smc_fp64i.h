@@ -95,88 +95,84 @@ FP64I_HD float fp64i_rcp_approx(float f)  // about 1/f (f in [2^23, 2^24))
 #define FP64I_FRAC 0x000FFFFFFFFFFFFFull
 #define FP64I_ONE (1ull << 52)
 
-// n / d, correctly rounded (nearest, ties to even).
+// n / d, correctly rounded (nearest, ties to even).  The integer path has
+// no branch (so the compiler can interleave it with independent work); the
+// operands and quotients it does not cover are redone by the FP64 division
+// at the end.
 FP64I_HD double fp64i_div(double n, double d)
 {
     const uint64_t bn = fp64i_bits(n), bd = fp64i_bits(d);
     const uint32_t en = (uint32_t)(bn >> 52), ed = (uint32_t)(bd >> 52);  // sign bit included
-    if (en - 1u >= 0x7FEu || ed - 1u >= 0x7FEu) return n / d;  // zero, subnormal, inf, nan, negative
+    // zero, subnormal, inf, nan or negative operands
+    bool special = (en - 1u >= 0x7FEu) | (ed - 1u >= 0x7FEu);
     uint64_t mn = (bn & FP64I_FRAC) | FP64I_ONE;
     const uint64_t md = (bd & FP64I_FRAC) | FP64I_ONE;
-    int e = (int)en - (int)ed + 1023;  // biased exponent of the quotient for mn >= md
-    if (mn < md) {
-        mn <<= 1;
-        --e;
-    }
-    if (e < 1 || e > 2046) return n / d;  // subnormal or infinite quotient
-    if (md == FP64I_ONE)                  // a power of two: exact
-        return fp64i_from_bits(((uint64_t)e << 52) | (mn & FP64I_FRAC));
-    // 1/delta for delta = md / 2^53 in (1/2, 1), as y = Y 2^-63 in (1, 2):
-    // a single-precision seed (relative error below 2^-21), then two Newton
-    // steps y <- y (2 - delta y) in 64-bit fixed point (error about 2^-62).
+    const bool lt = mn < md;
+    mn <<= lt;                                       // mn / md in [1, 2)
+    int e = (int)en - (int)ed + 1023 - (int)lt;      // biased exponent of the quotient
+    // 1/delta for delta = md / 2^53 in [1/2, 1), as y = Y 2^-63: a single-
+    // precision seed (relative error below 2^-21; 2 clamps to 2 - 2^-23),
+    // then two Newton steps y <- y (2 - delta y) in fixed point, the first
+    // with the seed as one 32-bit factor (error about 2^-42), the second in
+    // 64-bit (about 2^-62).  Truncation keeps every step at or below 1/delta.
     const uint64_t D = md << 11;  // delta 2^64
     const float s = fp64i_rcp_approx((float)(uint32_t)(D >> 40)) * 16777216.0f;
+    uint32_t sb;
+#if defined(__CUDA_ARCH__)
+    sb = __float_as_uint(s);
+#else
+    memcpy(&sb, &s, 4);
+#endif
+    const uint32_t y24 = (sb >= 0x40000000u) ? 0xFFFFFFu : ((sb & 0x7FFFFFu) | 0x800000u);
     uint64_t Y;
     {
-        uint32_t sb;
-#if defined(__CUDA_ARCH__)
-        sb = __float_as_uint(s);
-#else
-        memcpy(&sb, &s, 4);
-#endif
-        // s in [1, 2]: its 24-bit significand scaled to 2^63; s = 2 saturates
-        Y = (sb >= 0x40000000u) ? ~0ull : (((uint64_t)((sb & 0x7FFFFFu) | 0x800000u)) << 40);
+        // Y0 = y24 2^40: W = (2^88 - D y24) 2^-24, Y = y24 W 2^-23
+        const uint64_t pl = (uint64_t)(uint32_t)D * y24;
+        const uint64_t pm = (D >> 32) * (uint64_t)y24 + (pl >> 32);  // D y24 = pm 2^32 + low word of pl
+        const uint32_t low = (uint32_t)pl;
+        const uint64_t nm = (1ull << 56) - pm - (low != 0u);          // 2^88 - D y24 = nm 2^32 + nl
+        const uint32_t nl = 0u - low;
+        const uint64_t W = (nm << 8) | (nl >> 24);
+        const uint64_t ql = (uint64_t)(uint32_t)W * y24;
+        const uint64_t qm = (W >> 32) * (uint64_t)y24 + (ql >> 32);  // y24 W = qm 2^32 + low word of ql
+        Y = (qm << 9) | ((ql & 0xFFFFFFFFull) >> 23);
     }
-    for (int it = 0; it < 2; ++it) {
-        // W = (2 - delta y) 2^63 = high word of 2^128 - D Y
+    {
+        // W = high word of 2^128 - D Y, Y = Y W 2^-63
         const uint64_t pl = D * Y, ph = fp64i_mulhi(D, Y);
         const uint64_t W = ~ph + (pl == 0);
-        // Y <- Y W 2^-63
         const uint64_t ql = Y * W, qh = fp64i_mulhi(Y, W);
         Y = (qh << 1) | (ql >> 63);
     }
-    // Qt = floor(mn 2^53 / md), in [2^53, 2^54): estimate mn Y 2^-63 (off by
-    // at most 2), then the exact remainder fixes it
+    // Qt = floor(mn 2^53 / md), in [2^53, 2^54): the estimate mn Y 2^-63 is
+    // Qt or Qt - 1 (Y <= 2^63 / delta, relative error about 2^-62); the
+    // exact remainder (64-bit wrap-around arithmetic) settles it
     uint64_t qt = (fp64i_mulhi(mn, Y) << 1) | ((mn * Y) >> 63);
-    int64_t rem = (int64_t)((mn << 53) - qt * md);
-    while (rem < 0) {
-        --qt;
-        rem += (int64_t)md;
-    }
-    while (rem >= (int64_t)md) {
-        ++qt;
-        rem -= (int64_t)md;
+    uint64_t rem = (mn << 53) - qt * md;
+    for (int c = 0; c < 2; ++c) {
+        const bool up = rem >= md;
+        qt += up;
+        rem -= up ? md : 0ull;
     }
     uint64_t q = qt >> 1;
     q += (qt & 1u) & (uint64_t)((rem != 0) | (int)(q & 1u));
-    if (q >> 53) {  // rounded up to 2: next binade
-        q >>= 1;
-        if (++e > 2046) return n / d;
-    }
+    const uint64_t carry = q >> 53;  // rounded up to 2: next binade
+    q >>= carry;
+    e += (int)carry;
+    special |= (e < 1) | (e > 2046);  // subnormal or infinite quotient
+    if (special) return n / d;
     return fp64i_from_bits(((uint64_t)e << 52) | (q & FP64I_FRAC));
 }
 
-// ln u.  u = 2^k m' with m' in [0.75, 1.5); j = nearest multiple of 1/256
-// to m' - 0.75; r = m' G_j - 1 is exact (|r| < 2^-8); then
-//   ln u = k ln 2 - ln G_j + r P(r),
-//   P(r) = 1 - r/2 + r^2/3 - r^3/4 + r^4/5 - r^5/6 + r^6/7 - r^7/8
-// (the Taylor series of ln(1 + r) / r, truncated below 2^-64), with the
-// high-order part in 32-bit arithmetic, the rest in 64-bit, and the sum in
-// 128-bit fixed point (scale 2^117) rounded once to binary64.
-FP64I_HD double fp64i_log(double u, const uint64_t *tab)
+// |r| P(r) at scale 2^117 as (lo, hi), for r = m' G_j - 1 given as r 2^63
+// (|r| < 2^-8): P(r) = 1 - r/2 + r^2/3 - r^3/4 + r^4/5 - r^5/6 + r^6/7 - r^7/8,
+// the Taylor series of ln(1 + r) / r truncated below 2^-64, with the terms
+// from r^4 on in 32-bit arithmetic (relative error 2^-31 suffices there) and
+// the rest in 64-bit fixed point (relative error of the result about 2^-63).
+FP64I_HD void fp64i_log1p_abs(int64_t r, uint64_t &blo, uint64_t &bhi)
 {
-    const uint64_t b = fp64i_bits(u);
-    const uint32_t E = (uint32_t)(b >> 52);
-    if (E - 1u >= 0x7FEu) return log(u);  // zero, subnormal, inf, nan, negative
-    uint64_t M = (b & FP64I_FRAC) | FP64I_ONE;
-    int k = (int)E - 1023;
-    if (M >= (3ull << 51)) ++k;  // m' = m / 2 = M 2^-53
-    else M <<= 1;                // m' = m = (2M) 2^-53
-    const int j = (int)((M - (3ull << 51) + (1ull << 44)) >> 45);
-    const uint32_t g = reinterpret_cast<const uint32_t *>(tab + 388)[j];
-    const int64_t r = (int64_t)(M * (uint64_t)g - (1ull << 63));  // r 2^63, |r| < 2^55
     const uint64_t ra = r < 0 ? (uint64_t)(-r) : (uint64_t)r;
-    // Q4 = 1/5 - r/6 + r^2/7 - r^3/8 at scale 2^33 (relative error 2^-31 suffices)
+    // Q4 = 1/5 - r/6 + r^2/7 - r^3/8 at scale 2^33
     const int64_t r32 = (int64_t)(int32_t)(r >> 25);  // r 2^38
     int32_t q = -(1 << 30);
     q = 1227133513 + (int32_t)(((int64_t)q * r32) >> 38);
@@ -187,9 +183,74 @@ FP64I_HD double fp64i_log(double u, const uint64_t *tab)
     const int64_t r2q4 = ((int64_t)(uint32_t)(R2 >> 30) * (int64_t)q) >> 17;
     const uint64_t Q2 = 0x5555555555555555ull - (uint64_t)(r >> 1) + (uint64_t)r2q4;
     const uint64_t P = (1ull << 63) - (uint64_t)(r >> 1) + (fp64i_mulhi(R2 << 1, Q2) >> 16);
-    // B = r P at 2^117 (sign of r)
     const uint64_t pl = ra * P, ph = fp64i_mulhi(ra, P);
-    const uint64_t blo = (pl >> 9) | (ph << 55), bhi = ph >> 9;
+    blo = (pl >> 9) | (ph << 55);
+    bhi = ph >> 9;
+}
+
+// A positive 128-bit value v (scale 2^117) rounded to binary64, nearest-even.
+FP64I_HD uint64_t fp64i_round117(uint64_t lo, uint64_t hi)
+{
+    const int lz = hi ? fp64i_clz(hi) : 64 + fp64i_clz(lo);
+    uint64_t h, l;
+    if (lz >= 64) {
+        h = lo << (lz - 64);
+        l = 0;
+    } else if (lz > 0) {
+        h = (hi << lz) | (lo >> (64 - lz));
+        l = lo << lz;
+    } else {
+        h = hi;
+        l = lo;
+    }
+    uint64_t mant = h >> 11;
+    mant += ((h >> 10) & 1u) & (uint64_t)((((h & 0x3FFu) | l) != 0) | (int)(mant & 1u));
+    uint64_t ex = (uint64_t)(1023 + 10 - lz);  // leading bit 127 - lz at scale 2^117
+    if (mant >> 53) {
+        mant >>= 1;
+        ++ex;
+    }
+    return (ex << 52) | (mant & FP64I_FRAC);
+}
+
+// The same for 2^64 <= v < 2^127 (the leading bit in the high word, below
+// its top bit): no branch.
+FP64I_HD uint64_t fp64i_round117_hi(uint64_t lo, uint64_t hi)
+{
+    const int lz = fp64i_clz(hi);  // 1..63
+    const uint64_t h = (hi << lz) | (lo >> (64 - lz)), l = lo << lz;
+    uint64_t mant = h >> 11;
+    mant += ((h >> 10) & 1u) & (uint64_t)((((h & 0x3FFu) | l) != 0) | (int)(mant & 1u));
+    const uint64_t carry = mant >> 53;
+    return ((uint64_t)(1023 + 10 - lz + (int)carry) << 52) + ((mant >> carry) & FP64I_FRAC);
+}
+
+// The reduction of m' = M 2^-53 (M in [3 2^51, 3 2^52)): bucket j and
+// r = m' G_j - 1 as r 2^63 (exact, |r| < 2^55).
+FP64I_HD int64_t fp64i_reduce(uint64_t M, const uint64_t *tab, int &j)
+{
+    j = (int)((M - (3ull << 51) + (1ull << 44)) >> 45);
+    const uint32_t g = reinterpret_cast<const uint32_t *>(tab + 388)[j];
+    return (int64_t)(M * (uint64_t)g - (1ull << 63));
+}
+
+// ln u.  u = 2^k m' with m' in [0.75, 1.5); j = nearest multiple of 1/256
+// to m' - 0.75; r = m' G_j - 1 is exact (|r| < 2^-8); then
+//   ln u = k ln 2 - ln G_j + r P(r)
+// summed in 128-bit fixed point (scale 2^117) and rounded once to binary64.
+FP64I_HD double fp64i_log(double u, const uint64_t *tab)
+{
+    const uint64_t b = fp64i_bits(u);
+    const uint32_t E = (uint32_t)(b >> 52);
+    if (E - 1u >= 0x7FEu) return log(u);  // zero, subnormal, inf, nan, negative
+    uint64_t M = (b & FP64I_FRAC) | FP64I_ONE;
+    int k = (int)E - 1023;
+    if (M >= (3ull << 51)) ++k;  // m' = m / 2 = M 2^-53
+    else M <<= 1;                // m' = m = (2M) 2^-53
+    int j;
+    const int64_t r = fp64i_reduce(M, tab, j);
+    uint64_t blo, bhi;
+    fp64i_log1p_abs(r, blo, bhi);
     // A = k ln 2 - ln G_j at 2^117
     const uint32_t ka = (uint32_t)(k < 0 ? -k : k);
     uint64_t lo = tab[387] * ka;
@@ -213,33 +274,48 @@ FP64I_HD double fp64i_log(double u, const uint64_t *tab)
         hi = hi + bhi + (nl < lo);
         lo = nl;
     }
-    // round the 128-bit value to binary64
     const uint64_t neg = hi >> 63;
     if (neg) {
         lo = ~lo + 1;
         hi = ~hi + (lo == 0);
     }
     if ((hi | lo) == 0) return 0.0;
-    const int lz = hi ? fp64i_clz(hi) : 64 + fp64i_clz(lo);
-    uint64_t h, l;
-    if (lz >= 64) {
-        h = lo << (lz - 64);
-        l = 0;
-    } else if (lz > 0) {
-        h = (hi << lz) | (lo >> (64 - lz));
-        l = lo << lz;
+    return fp64i_from_bits((neg << 63) | fp64i_round117(lo, hi));
+}
+
+// -ln(n 2^-53) for an odd integer 1 <= n < 2^53: the SSA's uniform
+// u = (2v + 1) 2^-53 taken as its integer n, so neither u nor its bit
+// pattern is formed; the same arithmetic as -fp64i_log(u) (equal bits):
+//   -ln u = |k| ln 2 + ln G_j - r P(r),  k <= 0, the sum positive.
+FP64I_HD double fp64i_neglog53(uint64_t n, const uint64_t *tab)
+{
+    const int p = 63 - fp64i_clz(n);  // u = (n 2^-p) 2^(p - 53), n 2^-p in [1, 2)
+    uint64_t M = n << (52 - p);       // m 2^52
+    int ka = 53 - p;                  // -k
+    if (M >= (3ull << 51)) --ka;      // m' = m / 2 = M 2^-53
+    else M <<= 1;                     // m' = m = (2M) 2^-53
+    int j;
+    const int64_t r = fp64i_reduce(M, tab, j);
+    uint64_t blo, bhi;
+    fp64i_log1p_abs(r, blo, bhi);
+    uint64_t lo = tab[387] * (uint32_t)ka;
+    uint64_t hi = tab[386] * (uint32_t)ka + fp64i_mulhi(tab[387], (uint32_t)ka);
+    {
+        const uint64_t gl = tab[FP64I_LOG_N + j], gh = tab[j];
+        const uint64_t nl = lo + gl;
+        hi = hi + gh + (nl < lo);
+        lo = nl;
+    }
+    if (r < 0) {
+        const uint64_t nl = lo + blo;
+        hi = hi + bhi + (nl < lo);
+        lo = nl;
     } else {
-        h = hi;
-        l = lo;
+        const uint64_t nl = lo - blo;
+        hi = hi - bhi - (nl > lo);
+        lo = nl;
     }
-    uint64_t mant = h >> 11;
-    mant += ((h >> 10) & 1u) & (uint64_t)((((h & 0x3FFu) | l) != 0) | (int)(mant & 1u));
-    uint64_t ex = (uint64_t)(1023 + 10 - lz);
-    if (mant >> 53) {
-        mant >>= 1;
-        ++ex;
-    }
-    return fp64i_from_bits((neg << 63) | (ex << 52) | (mant & FP64I_FRAC));
+    return fp64i_from_bits(fp64i_round117_hi(lo, hi));  // the sum is in [2^64, 2^123)
 }
 
 #if !defined(__CUDACC_RTC__)

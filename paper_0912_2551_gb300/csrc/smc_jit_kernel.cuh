@@ -34,6 +34,32 @@
 
 namespace {
 
+// One event's random numbers (Sec. 2.2, step 2 and Eq. 2a): -ln u_tau and
+// u_sel from the Philox block of (event e, trajectory, instance).  They
+// depend on the event index alone, so the kernel draws them one event ahead
+// and the logarithm leaves the chain that runs through the counts.
+template <bool PLAIN>
+struct JitDraw {
+    typename Prec<PLAIN>::T nl, us;
+};
+
+template <bool PLAIN>
+__device__ __forceinline__ JitDraw<PLAIN> jit_draw(uint32_t e, uint32_t traj, uint32_t m, const SsaParams &p,
+                                                   const uint64_t *ltab)
+{
+    uint32_t w0, w1, w2, w3;
+    philox10(e, traj, m, 0u, p.rk0, p.rk1, w0, w1, w2, w3);
+    JitDraw<PLAIN> d;
+    if constexpr (PLAIN) {
+        d.nl = fp64i_neglog53(odd53(w0, w1), ltab);  // -ln u01_52(w0, w1)
+        d.us = u01_52(w2, w3);
+    } else {
+        d.nl = -__logf(u01_23(w0));
+        d.us = u01_23(w2);
+    }
+    return d;
+}
+
 template <bool PLAIN>
 __device__ __forceinline__ void jit_run_instance(const SsaParams &p, const MonProg &P, const uint64_t *ltab,
                                                  const int m, double *tc, typename Prec<PLAIN>::T *crate,
@@ -75,6 +101,7 @@ __device__ __forceinline__ void jit_run_instance(const SsaParams &p, const MonPr
     uint32_t traj = 0, e = 0;
     double t = 0.0;
     int32_t x[JS];
+    JitDraw<PLAIN> nd;  // the current event's random numbers
     MonLane ml;
     MonHot mh;
     uint32_t c_yes = 0, c_dec = 0, c_bud = 0;
@@ -123,6 +150,7 @@ __device__ __forceinline__ void jit_run_instance(const SsaParams &p, const MonPr
                         snapped = false;
 #pragma unroll
                         for (int i = 0; i < JS; ++i) x[i] = x0[i];
+                        nd = jit_draw<PLAIN>(0u, traj, (uint32_t)m, p, ltab);
                         ml.ab = jit_atoms(x);
                         mon_start(ml, P);
                         active = true;
@@ -149,20 +177,27 @@ __device__ __forceinline__ void jit_run_instance(const SsaParams &p, const MonPr
             finish(mon_close(ml, P));  // absorbing state: no further position
             continue;
         }
-        uint32_t w0, w1, w2, w3;
-        philox10(e, traj, (uint32_t)m, 0u, p.rk0, p.rk1, w0, w1, w2, w3);
         double tn;
         T r;
         if (PLAIN) {
-            const double ut = u01_52(w0, w1), us = u01_52(w2, w3);
-            tn = __dadd_rn(t, fp64i_div(neg_log(ut, ltab), (double)a0));
-            r = (T)__dmul_rn(us, (double)a0);
+            tn = __dadd_rn(t, fp64i_div((double)nd.nl, (double)a0));
+            r = (T)__dmul_rn((double)nd.us, (double)a0);
         } else {
-            const float ut = u01_23(w0), us = u01_23(w2);
-            const float tau = __fdividef(-__logf(ut), (float)a0);
+            const float tau = __fdividef((float)nd.nl, (float)a0);
             tn = __dadd_rn(t, f32_to_f64(tau));
-            r = (T)__fmul_rn(us, (float)a0);
+            r = (T)__fmul_rn((float)nd.us, (float)a0);
         }
+        // step 2: the first j whose running sum exceeds r (taken before the
+        // monitor looks at tn, so the two chains overlap)
+        int j = -1;
+#pragma unroll
+        for (int k = JR - 1; k >= 0; --k) {
+            const bool hit = PLAIN ? __double_as_longlong((double)pre[k]) > __double_as_longlong((double)r)
+                                   : pre[k] > r;
+            if (hit) j = k;
+        }
+        if (j < 0) j = 31 - __clz(pos);  // r reached the full sum: last positive a_k
+        nd = jit_draw<PLAIN>(e + 1u, traj, (uint32_t)m, p, ltab);
         if (snap_mode && !snapped && dgt(tn, t_snap)) {
             snapped = true;
             const uint64_t idx = (uint64_t)m * p.out_stride + ((uint64_t)traj - p.out_base);
@@ -179,16 +214,6 @@ __device__ __forceinline__ void jit_run_instance(const SsaParams &p, const MonPr
         }
         if (!v && unbounded && dgt(tn, t_max)) v = 1;  // pessimistic rule (Sec. 3.2)
         if (v) { finish(v); continue; }
-
-        // step 2: the first j whose running sum exceeds r
-        int j = -1;
-#pragma unroll
-        for (int k = JR - 1; k >= 0; --k) {
-            const bool hit = PLAIN ? __double_as_longlong((double)pre[k]) > __double_as_longlong((double)r)
-                                   : pre[k] > r;
-            if (hit) j = k;
-        }
-        if (j < 0) j = 31 - __clz(pos);  // r reached the full sum: last positive a_k
 
         // step 4: x += v_j, then the monitor at the new state
 #ifdef JIT_MEDIUM

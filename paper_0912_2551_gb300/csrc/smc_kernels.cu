@@ -234,8 +234,8 @@ __device__ __forceinline__ void run_instance(const SsaParams &p, const MonProg &
         double tn;
         T r;
         if (PLAIN) {
-            const double ut = u01_52(w0, w1), us = u01_52(w2, w3);
-            tn = __dadd_rn(t, fp64i_div(neg_log(ut, ltab), (double)a0));
+            const double us = u01_52(w2, w3);  // -ln u01_52(w0, w1), from the integer:
+            tn = __dadd_rn(t, fp64i_div(fp64i_neglog53(odd53(w0, w1), ltab), (double)a0));
             r = (T)__dmul_rn(us, (double)a0);
         } else {
             const float ut = u01_23(w0), us = u01_23(w2);

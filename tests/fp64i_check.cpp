@@ -67,6 +67,10 @@ int main(int argc, char **argv)
             b = bits_to_double((next_u64() & 0x000FFFFFFFFFFFFFull) | (1023ull << 52));
             a = q * b;
             a = bits_to_double(double_bits(a) + (int)(next_u64() % 5) - 2);
+        } else if (kind == 3 && (i & 4)) {  // divisors just above and below powers of two
+            a = bits_to_double((next_u64() & 0x000FFFFFFFFFFFFFull) | ((uint64_t)(1000 + next_u64() % 48) << 52));
+            const uint64_t f = (i & 8) ? (next_u64() >> 34) : (0x000FFFFFFFFFFFFFull - (next_u64() >> 34));
+            b = bits_to_double(f | ((uint64_t)(1000 + next_u64() % 48) << 52));
         } else {  // few significand bits (ties and short patterns)
             a = bits_to_double((next_u64() & 0x000FF00000000000ull) | ((uint64_t)(1000 + next_u64() % 48) << 52));
             b = bits_to_double((next_u64() & 0x000F000000000000ull) | ((uint64_t)(1000 + next_u64() % 48) << 52));
@@ -119,6 +123,18 @@ int main(int argc, char **argv)
             check(bits_to_double(double_bits(c) + s));
         }
     for (long i = 0; i < n / 4; ++i) check(exp(-700.0 + 1400.0 * (double)(next_u64() >> 11) * 0x1p-53));
+    // the SSA form: -ln((2v + 1) 2^-53) from the integer, equal bits to -ln u
+    long neglog_bad = 0;
+    for (long i = 0; i < n; ++i) {
+        const uint64_t v = (i < 64) ? (uint64_t)i : (i < 128 ? (1ull << 52) - 1 - (uint64_t)(i - 64) : next_u64() >> 12);
+        const uint64_t nn = 2 * v + 1;
+        const double u = (double)nn * 0x1p-53;
+        const double want = -fp64i_log(u, tab), got = fp64i_neglog53(nn, tab);
+        if (double_bits(got) != double_bits(want)) {
+            if (neglog_bad < 5) printf("neglog53_mismatch n=%llu got=%a want=%a\n", (unsigned long long)nn, got, want);
+            ++neglog_bad;
+        }
+    }
     const double log_edges[] = {0x1p-53, 1 - 0x1p-53, 0.5, 0.75, 1.0, 1.5, 2.0, 3.0, 0.1, 1e-300, 1e300,
                                 1.7976931348623157e308, 2.2250738585072014e-308};
     for (double u : log_edges) check(u);
@@ -127,7 +143,7 @@ int main(int argc, char **argv)
                             fp64i_log(1.0, tab) == 0.0;
     const double frac_ok = (double)rounded_ok / (double)log_n;
     printf("div_checked=%ld div_mismatches=%ld log_checked=%ld log_max_ulp=%.6f log_max_at=%a "
-           "log_correctly_rounded=%.7f special_ok=%d\n",
-           div_n, div_bad, log_n, worst, worst_u, frac_ok, (int)special_ok);
-    return (div_bad == 0 && worst <= 0.502 && frac_ok >= 0.9995 && special_ok) ? 0 : 1;
+           "log_correctly_rounded=%.7f special_ok=%d neglog53_mismatches=%ld\n",
+           div_n, div_bad, log_n, worst, worst_u, frac_ok, (int)special_ok, neglog_bad);
+    return (div_bad == 0 && worst <= 0.502 && frac_ok >= 0.9995 && special_ok && neglog_bad == 0) ? 0 : 1;
 }

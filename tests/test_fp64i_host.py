@@ -4,7 +4,8 @@ against the platform's arithmetic by tests/fp64i_check.cpp: the division
 bit for bit against IEEE-754 division on 10^6 operand pairs of every class,
 the logarithm within 0.502 ulp of long-double logl and correctly rounded on
 more than 99.99% of 1.75 x 10^6 arguments (the SSA's uniforms, values near
-1, the table's bucket edges, general positive doubles)."""
+1, the table's bucket edges, general positive doubles), and the SSA's form
+-ln((2v + 1) 2^-53) from the integer equal bit for bit to -ln u."""
 import os
 import shutil
 import subprocess
@@ -26,7 +27,8 @@ def test_fp64i_against_host_arithmetic(tmp_path):
                     os.path.join(ROOT, 'tests', 'fp64i_check.cpp'), '-o', exe, '-lm'], check=True)
     r = subprocess.run([exe, '1000000'], capture_output=True, text=True, timeout=300)
     assert r.returncode == 0, r.stdout + r.stderr
-    kv = dict(f.split('=', 1) for f in r.stdout.split()[-7:])
+    kv = dict(f.split('=', 1) for f in r.stdout.split()[-8:])
     assert int(kv['div_mismatches']) == 0
     assert float(kv['log_max_ulp']) <= 0.502
     assert float(kv['log_correctly_rounded']) >= 0.9999
+    assert int(kv['neglog53_mismatches']) == 0
