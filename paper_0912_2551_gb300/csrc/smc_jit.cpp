@@ -124,12 +124,12 @@ std::string jit_model_header(const JitModel &M, std::string &why)
                 o << (k || w ? ", " : "") << word << "u";
             }
         o << "};\n";
-        o << "__device__ __forceinline__ void jit_apply_row(const uint32_t *row, int32_t *x)\n{\n";
+        o << "__device__ __forceinline__ void jit_apply_row(const uint32_t *row, int32_t *x, int sgn)\n{\n";
         for (int i = 0; i < S; ++i) {
             bool any = false;
             for (int k = 0; k < R; ++k) any = any || M.stoich[(size_t)k * S + i] != 0;
             if (any)
-                o << "    x[" << i << "] += (int32_t)(int8_t)(row[" << i / 4 << "] >> " << 8 * (i % 4) << ");\n";
+                o << "    x[" << i << "] += sgn * (int32_t)(int8_t)(row[" << i / 4 << "] >> " << 8 * (i % 4) << ");\n";
         }
         o << "}\n";
     }
@@ -187,15 +187,15 @@ std::string jit_model_header(const JitModel &M, std::string &why)
     }
     // x += v_j as selects (no divergent branch on j); medium networks use the
     // table above instead
-    o << "__device__ __forceinline__ void jit_apply(int j, int32_t *x)\n{\n";
-    if (medium) o << "    (void)j; (void)x;\n";
+    o << "__device__ __forceinline__ void jit_apply(int j, int32_t *x, int sgn)\n{\n";
+    if (medium) o << "    (void)j; (void)x; (void)sgn;\n";
     for (int i = 0; i < S; ++i) {
         std::ostringstream d;
         for (int k = 0; k < R; ++k) {
             const int32_t v = M.stoich[(size_t)k * S + i];
             if (v) d << (d.tellp() > 0 ? " + " : "") << "(j == " << k << " ? " << v << " : 0)";
         }
-        if (d.tellp() > 0 && !medium) o << "    x[" << i << "] += " << d.str() << ";\n";
+        if (d.tellp() > 0 && !medium) o << "    x[" << i << "] += sgn * (" << d.str() << ");\n";
     }
     o << "}\n";
     // atoms: (lo <= L <= hi) xor neg, L = sum coef x (exact int64)

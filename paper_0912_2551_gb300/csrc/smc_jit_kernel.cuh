@@ -6,7 +6,7 @@
 //   jit_props_plain / _mixed     a_k = c_k h_k(x) for every k, their running
 //                                sums (the selection table of Eq. 2b) and the
 //                                bit set of positive a_k
-//   jit_apply(j, x)              x += v_j
+//   jit_apply(j, x, sgn)         x += sgn v_j
 //   jit_atoms(x)                 the atom bit vector of the monitor
 // so each lane keeps its counts x in registers and no table is read per
 // event.  Rates (and x0) stay data, read once per instance, so one compiled
@@ -168,15 +168,17 @@ __device__ __forceinline__ void jit_run_instance(const SsaParams &p, const MonPr
         if (!active) continue;
 
         // ---- one event (Sec. 2.2 steps 1-5) ----------------------------------
+        // Small networks: everything an ordinary event needs is computed
+        // without a branch (propensities, clock, selection, the next event's
+        // draw, x += v_j, atoms); one test then sends the rare events
+        // (absorbing state, snapshot, the monitor's clock window or atoms,
+        // the event budget) through the full sequence, with x restored first.
         T pre[JR];
         uint32_t pos = 0;
         if constexpr (PLAIN) jit_props_plain(x, c, pre, pos);
         else jit_props_mixed(x, c, pre, pos);
         const T a0 = pre[JR - 1];
-        if (PLAIN ? __double_as_longlong((double)a0) <= 0 : !(a0 > (T)0)) {
-            finish(mon_close(ml, P));  // absorbing state: no further position
-            continue;
-        }
+        const bool dead = PLAIN ? __double_as_longlong((double)a0) <= 0 : !(a0 > (T)0);
         double tn;
         T r;
         if (PLAIN) {
@@ -187,8 +189,7 @@ __device__ __forceinline__ void jit_run_instance(const SsaParams &p, const MonPr
             tn = __dadd_rn(t, f32_to_f64(tau));
             r = (T)__fmul_rn((float)nd.us, (float)a0);
         }
-        // step 2: the first j whose running sum exceeds r (taken before the
-        // monitor looks at tn, so the two chains overlap)
+        // step 2: the first j whose running sum exceeds r
         int j = -1;
 #pragma unroll
         for (int k = JR - 1; k >= 0; --k) {
@@ -196,8 +197,31 @@ __device__ __forceinline__ void jit_run_instance(const SsaParams &p, const MonPr
                                    : pre[k] > r;
             if (hit) j = k;
         }
-        if (j < 0) j = 31 - __clz(pos);  // r reached the full sum: last positive a_k
-        nd = jit_draw<PLAIN>(e + 1u, traj, (uint32_t)m, p, ltab);
+        if (j < 0) j = dead ? 0 : 31 - __clz(pos);  // r reached the full sum: last positive a_k
+        const JitDraw<PLAIN> nd_next = jit_draw<PLAIN>(e + 1u, traj, (uint32_t)m, p, ltab);
+#ifndef JIT_MEDIUM
+        // step 4: x += v_j, then the common case: nothing for the monitor,
+        // no snapshot, no stop (medium networks measured faster without it)
+        jit_apply(j, x, 1);
+        {
+            const uint32_t abn = jit_atoms(x);
+            const bool rare = dead | (mh.pend != 0u) | (__double_as_longlong(tn) > mh.hb) | always_step |
+                              (abn != mh.ab) | ((uint64_t)e + 1u >= budget) |
+                              ((snap_mode != 0) & !snapped & dgt(tn, t_snap)) | (unbounded & dgt(tn, t_max));
+            if (!rare) {
+                ++e;
+                t = tn;
+                nd = nd_next;
+                continue;
+            }
+        }
+        jit_apply(j, x, -1);
+#endif
+        if (dead) {
+            finish(mon_close(ml, P));  // absorbing state: no further position
+            continue;
+        }
+        nd = nd_next;
         if (snap_mode && !snapped && dgt(tn, t_snap)) {
             snapped = true;
             const uint64_t idx = (uint64_t)m * p.out_stride + ((uint64_t)traj - p.out_base);
@@ -217,9 +241,9 @@ __device__ __forceinline__ void jit_run_instance(const SsaParams &p, const MonPr
 
         // step 4: x += v_j, then the monitor at the new state
 #ifdef JIT_MEDIUM
-        jit_apply_row(sdelta + j * JW, x);
+        jit_apply_row(sdelta + j * JW, x, 1);
 #else
-        jit_apply(j, x);
+        jit_apply(j, x, 1);
 #endif
         ++e;
         t = tn;
