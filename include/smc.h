@@ -411,7 +411,9 @@ int smc_mlp_predict_masked(smc_mlp *mlp, const float *x, uint64_t n, const uint8
  * trajectories only to t_snap; G = Y when the verdict was fixed before t_snap,
  * else G = g(snapshot features).  p_hat = mean_full(Y - beta G) +
  * beta mean_all(G), unbiased for any fixed beta.  Var is estimated from the
- * samples, n_eff = p_hat (1 - p_hat) / Var, and [lo, hi] is Eq. 4 at n_eff.
+ * samples, n_eff = p_hat (1 - p_hat) / Var (n_eff = n_full while the full
+ * runs hold only one verdict, as Fig. 2 treats p_hat = 0 or 1), and
+ * [lo, hi] is Eq. 4 at n_eff.
  * The sample sizes grow (cost-optimal split between full and prefix runs,
  * with the events per full run and per prefix run measured on the full
  * runs) until n_eff >= Wilson_sample(p', half_width) with p' = p_hat +-
@@ -426,7 +428,7 @@ int smc_mlp_predict_masked(smc_mlp *mlp, const float *x, uint64_t n, const uint8
  * the context for later calls. */
 typedef struct {
     double p_hat, lo, hi;
-    double n_eff;      /* p_hat (1 - p_hat) / var */
+    double n_eff;      /* p_hat (1 - p_hat) / var, or n_full (one verdict only) */
     double var;        /* estimated variance of p_hat */
     double beta;
     uint64_t n_full, n_prefix;

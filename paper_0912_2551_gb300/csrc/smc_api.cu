@@ -1651,7 +1651,10 @@ int smc_estimate_cv(smc_ctx *ctx, smc_mlp *mlp, double confidence, double half_w
         const double cDG = (sDG - c1n * mD * mG1) / (c1n - 1.0);
         const double a = vD, bb = std::max(0.0, beta * beta * vG + 2.0 * beta * cDG);
         V = a / c1n + bb / nn;
-        const bool interior = p > 0.0 && p < 1.0 && V > 0.0;
+        // Until the full runs hold both verdicts, the sample variance says
+        // nothing about Y (the control variate only adds noise around a
+        // constant): n_eff = the full runs, as Fig. 2 treats p = 0 or 1.
+        const bool interior = p > 0.0 && p < 1.0 && V > 0.0 && sY > 0.0 && sY < c1n;
         neff = interior ? p * (1.0 - p) / V : c1n;
         const double pp = p <= 0.5 ? p + half_width : p - half_width;
         const double target = wilson_sample_real(pp, half_width, z);

@@ -124,6 +124,26 @@ def test_control_variate_untrained_is_unbiased(env):
     assert res['n_full'] >= 4000
 
 
+def test_control_variate_with_one_verdict_stops_like_fig2(env):
+    # p = 0 (the threshold is never reached): while the full runs hold only
+    # one verdict the variance estimate says nothing about Y, so n_eff is the
+    # full sample and the loop stops where Fig. 2 stops at p_hat = 0
+    torch, smc = env
+    m, _ = workloads.immigration_death()
+    never = workloads.Property([workloads.atom(['A'], 'A', '>=', 100000)], ('F', 0.0, 100.0, ('atom', 0)))
+    net = smc.Mlp(4, seed=11)
+    xs, ts = _c1_features(50.0)
+    with smc.Context(0) as ctx:
+        ctx.load_model(m)
+        ctx.load_property(never)
+        res = ctx.estimate_cv(net, 0.95, 0.01, seed=7, precision='mixed', t_snap=50.0, x_scale=xs,
+                              t_scale=ts, beta=1.0, pilot=100)
+        plain = ctx.estimate(0.95, 0.01, seed=7, precision='mixed', sampling='iterative')[0]
+    assert plain['p_hat'] == 0.0
+    assert res['n_full'] <= plain['n'] and res['n_prefix'] == 0, (res, plain)
+    assert res['n_eff'] == res['n_full'] and res['lo'] <= 0.0 + 1e-12 and res['hi'] <= 0.01, res
+
+
 def _held_out_beta(ctx, net, t_snap, xs, ts, seed):
     """beta = Cov(Y, G) / Var(G) and the residual share Var(Y - beta G) / Var(Y)
     on held-out trajectories (a seed disjoint from training and estimation)."""
