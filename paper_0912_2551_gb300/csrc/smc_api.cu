@@ -1667,7 +1667,7 @@ int smc_estimate_cv(smc_ctx *ctx, smc_mlp *mlp, double confidence, double half_w
         const double aim = 1.05 * target;
         uint64_t t1, t2;
         if (!interior) {  // no variance information yet: grow the full sample as Fig. 2 does
-            t1 = (uint64_t)std::ceil(aim);
+            t1 = (uint64_t)std::ceil(target);
             t2 = n2;
         } else {
             const double Vt = p * (1.0 - p) / aim;

@@ -132,10 +132,12 @@ __device__ __forceinline__ void jit_run_instance(const SsaParams &p, const MonPr
     };
 
     for (;;) {
-        if (!exhausted) {
-            const unsigned need = __ballot_sync(FULL_MASK, !active);
+        // one vote per iteration: which lanes hold a trajectory
+        unsigned act = __ballot_sync(FULL_MASK, active);
+        if (!exhausted && act != FULL_MASK) {
+            const unsigned need = ~act;
             const int nneed = __popc(need);
-            if (nneed && (nneed >= p.refill || nneed == 32)) {
+            if (nneed >= p.refill || nneed == 32) {
                 const int leader = __ffs(need) - 1;
                 unsigned long long base = 0;
                 if (lane == leader) base = atomicAdd(&p.tnext[m], (unsigned long long)nneed);
@@ -159,9 +161,10 @@ __device__ __forceinline__ void jit_run_instance(const SsaParams &p, const MonPr
                         if (v) finish(v);
                     }
                 }
+                act = __ballot_sync(FULL_MASK, active);
             }
         }
-        if (!__any_sync(FULL_MASK, active)) {
+        if (!act) {
             if (exhausted) break;
             continue;
         }
