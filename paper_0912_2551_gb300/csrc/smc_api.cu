@@ -511,11 +511,10 @@ int tc_bytes_of(const MonProg &prog)
     return 0;
 }
 
-// warp slice: table | x[(s_max + 1)][32] | tc | a[r_max][32]
+// warp slice: x[(s_max + 1)][32] | tc | a[r_max][32] (tables stay in global memory)
 int warp_bytes_of(const SizeClass &c, int plain, int tc_bytes)
 {
-    const int blob_words = (c.blob_words + 3) & ~3;
-    const int b = blob_words * 4 + (c.s_max + 1) * 128 + tc_bytes + c.r_max * 32 * (plain ? 8 : 4);
+    const int b = (c.s_max + 1) * 128 + tc_bytes + c.r_max * 32 * (plain ? 8 : 4);
     return (b + 15) & ~15;
 }
 
@@ -575,7 +574,6 @@ int issue_class(smc_ctx *ctx, int plain, const SsaParams &common, const Launch &
     p.inst_list = L.c->d_list;
     p.n_list = (int)L.c->inst.size();
     p.refill = L.refill;
-    p.blob_words = (L.c->blob_words + 3) & ~3;
     p.s_max = L.c->s_max;
     p.r_max = L.c->r_max;
     p.tc_bytes = L.tc_bytes;

@@ -143,7 +143,6 @@ struct SsaParams {
     uint64_t budget;             // max reactions per trajectory
     uint32_t renorm_mask;        // mixed path: renormalise when (e & mask) == 0
     int32_t refill;              // refill when >= refill lanes are idle
-    int32_t blob_words;          // per-warp table area (words, multiple of 4)
     int32_t s_max, r_max;        // per-lane state area
     int32_t tc_bytes;            // per-warp candidate clocks (0: no nested unit)
     int32_t warp_bytes;          // shared memory per warp

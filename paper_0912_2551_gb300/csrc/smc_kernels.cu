@@ -2,10 +2,9 @@
 //
 // One trajectory per thread (the "multiple replications in parallel" policy
 // of Sec. 4, one replica per lane instead of one per MPI process).  Each warp
-// works on one instance at a time and keeps that instance's model table in
-// its own slice of shared memory; each lane keeps its counts x and
-// propensities a in shared memory columns (lane-minor, so lane i always hits
-// bank i).  Lanes that finish a trajectory claim the next index of the
+// works on one instance at a time (its model table read through L1); each
+// lane keeps its counts x and propensities a in shared-memory columns of the
+// warp's slice (lane-minor, so lane i always hits bank i).  Lanes that finish a trajectory claim the next index of the
 // instance's work queue by warp ballot (one atomic per refill).
 //
 // Per event (Sec. 2.2, steps 1-5; Eq. 2a/2b):
@@ -154,10 +153,12 @@ __device__ __forceinline__ void run_instance(const SsaParams &p, const MonProg &
     };
 
     for (;;) {
-        if (!exhausted) {
-            const unsigned need = __ballot_sync(FULL_MASK, !active);
+        // one vote per iteration: which lanes hold a trajectory
+        unsigned act = __ballot_sync(FULL_MASK, active);
+        if (!exhausted && act != FULL_MASK) {
+            const unsigned need = ~act;
             const int nneed = __popc(need);
-            if (nneed && (nneed >= p.refill || nneed == 32)) {
+            if (nneed >= p.refill || nneed == 32) {
                 const int leader = __ffs(need) - 1;
                 unsigned long long base = 0;
                 if (lane == leader) base = atomicAdd(&p.tnext[m], (unsigned long long)nneed);
@@ -191,9 +192,10 @@ __device__ __forceinline__ void run_instance(const SsaParams &p, const MonProg &
                         if (v) finish(v);
                     }
                 }
+                act = __ballot_sync(FULL_MASK, active);
             }
         }
-        if (!__any_sync(FULL_MASK, active)) {
+        if (!act) {
             if (exhausted) break;
             continue;
         }
@@ -368,10 +370,13 @@ __global__ void __launch_bounds__(256, PLAIN ? 3 : 4) ssa_kernel(const SsaParams
     const MonProg &P = *reinterpret_cast<const MonProg *>(smem);
     const uint64_t *ltab = reinterpret_cast<const uint64_t *>(smem + sizeof(MonProg));
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    // warp slice: table | x[(s_max + 1)][32] | tc[units][32] | a[r_max][32]
+    // warp slice: x[(s_max + 1)][32] | tc[units][32] | a[r_max][32]; the
+    // instance's table is read from global memory through L1, where it stays
+    // while the warp works on that instance (shared memory holding it cost
+    // occupancy: measured 7.7M vs 8.9M trajectories/s on 4096 networks)
     unsigned char *wb = smem + sizeof(MonProg) + p.logtab_bytes + (size_t)warp * p.warp_bytes;
-    uint32_t *blob = reinterpret_cast<uint32_t *>(wb);
-    unsigned char *lanes = wb + (size_t)p.blob_words * 4;
+    const uint32_t *blob = nullptr;
+    unsigned char *lanes = wb;
     int32_t *xs = reinterpret_cast<int32_t *>(lanes) + lane;
     lanes += (size_t)(p.s_max + 1) * 128;
     double *tc = reinterpret_cast<double *>(lanes) + lane;
@@ -385,10 +390,7 @@ __global__ void __launch_bounds__(256, PLAIN ? 3 : 4) ssa_kernel(const SsaParams
         const int m = acquire_instance(p, first, gw, lane);
         if (m < 0) break;
         if (m != cur) {
-            const uint32_t *src = p.blobs + p.blob_off[m];
-            const int words = (int)src[BH_WORDS];
-            for (int i = lane; i < words; i += 32) blob[i] = src[i];
-            __syncwarp();
+            blob = p.blobs + p.blob_off[m];
             cur = m;
         }
         run_instance<PLAIN, EXT>(p, P, ltab, m, blob, xs, tc, as, lane);
