@@ -547,7 +547,7 @@ int plan_class(smc_ctx *ctx, int plain, const SizeClass &c, const Shape &sh, Lau
     // warp slice holds only the nested operators' candidate clocks
     L.kernel = ctx->jit_ready ? (plain ? ctx->jit_k.plain : ctx->jit_k.mixed) : nullptr;
     const int rate_bytes = (ctx->jit_k.rate_count * (plain ? 8 : 4) + 15) / 16 * 16;
-    L.warp_bytes = L.kernel ? L.tc_bytes + rate_bytes : warp_bytes_of(c, plain, L.tc_bytes);
+    L.warp_bytes = L.kernel ? L.tc_bytes + rate_bytes + SMC_JIT_COOP_BYTES : warp_bytes_of(c, plain, L.tc_bytes);
     L.block = 32 * sh.warps;
     L.smem = (int)sizeof(MonProg) + (plain ? SMC_LOGTAB_BYTES : 0) + (L.kernel ? ctx->jit_k.delta_bytes : 0) +
              sh.warps * L.warp_bytes;

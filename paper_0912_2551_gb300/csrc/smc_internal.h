@@ -10,7 +10,10 @@
 // ln 2 high | ln 2 low | pad.  The high parts are multiples of 2^-42, so
 // k ln2_high + ln(1/G_j) high is exact for |k| <= 1075.
 #include "smc_fp64i.h"
-#define SMC_LOGTAB_BYTES FP64I_LOG_BYTES  // the FP64 path's log table (a multiple of 16 bytes)
+#define SMC_LOGTAB_BYTES FP64I_LOG_BYTES
+// per-warp scratch of the specialized kernel's cooperative tail (the end of
+// its warp slice)
+#define SMC_JIT_COOP_BYTES 64  // the FP64 path's log table (a multiple of 16 bytes)
 #define SMC_MAX_UNITS 4   // temporal operators (monitor units) per formula
 #define SMC_MAX_ATOMS 6   // distinct atoms (truth tables are 64-bit)
 #define SMC_MAX_SPECIES 255

@@ -109,6 +109,19 @@ def test_specialized_kernel_reproduces_generic(smc, name, precision):
     assert np.array_equal(spec['wilson'], gen['wilson'])
 
 
+@pytest.mark.parametrize('name', ['lotka_volterra', 'immigration_death', 'nested_lv', 'next'])
+def test_cooperative_tail_reproduces_generic(smc, name):
+    # a handful of trajectories: warps run out of work at once, and a warp's
+    # last trajectory is advanced by its 32 lanes speculating over the
+    # reactions (FP64 path): the trajectories must be the sequential ones
+    model, prop = MODELS[name]()
+    for n in (1, 3, 37):
+        spec, _ = _run(smc, model, prop, 1, 'plain', n)
+        gen, _ = _run(smc, model, prop, 0, 'plain', n)
+        for k in OUTPUTS + ('counts',):
+            assert np.array_equal(spec[k], gen[k]), (name, n, k, np.argwhere(spec[k] != gen[k])[:5])
+
+
 @pytest.mark.parametrize('precision', ['plain', 'mixed'])
 def test_specialized_snapshots_reproduce_generic(smc, precision):
     import torch
