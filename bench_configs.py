@@ -134,6 +134,7 @@ def random_networks(args):
         dt = (time.perf_counter() - t0) / steps
         clk = clocks.stop()
         ev_step = tot / steps
+        shapes = ctx.launch_shapes('mixed')
     # oracle on a bounded sample: 2 trajectories of every 16th instance
     t0 = time.perf_counter()
     k = 0
@@ -148,9 +149,11 @@ def random_networks(args):
           'one graph-captured estimate per step',
           {'events_per_s': ev_step / dt, 'events_per_trajectory': ev_step / (4096 * n), 'clocks': clk,
            'roofline': _issue_roofline(ev_step / dt, ops, 'ssa_kernel<mixed>'),
-           'note': 'host-timed smc_estimate (graph launch, ranges up, counts down); throughput-bound at '
-                   '10,000 trajectories per instance (6.2e10 events per step; the longest trajectories, '
-                   '~8e5 events, bound the step only below ~1,000 per instance)',
+           'note': 'host-timed smc_estimate (graph launch, ranges up, counts down); at 10,000 trajectories '
+                   'per instance (6.2e10 events per step) the heaviest networks\' trajectories (up to ~8e5 '
+                   'events each) add about 0.7 s of tail; the marginal rate from 1e4 to 2e4 per instance '
+                   'is higher',
+           'launch': shapes,
            'cpu_baseline': {'value': k / cpu, 'unit': 'trajectories/s', 'cores': os.cpu_count(),
                             'kind': 'oracle', 'sample': f'2 trajectories of every 16th instance, {cpu:.1f} s'}})
 
