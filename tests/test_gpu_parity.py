@@ -86,6 +86,30 @@ def test_lotka_volterra_plain(ctx, orc):
     assert abs(g['verdict'][0].mean() - r['verdict'].mean()) <= 1e-3
 
 
+def test_lotka_volterra_full_size_sampled(ctx, orc):
+    # the benchmark's workload at full size (10^6 trajectories of one launch,
+    # in the launch shape the autotuner picks, as bench.py times it): blocks
+    # of trajectories spread over the whole range, including the last ones
+    # claimed, recomputed by the oracle one index range at a time
+    from oracle import wilson
+    m, p = workloads.lotka_volterra()
+    n = 1_000_000
+    g = _gpu(ctx, m, p, n, seed=0, confidence=0.99)
+    starts = [0, 1000, 123_457, 400_000, 777_777, n - 200]
+    v, ev, tf, st = g['verdict'][0], g['events'][0], g['t_final'][0], g['status'][0]
+    idx = np.concatenate([np.arange(b, b + 200) for b in starts])
+    rs = [orc.run(m, p, seed=0, traj_begin=b, n_traj=200) for b in starts]
+    r = {k: np.concatenate([x[k] for x in rs]) for k in ('verdict', 'events', 't_final', 'status')}
+    sub = {'verdict': v[None, idx], 'events': ev[None, idx], 't_final': tf[None, idx], 'status': st[None, idx]}
+    _compare_plain(sub, r, min_agree=1.0 - 1.5 / idx.size)  # at most one of the 1200 may part
+    # properties of the whole launch: counts, events, the interval from them
+    yes, dec = int(g['counts'][0, 0]), int(g['counts'][0, 1])
+    assert dec == n and yes == int(v.sum()) and int(g['counts'][0, 2]) == int(ev.astype(np.int64).sum())
+    p_hat, lo, hi = wilson.wilson_interval(yes, dec, 0.99)
+    assert abs(g['wilson'][0, 1] - lo) <= 1e-12 * lo and abs(g['wilson'][0, 2] - hi) <= 1e-12 * hi
+    assert 2.0e-4 < p_hat < 7.0e-4 and abs(ev.mean() - 2358.7) < 5.0
+
+
 @pytest.mark.parametrize('name', ['dimerisation', 'hetero', 'decay'])
 def test_small_networks_plain_with_final_states(ctx, orc, name):
     if name == 'dimerisation':
