@@ -335,8 +335,9 @@ def main():
         for s in range(e2e_steps):
             ctx2.load_model(model)
             ctx2.load_property(prop)
-            ctx2.estimate(CONFIDENCE, HALF_WIDTH, seed=SEED + s, precision='plain', sampling='fixed',
-                          fixed_n=N_TRAJ)
+            # each rank its own trajectories (a seed of its own: the estimate numbers them from 0)
+            ctx2.estimate(CONFIDENCE, HALF_WIDTH, seed=SEED + s + 7919 * rank, precision='plain',
+                          sampling='fixed', fixed_n=N_TRAJ)
         barrier()
         e2e_dt = reduce_max(time.perf_counter() - t0)
         ctx2.close()
