@@ -229,6 +229,20 @@ __device__ __forceinline__ void jit_run_instance(const SsaParams &p, const MonPr
     MonLane ml;
     MonHot mh;
     uint32_t c_yes = 0, c_dec = 0, c_bud = 0;
+    // The common event's test folded into two numbers: hbe, the bit pattern
+    // above which a clock must go through the full sequence (the monitor's
+    // horizon, the snapshot time while it is open, t_max for the pessimistic
+    // rule; -1 while the monitor sees every draw), and the event count from
+    // which the budget stops a trajectory.
+    long long hbe = -1;
+    const uint32_t elim = budget == 0u ? 0u : (budget - 1u >= 0xFFFFFFFFull ? 0xFFFFFFFFu : (uint32_t)(budget - 1u));
+    const long long snap_bits = __double_as_longlong(t_snap), tmax_bits = __double_as_longlong(t_max);
+    auto horizon = [&]() {
+        long long h = mh.hb;
+        if (snap_mode && !snapped) h = snap_bits < h ? snap_bits : h;
+        if (unbounded) h = tmax_bits < h ? tmax_bits : h;
+        hbe = (always_step || mh.pend) ? -1ll : h;
+    };
     unsigned long long c_ev = 0;
 
     // verdict codes: 1 false, 2 true, 3 event budget exhausted, 4 stopped at
@@ -282,6 +296,7 @@ __device__ __forceinline__ void jit_run_instance(const SsaParams &p, const MonPr
                         active = true;
                         const int v = mon_state(ml, P, 0.0, tc);
                         mh.load(ml);
+                        horizon();
                         if (v) finish(v);
                     }
                 }
@@ -366,9 +381,7 @@ __device__ __forceinline__ void jit_run_instance(const SsaParams &p, const MonPr
         jit_apply(j, x, 1);
         {
             const uint32_t abn = jit_atoms(x);
-            const bool rare = dead | (mh.pend != 0u) | (__double_as_longlong(tn) > mh.hb) | always_step |
-                              (abn != mh.ab) | ((uint64_t)e + 1u >= budget) |
-                              ((snap_mode != 0) & !snapped & dgt(tn, t_snap)) | (unbounded & dgt(tn, t_max));
+            const bool rare = dead | (__double_as_longlong(tn) > hbe) | (abn != mh.ab) | (e >= elim);
             if (!rare) {
                 ++e;
                 t = tn;
@@ -385,6 +398,7 @@ __device__ __forceinline__ void jit_run_instance(const SsaParams &p, const MonPr
         nd = nd_next;
         if (snap_mode && !snapped && dgt(tn, t_snap)) {
             snapped = true;
+            horizon();
             const uint64_t idx = (uint64_t)m * p.out_stride + ((uint64_t)traj - p.out_base);
             p.o_snap[idx] = 0;
             if (p.o_esnap) p.o_esnap[idx] = e;
@@ -396,6 +410,7 @@ __device__ __forceinline__ void jit_run_instance(const SsaParams &p, const MonPr
         if (mh.pend || __double_as_longlong(tn) > mh.hb) {
             v = mon_draw(ml, P, tn, tc);
             mh.load(ml);
+            horizon();
         }
         if (!v && unbounded && dgt(tn, t_max)) v = 1;  // pessimistic rule (Sec. 3.2)
         if (v) { finish(v); continue; }
@@ -413,6 +428,7 @@ __device__ __forceinline__ void jit_run_instance(const SsaParams &p, const MonPr
             ml.ab = ab;
             v = mon_state(ml, P, t, tc);
             mh.load(ml);
+            horizon();
         }
         if (v) finish(v);
         else if ((uint64_t)e >= budget) finish(3);
