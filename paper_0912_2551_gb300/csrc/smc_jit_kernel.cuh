@@ -373,7 +373,13 @@ __device__ __forceinline__ void jit_run_instance(const SsaParams &p, const MonPr
                                    : pre[k] > r;
             if (hit) j = k;
         }
-        if (j < 0) j = dead ? 0 : 31 - __clz(pos);  // r reached the full sum: last positive a_k
+        if (j < 0) {  // r reached the full sum (rounding): the last positive a_k, recomputed here
+            T pre2[JR];
+            uint32_t pos2 = 0;
+            if constexpr (PLAIN) jit_props_plain(x, c, pre2, pos2);
+            else jit_props_mixed(x, c, pre2, pos2);
+            j = dead ? 0 : 31 - __clz(pos2);
+        }
         const JitDraw<PLAIN> nd_next = jit_draw<PLAIN>(e + 1u, traj, (uint32_t)m, p, ltab);
 #ifndef JIT_MEDIUM
         // step 4: x += v_j, then the common case: nothing for the monitor,
