@@ -77,8 +77,8 @@ def peaks():
 
 
 def algorithmic_ops_per_event(model, n_atoms: int, plain: bool) -> float:
-    """Thread-level operations the method needs per SSA event (see the design doc,
-    'Roofline'): Philox4x32-10 (10 rounds x 4), two uniform maps (2 x 2), ln
+    """Thread-level operations the method needs per SSA event (the issue
+    roofline's work count): Philox4x32-10 (10 rounds x 4), two uniform maps (2 x 2), ln
     (1), clock (divide, add: 2), selection (add + compare per scanned
     reaction, (R+1)/2 expected), x += v_j (nnz), propensities (plain: R
     multiplies, R conversions and R adds for a_0; mixed: 3 per dependent
