@@ -108,6 +108,16 @@ def test_lotka_volterra_full_size_sampled(ctx, orc):
     p_hat, lo, hi = wilson.wilson_interval(yes, dec, 0.99)
     assert abs(g['wilson'][0, 1] - lo) <= 1e-12 * lo and abs(g['wilson'][0, 2] - hi) <= 1e-12 * hi
     assert 2.0e-4 < p_hat < 7.0e-4 and abs(ev.mean() - 2358.7) < 5.0
+    # the chosen (mixed) path on the same launch: same random numbers, so the
+    # verdicts mostly agree, and the estimates lie within the 99.9% intervals
+    gm = _gpu(ctx, m, p, n, seed=0, precision='mixed', outputs=('verdict',))
+    vm = gm['verdict'][0]
+    assert (vm == v).mean() >= 0.99
+    ym = int(gm['counts'][0, 0])
+    assert ym == int(vm.sum()) and int(gm['counts'][0, 1]) == n
+    _, lo_p, hi_p = wilson.wilson_interval(yes, n, 0.999)
+    _, lo_m, hi_m = wilson.wilson_interval(ym, n, 0.999)
+    assert abs(ym - yes) / n <= (hi_p - lo_p) / 2 + (hi_m - lo_m) / 2
 
 
 @pytest.mark.parametrize('name', ['dimerisation', 'hetero', 'decay'])
