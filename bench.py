@@ -211,7 +211,8 @@ def main():
     ap.add_argument('--traj', type=int, default=None,
                     help='trajectories per step (per instance for --config workloads; profiling runs)')
     ap.add_argument('--config', default='lotka_volterra',
-                    choices=['lotka_volterra', 'immigration_death', 'random_networks', 'surrogate', 'cascade'])
+                    choices=['lotka_volterra', 'immigration_death', 'random_networks', 'surrogate', 'cascade',
+                             'surrogate_inference'])
     args = ap.parse_args()
     if args.traj is not None and args.config == 'lotka_volterra':
         N_TRAJ = args.traj

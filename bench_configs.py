@@ -15,6 +15,11 @@
   linear birth-death survival problem, where the checkpoint pays.
 * cascade: three-tier phosphorylation cascade, 256 rate-perturbed instances,
   literal and variant properties, mixed path.
+* surrogate_inference: the control variate's network (6 -> 128 x 3 -> 1,
+  BF16, FP32 accumulation) on 6,000,000 rows of Lotka-Volterra-family
+  features (x / x_scale, t_c / t_scale, centred log rates: 6 per row), one
+  tcgen05 launch per step; rows/s and TFLOP/s against the measured BF16
+  peak.
 """
 from __future__ import annotations
 
@@ -350,6 +355,75 @@ def cascade(args):
                             'kind': 'oracle', 'sample': f'64 trajectories of instance 0 (literal), {cpu:.1f} s'}})
 
 
+# DRAM bytes (read + write) of one launch of the inference kernel on
+# 6,000,000 rows (ncu: the FP32 features read once, the outputs written
+# once; the weights come from L2)
+TRAFFIC_INFER = 144110336 + 14355712
+
+
+def surrogate_inference(args):
+    import torch
+    import paper_0912_2551_gb300 as smc
+    from oracle import mlp as om
+    n = args.traj or 6_000_000
+    n_in = 6
+    dev = torch.device('cuda', 0)
+    g = torch.Generator().manual_seed(0)
+    # features as smc_snapshot_features scales them: counts / x_scale in
+    # [0, 3), t_c / t_scale, log-rate offsets within +-ln 1.3
+    x = torch.empty((n, n_in), dtype=torch.float32)
+    x[:, :2] = torch.rand((n, 2), generator=g) * 3.0
+    x[:, 2] = 0.5
+    x[:, 3:] = (torch.rand((n, 3), generator=g) * 2.0 - 1.0) * math.log(1.3)
+    xd = x.to(dev)
+    net = smc.Mlp(n_in, seed=1)
+    out = torch.empty((n,), dtype=torch.float32, device=dev)
+    for _ in range(args.warmup):
+        net.predict(xd, out=out)
+    torch.cuda.synchronize()
+    flush = torch.empty(256 * 2**20 // 4, dtype=torch.int32, device=dev)  # > L2 between steps
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clocks = bench.Clocks(0)
+    clocks.start()
+    stream = torch.cuda.current_stream(dev)
+    for s in range(args.steps):
+        flush.fill_(s)
+        ev[s][0].record(stream)
+        net.predict(xd, out=out)
+        ev[s][1].record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = sum(a.elapsed_time(b) for a, b in ev) / args.steps
+    flop_row = 2.0 * (16 * 128 + 2 * 128 * 128 + 128)  # the padded network's multiply-adds
+    tflops = n * flop_row / (ms * 1e-3) / 1e12
+    pk, src = bench.peaks()
+    peak = float(pk.get('bf16_tflops', 1899.0))
+    # sampled rows against the FP64 oracle network (BF16 weights and inputs)
+    theta = net.get_params().astype(np.float64)
+    for name in ('W1', 'W2', 'W3'):
+        o, sz = om.OFF[name]
+        theta[o:o + sz] = om.bf16_round(theta[o:o + sz])
+    idx = np.random.default_rng(0).choice(n, 4096, replace=False)
+    z, _ = om.forward(theta, om.bf16_round(x[idx].numpy()))
+    err = float(np.max(np.abs(out.cpu().numpy()[idx] - 1.0 / (1.0 + np.exp(-z)))))
+    extra = {'tflops': tflops, 'rows': n,
+             'roofline': {'bound': 'tensor', 'kernel': 'mlp_infer_kernel (tcgen05, TMEM accumulators)',
+                          'achieved': tflops, 'peak': peak, 'unit': 'TFLOP/s', 'frac': tflops / peak,
+                          'traffic': TRAFFIC_INFER if n == 6_000_000 else None,
+                          'flop_per_row': flop_row,
+                          'peak_source': f'bf16_tflops ({src}: cuBLAS bf16 GEMM, burst)'},
+             'oracle_max_abs_err': err, 'gpu_launches': args.steps, 'clocks': clk}
+    if not args.no_cpu_baseline:
+        t0 = time.perf_counter()
+        m = 500_000
+        om.forward(theta, om.bf16_round(x[:m].numpy()))
+        dt = time.perf_counter() - t0
+        extra['cpu_baseline'] = {'value': m / dt, 'unit': 'rows/s', 'cores': os.cpu_count(), 'kind': 'oracle',
+                                 'sample': f'first {m} rows, FP64 NumPy (BLAS on all host cores), {dt:.1f} s'}
+    _line(n / (ms * 1e-3), 'rows/s', args.steps, args.warmup, ms, 'bf16 (fp32 accumulate)',
+          f'surrogate network 6 -> 128 x 3 -> 1 on {n:,} rows of Lotka-Volterra-family features', extra)
+
+
 def run(args):
     {'immigration_death': immigration_death, 'random_networks': random_networks, 'surrogate': surrogate,
-     'cascade': cascade}[args.config](args)
+     'cascade': cascade, 'surrogate_inference': surrogate_inference}[args.config](args)

@@ -397,11 +397,16 @@ int smc_mlp_gradient(smc_mlp *mlp, const float *x, const float *y, int n, float 
 int smc_mlp_train(smc_mlp *mlp, const float *x, const float *y, uint64_t n, int epochs, int batch,
                   float lr, uint64_t seed, float *loss_host, void *stream);
 /* g[i] = network output for row i of x (device [n][n_in] -> device [n]):
- * one persistent launch, features rounded to BF16 as in training. */
+ * one persistent launch over 128-row tiles on the tcgen05 tensor cores
+ * (one CTA per SM holding all of its tensor memory for the layers'
+ * accumulators), features rounded to BF16 as in training.  Asynchronous on `stream`.  Should a
+ * launch give up waiting for its tensor-core operations (a bounded wait,
+ * about a second), it leaves NaN in the rows of the tile it was on and
+ * every later predict call on this network returns SMC_E_CUDA. */
 int smc_mlp_predict(smc_mlp *mlp, const float *x, uint64_t n, float *g, void *stream);
 /* The same, computing only rows with skip[i] == 0 (device uint8 [n], may be
- * NULL): other entries of g are left as they were (16-row tiles whose rows
- * all skip are not computed).  Used for trajectories decided before the
+ * NULL): other entries of g are left as they were (tiles whose rows all
+ * skip are not computed).  Used for trajectories decided before the
  * checkpoint, whose control variate is their verdict. */
 int smc_mlp_predict_masked(smc_mlp *mlp, const float *x, uint64_t n, const uint8_t *skip, float *g,
                            void *stream);

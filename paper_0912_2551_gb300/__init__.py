@@ -394,13 +394,21 @@ class Mlp:
                                     loss.ctypes.data_as(ctypes.c_void_p), _stream(s)), 'smc_mlp_train')
         return loss
 
-    def predict(self, x):
+    def predict(self, x, skip=None, out=None):
+        """smc_mlp_predict (or smc_mlp_predict_masked when skip, a uint8
+        device tensor [n], is given: rows with skip != 0 keep out's values)."""
         import torch
-        g = torch.empty((x.shape[0],), dtype=torch.float32, device=x.device)
+        g = out if out is not None else torch.empty((x.shape[0],), dtype=torch.float32, device=x.device)
         s = torch.cuda.current_stream(x.device)
-        self._check(N.smc_mlp_predict(self.h, ctypes.c_void_p(x.data_ptr()), int(x.shape[0]),
-                                      ctypes.c_void_p(g.data_ptr()), _stream(s)),
-                    'smc_mlp_predict')
+        if skip is None:
+            self._check(N.smc_mlp_predict(self.h, ctypes.c_void_p(x.data_ptr()), int(x.shape[0]),
+                                          ctypes.c_void_p(g.data_ptr()), _stream(s)),
+                        'smc_mlp_predict')
+        else:
+            self._check(N.smc_mlp_predict_masked(self.h, ctypes.c_void_p(x.data_ptr()), int(x.shape[0]),
+                                                 ctypes.c_void_p(skip.data_ptr()), ctypes.c_void_p(g.data_ptr()),
+                                                 _stream(s)),
+                        'smc_mlp_predict_masked')
         return g
 
 

@@ -1637,6 +1637,10 @@ int smc_estimate_cv(smc_ctx *ctx, smc_mlp *mlp, double confidence, double half_w
         CK(cudaMemcpyAsync(hc, b.counts, sizeof(hc), cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
         // S1: full runs (Y, G); S2: prefix runs (G only)
+        for (double v : hs)
+            if (!std::isfinite(v))
+                return fail(ctx, SMC_E_CUDA, std::string("surrogate prediction gave non-finite values: ") +
+                                                 smc_mlp_last_error(mlp));
         const double c1n = hs[0], sY = hs[1], sG1 = hs[2], sYY = hs[3], sGG1 = hs[4], sYG = hs[5];
         const double sE1 = hs[6];  // events the full runs spent up to the snapshot (or their verdict)
         const double c2n = hs[7], sG2 = hs[9], sGG2 = hs[11];

@@ -1,6 +1,8 @@
 // smc_mlp.cu -- the surrogate network used as a control variate: forward,
-// backward and Adam update as hand-written BF16 tensor-core kernels
-// (mma.sync m16n8k16, FP32 accumulation), FP32 master weights.
+// backward and Adam update as hand-written BF16 tensor-core kernels with
+// FP32 accumulation and FP32 master weights.  Inference (on the estimator's
+// path) runs on tcgen05 with the accumulator in tensor memory; training
+// (tiny minibatches) runs on mma.sync m16n8k16.
 //
 // Network: g(x) = sigmoid(w4 . h3 + b4), h_l = relu(W_l h_{l-1} + b_l),
 // x in R^16 (zero-padded features), hidden width 128.  Training minimises the
@@ -185,36 +187,386 @@ __global__ void __launch_bounds__(128) mlp_fwd_kernel(const bf16 *__restrict__ x
     }
 }
 
-// Inference over n rows of FP32 features x [n][n_in] (n_in <= 16): one
-// persistent launch, the weights staged once per CTA, 16-row tiles per warp
-// (grid-stride); features rounded to BF16 as the training input is;
-// g[r] = 1 / (1 + e^-z).  Rows with skip[r] != 0 (may be null) need no
-// output; a tile whose rows all skip is not computed.
-__global__ void __launch_bounds__(128) mlp_infer_kernel(const float *__restrict__ x, uint64_t n, int n_in,
-                                                        const uint8_t *__restrict__ skip, const bf16 *w1b,
-                                                        const bf16 *w2b, const bf16 *w3b, const float *master,
-                                                        float *g_out)
+// ---------------------------------------------------------------------------
+// Inference on the fifth-generation tensor cores (tcgen05).  A CTA runs
+// kTcGroups independent pipelines of 128 threads; each pipeline works on one
+// 128-row tile at a time with its layer accumulator (128 rows x 128 FP32
+// columns) in its own quarter of the SM's tensor memory.  The weights are
+// staged once per CTA and shared; while one pipeline runs its epilogue on
+// the CUDA cores, the others' MMAs keep the tensor cores busy.
+//
+// Operand layout (K-major, no swizzle): an R x K BF16 operand is stored as
+// core matrices of 8 rows x 16 bytes (8 values along K), 128 contiguous
+// bytes each; core matrix (r / 8, k / 8) starts at byte
+//   ((r / 8) * (K / 8) + k / 8) * 128,
+// so neighbours along K are 128 bytes apart (the descriptor's leading
+// byte offset) and neighbouring 8-row groups K * 16 bytes apart (its stride
+// byte offset).  One MMA consumes K = 16, i.e. two core matrices along K:
+// step s starts 256 * s bytes into the operand.
+//
+// Everything but the ReLU runs on the tensor cores.  Each layer's
+// accumulator starts as its bias: an MMA of a constant tile of ones (A,
+// columns 0 and 1) with a bias tile (B, columns 0 and 1 = the FP32 bias
+// split into BF16 high and low parts, b = hi + lo to about 2^-17).  The
+// output unit is an N = 16 MMA whose B rows 0 and 1 are w4's high and low
+// parts, so z = D[:, 0] + D[:, 1].
+//
+// Per tile: features -> X (K = 16, in the first 4 KB of the activation
+// buffer); bias + MMA (W1); epilogue: tensor memory -> registers (thread i
+// of the pipeline holds row i, the accumulator's lane i), ReLU and BF16 in
+// one conversion, back to shared memory as the next layer's A operand;
+// bias + MMAs (W2, K = 128), epilogue; bias + MMAs (W3), epilogue; bias +
+// MMAs (w4, N = 16); g = 1 / (1 + e^-z).  The pipeline's first thread
+// issues the MMAs and commits them to the pipeline's mbarrier, which its
+// 128 threads wait on.
+// ---------------------------------------------------------------------------
+
+constexpr int kTcRows = 128;                    // rows per tile = TMEM lanes
+constexpr int kTcGroups = 4;                    // pipelines per CTA
+constexpr int kTcThreads = 128 * kTcGroups;
+constexpr int kTcSmW1 = 0;                      // W1 [128][16]  BF16, 4 KB
+constexpr int kTcSmW2 = kTcSmW1 + H * IN * 2;   // W2 [128][128] BF16, 32 KB
+constexpr int kTcSmW3 = kTcSmW2 + H * H * 2;    // W3 [128][128] BF16, 32 KB
+constexpr int kTcSmW4 = kTcSmW3 + H * H * 2;    // [16][128]: w4 high, w4 low, zeros; 4 KB
+constexpr int kTcSmOnes = kTcSmW4 + 16 * H * 2; // [128][16]: ones in columns 0, 1; 4 KB
+constexpr int kTcSmB1 = kTcSmOnes + kTcRows * 16 * 2;  // bias tiles [128][16], 4 KB each (layers 1-3)
+constexpr int kTcSmB4 = kTcSmB1 + 3 * H * 16 * 2;      // [16][16]: b4 high, low in row 0
+constexpr int kTcSmBar = kTcSmB4 + 16 * 16 * 2;        // one mbarrier per pipeline, then the TMEM address
+constexpr int kTcSmGroup = (kTcSmBar + 8 * kTcGroups + 4 + 1023) / 1024 * 1024;
+constexpr int kTcGroupBytes = kTcRows * H * 2;  // activations [128][128] (features [128][16] at the start)
+constexpr int kTcSmem = kTcSmGroup + kTcGroups * kTcGroupBytes;
+constexpr uint32_t kTcCols = 128 * kTcGroups;   // TMEM columns per CTA: all 512 of the SM
+constexpr uint32_t kTcWaitLimit = 1u << 26;     // mbarrier polls before a wait gives up
+constexpr uint64_t kTcWaitNs = 1000000000ull;   // or this much wall time (1 s)
+static_assert(kTcSmBar % 8 == 0, "mbarrier alignment");
+static_assert(kTcSmem <= 227 * 1024, "shared memory per CTA");
+// the CTA takes the whole tensor memory, so two must never share an SM
+static_assert(2 * (kTcSmem + 1024) > 228 * 1024, "one CTA per SM");
+
+// instruction descriptor of tcgen05.mma kind::f16 for M = 128: D FP32 (bits
+// 4-5 = 1), A and B BF16 (bits 7-9, 10-12 = 1), both K-major (bits 15, 16 =
+// 0), N >> 3 in bits 17-22, M >> 4 in bits 24-28
+__host__ __device__ constexpr uint32_t tc_idesc(int N)
 {
-    extern __shared__ __align__(16) unsigned char sm[];
-    stage_forward_weights(sm, w1b, w2b, w3b, master);
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-    const uint64_t tiles = (n + 15) / 16;
-    for (uint64_t tile = (uint64_t)blockIdx.x * 4 + warp; tile < tiles; tile += (uint64_t)gridDim.x * 4) {
-        const uint64_t ra = tile * 16 + g, rb = ra + 8;
-        const bool need = (ra < n && !(skip && skip[ra])) || (rb < n && !(skip && skip[rb]));
-        if (!__any_sync(0xffffffffu, need)) continue;
-        auto feat = [&](uint64_t r, int k) { return (r < n && k < n_in) ? x[r * n_in + k] : 0.0f; };
-        uint32_t a[4];
-        a[0] = pack2(feat(ra, 2 * t), feat(ra, 2 * t + 1));
-        a[1] = pack2(feat(rb, 2 * t), feat(rb, 2 * t + 1));
-        a[2] = pack2(feat(ra, 2 * t + 8), feat(ra, 2 * t + 9));
-        a[3] = pack2(feat(rb, 2 * t + 8), feat(rb, 2 * t + 9));
-        float za, zb;
-        forward_tile(a, sm, g, t, 0, 0, 0, nullptr, nullptr, nullptr, za, zb);
-        if (t == 0) {
-            if (ra < n) g_out[ra] = 1.0f / (1.0f + expf(-za));
-            if (rb < n) g_out[rb] = 1.0f / (1.0f + expf(-zb));
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(kTcRows >> 4) << 24);
+}
+
+__host__ __device__ constexpr int tc_core_offset(int r, int kg, int K)
+{
+    return ((r >> 3) * (K >> 3) + kg) * 128 + (r & 7) * 16;
+}
+
+// shared-memory matrix descriptor: start address, leading byte offset (next
+// core matrix along K), stride byte offset (next 8-row group), all >> 4;
+// bit 46 = descriptor version 1; swizzle mode (bits 61-63) 0 = none
+__device__ __forceinline__ uint64_t tc_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo)
+{
+    return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)(lbo >> 4) << 16) | ((uint64_t)(sbo >> 4) << 32) |
+           (1ull << 46);
+}
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void tc_mma(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                       uint32_t accumulate)
+{
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
+}
+
+__device__ __forceinline__ void tc_commit(uint32_t bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+                 : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// barrier over one pipeline's 128 threads (named barrier id, 1..kTcGroups)
+__device__ __forceinline__ void group_sync(int id) { asm volatile("bar.sync %0, 128;" ::"r"(id) : "memory"); }
+
+// the same barrier, returning whether v was true in any of the 128 threads
+__device__ __forceinline__ bool group_or(int id, bool v)
+{
+    uint32_t r;
+    asm volatile(
+        "{\n .reg .pred pi, po;\n setp.ne.u32 pi, %1, 0;\n bar.red.or.pred po, %2, 128, pi;\n"
+        " selp.u32 %0, 1, 0, po;\n}\n"
+        : "=r"(r)
+        : "r"((uint32_t)v), "r"(id)
+        : "memory");
+    return r != 0;
+}
+
+// waits for the mbarrier's phase `parity` to complete; false once about
+// kTcWaitNs of wall time (global timer) or kTcWaitLimit polls have passed
+__device__ __forceinline__ bool tc_wait(uint32_t bar, uint32_t parity)
+{
+    uint64_t t0 = 0;
+    for (uint32_t i = 0; i < kTcWaitLimit; ++i) {
+        uint32_t done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+            " selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        if (done) return true;
+        if ((i & 63) == 0) {
+            uint64_t t;
+            asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+            if (i == 0) t0 = t;
+            else if (t - t0 > kTcWaitNs) return false;
         }
+    }
+    return false;
+}
+
+// starts loading 32 consecutive FP32 columns of this thread's accumulator
+// lane; the registers hold them only after tc_wait_ld(r)
+__device__ __forceinline__ void tc_load32_async(uint32_t taddr, uint32_t (&r)[32])
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr)
+        : "memory");
+}
+
+// waits for this thread's outstanding tensor-memory loads; naming r as
+// read-write keeps the compiler from using r before the wait
+__device__ __forceinline__ void tc_wait_ld(uint32_t (&r)[32])
+{
+    asm volatile("tcgen05.wait::ld.sync.aligned;\n"
+                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
+                   "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]),
+                   "+r"(r[15]), "+r"(r[16]), "+r"(r[17]), "+r"(r[18]), "+r"(r[19]), "+r"(r[20]), "+r"(r[21]),
+                   "+r"(r[22]), "+r"(r[23]), "+r"(r[24]), "+r"(r[25]), "+r"(r[26]), "+r"(r[27]), "+r"(r[28]),
+                   "+r"(r[29]), "+r"(r[30]), "+r"(r[31])
+                 :
+                 : "memory");
+}
+
+// two consecutive FP32 columns of this thread's accumulator lane
+__device__ __forceinline__ void tc_load2(uint32_t taddr, uint32_t (&r)[2])
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x2.b32 {%0,%1}, [%2];\n"
+        "tcgen05.wait::ld.sync.aligned;\n"
+        : "=r"(r[0]), "=r"(r[1])
+        : "r"(taddr)
+        : "memory");
+}
+
+// relu, rounded to BF16 and packed: lo in the low half (first in memory)
+__device__ __forceinline__ uint32_t relu_pack2(uint32_t lo, uint32_t hi)
+{
+    uint32_t d;
+    asm("cvt.rn.relu.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(__uint_as_float(hi)), "f"(__uint_as_float(lo)));
+    return d;
+}
+
+// stages an N x K row-major BF16 matrix (global) into the core-matrix layout
+__device__ __forceinline__ void tc_stage_operand(unsigned char *dst, const bf16 *src, int N, int K)
+{
+    const int chunks = N * (K / 8);
+    for (int i = threadIdx.x; i < chunks; i += blockDim.x) {
+        const int r = i / (K / 8), kg = i % (K / 8);
+        *reinterpret_cast<uint4 *>(dst + tc_core_offset(r, kg, K)) =
+            *reinterpret_cast<const uint4 *>(src + (size_t)r * K + kg * 8);
+    }
+}
+
+// element (r, k) of an operand with K columns in the core-matrix layout
+__device__ __forceinline__ bf16 *tc_elem(unsigned char *base, int r, int k, int K)
+{
+    return reinterpret_cast<bf16 *>(base + tc_core_offset(r, k >> 3, K) + (k & 7) * 2);
+}
+
+// high and low BF16 parts of an FP32 value (v = hi + lo to about 2^-17 relative)
+__device__ __forceinline__ bf16 bf16_hi(float v) { return __float2bfloat16_rn(v); }
+__device__ __forceinline__ bf16 bf16_lo(float v) { return __float2bfloat16_rn(v - __bfloat162float(__float2bfloat16_rn(v))); }
+
+// Inference over n rows of FP32 features x [n][n_in] (n_in <= 16): one
+// persistent launch (one CTA of kTcThreads per SM) over 128-row tiles,
+// weights staged once per CTA, features rounded to BF16 as the training
+// input is; g[r] = 1 / (1 + e^-z).  Rows with skip[r] != 0 (may be null)
+// need no output; a tile whose rows all skip is not computed.  A wait that
+// gives up sets *err and leaves NaN in the outputs of the tile it was
+// working on, and that pipeline stops.
+__global__ void __launch_bounds__(kTcThreads) mlp_infer_kernel(const float *__restrict__ x, uint64_t n, int n_in,
+                                                               const uint8_t *__restrict__ skip, const bf16 *w1b,
+                                                               const bf16 *w2b, const bf16 *w3b,
+                                                               const float *master, float *g_out, int *err)
+{
+    extern __shared__ __align__(1024) unsigned char sm[];
+    uint64_t *bars = reinterpret_cast<uint64_t *>(sm + kTcSmBar);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(sm + kTcSmBar + 8 * kTcGroups);
+    const int tid = threadIdx.x, warp = tid >> 5, grp = tid >> 7, gt = tid & 127;
+    const int bid = 1 + grp;  // the pipeline's named barrier
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(kTcCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) {
+        for (int i = 0; i < kTcGroups; ++i)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bars + i)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    tc_stage_operand(sm + kTcSmW1, w1b, H, IN);
+    tc_stage_operand(sm + kTcSmW2, w2b, H, H);
+    tc_stage_operand(sm + kTcSmW3, w3b, H, H);
+    const bf16 zero = __float2bfloat16_rn(0.0f), one = __float2bfloat16_rn(1.0f);
+    for (int i = tid; i < H * 16; i += blockDim.x) {  // ones, bias tiles (rows x 16 columns)
+        const int r = i >> 4, k = i & 15;
+        *tc_elem(sm + kTcSmOnes, r, k, 16) = k < 2 ? one : zero;
+#pragma unroll
+        for (int l = 0; l < 3; ++l) {
+            const float b = master[MLP_OFF_B1 + l * (H * H + H) + r];
+            *tc_elem(sm + kTcSmB1 + l * H * 16 * 2, r, k, 16) = k == 0 ? bf16_hi(b) : k == 1 ? bf16_lo(b) : zero;
+        }
+    }
+    for (int i = tid; i < 16 * H; i += blockDim.x) {  // output unit: rows 0, 1 = w4 high, low
+        const int r = i / H, k = i % H;
+        const float w = master[MLP_OFF_W4 + k];
+        *tc_elem(sm + kTcSmW4, r, k, H) = r == 0 ? bf16_hi(w) : r == 1 ? bf16_lo(w) : zero;
+    }
+    for (int i = tid; i < 16 * 16; i += blockDim.x) {
+        const int r = i >> 4, k = i & 15;
+        const float b = master[MLP_OFF_B4];
+        *tc_elem(sm + kTcSmB4, r, k, 16) = (r == 0 && k == 0) ? bf16_hi(b) : (r == 0 && k == 1) ? bf16_lo(b) : zero;
+    }
+    fence_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+    const uint32_t tacc = tmem + 128u * grp;                              // the pipeline's columns
+    const uint32_t t_row = tacc + ((uint32_t)(32 * (warp & 3)) << 16);  // this warp's 32 lanes
+
+    unsigned char *act = sm + kTcSmGroup + grp * kTcGroupBytes;
+    const uint32_t bar = smem_u32(bars + grp);
+    const uint32_t aAct = smem_u32(act), aOnes = smem_u32(sm + kTcSmOnes);
+    uint32_t phase = 0;
+    bool failed = false;
+    const uint64_t tiles = (n + kTcRows - 1) / kTcRows;
+
+    // a tile's features and mask are loaded one tile ahead, so their
+    // latency overlaps the previous tile's layers
+    const uint64_t stride = (uint64_t)gridDim.x * kTcGroups;
+    auto load_tile = [&](uint64_t t, float (&f)[IN], bool &nd) {
+        const uint64_t r = t * kTcRows + gt;
+        nd = r < n && !(skip && skip[r]);
+#pragma unroll
+        for (int k = 0; k < IN; ++k) f[k] = (r < n && k < n_in) ? x[r * n_in + k] : 0.0f;
+    };
+    float f_next[IN];
+    bool need_next = false;
+    uint64_t tile = (uint64_t)blockIdx.x * kTcGroups + grp;
+    if (tile < tiles) load_tile(tile, f_next, need_next);
+    for (; tile < tiles; tile += stride) {
+        const uint64_t row = tile * kTcRows + gt;
+        float f[IN];
+#pragma unroll
+        for (int k = 0; k < IN; ++k) f[k] = f_next[k];
+        const bool need = need_next;
+        if (tile + stride < tiles) load_tile(tile + stride, f_next, need_next);
+        if (!group_or(bid, need)) continue;
+        {   // features -> X (zero-padded to 16, BF16)
+#pragma unroll
+            for (int kg = 0; kg < IN / 8; ++kg) {
+                uint4 v;
+                v.x = pack2(f[8 * kg], f[8 * kg + 1]);
+                v.y = pack2(f[8 * kg + 2], f[8 * kg + 3]);
+                v.z = pack2(f[8 * kg + 4], f[8 * kg + 5]);
+                v.w = pack2(f[8 * kg + 6], f[8 * kg + 7]);
+                *reinterpret_cast<uint4 *>(act + tc_core_offset(gt, kg, IN)) = v;
+            }
+        }
+        uint32_t zc[2] = {0u, 0u};
+        for (int layer = 0; layer < 4; ++layer) {
+            // operands written by every thread -> visible to the tensor core;
+            // the previous epilogue's tensor-memory reads are complete
+            fence_async_smem();
+            tc_fence_before();
+            group_sync(bid);
+            if (gt == 0) {
+                tc_fence_after();
+                if (layer == 0) {
+                    tc_mma(tacc, tc_desc(aOnes, 128, 256), tc_desc(smem_u32(sm + kTcSmB1), 128, 256), tc_idesc(H), 0);
+                    tc_mma(tacc, tc_desc(aAct, 128, 256), tc_desc(smem_u32(sm + kTcSmW1), 128, 256), tc_idesc(H), 1);
+                } else {
+                    const int N = layer == 3 ? 16 : H;
+                    const uint32_t aB = smem_u32(sm + (layer == 3 ? kTcSmB4 : kTcSmB1 + layer * H * 16 * 2));
+                    const uint32_t aW = smem_u32(sm + (layer == 1 ? kTcSmW2 : layer == 2 ? kTcSmW3 : kTcSmW4));
+                    tc_mma(tacc, tc_desc(aOnes, 128, 256), tc_desc(aB, 128, 256), tc_idesc(N), 0);
+#pragma unroll
+                    for (int s = 0; s < H / 16; ++s)
+                        tc_mma(tacc, tc_desc(aAct + 256 * s, 128, 16 * 128), tc_desc(aW + 256 * s, 128, 16 * 128),
+                               tc_idesc(N), 1);
+                }
+                tc_commit(bar);
+            }
+            const bool ok = tc_wait(bar, phase);
+            phase ^= 1;
+            if (group_or(bid, !ok)) {
+                failed = true;
+                break;
+            }
+            tc_fence_after();
+            if (layer == 3) {
+                tc_load2(t_row, zc);
+                break;
+            }
+            {   // 4 chunks of 32 columns; the next chunk loads while this one converts
+                uint32_t va[32], vb[32];
+                auto store_chunk = [&](int c, const uint32_t (&v)[32]) {
+#pragma unroll
+                    for (int q = 0; q < 4; ++q)
+                        *reinterpret_cast<uint4 *>(act + tc_core_offset(gt, 4 * c + q, H)) =
+                            make_uint4(relu_pack2(v[8 * q], v[8 * q + 1]), relu_pack2(v[8 * q + 2], v[8 * q + 3]),
+                                       relu_pack2(v[8 * q + 4], v[8 * q + 5]), relu_pack2(v[8 * q + 6], v[8 * q + 7]));
+                };
+                tc_load32_async(t_row, va);
+                tc_wait_ld(va);
+                tc_load32_async(t_row + 32, vb);
+                store_chunk(0, va);
+                tc_wait_ld(vb);
+                tc_load32_async(t_row + 64, va);
+                store_chunk(1, vb);
+                tc_wait_ld(va);
+                tc_load32_async(t_row + 96, vb);
+                store_chunk(2, va);
+                tc_wait_ld(vb);
+                store_chunk(3, vb);
+            }
+        }
+        if (failed) {
+            if (row < n) g_out[row] = __int_as_float(0x7fc00000);
+            if (gt == 0) atomicExch(err, 1);
+            break;
+        }
+        const float z = __uint_as_float(zc[0]) + __uint_as_float(zc[1]);
+        if (need) g_out[row] = 1.0f / (1.0f + expf(-z));
+    }
+    // release tensor memory once every MMA and load of this CTA has finished
+    if (failed && gt == 0) tc_wait(bar, phase ^ 1);
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTcCols) : "memory");
     }
 }
 
@@ -458,6 +810,7 @@ struct smc_mlp {
     bf16 *w1b = nullptr, *w2b = nullptr, *w3b = nullptr, *w2t = nullptr, *w3t = nullptr;
     bf16 *xb = nullptr, *h1 = nullptr, *h2 = nullptr, *h3 = nullptr, *dh1 = nullptr, *dh2 = nullptr, *dh3 = nullptr;
     float *yb = nullptr, *z = nullptr, *dz = nullptr, *loss = nullptr;
+    int *h_err = nullptr, *d_err = nullptr;  // inference wait gave up (mapped host memory)
     uint64_t adam_t = 0;
 };
 
@@ -544,9 +897,12 @@ int smc_mlp_create(smc_mlp **out, int device, int n_in, uint64_t seed)
     for (void **p : vec)
         if (cudaMalloc(p, (size_t)kMaxBatch * 4) != cudaSuccess) return fin(SMC_E_OOM);
     if (cudaMalloc((void **)&m->loss, 4096 * 4) != cudaSuccess) return fin(SMC_E_OOM);
+    if (cudaHostAlloc((void **)&m->h_err, sizeof(int), cudaHostAllocMapped) != cudaSuccess) return fin(SMC_E_OOM);
+    *m->h_err = 0;
+    if (cudaHostGetDevicePointer((void **)&m->d_err, m->h_err, 0) != cudaSuccess) return fin(SMC_E_CUDA);
     const void *kern[] = {(const void *)mlp_fwd_kernel, (const void *)mlp_bwd_kernel,
                           (const void *)mlp_wgrad_kernel, (const void *)mlp_infer_kernel};
-    const int smem[] = {kFwdSmem, kBwdSmem, kWgSmem, kFwdSmem};
+    const int smem[] = {kFwdSmem, kBwdSmem, kWgSmem, kTcSmem};
     for (int k = 0; k < 4; ++k)
         if (cudaFuncSetAttribute(kern[k], cudaFuncAttributeMaxDynamicSharedMemorySize, smem[k]) != cudaSuccess)
             return fin(SMC_E_CUDA);
@@ -579,6 +935,7 @@ void smc_mlp_destroy(smc_mlp *m)
                     m->xb, m->h1, m->h2, m->h3, m->dh1, m->dh2, m->dh3, m->yb, m->z, m->dz, m->loss};
     for (void *p : ptrs)
         if (p) cudaFree(p);
+    if (m->h_err) cudaFreeHost(m->h_err);
     if (m->stream) cudaStreamDestroy(m->stream);
     delete m;
 }
@@ -675,16 +1032,19 @@ int smc_mlp_train(smc_mlp *m, const float *x, const float *y, uint64_t n, int ep
 int smc_mlp_predict_masked(smc_mlp *m, const float *x, uint64_t n, const uint8_t *skip, float *g, void *stream)
 {
     if (!m || (n && (!x || !g))) return SMC_E_INVALID_ARG;
+    if (*m->h_err) return mfail(m, SMC_E_CUDA, "an earlier inference launch gave up waiting for the tensor cores");
     if (n == 0) return SMC_OK;
     MCK(cudaSetDevice(m->device));
     cudaStream_t s = stream ? (cudaStream_t)stream : m->stream;
-    int dev_sm = 0, per_sm = 0;
+    int dev_sm = 0;
     MCK(cudaDeviceGetAttribute(&dev_sm, cudaDevAttrMultiProcessorCount, m->device));
-    MCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, mlp_infer_kernel, 128, kFwdSmem));
-    const uint64_t tiles = (n + 15) / 16;
-    const uint64_t want = (tiles + 3) / 4;
-    const int grid = (int)std::max<uint64_t>(1, std::min<uint64_t>(want, (uint64_t)dev_sm * std::max(per_sm, 1)));
-    mlp_infer_kernel<<<grid, 128, kFwdSmem, s>>>(x, n, m->n_in, skip, m->w1b, m->w2b, m->w3b, m->master, g);
+    // one CTA per SM (its shared memory rules out a second, which its
+    // allocation of the whole tensor memory requires)
+    const uint64_t tiles = (n + kTcRows - 1) / kTcRows;
+    const uint64_t want = (tiles + kTcGroups - 1) / kTcGroups;
+    const int grid = (int)std::max<uint64_t>(1, std::min<uint64_t>(want, (uint64_t)dev_sm));
+    mlp_infer_kernel<<<grid, kTcThreads, kTcSmem, s>>>(x, n, m->n_in, skip, m->w1b, m->w2b, m->w3b, m->master, g,
+                                                       m->d_err);
     MCK(cudaGetLastError());
     return SMC_OK;
 }

@@ -63,6 +63,44 @@ def test_network_matches_oracle(env):
         assert rel < 0.06 and cos > 0.998, (name, rel, cos)
 
 
+def _forward_bf16_activations(theta, x):
+    """The oracle network's layers with every hidden activation rounded to
+    BF16, as the library's kernels store them between layers."""
+    from oracle import mlp as om
+    P = om.unpack(theta)
+    h = om.pad(om.bf16_round(x))
+    for W, b in (('W1', 'b1'), ('W2', 'b2'), ('W3', 'b3')):
+        h = om.bf16_round(np.maximum(h @ P[W].T + P[b], 0.0))
+    z = h @ P['w4'] + P['b4'][0]
+    return 1 / (1 + np.exp(-z))
+
+
+@pytest.mark.parametrize('n', [1, 127, 128, 129, 3000, 100_003])
+def test_inference_tiles_and_mask(env, n):
+    """Inference kernel (128-row tensor-core tiles, persistent over the
+    tiles): exact tile sizes, ragged tails, more tiles than CTAs, and a mask
+    that skips single rows and whole tiles, whose outputs must stay as they
+    were."""
+    torch, smc = env
+    rng = np.random.default_rng(n)
+    x = rng.normal(size=(n, 6)).astype(np.float32)
+    net = smc.Mlp(6, seed=11)
+    theta = _bf16_weights(net.get_params())
+    g_ref = _forward_bf16_activations(theta, x)
+    xt = torch.tensor(x, device='cuda')
+    g = net.predict(xt).cpu().numpy()
+    assert np.all(np.isfinite(g))
+    err = np.abs(g.astype(np.float64) - g_ref)
+    assert err.max() < 5e-3 and err.mean() < 5e-4, (err.max(), err.mean())
+    skip = (rng.random(n) < 0.3).astype(np.uint8)
+    skip[128:256] = 1  # a whole tile skipped
+    sentinel = np.float32(-7.0)
+    out = torch.full((n,), float(sentinel), dtype=torch.float32, device='cuda')
+    gm = net.predict(xt, skip=torch.tensor(skip, device='cuda'), out=out).cpu().numpy()
+    assert np.all(gm[skip == 1] == sentinel)
+    assert np.array_equal(gm[skip == 0], g[skip == 0])
+
+
 def test_training_learns_a_logistic_target(env):
     torch, smc = env
     rng = np.random.default_rng(1)
