@@ -29,6 +29,7 @@
 
 #include "smc.h"
 #include "smc_mlp.h"
+#include "smc_tc.h"
 
 typedef __nv_bfloat16 bf16;
 
@@ -195,14 +196,10 @@ __global__ void __launch_bounds__(128) mlp_fwd_kernel(const bf16 *__restrict__ x
 // staged once per CTA and shared; while one pipeline runs its epilogue on
 // the CUDA cores, the others' MMAs keep the tensor cores busy.
 //
-// Operand layout (K-major, no swizzle): an R x K BF16 operand is stored as
-// core matrices of 8 rows x 16 bytes (8 values along K), 128 contiguous
-// bytes each; core matrix (r / 8, k / 8) starts at byte
-//   ((r / 8) * (K / 8) + k / 8) * 128,
-// so neighbours along K are 128 bytes apart (the descriptor's leading
-// byte offset) and neighbouring 8-row groups K * 16 bytes apart (its stride
-// byte offset).  One MMA consumes K = 16, i.e. two core matrices along K:
-// step s starts 256 * s bytes into the operand.
+// Operands in shared memory use the K-major core-matrix layout without
+// swizzling of smc_tc.h (8-row x 16-byte core matrices of 128 contiguous
+// bytes); one MMA consumes K = 16, i.e. two core matrices along K: step s
+// starts 256 * s bytes into the operand.
 //
 // Everything but the ReLU runs on the tensor cores.  Each layer's
 // accumulator starts as its bias: an MMA of a constant tile of ones (A,
@@ -243,27 +240,7 @@ static_assert(kTcSmem <= 227 * 1024, "shared memory per CTA");
 // the CTA takes the whole tensor memory, so two must never share an SM
 static_assert(2 * (kTcSmem + 1024) > 228 * 1024, "one CTA per SM");
 
-// instruction descriptor of tcgen05.mma kind::f16 for M = 128: D FP32 (bits
-// 4-5 = 1), A and B BF16 (bits 7-9, 10-12 = 1), both K-major (bits 15, 16 =
-// 0), N >> 3 in bits 17-22, M >> 4 in bits 24-28
-__host__ __device__ constexpr uint32_t tc_idesc(int N)
-{
-    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(kTcRows >> 4) << 24);
-}
-
-__host__ __device__ constexpr int tc_core_offset(int r, int kg, int K)
-{
-    return ((r >> 3) * (K >> 3) + kg) * 128 + (r & 7) * 16;
-}
-
-// shared-memory matrix descriptor: start address, leading byte offset (next
-// core matrix along K), stride byte offset (next 8-row group), all >> 4;
-// bit 46 = descriptor version 1; swizzle mode (bits 61-63) 0 = none
-__device__ __forceinline__ uint64_t tc_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo)
-{
-    return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)(lbo >> 4) << 16) | ((uint64_t)(sbo >> 4) << 32) |
-           (1ull << 46);
-}
+__host__ __device__ constexpr uint32_t tc_idesc(int N) { return tc_idesc_bf16(kTcRows, N); }
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -388,7 +365,7 @@ __device__ __forceinline__ void tc_stage_operand(unsigned char *dst, const bf16 
 // element (r, k) of an operand with K columns in the core-matrix layout
 __device__ __forceinline__ bf16 *tc_elem(unsigned char *base, int r, int k, int K)
 {
-    return reinterpret_cast<bf16 *>(base + tc_core_offset(r, k >> 3, K) + (k & 7) * 2);
+    return reinterpret_cast<bf16 *>(base + tc_elem_offset(r, k, K));
 }
 
 // high and low BF16 parts of an FP32 value (v = hi + lo to about 2^-17 relative)
@@ -504,16 +481,18 @@ __global__ void __launch_bounds__(kTcThreads) mlp_infer_kernel(const float *__re
             if (gt == 0) {
                 tc_fence_after();
                 if (layer == 0) {
-                    tc_mma(tacc, tc_desc(aOnes, 128, 256), tc_desc(smem_u32(sm + kTcSmB1), 128, 256), tc_idesc(H), 0);
-                    tc_mma(tacc, tc_desc(aAct, 128, 256), tc_desc(smem_u32(sm + kTcSmW1), 128, 256), tc_idesc(H), 1);
+                    tc_mma(tacc, tc_desc(aOnes, kTcLbo, tc_sbo(16)),
+                           tc_desc(smem_u32(sm + kTcSmB1), kTcLbo, tc_sbo(16)), tc_idesc(H), 0);
+                    tc_mma(tacc, tc_desc(aAct, kTcLbo, tc_sbo(IN)), tc_desc(smem_u32(sm + kTcSmW1), kTcLbo, tc_sbo(IN)),
+                           tc_idesc(H), 1);
                 } else {
                     const int N = layer == 3 ? 16 : H;
                     const uint32_t aB = smem_u32(sm + (layer == 3 ? kTcSmB4 : kTcSmB1 + layer * H * 16 * 2));
                     const uint32_t aW = smem_u32(sm + (layer == 1 ? kTcSmW2 : layer == 2 ? kTcSmW3 : kTcSmW4));
-                    tc_mma(tacc, tc_desc(aOnes, 128, 256), tc_desc(aB, 128, 256), tc_idesc(N), 0);
+                    tc_mma(tacc, tc_desc(aOnes, kTcLbo, tc_sbo(16)), tc_desc(aB, kTcLbo, tc_sbo(16)), tc_idesc(N), 0);
 #pragma unroll
                     for (int s = 0; s < H / 16; ++s)
-                        tc_mma(tacc, tc_desc(aAct + 256 * s, 128, 16 * 128), tc_desc(aW + 256 * s, 128, 16 * 128),
+                        tc_mma(tacc, tc_desc(aAct + 256 * s, kTcLbo, tc_sbo(H)), tc_desc(aW + 256 * s, kTcLbo, tc_sbo(H)),
                                tc_idesc(N), 1);
                 }
                 tc_commit(bar);
