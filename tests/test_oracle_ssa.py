@@ -214,3 +214,38 @@ def test_next_operator_closed_form(orc):
     # decided by the first event: when its time falls outside the window, at
     # the draw (no reaction applied); otherwise at the first state
     assert set(np.unique(r['events'])) <= {0, 1}
+
+
+# Totals of the three-tier cascade that no reaction changes: each enzyme is
+# free or in one of its complexes, and each tier's protein is in one of its
+# phosphorylation states, free or bound.
+MAPK_TOTALS = [
+    ['E1', 'KKK_E1'],
+    ['E2', 'KKKs_E2'],
+    ['KKK', 'KKKs', 'KKK_E1', 'KKKs_E2', 'KK_KKKs', 'KKP_KKKs'],
+    ['KKPase', 'KKPP_KKPase', 'KKP_KKPase'],
+    ['KK', 'KKP', 'KKPP', 'KK_KKKs', 'KKP_KKKs', 'KKPP_KKPase', 'KKP_KKPase', 'K_KKPP', 'KP_KKPP'],
+    ['KPase', 'KPP_KPase', 'KP_KPase'],
+    ['K', 'KP', 'KPP', 'K_KKPP', 'KP_KKPP', 'KPP_KPase', 'KP_KPase'],
+]
+
+
+def test_state_updates_keep_the_cascade_totals(orc):
+    """x += v_j on a 22-species, 30-reaction network: the seven totals of
+    the cascade (the whole left null space of its stoichiometry, rank 15)
+    stay at their initial values and no count goes negative, over
+    trajectories of about 1.9e4 events each."""
+    m, p = workloads.mapk_cascade(n_inst=2)
+    W = np.zeros((len(MAPK_TOTALS), m.n_species), np.int64)
+    for i, names in enumerate(MAPK_TOTALS):
+        for nm in names:
+            W[i, m.species.index(nm)] = 1
+    st = m.stoich.astype(np.int64)
+    assert not (st @ W.T).any()                                  # no reaction changes a total
+    assert np.linalg.matrix_rank(W) == m.n_species - np.linalg.matrix_rank(st) == 7
+    r = orc.run(m, p, seed=3, instance=1, n_traj=6, want_x=True)
+    assert (r['events'] > 10_000).all()
+    xf = r['x_final'].astype(np.int64)
+    assert (xf >= 0).all()
+    assert np.array_equal(xf @ W.T, np.tile(m.x0[1].astype(np.int64) @ W.T, (len(xf), 1)))
+    assert not np.array_equal(xf[0], m.x0[1])                   # the state did move
