@@ -5,6 +5,7 @@ import ctypes
 import os
 import re
 import subprocess
+import sys
 
 import numpy as np
 import pytest
@@ -74,3 +75,28 @@ def test_formula_postfix():
     nodes = smc.postfix(f)
     assert [n[0] for n in nodes] == [2, 2, 2, 8, 4, 7]
     assert nodes[3][2:] == (0.0, 50.0) and nodes[5][2:] == (0.0, 200.0)
+
+
+def test_missing_library_fails_loudly(tmp_path):
+    """No fallback: with the library absent (and no rebuild), the binding
+    raises instead of computing anything on the CPU; and no module of the
+    package imports the oracle."""
+    code = (
+        "import sys; sys.path.insert(0, %r)\n"
+        "from paper_0912_2551_gb300 import _native\n"
+        "_native.LIB_PATH = %r\n"
+        "_native._lib = None\n"
+        "try:\n"
+        "    _native.load(build_if_missing=False)\n"
+        "except RuntimeError as e:\n"
+        "    print('raised:', e)\n"
+        "else:\n"
+        "    print('loaded')\n" % (ROOT, str(tmp_path / 'missing' / 'libsmc.so')))
+    r = subprocess.run([sys.executable, '-c', code], capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0, r.stderr
+    assert r.stdout.startswith('raised:'), r.stdout
+    pkg = os.path.join(ROOT, 'paper_0912_2551_gb300')
+    for name in os.listdir(pkg):
+        if name.endswith('.py'):
+            src = open(os.path.join(pkg, name)).read()
+            assert not re.search(r'^\s*(from|import)\s+oracle\b', src, flags=re.M), name
