@@ -1,0 +1,128 @@
+// Host replay of the compiled BLTLc monitor: the device code of
+// paper_0912_2551_gb300/csrc/smc_device.cuh (mon_start, mon_state,
+// mon_draw, mon_close), compiled for the host with the CUDA intrinsics it
+// names replaced by the operations they denote, driven over given paths in
+// the order the SSA kernels use (as the library's replay kernel does), with
+// the monitor program and atom thresholds from the library's compiler
+// (smc_compile.cpp).  tests/test_monitor_host.py compares the verdicts and
+// the points where they become fixed with the oracle's trace semantics.
+// Input: S n_atoms n_nodes; per atom op bound coef[S]; per node kind arg lo
+// hi; n_paths; per path len closed tmin, then len x [S] and len t.
+// Output: one line "verdict decided_at" per path (verdict 0 undetermined,
+// 1 false, 2 true).
+#include <math.h>
+#include <stdint.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <string>
+#include <vector>
+
+#define __device__
+#define __global__
+#define __constant__
+#define __forceinline__ inline
+#define __noinline__ __attribute__((noinline))
+struct HostDim {
+    unsigned x, y, z;
+};
+static HostDim threadIdx = {0, 0, 0}, blockIdx = {0, 0, 0}, blockDim = {32, 1, 1}, gridDim = {1, 1, 1};
+struct uint4 {
+    unsigned x, y, z, w;
+};
+static inline void __syncthreads() {}
+static inline void __threadfence() {}
+template <class T> static inline T __shfl_xor_sync(unsigned, T v, int, int = 32) { return v; }
+template <class T> static inline T __shfl_sync(unsigned, T v, int, int = 32) { return v; }
+template <class T> static inline T atomicAdd(T *p, T v) { const T o = *p; *p += v; return o; }
+static inline double __dmul_rn(double a, double b) { return a * b; }
+static inline double __dadd_rn(double a, double b) { return a + b; }
+static inline double __dsub_rn(double a, double b) { return a - b; }
+static inline double __ddiv_rn(double a, double b) { return a / b; }
+static inline double __dsqrt_rn(double a) { return sqrt(a); }
+static inline float __fmaf_rn(float a, float b, float c) { return fmaf(a, b, c); }
+static inline long long __double_as_longlong(double d) { long long v; memcpy(&v, &d, 8); return v; }
+static inline double __longlong_as_double(long long v) { double d; memcpy(&d, &v, 8); return d; }
+static inline unsigned __float_as_uint(float f) { unsigned u; memcpy(&u, &f, 4); return u; }
+static inline double __ull2double_rn(unsigned long long v) { return (double)v; }
+static inline double __ll2double_rn(long long v) { return (double)v; }
+static inline double __hiloint2double(int hi, int lo)
+{
+    return __longlong_as_double((long long)(((unsigned long long)(unsigned)hi << 32) | (unsigned)lo));
+}
+
+#include "smc.h"
+#include "smc_compile.h"
+#include "smc_device.cuh"
+
+int main()
+{
+    int S, NA, NN;
+    if (scanf("%d %d %d", &S, &NA, &NN) != 3) return 2;
+    std::vector<int32_t> coef((size_t)NA * S), op(NA);
+    std::vector<double> bound(NA);
+    for (int a = 0; a < NA; ++a) {
+        if (scanf("%d %lf", &op[a], &bound[a]) != 2) return 2;
+        for (int i = 0; i < S; ++i) if (scanf("%d", &coef[(size_t)a * S + i]) != 1) return 2;
+    }
+    std::vector<smc_node> nodes(NN);
+    for (auto &nd : nodes)
+        if (scanf("%d %d %lf %lf", &nd.kind, &nd.arg, &nd.lo, &nd.hi) != 4) return 2;
+    std::vector<smc::FNode> tree;
+    int root = -1;
+    std::string err;
+    if (smc::parse_formula(nodes.data(), NN, NA, tree, root, err) != SMC_OK) { printf("parse: %s\n", err.c_str()); return 1; }
+    MonProg P;
+    std::vector<int> used;
+    if (smc::compile_formula(tree, root, NA, INFINITY, P, used, err) != SMC_OK) { printf("compile: %s\n", err.c_str()); return 1; }
+    const int nu = (int)used.size();
+    std::vector<int64_t> thr(2 * (size_t)std::max(nu, 1));
+    uint32_t aneg = 0;
+    for (int b = 0; b < nu; ++b) {
+        bool ng;
+        smc::atom_threshold(op[used[b]], bound[used[b]], thr[2 * b], thr[2 * b + 1], ng);
+        if (ng) aneg |= 1u << b;
+    }
+    int n_paths;
+    if (scanf("%d", &n_paths) != 1) return 2;
+    for (int i = 0; i < n_paths; ++i) {
+        int n, closed;
+        double tmin;
+        if (scanf("%d %d %lf", &n, &closed, &tmin) != 3) return 2;
+        std::vector<int32_t> x((size_t)n * S);
+        std::vector<double> t(n);
+        for (auto &v : x) if (scanf("%d", &v) != 1) return 2;
+        for (auto &v : t) if (scanf("%lf", &v) != 1) return 2;
+        // the replay order of the SSA kernels: draw of state k's entry time
+        // (when the monitor asks for it), then state k; after the last state
+        // the end of the path (closed) or a lower bound on the next entry time
+        double tc[SMC_MAX_UNITS * 32];
+        MonLane ml;
+        int v = 0;
+        long long q = -1;
+        for (int k = 0; k < n && !v; ++k) {
+            if (k > 0) {
+                if (ml.pend || __double_as_longlong(t[k]) > ml.hb) v = mon_draw(ml, P, t[k], tc);
+                if (v) { q = 2 * (long long)k - 1; break; }
+            }
+            uint32_t ab = 0;
+            for (int b = 0; b < nu; ++b) {
+                long long L = 0;
+                for (int s = 0; s < S; ++s) L += (long long)coef[(size_t)used[b] * S + s] * x[(size_t)k * S + s];
+                const uint32_t in = (L >= thr[2 * b]) & (L <= thr[2 * b + 1]);
+                ab |= (in ^ ((aneg >> b) & 1u)) << b;
+            }
+            ml.ab = ab;
+            if (k == 0) mon_start(ml, P);
+            v = mon_state(ml, P, t[k], tc);
+            if (v) q = 2 * (long long)k;
+        }
+        if (!v && n > 0) {
+            if (closed) v = mon_close(ml, P);
+            else v = mon_draw<false>(ml, P, tmin, tc);
+            if (v) q = 2 * (long long)n - 1;
+        }
+        printf("%d %lld\n", v, q);
+    }
+    return 0;
+}

@@ -1,0 +1,68 @@
+"""The compiled BLTLc monitor on the host: the device code the SSA kernels
+step (smc_device.cuh), compiled for the host by tests/monitor_host.cpp and
+driven over exhaustive tiny paths (all count sequences of length <= 5 over
+{0..3}, entry times on and off the window bounds), must fix the same
+verdict at the same point as the oracle's trace semantics, for every
+formula of the oracle's monitor tests (nested F / G, until with windows,
+boolean combinations, Next).  The GPU test of the replay kernel runs the
+same comparison on the device."""
+import math
+import os
+import random
+import shutil
+import subprocess
+
+import numpy as np
+import pytest
+
+import workloads
+from paper_0912_2551_gb300 import postfix
+from paper_0912_2551_gb300._native import OP
+from tests.test_gpu_parity import _oracle_decision_point
+from tests.test_oracle_monitor import FORMULAS, _atoms, _paths
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+CSRC = os.path.join(ROOT, 'paper_0912_2551_gb300', 'csrc')
+CUDA = os.environ.get('CUDA_HOME', '/usr/local/cuda')
+
+
+@pytest.fixture(scope='module')
+def exe(tmp_path_factory):
+    gxx = shutil.which('g++')
+    if gxx is None or not os.path.exists(os.path.join(CUDA, 'include', 'cuda_runtime.h')):
+        pytest.skip('no g++ or CUDA headers')
+    out = str(tmp_path_factory.mktemp('mon') / 'monitor_host')
+    subprocess.run([gxx, '-O1', '-std=c++17', '-I', CSRC, '-I', os.path.join(ROOT, 'include'),
+                    '-I', os.path.join(CUDA, 'include'), os.path.join(ROOT, 'tests', 'monitor_host.cpp'),
+                    os.path.join(CSRC, 'smc_compile.cpp'), '-o', out], check=True)
+    return out
+
+
+@pytest.mark.parametrize('fi', range(len(FORMULAS)))
+def test_monitor_matches_oracle_on_tiny_paths(exe, orc, fi):
+    prop = workloads.Property(_atoms(), FORMULAS[fi])
+    S = 1
+    rng = random.Random(1000 + fi)
+    paths = []
+    for xs, ts in _paths(rng, 400):
+        closed = rng.random() < 0.3
+        tmin = math.inf if closed else ts[-1] + rng.choice([0.0, 0.5, 1.0, 3.0])
+        paths.append((np.asarray(xs), np.asarray(ts, float), tmin, closed))
+    lines = [f'{S} {len(prop.atoms)} {len(postfix(prop.formula))}']
+    for a in prop.atoms:
+        lines.append(f'{OP[a.op]} {a.bound!r} ' + ' '.join(str(int(c)) for c in a.coef))
+    for kind, arg, lo, hi in postfix(prop.formula):
+        lines.append(f'{kind} {arg} {lo!r} {hi!r}')
+    lines.append(str(len(paths)))
+    for xs, ts, tmin, closed in paths:
+        lines.append(f'{len(ts)} {int(closed)} {"inf" if math.isinf(tmin) else repr(float(tmin))}')
+        lines.append(' '.join(str(int(v)) for v in xs))
+        lines.append(' '.join(repr(float(v)) for v in ts))
+    r = subprocess.run([exe], input='\n'.join(lines) + '\n', capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0, r.stdout + r.stderr
+    out = [tuple(int(w) for w in ln.split()) for ln in r.stdout.splitlines()]
+    assert len(out) == len(paths)
+    for (v, q), (xs, ts, tmin, closed) in zip(out, paths):
+        ov, oq = _oracle_decision_point(orc, prop, S, xs, ts, tmin, closed)
+        want = {0: 1, 1: 2, 2: 0}[ov]
+        assert (v, q) == (want, oq), (FORMULAS[fi], xs.tolist(), ts.tolist(), tmin, closed, v, q, ov, oq)
