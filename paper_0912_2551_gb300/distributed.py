@@ -24,10 +24,10 @@ from . import _native as N
 
 
 def _slice(total_begin: int, count: int, rank: int, world: int):
-    per = -(-count // world) if count else 0
-    b = total_begin + min(count, rank * per)
-    e = total_begin + min(count, (rank + 1) * per)
-    return b, e - b
+    """This rank's contiguous part of trajectories [total_begin,
+    total_begin + count): the first count % world ranks take one more."""
+    q, r = divmod(count, world)
+    return total_begin + rank * q + min(rank, r), q + (1 if rank < r else 0)
 
 
 def fig2(run: Callable[[int, int], np.ndarray], half_width: float, confidence: float, group=None,
