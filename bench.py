@@ -199,8 +199,7 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def main():
-    global N_TRAJ
+def make_parser() -> argparse.ArgumentParser:
     ap = argparse.ArgumentParser()
     ap.add_argument('--gpus', type=int, default=1)
     ap.add_argument('--steps', type=int, default=10)
@@ -213,6 +212,12 @@ def main():
     ap.add_argument('--config', default='lotka_volterra',
                     choices=['lotka_volterra', 'immigration_death', 'random_networks', 'surrogate', 'cascade',
                              'surrogate_inference'])
+    return ap
+
+
+def main():
+    global N_TRAJ
+    ap = make_parser()
     args = ap.parse_args()
     if args.traj is not None and args.config == 'lotka_volterra':
         N_TRAJ = args.traj
