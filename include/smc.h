@@ -92,7 +92,7 @@ extern "C" {
 #define SMC_OPT_REFILL 5          /* refill a warp when >= this many lanes idle (default 1) */
 #define SMC_OPT_RECORD 6          /* 1 = keep per-trajectory verdicts of FIXED_N estimates */
 #define SMC_OPT_JIT 7             /* 1 = model-specialized kernels when every instance shares one
-                                     structure with S, R <= 8 (default 1; compiled at run time
+                                     structure with S, R <= 32 (default 1; compiled at run time
                                      with NVRTC, same results as the generic kernels) */
 
 /* A node of the formula in postfix order: operands precede their operator. */
@@ -470,6 +470,31 @@ double smc_normal_quantile(double p);                           /* Phi^{-1}(p) *
 int smc_wilson_interval(uint64_t yes, uint64_t n, double confidence, double *lo,
                         double *hi);                            /* Eq. 4 */
 double smc_wilson_sample(double p, double half_width, double confidence); /* Eq. 5 */
+
+/* One step of the iterative sample-size procedure of Fig. 2 (Sec. 3.3.2),
+ * the decision smc_estimate takes between its batches, for callers that run
+ * the batches themselves (e.g. several processes, each running a slice of
+ * every batch and summing the counts).  Host only, no GPU needed.
+ *
+ *  sampling   SMC_ITERATIVE, SMC_CONSERVATIVE or SMC_FIXED_N;
+ *  fixed_n    the batch of SMC_FIXED_N (1 .. 2^32-1), unused otherwise;
+ *  confidence in (0, 1); half_width = epsilon of Eq. 5, in (0, 0.5) (unused
+ *             for SMC_FIXED_N);
+ *  yes, n     cumulative counts so far: verdicts true, verdicts decided
+ *             (n <= n_tot; trajectories stopped by the event budget are in
+ *             n_tot but not in n);
+ *  n_tot      trajectories launched so far (0 before the first batch);
+ *  *next      (out) trajectories to launch next, 0 = stop:
+ *               n_tot = 0: fixed_n, ceil(Wilson_sample(0.5)) or
+ *                          ceil(Wilson_sample(1)) (Eq. 5) by mode;
+ *               else, SMC_ITERATIVE: p = yes / n (0 when n = 0),
+ *                          p' = p + eps if p <= 1/2, else p - eps,
+ *                          max(0, ceil(Wilson_sample(p')) - n_tot);
+ *               else 0 (one batch).
+ * Returns SMC_OK, or SMC_E_INVALID_ARG (bad mode or argument, yes > n,
+ * n > n_tot, null next). */
+int smc_fig2_next_batch(int sampling, uint64_t fixed_n, double confidence, double half_width,
+                        uint64_t yes, uint64_t n, uint64_t n_tot, uint64_t *next);
 
 #ifdef __cplusplus
 }

@@ -155,6 +155,9 @@ SIGNATURES = {
     'smc_wilson_interval': (ctypes.c_int, [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_double, c_f64p,
                                            c_f64p]),
     'smc_wilson_sample': (ctypes.c_double, [ctypes.c_double, ctypes.c_double, ctypes.c_double]),
+    'smc_fig2_next_batch': (ctypes.c_int, [ctypes.c_int, ctypes.c_uint64, ctypes.c_double, ctypes.c_double,
+                                           ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64,
+                                           ctypes.POINTER(ctypes.c_uint64)]),
 }
 
 

@@ -73,7 +73,10 @@ def build(force: bool = False, verbose: bool = False) -> str:
     _write_embedded_sources()
     nvcc = _nvcc()
     srcs, _ = _inputs()
+    # host code: no contraction into fused multiply-adds, so the host's Eq. 4 /
+    # Eq. 5 arithmetic rounds every operation as written on x86 and Arm alike
     common = ARCH + ['-O3', '-lineinfo', '-std=c++17', '-Xcompiler', '-fPIC', '-Xcompiler', '-O2',
+                     '-Xcompiler', '-ffp-contract=off',
                      '-I', CSRC, '-I', BUILD, '-I', os.path.join(os.path.dirname(HERE), 'include')]
     if verbose:
         common += ['-Xptxas', '-v']

@@ -257,6 +257,21 @@ uint64_t wilson_sample_n(double p, double eps, double z)
     return n < 1.0 ? 1 : (uint64_t)n;
 }
 
+// Fig. 2: the batch after n_tot launched trajectories with cumulative counts
+// (yes, dec); 0 = stop.  The first batch is Eq. 5 at the mode's starting p.
+uint64_t fig2_next(int sampling, uint64_t fixed_n, double eps, double z, uint64_t yes, uint64_t dec, uint64_t n_tot)
+{
+    if (n_tot == 0) {
+        if (sampling == SMC_FIXED_N) return fixed_n;
+        return wilson_sample_n(sampling == SMC_CONSERVATIVE ? 0.5 : 1.0, eps, z);
+    }
+    if (sampling != SMC_ITERATIVE) return 0;
+    const double p_est = dec ? (double)yes / (double)dec : 0.0;
+    const double p_prime = p_est <= 0.5 ? p_est + eps : p_est - eps;
+    const uint64_t n_prime = wilson_sample_n(p_prime, eps, z);
+    return n_prime > n_tot ? n_prime - n_tot : 0;
+}
+
 // Eq. 4 on the host (same operation order as the device epilogue).
 void wilson_host(uint64_t yes, uint64_t n, double z, double *p_out, double *lo_out, double *hi_out)
 {
@@ -1255,11 +1270,7 @@ int smc_estimate(smc_ctx *ctx, double confidence, double half_width, uint64_t se
     const int n = ctx->n_inst;
     const double z = z_of(confidence);
     std::vector<uint64_t> n_tot(n, 0), want(n, 0);
-    uint64_t first;
-    if (sampling == SMC_FIXED_N) first = fixed_n;
-    else if (sampling == SMC_CONSERVATIVE) first = wilson_sample_n(0.5, half_width, z);
-    else first = wilson_sample_n(1.0, half_width, z);
-    std::fill(want.begin(), want.end(), first);
+    std::fill(want.begin(), want.end(), fig2_next(sampling, fixed_n, half_width, z, 0, 0, 0));
     const bool record = ctx->record && sampling == SMC_FIXED_N;
     if (record) {
         const uint64_t need = (uint64_t)n * fixed_n;
@@ -1330,13 +1341,9 @@ int smc_estimate(smc_ctx *ctx, double confidence, double half_width, uint64_t se
         bool more = false;
         for (int m = 0; m < n; ++m) {
             n_tot[m] += want[m];
-            want[m] = 0;
-            if (sampling != SMC_ITERATIVE) continue;
-            const uint64_t yes = ctx->h_counts[4 * m], dec = ctx->h_counts[4 * m + 1];
-            const double p_est = dec ? (double)yes / (double)dec : 0.0;
-            const double p_prime = p_est <= 0.5 ? p_est + half_width : p_est - half_width;
-            const uint64_t n_prime = wilson_sample_n(p_prime, half_width, z);
-            if (n_prime > n_tot[m]) { want[m] = n_prime - n_tot[m]; more = true; }
+            want[m] = fig2_next(sampling, fixed_n, half_width, z, ctx->h_counts[4 * m], ctx->h_counts[4 * m + 1],
+                                n_tot[m]);
+            more |= want[m] > 0;
         }
         if (!more) break;
     }
@@ -1380,6 +1387,19 @@ double smc_wilson_sample(double p, double half_width, double confidence)
 {
     if (!(confidence > 0.0 && confidence < 1.0) || !(half_width > 0.0)) return std::nan("");
     return wilson_sample_real(p, half_width, z_of(confidence));
+}
+
+int smc_fig2_next_batch(int sampling, uint64_t fixed_n, double confidence, double half_width, uint64_t yes,
+                        uint64_t n, uint64_t n_tot, uint64_t *next)
+{
+    if (!next) return SMC_E_INVALID_ARG;
+    if (sampling != SMC_FIXED_N && sampling != SMC_ITERATIVE && sampling != SMC_CONSERVATIVE)
+        return SMC_E_INVALID_ARG;
+    if (!(confidence > 0.0 && confidence < 1.0) || yes > n || n > n_tot) return SMC_E_INVALID_ARG;
+    if (sampling == SMC_FIXED_N && (fixed_n < 1 || fixed_n >= (1ull << 32))) return SMC_E_INVALID_ARG;
+    if (sampling != SMC_FIXED_N && !(half_width > 0.0 && half_width < 0.5)) return SMC_E_INVALID_ARG;
+    *next = fig2_next(sampling, fixed_n, half_width, z_of(confidence), yes, n, n_tot);
+    return SMC_OK;
 }
 
 // Diagnostic: replays given paths through the compiled monitor on the GPU

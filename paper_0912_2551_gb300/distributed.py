@@ -15,12 +15,14 @@ contexts).
 """
 from __future__ import annotations
 
-import math
+import ctypes
 from typing import Callable, Optional
 
 import numpy as np
 
 from . import _native as N
+
+SAMPLING = {'fixed': N.SMC_FIXED_N, 'iterative': N.SMC_ITERATIVE, 'conservative': N.SMC_CONSERVATIVE}
 
 
 def _slice(total_begin: int, count: int, rank: int, world: int):
@@ -30,43 +32,47 @@ def _slice(total_begin: int, count: int, rank: int, world: int):
     return total_begin + rank * q + min(rank, r), q + (1 if rank < r else 0)
 
 
+def _next_batch(sampling: int, fixed_n: int, confidence: float, half_width: float, tot, n_tot: int) -> int:
+    """Fig. 2's decision between batches, taken by the library
+    (smc_fig2_next_batch): the next batch size, 0 = stop."""
+    nxt = ctypes.c_uint64()
+    rc = N.smc_fig2_next_batch(sampling, int(fixed_n), float(confidence), float(half_width), int(tot[0]),
+                               int(tot[1]), int(n_tot), ctypes.byref(nxt))
+    if rc != N.SMC_OK:
+        raise ValueError(f'smc_fig2_next_batch failed ({rc})')
+    return int(nxt.value)
+
+
 def fig2(run: Callable[[int, int], np.ndarray], half_width: float, confidence: float, group=None,
-         start_p: float = 1.0, fixed_n: Optional[int] = None, max_iter: int = 1000,
+         sampling: str = 'iterative', fixed_n: Optional[int] = None, max_iter: int = 1000,
          reduce_device=None):
-    """Iterative Wilson procedure over ranks.  ``run(begin, count)`` runs this
-    rank's trajectories and returns int64 counts [yes, n, events, budget].
-    start_p = 1: iterative; 0.5: conservative (one batch); fixed_n: one batch
-    of that size.  Returns a dict like smc_estimate's result."""
+    """The iterative Wilson procedure over ranks.  ``run(begin, count)`` runs
+    this rank's trajectories and returns int64 counts [yes, n, events,
+    budget].  ``sampling``: 'iterative' (Fig. 2), 'conservative' (one batch
+    of Eq. 5 at p = 1/2) or 'fixed' (one batch of ``fixed_n``).  The batch
+    sizes come from the library's smc_fig2_next_batch; this loop only cuts
+    each batch into the ranks' slices and sums the counts.  Returns a dict
+    like smc_estimate's result."""
     import torch
     import torch.distributed as dist
     world = dist.get_world_size(group) if dist.is_initialized() else 1
     rank = dist.get_rank(group) if dist.is_initialized() else 0
-    if fixed_n is not None:
-        N_batch = int(fixed_n)
-    else:
-        N_batch = int(math.ceil(N.smc_wilson_sample(start_p, half_width, confidence)))
+    mode = SAMPLING[sampling]
+    fixed = int(fixed_n) if sampling == 'fixed' else 0
     tot = np.zeros(4, np.int64)
     n_tot = 0
     it = 0
-    while True:
+    batch = _next_batch(mode, fixed, confidence, half_width, tot, n_tot)
+    while batch > 0 and it < max_iter:
         it += 1
-        b, c = _slice(n_tot, N_batch, rank, world)
+        b, c = _slice(n_tot, batch, rank, world)
         local = np.asarray(run(b, c) if c > 0 else np.zeros(4, np.int64), np.int64)
         t = torch.tensor(local, dtype=torch.int64, device=reduce_device or 'cpu')
-        if world > 1:
+        if dist.is_initialized():
             dist.all_reduce(t, op=dist.ReduceOp.SUM, group=group)
         tot += t.cpu().numpy()
-        n_tot += N_batch
-        if fixed_n is not None or start_p == 0.5 or it >= max_iter:
-            break
-        p = tot[0] / tot[1] if tot[1] else 0.0
-        pp = p + half_width if p <= 0.5 else p - half_width
-        n_prime = int(math.ceil(N.smc_wilson_sample(pp, half_width, confidence)))
-        if n_prime - n_tot > 0:
-            N_batch = n_prime - n_tot
-            continue
-        break
-    import ctypes
+        n_tot += batch
+        batch = _next_batch(mode, fixed, confidence, half_width, tot, n_tot)
     lo, hi = ctypes.c_double(), ctypes.c_double()
     yes, n = int(tot[0]), int(tot[1])
     N.smc_wilson_interval(yes, n, confidence, ctypes.byref(lo), ctypes.byref(hi))
@@ -92,7 +98,6 @@ def estimate(ctx, confidence: float, half_width: float, seed: int = 0, precision
         torch.cuda.synchronize(dev)
         return out['counts'].cpu().numpy()[0]
 
-    start_p = {'iterative': 1.0, 'conservative': 0.5, 'fixed': 1.0}[sampling]
-    return fig2(run, half_width, confidence, group, start_p=start_p,
+    return fig2(run, half_width, confidence, group, sampling=sampling,
                 fixed_n=fixed_n if sampling == 'fixed' else None,
                 reduce_device=dev if backend == 'nccl' else None)

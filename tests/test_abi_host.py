@@ -100,3 +100,49 @@ def test_missing_library_fails_loudly(tmp_path):
         if name.endswith('.py'):
             src = open(os.path.join(pkg, name)).read()
             assert not re.search(r'^\s*(from|import)\s+oracle\b', src, flags=re.M), name
+
+
+def test_fig2_step_matches_oracle_procedure(native, orc):
+    """smc_fig2_next_batch, driven over Bernoulli verdict streams, gives the
+    batch sequence and totals of the oracle's Fig. 2 (oracle/wilson.py), for
+    the iterative, conservative and fixed-size modes."""
+    from oracle import wilson
+    rng = np.random.default_rng(7)
+    for p_true in (0.0, 0.003, 0.1, 0.5, 0.93, 1.0):
+        for eps, conf in ((0.025, 0.99), (0.01, 0.95), (0.002, 0.95)):
+            stream = rng.random(400000) < p_true
+
+            def run(begin, count):
+                return int(stream[begin:begin + count].sum()), count
+
+            ref = wilson.iterative(run, eps, conf)
+            sizes, n_tot, yes = [], 0, 0
+            nxt = ctypes.c_uint64()
+            while True:
+                assert native.smc_fig2_next_batch(native.SMC_ITERATIVE, 0, conf, eps, yes, n_tot, n_tot,
+                                                  ctypes.byref(nxt)) == 0
+                if nxt.value == 0:
+                    break
+                y, _ = run(n_tot, nxt.value)
+                sizes.append(nxt.value)
+                yes += y
+                n_tot += nxt.value
+            assert sizes == ref['sizes'] and n_tot == ref['n_tot'] and yes == ref['yes'], (p_true, eps, conf)
+            assert native.smc_fig2_next_batch(native.SMC_CONSERVATIVE, 0, conf, eps, 0, 0, 0, ctypes.byref(nxt)) == 0
+            assert nxt.value == wilson.wilson_sample(0.5, eps, conf)
+            assert native.smc_fig2_next_batch(native.SMC_CONSERVATIVE, 0, conf, eps, 3, 10, 10,
+                                              ctypes.byref(nxt)) == 0 and nxt.value == 0
+    assert native.smc_fig2_next_batch(native.SMC_FIXED_N, 777, 0.95, 0.0, 0, 0, 0, ctypes.byref(nxt)) == 0
+    assert nxt.value == 777
+    assert native.smc_fig2_next_batch(native.SMC_FIXED_N, 777, 0.95, 0.0, 5, 777, 777, ctypes.byref(nxt)) == 0
+    assert nxt.value == 0
+    # Table 1 / Fig. 2: the first iterative batch at 99%, eps = 0.025 is 127
+    assert native.smc_fig2_next_batch(native.SMC_ITERATIVE, 0, 0.99, 0.025, 0, 0, 0, ctypes.byref(nxt)) == 0
+    assert nxt.value == 127
+    bad = [(99, 0, 0.95, 0.01, 0, 0, 0), (native.SMC_ITERATIVE, 0, 1.0, 0.01, 0, 0, 0),
+           (native.SMC_ITERATIVE, 0, 0.95, 0.5, 0, 0, 0), (native.SMC_ITERATIVE, 0, 0.95, 0.01, 5, 4, 10),
+           (native.SMC_ITERATIVE, 0, 0.95, 0.01, 1, 11, 10), (native.SMC_FIXED_N, 0, 0.95, 0.01, 0, 0, 0)]
+    for args in bad:
+        assert native.smc_fig2_next_batch(*args, ctypes.byref(nxt)) == native.SMC_E_INVALID_ARG, args
+    assert native.smc_fig2_next_batch(native.SMC_ITERATIVE, 0, 0.95, 0.01, 0, 0, 0, None) == \
+        native.SMC_E_INVALID_ARG
