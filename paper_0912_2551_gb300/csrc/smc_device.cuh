@@ -39,9 +39,9 @@ __device__ __forceinline__ void philox10(uint32_t c0, uint32_t c1, uint32_t c2, 
 }
 
 // (0,1) from 52 bits: ((hi:lo) >> 12 + 1/2) 2^-52 = (2v + 1) 2^-53, exact, in
-// [2^-53, 1 - 2^-53]: the odd integer 2v + 1 < 2^53 converted exactly (one
-// conversion on the FP64 pipe, which has room on the FP64 path; the integer
-// assembly costs 18 more issue slots), then 2^-53 applied to the exponent.
+// [2^-53, 1 - 2^-53]: the odd integer 2v + 1 < 2^53 converted exactly, then
+// 2^-53 applied to the exponent.  The FP64 event loop never forms it: it
+// keeps the odd integer (odd53) and takes -ln u and u a_0 from it.
 __device__ __forceinline__ double u01_52(uint32_t hi, uint32_t lo)
 {
     const uint64_t n = ((((((uint64_t)hi) << 32) | (uint64_t)lo) >> 12) << 1) | 1ull;
@@ -65,8 +65,10 @@ __device__ __forceinline__ float u01_23(uint32_t w)
 }
 
 // An integer h as a double (exact for |h| < 2^53, rounded to nearest
-// otherwise): the conversion instruction.
-__device__ __forceinline__ double int_to_double(long long h) { return __ll2double_rn(h); }
+// otherwise): on the integer pipes for 0 <= h < 2^53 (fp64i_i2d), else the
+// conversion instruction.  GB300's FP64 pipe retires 2 lane-operations per
+// clock per SM, so the event loop keeps its conversions off it.
+__device__ __forceinline__ double int_to_double(long long h) { return fp64i_i2d(h); }
 
 // The odd integer n = 2v + 1 < 2^53 of the uniform (2v + 1) 2^-53 that
 // u01_52(hi, lo) returns (v = the top 52 bits of hi:lo).

@@ -95,26 +95,58 @@ FP64I_HD float fp64i_rcp_approx(float f)  // about 1/f (f in [2^23, 2^24))
 #define FP64I_FRAC 0x000FFFFFFFFFFFFFull
 #define FP64I_ONE (1ull << 52)
 
-// n / d, correctly rounded (nearest, ties to even).  The integer path has
-// no branch (so the compiler can interleave it with independent work); the
-// operands and quotients it does not cover are redone by the FP64 division
-// at the end.
-FP64I_HD double fp64i_div(double n, double d)
+// An integer h as a binary64, for 0 <= h < 2^53 built on the integer pipes
+// (exact: leading bit found with clz, the significand shifted into place,
+// the exponent added); negative h and h >= 2^53 (rare) take the conversion
+// instruction, which rounds to nearest.  Same value as the conversion for
+// every h.
+FP64I_HD double fp64i_i2d(int64_t h)
 {
-    const uint64_t bn = fp64i_bits(n), bd = fp64i_bits(d);
-    const uint32_t en = (uint32_t)(bn >> 52), ed = (uint32_t)(bd >> 52);  // sign bit included
-    // zero, subnormal, inf, nan or negative operands
-    bool special = (en - 1u >= 0x7FEu) | (ed - 1u >= 0x7FEu);
-    uint64_t mn = (bn & FP64I_FRAC) | FP64I_ONE;
-    const uint64_t md = (bd & FP64I_FRAC) | FP64I_ONE;
-    const bool lt = mn < md;
-    mn <<= lt;                                       // mn / md in [1, 2)
-    int e = (int)en - (int)ed + 1023 - (int)lt;      // biased exponent of the quotient
-    // 1/delta for delta = md / 2^53 in [1/2, 1), as y = Y 2^-63: a single-
-    // precision seed (relative error below 2^-21; 2 clamps to 2 - 2^-23),
-    // then two Newton steps y <- y (2 - delta y) in fixed point, the first
-    // with the seed as one 32-bit factor (error about 2^-42), the second in
-    // 64-bit (about 2^-62).  Truncation keeps every step at or below 1/delta.
+    const uint64_t u = (uint64_t)h;
+    if (u >> 53) return (double)h;
+    const int p = 63 - fp64i_clz(u | 1u);  // leading bit (h = 0 handled below)
+    const uint64_t b = ((uint64_t)(1022 + p) << 52) + (u << (52 - p));
+    return fp64i_from_bits(u ? b : 0ull);
+}
+
+// The bits of u a rounded to nearest-even, for u = n 2^-53 (n odd,
+// 1 <= n < 2^53: the SSA's uniform as its integer) and a > 0: the IEEE
+// product, the FP64 pipe's multiplication replaced by a 53 x 53-bit integer
+// product P = n' m_a in [2^104, 2^106) (n' = n normalised), its top 53 bits,
+// the guard bit and the sticky bit.  Zero, subnormal, infinite or negative
+// a, and subnormal products, take the FP64 multiplication.
+FP64I_HD uint64_t fp64i_mul_u53(uint64_t n, double a)
+{
+    const uint64_t ba = fp64i_bits(a);
+    const uint32_t ea = (uint32_t)(ba >> 52);  // sign bit included
+    const int p = 63 - fp64i_clz(n);
+    const uint64_t nn = n << (52 - p);         // [2^52, 2^53)
+    const uint64_t ma = (ba & FP64I_FRAC) | FP64I_ONE;
+    const uint64_t lo = nn * ma, hi = fp64i_mulhi(nn, ma);
+    const bool top = (hi >> 41) != 0;  // P >= 2^105
+    // P >> 52 or P >> 53: 53 bits; then the guard bit and the bits below it
+    uint64_t m = top ? ((hi << 11) | (lo >> 53)) : ((hi << 12) | (lo >> 52));
+    const uint64_t g = top ? (lo >> 52) & 1u : (lo >> 51) & 1u;
+    const uint64_t st = (lo & (top ? (1ull << 52) - 1u : (1ull << 51) - 1u)) != 0;
+    m += g & (st | (m & 1u));
+    // u a = (P / 2^(104 + top)) 2^(top + p + ea - 1076)
+    int e = (int)ea - 53 + p + (int)top;
+    const uint64_t carry = m >> 53;  // rounded up to 2^53
+    m >>= carry;
+    e += (int)carry;
+    if ((ea - 1u >= 0x7FEu) | (e < 1) | (e > 2046))
+        return fp64i_bits(fp64i_from_bits(((uint64_t)(1023 - 53 + p) << 52) + ((nn - FP64I_ONE) & FP64I_FRAC)) * a);
+    return ((uint64_t)e << 52) + (m & FP64I_FRAC);
+}
+
+// 1/delta for delta = md / 2^53 in [1/2, 1) (md in [2^52, 2^53)), as
+// y = Y 2^-63 with Y <= 2^63 / delta < 2^64: a single-precision seed (relative
+// error below 2^-21; 2 clamps to 2 - 2^-23), then two Newton steps
+// y <- y (2 - delta y) in fixed point, the first with the seed as one 32-bit
+// factor (error about 2^-42), the second in 64-bit (about 2^-62).
+// Truncation keeps every step at or below 1/delta.
+FP64I_HD uint64_t fp64i_recip63(uint64_t md)
+{
     const uint64_t D = md << 11;  // delta 2^64
     const float s = fp64i_rcp_approx((float)(uint32_t)(D >> 40)) * 16777216.0f;
     uint32_t sb;
@@ -144,6 +176,25 @@ FP64I_HD double fp64i_div(double n, double d)
         const uint64_t ql = Y * W, qh = fp64i_mulhi(Y, W);
         Y = (qh << 1) | (ql >> 63);
     }
+    return Y;
+}
+
+// n / d, correctly rounded (nearest, ties to even).  The integer path has
+// no branch (so the compiler can interleave it with independent work); the
+// operands and quotients it does not cover are redone by the FP64 division
+// at the end.
+FP64I_HD double fp64i_div(double n, double d)
+{
+    const uint64_t bn = fp64i_bits(n), bd = fp64i_bits(d);
+    const uint32_t en = (uint32_t)(bn >> 52), ed = (uint32_t)(bd >> 52);  // sign bit included
+    // zero, subnormal, inf, nan or negative operands
+    bool special = (en - 1u >= 0x7FEu) | (ed - 1u >= 0x7FEu);
+    uint64_t mn = (bn & FP64I_FRAC) | FP64I_ONE;
+    const uint64_t md = (bd & FP64I_FRAC) | FP64I_ONE;
+    const bool lt = mn < md;
+    mn <<= lt;                                       // mn / md in [1, 2)
+    int e = (int)en - (int)ed + 1023 - (int)lt;      // biased exponent of the quotient
+    const uint64_t Y = fp64i_recip63(md);
     // Qt = floor(mn 2^53 / md), in [2^53, 2^54): the estimate mn Y 2^-63 is
     // Qt or Qt - 1 (Y <= 2^63 / delta, relative error about 2^-62); the
     // exact remainder (64-bit wrap-around arithmetic) settles it
@@ -287,7 +338,7 @@ FP64I_HD double fp64i_log(double u, const uint64_t *tab)
 // u = (2v + 1) 2^-53 taken as its integer n, so neither u nor its bit
 // pattern is formed; the same arithmetic as -fp64i_log(u) (equal bits):
 //   -ln u = |k| ln 2 + ln G_j - r P(r),  k <= 0, the sum positive.
-FP64I_HD double fp64i_neglog53(uint64_t n, const uint64_t *tab)
+FP64I_HD void fp64i_neglog53_fx(uint64_t n, const uint64_t *tab, uint64_t &lo, uint64_t &hi)
 {
     const int p = 63 - fp64i_clz(n);  // u = (n 2^-p) 2^(p - 53), n 2^-p in [1, 2)
     uint64_t M = n << (52 - p);       // m 2^52
@@ -298,8 +349,8 @@ FP64I_HD double fp64i_neglog53(uint64_t n, const uint64_t *tab)
     const int64_t r = fp64i_reduce(M, tab, j);
     uint64_t blo, bhi;
     fp64i_log1p_abs(r, blo, bhi);
-    uint64_t lo = tab[387] * (uint32_t)ka;
-    uint64_t hi = tab[386] * (uint32_t)ka + fp64i_mulhi(tab[387], (uint32_t)ka);
+    lo = tab[387] * (uint32_t)ka;
+    hi = tab[386] * (uint32_t)ka + fp64i_mulhi(tab[387], (uint32_t)ka);
     {
         const uint64_t gl = tab[FP64I_LOG_N + j], gh = tab[j];
         const uint64_t nl = lo + gl;
@@ -315,7 +366,56 @@ FP64I_HD double fp64i_neglog53(uint64_t n, const uint64_t *tab)
         hi = hi - bhi - (nl > lo);
         lo = nl;
     }
+}
+
+FP64I_HD double fp64i_neglog53(uint64_t n, const uint64_t *tab)
+{
+    uint64_t lo, hi;
+    fp64i_neglog53_fx(n, tab, lo, hi);
     return fp64i_from_bits(fp64i_round117_hi(lo, hi));  // the sum is in [2^64, 2^123)
+}
+
+// -ln(n 2^-53) normalised: S = sm 2^(-53 - lz) with sm in [2^63, 2^64], the
+// top 64 bits of the 128-bit sum above (truncated: relative error below
+// 2^-63).  The SSA draws it one event ahead of its use.
+FP64I_HD void fp64i_neglog53_norm(uint64_t n, const uint64_t *tab, uint64_t &sm, int &lz)
+{
+    uint64_t lo, hi;
+    fp64i_neglog53_fx(n, tab, lo, hi);
+    lz = fp64i_clz(hi);  // hi >= 1: the sum is at least 2^64
+    sm = (hi << lz) | ((lo >> 1) >> (63 - lz));
+}
+
+// tau = S / a for S = sm 2^(-53 - lz) from fp64i_neglog53_norm and a > 0
+// (Eq. 2a), rounded once: S times the reciprocal of a (fp64i_recip63), the
+// high word of the 64 x 64-bit product rounded to 53 bits.  Each factor and
+// the product are truncated, so the unrounded value lies below S / a by a
+// relative 2^-60 at most, and the result is within 0.5 + 2^-7 ulp of S / a
+// (faithful; correctly rounded but within 2^-7 ulp of a rounding midpoint).
+// S / a is never a midpoint (S is a logarithm of a rational other than 1),
+// so a computed value exactly at one rounds up.  Zero, subnormal, infinite,
+// negative or NaN a, and quotients outside the normal range, take the
+// division of the rounded logarithm by a (within one ulp).
+FP64I_HD double fp64i_tau(uint64_t sm, int lz, double a)
+{
+    const uint64_t ba = fp64i_bits(a);
+    const uint32_t ea = (uint32_t)(ba >> 52);  // sign bit included
+    const uint64_t Y = fp64i_recip63((ba & FP64I_FRAC) | FP64I_ONE);
+    // S / a = sm Y 2^(906 - lz - ea); PH = floor(sm Y 2^-64) in [2^62, 2^64)
+    const uint64_t ph = fp64i_mulhi(sm, Y);
+    const uint32_t top = (uint32_t)(ph >> 63);
+    uint64_t m = ph >> (10 + top);
+    m += (ph >> (9 + top)) & 1u;          // guard bit: round half up (no exact midpoint)
+    const uint64_t carry = m >> 53;
+    m >>= carry;
+    const int e = 2055 + (int)top + (int)carry - lz - (int)ea;
+    if ((ea - 1u >= 0x7FEu) | (e < 1) | (e > 2046)) {
+        uint64_t s53 = (sm >> 11) + ((sm >> 10) & 1u);  // the logarithm rounded to 53 bits
+        const uint64_t c2 = s53 >> 53;
+        s53 >>= c2;
+        return fp64i_div(fp64i_from_bits(((uint64_t)(1023 + 10 - lz + (int)c2) << 52) + (s53 & FP64I_FRAC)), a);
+    }
+    return fp64i_from_bits(((uint64_t)e << 52) + (m & FP64I_FRAC));
 }
 
 #if !defined(__CUDACC_RTC__)

@@ -50,9 +50,19 @@ namespace {
 // u_sel from the Philox block of (event e, trajectory, instance).  They
 // depend on the event index alone, so the kernel draws them one event ahead
 // and the logarithm leaves the chain that runs through the counts.
+// FP64 path: -ln u_tau as the normalised 64-bit value of fp64i_neglog53_norm
+// (sm, lz), and u_sel as its odd integer n (u_sel = n 2^-53), so that tau
+// and u_sel a_0 are formed on the integer pipes (fp64i_tau, fp64i_mul_u53).
 template <bool PLAIN>
-struct JitDraw {
-    typename Prec<PLAIN>::T nl, us;
+struct JitDraw;
+template <>
+struct JitDraw<true> {
+    uint64_t sm, us;
+    int lz;
+};
+template <>
+struct JitDraw<false> {
+    float nl, us;
 };
 
 template <bool PLAIN>
@@ -63,13 +73,33 @@ __device__ __forceinline__ JitDraw<PLAIN> jit_draw(uint32_t e, uint32_t traj, ui
     philox10(e, traj, m, 0u, p.rk0, p.rk1, w0, w1, w2, w3);
     JitDraw<PLAIN> d;
     if constexpr (PLAIN) {
-        d.nl = fp64i_neglog53(odd53(w0, w1), ltab);  // -ln u01_52(w0, w1)
-        d.us = u01_52(w2, w3);
+        fp64i_neglog53_norm(odd53(w0, w1), ltab, d.sm, d.lz);  // -ln u01_52(w0, w1)
+        d.us = odd53(w2, w3);                                   // u01_52(w2, w3) = us 2^-53
     } else {
         d.nl = -__logf(u01_23(w0));
         d.us = u01_23(w2);
     }
     return d;
+}
+
+// tau = -ln(u_tau) / a_0 (Eq. 2a), widened to FP64: FP64 path rounded once
+// from the fixed-point logarithm (fp64i_tau, within 0.51 ulp), mixed path in
+// FP32.
+template <bool PLAIN>
+__device__ __forceinline__ double jit_tau(const JitDraw<PLAIN> &d, typename Prec<PLAIN>::T a0)
+{
+    if constexpr (PLAIN) return fp64i_tau(d.sm, d.lz, a0);
+    else return f32_to_f64(__fdividef(d.nl, a0));
+}
+
+// r = u_sel a_0 (Eq. 2b) rounded once: FP64 path on the integer pipes (bit
+// for bit the FP64 product), mixed path in FP32.
+template <bool PLAIN>
+__device__ __forceinline__ typename Prec<PLAIN>::T jit_sel_target(const JitDraw<PLAIN> &d,
+                                                                  typename Prec<PLAIN>::T a0)
+{
+    if constexpr (PLAIN) return __longlong_as_double((long long)fp64i_mul_u53(d.us, a0));
+    else return __fmul_rn(d.us, a0);
 }
 
 #ifndef JIT_MEDIUM
@@ -128,15 +158,8 @@ __device__ __noinline__ void jit_coop(const SsaParams &p, const MonProg &P, cons
         const T a0 = pre[JR - 1];
         const bool dead = PLAIN ? __double_as_longlong((double)a0) <= 0 : !(a0 > (T)0);
         const JitDraw<PLAIN> dr = jit_draw<PLAIN>(eb + (uint32_t)d, traj, (uint32_t)m, p, ltab);
-        double tau;  // the clock step, widened to FP64
-        T r;
-        if (PLAIN) {
-            tau = fp64i_div((double)dr.nl, (double)a0);
-            r = (T)__dmul_rn((double)dr.us, (double)a0);
-        } else {
-            tau = f32_to_f64(__fdividef((float)dr.nl, (float)a0));
-            r = (T)__fmul_rn((float)dr.us, (float)a0);
-        }
+        const double tau = jit_tau<PLAIN>(dr, a0);  // the clock step, widened to FP64
+        const T r = jit_sel_target<PLAIN>(dr, a0);
         int j = -1;
 #pragma unroll
         for (int k = JR - 1; k >= 0; --k) {
@@ -355,16 +378,8 @@ __device__ __forceinline__ void jit_run_instance(const SsaParams &p, const MonPr
         else jit_props_mixed(x, c, pre, pos);
         const T a0 = pre[JR - 1];
         const bool dead = PLAIN ? __double_as_longlong((double)a0) <= 0 : !(a0 > (T)0);
-        double tn;
-        T r;
-        if (PLAIN) {
-            tn = __dadd_rn(t, fp64i_div((double)nd.nl, (double)a0));
-            r = (T)__dmul_rn((double)nd.us, (double)a0);
-        } else {
-            const float tau = __fdividef((float)nd.nl, (float)a0);
-            tn = __dadd_rn(t, f32_to_f64(tau));
-            r = (T)__fmul_rn((float)nd.us, (float)a0);
-        }
+        const double tn = __dadd_rn(t, jit_tau<PLAIN>(nd, a0));
+        const T r = jit_sel_target<PLAIN>(nd, a0);
         // step 2: the first j whose running sum exceeds r
         int j = -1;
 #pragma unroll

@@ -5,7 +5,12 @@ bit for bit against IEEE-754 division on 10^6 operand pairs of every class,
 the logarithm within 0.502 ulp of long-double logl and correctly rounded on
 more than 99.99% of 1.75 x 10^6 arguments (the SSA's uniforms, values near
 1, the table's bucket edges, general positive doubles), and the SSA's form
--ln((2v + 1) 2^-53) from the integer equal bit for bit to -ln u."""
+-ln((2v + 1) 2^-53) from the integer equal bit for bit to -ln u; the exact
+integer-pipe conversion of integers and the product u a of the selection
+bit for bit against the IEEE conversion and product; and the step of Eq. 2a
+as the event loop forms it, tau = -ln u / a_0 rounded once from the
+fixed-point logarithm and reciprocal, within 0.51 ulp of the long-double
+quotient."""
 import os
 import shutil
 import subprocess
@@ -27,8 +32,13 @@ def test_fp64i_against_host_arithmetic(tmp_path):
                     os.path.join(ROOT, 'tests', 'fp64i_check.cpp'), '-o', exe, '-lm'], check=True)
     r = subprocess.run([exe, '1000000'], capture_output=True, text=True, timeout=300)
     assert r.returncode == 0, r.stdout + r.stderr
-    kv = dict(f.split('=', 1) for f in r.stdout.split()[-8:])
+    kv = dict(f.split('=', 1) for f in r.stdout.strip().splitlines()[-1].split())
     assert int(kv['div_mismatches']) == 0
     assert float(kv['log_max_ulp']) <= 0.502
     assert float(kv['log_correctly_rounded']) >= 0.9999
     assert int(kv['neglog53_mismatches']) == 0
+    assert int(kv['i2d_mismatches']) == 0 and int(kv['mul_u53_mismatches']) == 0
+    # tau = -ln u / a_0 rounded once: within 0.5 + 2^-7 ulp, and correctly rounded
+    # but for quotients within 2^-7 ulp of a midpoint
+    assert float(kv['tau_max_ulp']) <= 0.51 and int(kv['tau_bad']) == 0
+    assert float(kv['tau_correctly_rounded']) >= 0.99
