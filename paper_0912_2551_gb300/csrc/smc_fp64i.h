@@ -61,6 +61,7 @@ FP64I_HD int fp64i_clz(uint64_t a)  // a != 0
 #endif
 }
 
+
 FP64I_HD uint64_t fp64i_bits(double x)
 {
 #if defined(__CUDA_ARCH__)
@@ -95,6 +96,17 @@ FP64I_HD float fp64i_rcp_approx(float f)  // about 1/f (f in [2^23, 2^24))
 #define FP64I_FRAC 0x000FFFFFFFFFFFFFull
 #define FP64I_ONE (1ull << 52)
 
+// The rare operands of the functions below go to the FP64 pipe through
+// these out-of-line calls: kept out of line on the device so that the
+// compiler cannot evaluate them speculatively next to the integer path.
+#if defined(__CUDA_ARCH__)
+#define FP64I_SLOW __device__ __noinline__
+#else
+#define FP64I_SLOW static
+#endif
+FP64I_SLOW double fp64i_slow_i2d(int64_t h) { return (double)h; }
+FP64I_SLOW double fp64i_slow_div(double n, double d) { return n / d; }
+
 // An integer h as a binary64, for 0 <= h < 2^53 built on the integer pipes
 // (exact: leading bit found with clz, the significand shifted into place,
 // the exponent added); negative h and h >= 2^53 (rare) take the conversion
@@ -103,41 +115,12 @@ FP64I_HD float fp64i_rcp_approx(float f)  // about 1/f (f in [2^23, 2^24))
 FP64I_HD double fp64i_i2d(int64_t h)
 {
     const uint64_t u = (uint64_t)h;
-    if (u >> 53) return (double)h;
+    if (__builtin_expect(u >> 53, 0)) return fp64i_slow_i2d(h);
     const int p = 63 - fp64i_clz(u | 1u);  // leading bit (h = 0 handled below)
     const uint64_t b = ((uint64_t)(1022 + p) << 52) + (u << (52 - p));
     return fp64i_from_bits(u ? b : 0ull);
 }
 
-// The bits of u a rounded to nearest-even, for u = n 2^-53 (n odd,
-// 1 <= n < 2^53: the SSA's uniform as its integer) and a > 0: the IEEE
-// product, the FP64 pipe's multiplication replaced by a 53 x 53-bit integer
-// product P = n' m_a in [2^104, 2^106) (n' = n normalised), its top 53 bits,
-// the guard bit and the sticky bit.  Zero, subnormal, infinite or negative
-// a, and subnormal products, take the FP64 multiplication.
-FP64I_HD uint64_t fp64i_mul_u53(uint64_t n, double a)
-{
-    const uint64_t ba = fp64i_bits(a);
-    const uint32_t ea = (uint32_t)(ba >> 52);  // sign bit included
-    const int p = 63 - fp64i_clz(n);
-    const uint64_t nn = n << (52 - p);         // [2^52, 2^53)
-    const uint64_t ma = (ba & FP64I_FRAC) | FP64I_ONE;
-    const uint64_t lo = nn * ma, hi = fp64i_mulhi(nn, ma);
-    const bool top = (hi >> 41) != 0;  // P >= 2^105
-    // P >> 52 or P >> 53: 53 bits; then the guard bit and the bits below it
-    uint64_t m = top ? ((hi << 11) | (lo >> 53)) : ((hi << 12) | (lo >> 52));
-    const uint64_t g = top ? (lo >> 52) & 1u : (lo >> 51) & 1u;
-    const uint64_t st = (lo & (top ? (1ull << 52) - 1u : (1ull << 51) - 1u)) != 0;
-    m += g & (st | (m & 1u));
-    // u a = (P / 2^(104 + top)) 2^(top + p + ea - 1076)
-    int e = (int)ea - 53 + p + (int)top;
-    const uint64_t carry = m >> 53;  // rounded up to 2^53
-    m >>= carry;
-    e += (int)carry;
-    if ((ea - 1u >= 0x7FEu) | (e < 1) | (e > 2046))
-        return fp64i_bits(fp64i_from_bits(((uint64_t)(1023 - 53 + p) << 52) + ((nn - FP64I_ONE) & FP64I_FRAC)) * a);
-    return ((uint64_t)e << 52) + (m & FP64I_FRAC);
-}
 
 // 1/delta for delta = md / 2^53 in [1/2, 1) (md in [2^52, 2^53)), as
 // y = Y 2^-63 with Y <= 2^63 / delta < 2^64: a single-precision seed (relative
@@ -211,7 +194,7 @@ FP64I_HD double fp64i_div(double n, double d)
     q >>= carry;
     e += (int)carry;
     special |= (e < 1) | (e > 2046);  // subnormal or infinite quotient
-    if (special) return n / d;
+    if (__builtin_expect(special, 0)) return fp64i_slow_div(n, d);
     return fp64i_from_bits(((uint64_t)e << 52) | (q & FP64I_FRAC));
 }
 
@@ -375,9 +358,9 @@ FP64I_HD double fp64i_neglog53(uint64_t n, const uint64_t *tab)
     return fp64i_from_bits(fp64i_round117_hi(lo, hi));  // the sum is in [2^64, 2^123)
 }
 
-// -ln(n 2^-53) normalised: S = sm 2^(-53 - lz) with sm in [2^63, 2^64], the
-// top 64 bits of the 128-bit sum above (truncated: relative error below
-// 2^-63).  The SSA draws it one event ahead of its use.
+// -ln(n 2^-53) normalised from the 128-bit sum above: S = sm 2^(-53 - lz),
+// sm in [2^63, 2^64), the sum's top 64 bits (truncated: relative error
+// below 2^-63).  The SSA draws it one event ahead of its use.
 FP64I_HD void fp64i_neglog53_norm(uint64_t n, const uint64_t *tab, uint64_t &sm, int &lz)
 {
     uint64_t lo, hi;
@@ -409,11 +392,11 @@ FP64I_HD double fp64i_tau(uint64_t sm, int lz, double a)
     const uint64_t carry = m >> 53;
     m >>= carry;
     const int e = 2055 + (int)top + (int)carry - lz - (int)ea;
-    if ((ea - 1u >= 0x7FEu) | (e < 1) | (e > 2046)) {
+    if (__builtin_expect((ea - 1u >= 0x7FEu) | (e < 1) | (e > 2046), 0)) {
         uint64_t s53 = (sm >> 11) + ((sm >> 10) & 1u);  // the logarithm rounded to 53 bits
         const uint64_t c2 = s53 >> 53;
         s53 >>= c2;
-        return fp64i_div(fp64i_from_bits(((uint64_t)(1023 + 10 - lz + (int)c2) << 52) + (s53 & FP64I_FRAC)), a);
+        return fp64i_slow_div(fp64i_from_bits(((uint64_t)(1023 + 10 - lz + (int)c2) << 52) + (s53 & FP64I_FRAC)), a);
     }
     return fp64i_from_bits(((uint64_t)e << 52) + (m & FP64I_FRAC));
 }

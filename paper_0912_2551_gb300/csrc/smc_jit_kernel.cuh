@@ -51,13 +51,14 @@ namespace {
 // depend on the event index alone, so the kernel draws them one event ahead
 // and the logarithm leaves the chain that runs through the counts.
 // FP64 path: -ln u_tau as the normalised 64-bit value of fp64i_neglog53_norm
-// (sm, lz), and u_sel as its odd integer n (u_sel = n 2^-53), so that tau
-// and u_sel a_0 are formed on the integer pipes (fp64i_tau, fp64i_mul_u53).
+// (sm, lz), so that tau is formed on the integer pipes (fp64i_tau), and
+// u_sel as a double.
 template <bool PLAIN>
 struct JitDraw;
 template <>
 struct JitDraw<true> {
-    uint64_t sm, us;
+    uint64_t sm;
+    double us;
     int lz;
 };
 template <>
@@ -74,7 +75,7 @@ __device__ __forceinline__ JitDraw<PLAIN> jit_draw(uint32_t e, uint32_t traj, ui
     JitDraw<PLAIN> d;
     if constexpr (PLAIN) {
         fp64i_neglog53_norm(odd53(w0, w1), ltab, d.sm, d.lz);  // -ln u01_52(w0, w1)
-        d.us = odd53(w2, w3);                                   // u01_52(w2, w3) = us 2^-53
+        d.us = u01_52(w2, w3);
     } else {
         d.nl = -__logf(u01_23(w0));
         d.us = u01_23(w2);
@@ -92,13 +93,14 @@ __device__ __forceinline__ double jit_tau(const JitDraw<PLAIN> &d, typename Prec
     else return f32_to_f64(__fdividef(d.nl, a0));
 }
 
-// r = u_sel a_0 (Eq. 2b) rounded once: FP64 path on the integer pipes (bit
-// for bit the FP64 product), mixed path in FP32.
+// r = u_sel a_0 (Eq. 2b) rounded once, in the path's precision.  (The FP64
+// product stays on the FP64 pipe: its integer form costs about 55 issue
+// slots, more than the pipe time it frees.)
 template <bool PLAIN>
 __device__ __forceinline__ typename Prec<PLAIN>::T jit_sel_target(const JitDraw<PLAIN> &d,
                                                                   typename Prec<PLAIN>::T a0)
 {
-    if constexpr (PLAIN) return __longlong_as_double((long long)fp64i_mul_u53(d.us, a0));
+    if constexpr (PLAIN) return __dmul_rn(d.us, a0);
     else return __fmul_rn(d.us, a0);
 }
 

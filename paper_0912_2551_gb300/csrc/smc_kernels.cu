@@ -236,13 +236,12 @@ __device__ __forceinline__ void run_instance(const SsaParams &p, const MonProg &
         double tn;
         T r;
         if (PLAIN) {
-            // tau = -ln u01_52(w0, w1) / a_0 rounded once, and u01_52(w2, w3) a_0,
-            // both from the uniforms' integers on the integer pipes
+            // tau = -ln u01_52(w0, w1) / a_0 rounded once on the integer pipes
             uint64_t sm;
             int lz;
             fp64i_neglog53_norm(odd53(w0, w1), ltab, sm, lz);
             tn = __dadd_rn(t, fp64i_tau(sm, lz, (double)a0));
-            r = (T)__longlong_as_double((long long)fp64i_mul_u53(odd53(w2, w3), (double)a0));
+            r = (T)__dmul_rn(u01_52(w2, w3), (double)a0);
         } else {
             const float ut = u01_23(w0), us = u01_23(w2);
             const float tau = __fdividef(-__logf(ut), (float)a0);

@@ -1,7 +1,8 @@
 // Evaluates a generated model header (jit_model.h, from
 // tests/jit_header_dump.cpp) on the host: the CUDA intrinsics it calls are
 // replaced by the IEEE-754 operations they denote (round to nearest, no
-// contraction: compile with -ffp-contract=off), so the FP64 results are
+// contraction: compile with -ffp-contract=off), and its integer-to-double
+// conversions are the library's own (smc_fp64i.h), so the FP64 results are
 // those of the GPU bit for bit.  Reads R rate constants, then states (S
 // counts each) until end of input; per state prints the FP64 prefix sums
 // (bit patterns, hex), the positive-propensity mask, the FP32 prefix sums,
@@ -28,7 +29,10 @@ static inline long long __double_as_longlong(double d)
     memcpy(&v, &d, 8);
     return v;
 }
-static inline double int_to_double(long long v) { return (double)v; }
+// the integer-pipe conversions the generated code calls (smc_fp64i.h,
+// compiled for the host): their exactness is part of what is checked
+#include "smc_fp64i.h"
+static inline double int_to_double(long long v) { return fp64i_i2d(v); }
 
 #include "jit_model.h"
 

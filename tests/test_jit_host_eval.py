@@ -75,7 +75,7 @@ def _header(dumper, model, atoms, name):
     inc.mkdir()
     (inc / 'jit_model.h').write_text(r.stdout)
     ev = str(inc / 'eval')
-    subprocess.run([gxx, '-O1', '-std=c++17', '-ffp-contract=off', '-I', str(inc),
+    subprocess.run([gxx, '-O1', '-std=c++17', '-ffp-contract=off', '-I', str(inc), '-I', CSRC,
                     os.path.join(ROOT, 'tests', 'jit_host_eval.cpp'), '-o', ev], check=True)
     return ev
 
