@@ -38,7 +38,7 @@ METRIC = 'verified trajectories/s & SSA events/s at fixed 95% Wilson width, plai
 # (ncu, 262,144-trajectory launch: the tables read once per block; the figure
 # does not grow with the trajectories); None when not taken for the kernel
 # as it stands.
-TRAFFIC_PLAIN = 1546496
+TRAFFIC_PLAIN = 1820160
 WORKLOAD = ('Lotka-Volterra X->2X 1.0, X+Y->2Y 0.005, Y->0 0.6, X0=Y0=1000; G[0,30](X>0 & Y>0); '
             '1,000,000 trajectories per step; 99% Wilson half-width 0.001')
 
