@@ -539,8 +539,17 @@ __global__ void __launch_bounds__(kTcThreads) mlp_infer_kernel(const float *__re
         const float z = __uint_as_float(zc[0]) + __uint_as_float(zc[1]);
         if (need) g_out[row] = 1.0f / (1.0f + expf(-z));
     }
-    // release tensor memory once every MMA and load of this CTA has finished
-    if (failed && gt == 0) tc_wait(bar, phase ^ 1);
+    // Release tensor memory once every MMA and load of this CTA has finished.
+    // A pipeline that gave up waits again (bounded) for the completion of its
+    // last committed MMAs: up to four more periods of kTcWaitNs.  Only if the
+    // tensor cores never report it does the CTA release the memory without
+    // the confirmation (a CTA may not exit holding tensor memory), and it
+    // records that case (err = 2) for the host.
+    if (failed && gt == 0) {
+        bool drained = false;
+        for (int k = 0; k < 4 && !drained; ++k) drained = tc_wait(bar, phase ^ 1);
+        if (!drained) atomicExch(err, 2);
+    }
     tc_fence_before();
     __syncthreads();
     if (warp == 0) {
@@ -1011,7 +1020,10 @@ int smc_mlp_train(smc_mlp *m, const float *x, const float *y, uint64_t n, int ep
 int smc_mlp_predict_masked(smc_mlp *m, const float *x, uint64_t n, const uint8_t *skip, float *g, void *stream)
 {
     if (!m || (n && (!x || !g))) return SMC_E_INVALID_ARG;
-    if (*m->h_err) return mfail(m, SMC_E_CUDA, "an earlier inference launch gave up waiting for the tensor cores");
+    if (*m->h_err)
+        return mfail(m, SMC_E_CUDA, *m->h_err == 2 ? "an earlier inference launch gave up waiting for the tensor "
+                                                     "cores and released tensor memory without their completion"
+                                                   : "an earlier inference launch gave up waiting for the tensor cores");
     if (n == 0) return SMC_OK;
     MCK(cudaSetDevice(m->device));
     cudaStream_t s = stream ? (cudaStream_t)stream : m->stream;
