@@ -368,10 +368,26 @@ int smc_simulate_snapshot(smc_ctx *ctx, int precision, uint64_t seed, uint64_t t
                           uint64_t n_traj, double t_snap, int stop_at_snap, const smc_sim_out *out,
                           uint8_t *snap, int32_t *x_snap, uint32_t *e_snap, void *stream);
 
-/* Features of snapshots (single-network contexts): row (m, k) of feat
- * [n_inst * n_traj][S + 1 + R] (FP32, device) = x_snap / x_scale (S values),
- * t_snap / t_scale, then the log rate constants of instance m centred on
- * their mean over the instances.  x_scale: host [S]. */
+/* Which quantities the snapshot features carry (single-network contexts;
+ * not in the paper): the counts of n_species chosen species (species[i] in
+ * [0, S), in that order; n_species = 0: every species, the default), the
+ * time, then, if with_rates != 0, ln c_k - ref_k for every reaction k, with
+ * ref = log_rate_ref (host [R], copied) or, when it is NULL, the mean of
+ * ln c_k over the loaded instances (the default).  A context holding one
+ * held-out instance of a family passes the family's reference, so that its
+ * rate features match the ones the network was trained on.  At most 16
+ * features in all.  Reset to the default by every model load.
+ * Errors: STATE (no model), UNSUPPORTED (batched networks, more than 16
+ * features), INVALID_ARG (index out of range, null list with n_species > 0,
+ * a non-finite reference). */
+int smc_set_features(smc_ctx *ctx, const int32_t *species, int n_species, int with_rates,
+                     const double *log_rate_ref);
+
+/* Features of snapshots (single-network contexts), as smc_set_features
+ * chose them: row (m, k) of feat [n_inst * n_traj][F] (FP32, device), F =
+ * Fs + 1 + (R or 0) = the chosen species' counts / x_scale (Fs values),
+ * t_snap / t_scale, then the log-rate features of instance m.  x_scale: host
+ * [Fs]. */
 int smc_snapshot_features(smc_ctx *ctx, uint64_t n_traj, const int32_t *x_snap, double t_snap,
                           const float *x_scale, float t_scale, float *feat, void *stream);
 
@@ -412,7 +428,8 @@ int smc_mlp_predict_masked(smc_mlp *mlp, const float *x, uint64_t n, const uint8
                            void *stream);
 
 /* Control-variate estimate for a single-instance context (two-phase
- * sampling): n_full trajectories run to their verdict Y, n_prefix further
+ * sampling; the network's inputs must be the snapshot features as
+ * smc_set_features chose them, else INVALID_ARG): n_full trajectories run to their verdict Y, n_prefix further
  * trajectories only to t_snap; G = Y when the verdict was fixed before t_snap,
  * else G = g(snapshot features).  p_hat = mean_full(Y - beta G) +
  * beta mean_all(G), unbiased for any fixed beta.  Var is estimated from the

@@ -116,6 +116,7 @@ class Context:
         self.n_inst = model.n_inst
         self.s_max = model.n_species
         self._n_reactions = model.n_reactions
+        self._feat = None  # smc_load_model resets the feature choice
         self._batch = None
         factors = list(getattr(model, 'factors', None) or [])
         if factors:
@@ -292,12 +293,28 @@ class Context:
                                             _stream(s)), 'smc_simulate_snapshot')
         return out
 
+    def set_features(self, species=None, with_rates: bool = True, log_rate_ref=None):
+        """smc_set_features: which species (indices; None = all), whether the
+        log-rate features follow, and their reference (None = the mean over
+        the loaded instances)."""
+        idx = np.ascontiguousarray([] if species is None else species, np.int32)
+        ref = None if log_rate_ref is None else np.ascontiguousarray(log_rate_ref, np.float64)
+        self._check(N.smc_set_features(self.h, idx.ctypes.data_as(ctypes.c_void_p) if idx.size else None,
+                                       int(idx.size), int(bool(with_rates)),
+                                       ref.ctypes.data_as(ctypes.c_void_p) if ref is not None else None),
+                    'smc_set_features')
+        self._feat = (idx.size or self.s_max) + 1 + (int(self._n_reactions) if with_rates else 0)
+
+    def feature_count(self) -> int:
+        return getattr(self, '_feat', None) or self.s_max + 1 + int(self._n_reactions)
+
     def snapshot_features(self, x_snap, t_snap: float, x_scale, t_scale: float, stream=None):
-        """Features [n_inst * n_traj, S + 1 + R] (torch CUDA float32) of x_snap."""
+        """Features [n_inst * n_traj, F] (torch CUDA float32) of x_snap, F as
+        set_features chose (default S + 1 + R)."""
         import torch
         n_traj = x_snap.shape[1]
-        S, R = self.s_max, int(self._n_reactions)
-        feat = torch.zeros((self.n_inst * n_traj, S + 1 + R), dtype=torch.float32, device=x_snap.device)
+        feat = torch.zeros((self.n_inst * n_traj, self.feature_count()), dtype=torch.float32,
+                           device=x_snap.device)
         xs = np.ascontiguousarray(x_scale, np.float32)
         s = stream if stream is not None else torch.cuda.current_stream(x_snap.device)
         self._check(N.smc_snapshot_features(self.h, n_traj, ctypes.c_void_p(x_snap.data_ptr()), float(t_snap),

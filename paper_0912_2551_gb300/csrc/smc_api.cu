@@ -16,6 +16,7 @@
 #include "smc_compile.h"
 #include "smc_internal.h"
 #include "smc_jit.h"
+#include "smc_mlp.h"
 #include "smc_cme.h"
 
 namespace {
@@ -103,8 +104,13 @@ struct smc_ctx {
     double *h_wilson = nullptr;
     uint8_t *d_record = nullptr;
     uint64_t record_n = 0, record_valid = 0;
-    float *d_feat_aux = nullptr;  // feature scales and centred log rates
+    float *d_feat_aux = nullptr;  // feature scales, species indices and log-rate features
     size_t feat_aux_n = 0;
+    // the snapshot features (smc_set_features): species (empty: all), rate
+    // features on or off, their reference (empty: the mean over the instances)
+    std::vector<int32_t> feat_species;
+    int feat_rates = 1;
+    std::vector<double> feat_ref;
     uint64_t *d_logtab = nullptr;  // table of the FP64 path's logarithm (lives with the context)
     // control-variate estimator's buffers, grown on demand and kept (a
     // cudaFree per call would synchronise the device)
@@ -896,6 +902,9 @@ static int load_common(smc_ctx *ctx, int n_inst, const int32_t *S, const int32_t
     ctx->s_max = *std::max_element(Sv.begin(), Sv.end());
     ctx->batch = !same_network;
     ctx->have_model = true;
+    ctx->feat_species.clear();
+    ctx->feat_rates = 1;
+    ctx->feat_ref.clear();
     ctx->f_reac.clear();
     ctx->f_spec.clear();
     ctx->f_pow.clear();
@@ -1528,6 +1537,35 @@ int smc_simulate_snapshot(smc_ctx *ctx, int precision, uint64_t seed, uint64_t t
     return SMC_OK;
 }
 
+// Number of snapshot features of a single-network context (see smc_set_features).
+static int feature_count(const smc_ctx *ctx)
+{
+    const int Fs = ctx->feat_species.empty() ? ctx->S[0] : (int)ctx->feat_species.size();
+    return Fs + 1 + (ctx->feat_rates ? ctx->R[0] : 0);
+}
+
+int smc_set_features(smc_ctx *ctx, const int32_t *species, int n_species, int with_rates,
+                     const double *log_rate_ref)
+{
+    if (!ctx) return SMC_E_INVALID_ARG;
+    if (!ctx->have_model) return fail(ctx, SMC_E_STATE, "load a model first");
+    if (ctx->batch) return fail(ctx, SMC_E_UNSUPPORTED, "features need a single network");
+    const int S = ctx->S[0], R = ctx->R[0];
+    if (n_species < 0 || (n_species > 0 && !species)) return fail(ctx, SMC_E_INVALID_ARG, "bad species list");
+    for (int i = 0; i < n_species; ++i)
+        if (species[i] < 0 || species[i] >= S) return fail(ctx, SMC_E_INVALID_ARG, "species index out of range");
+    const int F = (n_species ? n_species : S) + 1 + (with_rates ? R : 0);
+    if (F > 16) return fail(ctx, SMC_E_UNSUPPORTED, "more than 16 features");
+    if (with_rates && log_rate_ref)
+        for (int j = 0; j < R; ++j)
+            if (!std::isfinite(log_rate_ref[j])) return fail(ctx, SMC_E_INVALID_ARG, "log_rate_ref not finite");
+    ctx->feat_species.assign(species, species + n_species);
+    ctx->feat_rates = with_rates ? 1 : 0;
+    if (with_rates && log_rate_ref) ctx->feat_ref.assign(log_rate_ref, log_rate_ref + R);
+    else ctx->feat_ref.clear();
+    return SMC_OK;
+}
+
 int smc_snapshot_features(smc_ctx *ctx, uint64_t n_traj, const int32_t *x_snap, double t_snap,
                           const float *x_scale, float t_scale, float *feat, void *stream)
 {
@@ -1535,28 +1573,38 @@ int smc_snapshot_features(smc_ctx *ctx, uint64_t n_traj, const int32_t *x_snap, 
     if (!ctx->have_model) return fail(ctx, SMC_E_STATE, "load a model first");
     if (ctx->batch) return fail(ctx, SMC_E_UNSUPPORTED, "features need a single network");
     if (!x_snap || !x_scale || !feat || !(t_scale > 0.0f)) return fail(ctx, SMC_E_INVALID_ARG, "bad feature arguments");
-    const int S = ctx->S[0], R = ctx->R[0], n = ctx->n_inst;
-    if (S + 1 + R > 16) return fail(ctx, SMC_E_UNSUPPORTED, "more than 16 features (S + 1 + R)");
-    for (int i = 0; i < S; ++i)
+    const int S = ctx->S[0], n = ctx->n_inst;
+    const int R = ctx->feat_rates ? ctx->R[0] : 0;
+    if (feature_count(ctx) > 16) return fail(ctx, SMC_E_UNSUPPORTED, "more than 16 features (see smc_set_features)");
+    std::vector<int32_t> sidx(ctx->feat_species);
+    if (sidx.empty())
+        for (int i = 0; i < S; ++i) sidx.push_back(i);
+    const int Fs = (int)sidx.size();
+    for (int i = 0; i < Fs; ++i)
         if (!(x_scale[i] > 0.0f)) return fail(ctx, SMC_E_INVALID_ARG, "x_scale must be > 0");
     CK(cudaSetDevice(ctx->device));
     cudaStream_t s = stream ? (cudaStream_t)stream : ctx->stream;
-    // centred log rate constants per instance
-    std::vector<float> lr((size_t)n * R), aux(S + (size_t)n * R);
+    // log rate constants per instance, minus the reference (given, or their
+    // mean over the instances)
+    std::vector<float> aux(2 * (size_t)Fs + (size_t)n * R);
     for (int j = 0; j < R; ++j) {
-        double mean = 0.0;
-        for (int m = 0; m < n; ++m) {
-            const double c = ctx->rates[ctx->rate_off[m] + j];
-            mean += c > 0.0 ? std::log(c) : 0.0;
+        double ref = 0.0;
+        if (!ctx->feat_ref.empty()) {
+            ref = ctx->feat_ref[j];
+        } else {
+            for (int m = 0; m < n; ++m) {
+                const double c = ctx->rates[ctx->rate_off[m] + j];
+                ref += c > 0.0 ? std::log(c) : 0.0;
+            }
+            ref /= n;
         }
-        mean /= n;
         for (int m = 0; m < n; ++m) {
             const double c = ctx->rates[ctx->rate_off[m] + j];
-            lr[(size_t)m * R + j] = (float)((c > 0.0 ? std::log(c) : 0.0) - mean);
+            aux[2 * (size_t)Fs + (size_t)m * R + j] = (float)((c > 0.0 ? std::log(c) : 0.0) - ref);
         }
     }
-    std::memcpy(aux.data(), x_scale, S * sizeof(float));
-    std::memcpy(aux.data() + S, lr.data(), lr.size() * sizeof(float));
+    std::memcpy(aux.data(), x_scale, Fs * sizeof(float));
+    std::memcpy(aux.data() + Fs, sidx.data(), Fs * sizeof(int32_t));  // indices as their bits
     if (ctx->feat_aux_n < aux.size()) {
         dfree(ctx->d_feat_aux);
         CK(cudaMalloc(&ctx->d_feat_aux, aux.size() * sizeof(float)));
@@ -1564,8 +1612,9 @@ int smc_snapshot_features(smc_ctx *ctx, uint64_t n_traj, const int32_t *x_snap, 
     }
     CK(cudaMemcpyAsync(ctx->d_feat_aux, aux.data(), aux.size() * sizeof(float), cudaMemcpyHostToDevice, s));
     CK(cudaStreamSynchronize(s));  // aux is a host temporary
-    if (smc_launch_snapshot_features((uint64_t)n * n_traj, n_traj, S, R, ctx->s_max, x_snap, ctx->d_feat_aux,
-                                     (float)(t_snap / t_scale), ctx->d_feat_aux + S, feat, s))
+    if (smc_launch_snapshot_features((uint64_t)n * n_traj, n_traj, Fs,
+                                     reinterpret_cast<const int32_t *>(ctx->d_feat_aux + Fs), R, ctx->s_max, x_snap,
+                                     ctx->d_feat_aux, (float)(t_snap / t_scale), ctx->d_feat_aux + 2 * Fs, feat, s))
         return fail(ctx, SMC_E_CUDA, "feature kernel launch failed");
     return SMC_OK;
 }
@@ -1582,7 +1631,9 @@ int smc_estimate_cv(smc_ctx *ctx, smc_mlp *mlp, double confidence, double half_w
         !std::isfinite(beta))
         return fail(ctx, SMC_E_INVALID_ARG, "bad confidence, half width, pilot or beta");
     const uint64_t kPrefixBase = 1ull << 31;
-    const int S = ctx->S[0], R = ctx->R[0], F = S + 1 + R;
+    const int F = feature_count(ctx);
+    if (smc_mlp_inputs(mlp) != F)
+        return fail(ctx, SMC_E_INVALID_ARG, "the network's inputs differ from the snapshot features (smc_set_features)");
     const double z = z_of(confidence);
     int rc = prepare(ctx);
     if (rc) return rc;

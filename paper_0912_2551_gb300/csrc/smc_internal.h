@@ -203,8 +203,8 @@ int smc_launch_queue_init(const SsaParams &p, void *stream);
 int smc_launch_replay(const ReplayParams &p, void *stream);
 int smc_launch_log_batch(const uint64_t *tab, const double *u, uint64_t n, double *out, void *stream);
 int smc_launch_div_batch(const double *num, const double *den, uint64_t n, double *out, void *stream);
-int smc_launch_snapshot_features(uint64_t n_rows, uint64_t n_traj, int S, int R, int x_stride,
-                                 const int32_t *x_snap, const float *x_scale, float t_feat,
+int smc_launch_snapshot_features(uint64_t n_rows, uint64_t n_traj, int Fs, const int32_t *sidx, int R,
+                                 int x_stride, const int32_t *x_snap, const float *x_scale, float t_feat,
                                  const float *lograte, float *feat, void *stream);
 int smc_launch_cv_sums(uint64_t n, const uint8_t *y, const uint8_t *snap, const float *g, const uint32_t *e_pre,
                        int prefix, double *sums, void *stream);

@@ -541,27 +541,29 @@ int smc_launch_div_batch(const double *num, const double *den, uint64_t n, doubl
 // ---------------------------------------------------------------------------
 // Snapshot features: row (m, k) = x_snap / x_scale, t_snap / t_scale, the
 // instance's centred log rate constants (zero for rows without a snapshot).
-__global__ void snapshot_features_kernel(uint64_t n_rows, uint64_t n_traj, int S, int R, int x_stride,
-                                         const int32_t *x_snap, const float *x_scale, float t_feat,
+// Row (m, k): the chosen species' counts scaled (Fs values, species sidx[i]),
+// the time, then R log-rate features of instance m (R = 0: none).
+__global__ void snapshot_features_kernel(uint64_t n_rows, uint64_t n_traj, int Fs, const int32_t *sidx, int R,
+                                         int x_stride, const int32_t *x_snap, const float *x_scale, float t_feat,
                                          const float *lograte, float *feat)
 {
     const uint64_t row = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (row >= n_rows) return;
     const uint64_t m = row / n_traj;
-    const int F = S + 1 + R;
+    const int F = Fs + 1 + R;
     float *f = feat + row * F;
-    for (int i = 0; i < S; ++i) f[i] = (float)x_snap[row * x_stride + i] / x_scale[i];
-    f[S] = t_feat;
-    for (int j = 0; j < R; ++j) f[S + 1 + j] = lograte[m * R + j];
+    for (int i = 0; i < Fs; ++i) f[i] = (float)x_snap[row * x_stride + sidx[i]] / x_scale[i];
+    f[Fs] = t_feat;
+    for (int j = 0; j < R; ++j) f[Fs + 1 + j] = lograte[m * R + j];
 }
 
-int smc_launch_snapshot_features(uint64_t n_rows, uint64_t n_traj, int S, int R, int x_stride,
-                                 const int32_t *x_snap, const float *x_scale, float t_feat,
+int smc_launch_snapshot_features(uint64_t n_rows, uint64_t n_traj, int Fs, const int32_t *sidx, int R,
+                                 int x_stride, const int32_t *x_snap, const float *x_scale, float t_feat,
                                  const float *lograte, float *feat, void *stream)
 {
     if (n_rows == 0) return 0;
     snapshot_features_kernel<<<(unsigned)((n_rows + 255) / 256), 256, 0, (cudaStream_t)stream>>>(
-        n_rows, n_traj, S, R, x_stride, x_snap, x_scale, t_feat, lograte, feat);
+        n_rows, n_traj, Fs, sidx, R, x_stride, x_snap, x_scale, t_feat, lograte, feat);
     return to_code(cudaGetLastError());
 }
 

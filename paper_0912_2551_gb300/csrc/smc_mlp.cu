@@ -930,6 +930,12 @@ void smc_mlp_destroy(smc_mlp *m)
 
 const char *smc_mlp_last_error(const smc_mlp *m) { return m ? m->err.c_str() : ""; }
 
+}  // extern "C"
+
+int smc_mlp_inputs(const smc_mlp *m) { return m ? m->n_in : 0; }
+
+extern "C" {
+
 int smc_mlp_get_params(smc_mlp *m, float *host)
 {
     if (!m || !host) return SMC_E_INVALID_ARG;

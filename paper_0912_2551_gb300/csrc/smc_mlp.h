@@ -22,3 +22,7 @@ enum {
     MLP_OFF_B4 = MLP_OFF_W4 + MLP_H,
     MLP_NPARAM = MLP_OFF_B4 + 1
 };
+
+struct smc_mlp;
+// The network's number of input features (library-internal).
+int smc_mlp_inputs(const smc_mlp *m);
