@@ -53,7 +53,9 @@ def _issue_roofline(events_per_s, ops_per_event, kernel):
             'peak_source': f'{n_sm} SMs x 4 x 32 lanes x {f / 1e6:.0f} MHz ({src})'}
 
 
-def _timed_simulate(ctx, precision, n, steps, warmup, seed=0, confidence=0.95, label='steps'):
+def _timed_simulate(ctx, precision, n, steps, warmup, seed=0, confidence=0.95, label='steps', warm_n=None):
+    """Device time per step of `steps` simulate calls of n trajectories per
+    instance, after `warmup` calls of warm_n (default n) trajectories."""
     import torch
     dev = torch.device('cuda', 0)
     stream = torch.cuda.Stream(dev)
@@ -61,8 +63,8 @@ def _timed_simulate(ctx, precision, n, steps, warmup, seed=0, confidence=0.95, l
     wil = torch.zeros((ctx.n_inst, 3), dtype=torch.float64, device=dev)
     with torch.cuda.stream(stream):
         for _ in range(warmup):
-            ctx.simulate(precision, seed=seed, traj_begin=0, n_traj=n, confidence=confidence, outputs=(),
-                         counts=counts, wilson=wil, stream=stream)
+            ctx.simulate(precision, seed=seed, traj_begin=0, n_traj=warm_n or n, confidence=confidence,
+                         outputs=(), counts=counts, wilson=wil, stream=stream)
     torch.cuda.synchronize()
     counts.zero_()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
@@ -206,13 +208,16 @@ def _predicted_cost_ratio(resid, r):
     return (math.sqrt(resid * (1 - r)) + math.sqrt(rho2 * r)) ** 2
 
 
-def _three_arms(smc, torch, inst, prop, net, t_c, x_scale, t_scale, beta, conf, eps, seed):
+def _three_arms(smc, torch, inst, prop, net, t_c, x_scale, t_scale, beta, conf, eps, seed, ref=None):
     """One held-out instance to the same Wilson half-width three ways: plain
-    FP64 (Fig. 2), plain mixed (Fig. 2), and mixed + control variate."""
+    FP64 (Fig. 2), plain mixed (Fig. 2), and mixed + control variate (rate
+    features centred on the family's reference `ref`, when given)."""
     out = {}
     with smc.Context(0) as ctx:
         ctx.load_model(inst)
         ctx.load_property(prop)
+        if ref is not None:
+            ctx.set_features(log_rate_ref=ref)
         for prec in ('plain', 'mixed'):
             ctx.estimate(conf, eps, seed=seed + 500, precision=prec, sampling='fixed', fixed_n=1000)  # warm
         torch.cuda.synchronize()
@@ -255,8 +260,9 @@ def _train(ctx, smc, torch, t_c, n_snap, x_scale, t_scale, seed):
 def surrogate(args):
     """Control variate on the Lotka-Volterra family (the configured
     workload): a sweep over the checkpoint t_c, each point training its own
-    network; then the same estimator on a linear birth-death survival
-    problem, where a checkpoint settles the verdict early."""
+    network on 2M prefixes still undecided at t_c; then the same estimator
+    on a linear birth-death survival problem, where a checkpoint settles the
+    verdict early."""
     import torch
     import paper_0912_2551_gb300 as smc
     import workloads
@@ -264,15 +270,17 @@ def surrogate(args):
     x_scale, t_scale = np.array([1000.0, 1000.0], np.float32), 30.0
     fam, p = workloads.lotka_volterra_family(512, seed=1)
     test, _ = workloads.lotka_volterra_family(4, seed=2)
+    ref = np.log(np.asarray(fam.rates, np.float64)).mean(axis=0)  # the family's log-rate centre
     sweep = []
     for t_c in (0.5, 1.0, 2.0, 5.0):
         with smc.Context(0) as ctx:
             ctx.load_model(fam)
             ctx.load_property(p)
-            net, tr = _train(ctx, smc, torch, t_c, 1_000_000, x_scale, t_scale, seed=11)
+            ctx.set_features(log_rate_ref=ref)
+            net, tr = _train(ctx, smc, torch, t_c, 2_000_000, x_scale, t_scale, seed=11)
             beta, resid, r, alive = _held_out(ctx, net, t_c, x_scale, t_scale, seed=12, n=256)
         rows = [_three_arms(smc, torch, test.instance(i), p, net, t_c, x_scale, t_scale, beta, conf, eps,
-                            1000 + 10 * i) for i in range(test.n_inst)]
+                            1000 + 10 * i, ref) for i in range(test.n_inst)]
         T = {k: sum(rw[k]['s'] for rw in rows) for k in ('plain', 'mixed', 'cv')}
         E = {k: sum(rw[k]['events'] for rw in rows) for k in ('plain', 'mixed', 'cv')}
         sweep.append(dict(t_c=t_c, alive_share=alive, prefix_cost_share=r, residual_variance_share=resid,
@@ -320,39 +328,106 @@ def surrogate(args):
                         'peak_source': f'cuBLAS bf16 burst ({src})'}})
 
 
+CASCADE_FEATURES = ('KKKs', 'KKP', 'KKPP', 'KP', 'KPP', 'KP_KKPP', 'KPP_KPase')
+
+
 def cascade(args):
+    """The configured cascade: 256 rate-perturbed instances x 100,000
+    trajectories per step in one batched launch (mixed path), for the literal
+    formula and the KPP<2000 variant; the FP64 path on a 1,000-trajectory
+    subsample per instance; and the variant's surrogate-assisted estimate (a
+    network trained on prefixes of the batch at t_c = 30, seven counts and
+    the time as its inputs) against the plain estimator on four held-out
+    instances."""
+    import torch
     import oracle
     import paper_0912_2551_gb300 as smc
     import workloads
     out = {}
-    n = args.traj or 2000
+    n = args.traj or 100_000
+    steps, warm = 1, 3
     for variant in (False, True):
         m, p = workloads.mapk_cascade(256, seed=5, variant=variant)
         name = 'variant' if variant else 'literal'
         with smc.Context(0) as ctx:
             ctx.load_model(m)
             ctx.load_property(p)
-            ms, c, wil, clk = _timed_simulate(ctx, 'mixed', n, max(1, min(args.steps, 3)), 1, seed=0, label=name)
+            ms, c, wil, clk = _timed_simulate(ctx, 'mixed', n, steps, warm, seed=0, label=name,
+                                              warm_n=max(1, n // 100))
             kname = bench.kernel_name(ctx, 'mixed')
-            msp, cp, _, _ = _timed_simulate(ctx, 'plain', min(n, 200), 1, 1, seed=0, label=name)
-        ev = float(c[:, 2].sum())
+            n64 = min(n, 1000)
+            msp, cp, _, _ = _timed_simulate(ctx, 'plain', n64, 1, warm, seed=0, label=name, warm_n=max(1, n64 // 10))
+        ev, evp = float(c[:, 2].sum()), float(cp[:, 2].sum())
         out[name] = dict(
             ms=ms, traj_s=256 * n / (ms / 1e3), events_per_s=ev / (ms / 1e3), events_per_traj=ev / (256 * n),
-            yes=int(c[:, 0].sum()), plain_traj_s=256 * min(n, 200) / (msp / 1e3), clocks=clk)
+            yes=int(c[:, 0].sum()), p_per_instance_quartiles=np.percentile(c[:, 0] / np.maximum(c[:, 1], 1),
+                                                                          [0, 25, 50, 75, 100]).tolist(),
+            plain_fp64=dict(trajectories_per_instance=n64, ms=msp, traj_s=256 * n64 / (msp / 1e3),
+                            events_per_s=evp / (msp / 1e3)),
+            clocks=clk)
+    # surrogate on the variant: train on prefixes at t_c, then four held-out
+    # instances to the same 95% half-width (0.01) with and without it
+    mv, pv = workloads.mapk_cascade(256, seed=5, variant=True)
+    idx = [workloads.MAPK_SPECIES.index(s_) for s_ in CASCADE_FEATURES]
+    t_c, xs, ts = 30.0, np.full(len(idx), 2000.0, np.float32), 200.0
+    with smc.Context(0) as ctx:
+        ctx.load_model(mv)
+        ctx.load_property(pv)
+        ctx.set_features(species=idx, with_rates=False)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        o = ctx.simulate_snapshot('mixed', seed=21, traj_begin=0, n_traj=4000, t_snap=t_c)
+        feat = ctx.snapshot_features(o['x_snap'], t_c, xs, ts)
+        alive = (o['snap'] == 0).reshape(-1)
+        x = feat[alive].contiguous()
+        y = o['verdict'].reshape(-1)[alive].to(torch.float32).contiguous()
+        torch.cuda.synchronize()
+        t_data = time.perf_counter() - t0
+        net = smc.Mlp(len(idx) + 1, seed=5)
+        t1 = time.perf_counter()
+        loss = net.train(x, y, epochs=4, batch=8192, lr=1e-3, seed=6)
+        torch.cuda.synchronize()
+        t_train = time.perf_counter() - t1
+    held = []
+    for i in (1, 3, 5, 7):
+        with smc.Context(0) as ctx:
+            ctx.load_model(mv.instance(i))
+            ctx.load_property(pv)
+            ctx.set_features(species=idx, with_rates=False)
+            ctx.estimate(0.95, 0.01, seed=5, precision='mixed', sampling='fixed', fixed_n=500)  # warm
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            pl = ctx.estimate(0.95, 0.01, seed=60 + i, precision='mixed', sampling='iterative')[0]
+            t_pl = time.perf_counter() - t0
+            t0 = time.perf_counter()
+            cv = ctx.estimate_cv(net, 0.95, 0.01, seed=70 + i, precision='mixed', t_snap=t_c, x_scale=xs,
+                                 t_scale=ts, beta=1.0, pilot=1000)
+            t_cv = time.perf_counter() - t0
+        held.append(dict(instance=i, plain=dict(p=pl['p_hat'], n=pl['launched'], events=pl['events'], s=t_pl),
+                         cv=dict(p=cv['p_hat'], n_eff=cv['n_eff'], n_full=cv['n_full'], n_prefix=cv['n_prefix'],
+                                 events=cv['events_full'] + cv['events_prefix'], s=t_cv)))
+    surrogate = dict(t_c=t_c, features=list(CASCADE_FEATURES) + ['t'], training_rows=int(x.shape[0]),
+                     label_mean=float(y.mean()), loss=[float(v) for v in loss], data_seconds=t_data,
+                     train_seconds=t_train, held_out=held,
+                     wall_ratio_plain_over_cv=sum(h['plain']['s'] for h in held) / sum(h['cv']['s'] for h in held),
+                     event_ratio_cv_over_plain=sum(h['cv']['events'] for h in held) /
+                     sum(h['plain']['events'] for h in held))
     t0 = time.perf_counter()
-    m, p = workloads.mapk_cascade(4, seed=5, variant=False)
-    oracle.run(m, p, seed=0, instance=0, n_traj=64)
+    mo, po = workloads.mapk_cascade(4, seed=5, variant=True)
+    ro = oracle.run(mo, po, seed=0, instance=0, n_traj=256)
     cpu = time.perf_counter() - t0
-    lit = out['literal']
+    lit, var = out['literal'], out['variant']
     ops = 40 + 4 + 1 + 2 + 31 + 2 + 3 * 5 + 2 * 3 + 2
-    _line(lit['traj_s'], 'trajectories/s', max(1, min(args.steps, 3)), 1, lit['ms'],
+    _line(lit['traj_s'], 'trajectories/s', steps, warm, lit['ms'],
           'mixed (f32 propensities, f64 clock)',
-          f'three-tier cascade, 22 species, 30 reactions, 256 rate-perturbed instances x {n:,} trajectories, '
-          '(KPP<500) U[0,200] (KPP>=2000 & F[0,50] KPP<500) and the KPP<2000 variant',
-          {'events_per_s': lit['events_per_s'], 'configs': out,
-           'roofline': _issue_roofline(lit['events_per_s'], ops, kname),
-           'cpu_baseline': {'value': 64 / cpu, 'unit': 'trajectories/s', 'cores': os.cpu_count(),
-                            'kind': 'oracle', 'sample': f'64 trajectories of instance 0 (literal), {cpu:.1f} s'}})
+          f'three-tier cascade, 22 species, 30 reactions, 256 rate-perturbed instances x {n:,} trajectories per '
+          'step, one batched launch; (KPP<500) U[0,200] (KPP>=2000 & F[0,50] KPP<500) and the KPP<2000 variant',
+          {'events_per_s': lit['events_per_s'], 'configs': out, 'surrogate_variant': surrogate,
+           'warmup_trajectories_per_instance': max(1, n // 100),
+           'roofline': _issue_roofline(var['events_per_s'], ops, kname),
+           'cpu_baseline': {'value': 256 / cpu, 'unit': 'trajectories/s',
+                            'events_per_s': float(ro['events'].sum()) / cpu, 'cores': os.cpu_count(),
+                            'kind': 'oracle', 'sample': f'256 trajectories of instance 0 (variant), {cpu:.1f} s'}})
 
 
 # DRAM bytes (read + write) of one launch of the inference kernel on

@@ -413,3 +413,63 @@ def test_control_variate_pays_where_the_fate_is_settled_early(env):
     assert res['n_prefix'] > res['n_full'], res
     plain_cost = res['n_eff'] * res['events_full'] / res['n_full']
     assert (res['events_full'] + res['events_prefix']) < 0.8 * plain_cost, res
+
+
+def _family_snapshots(ctx, torch, t_snap, want, xs, ts, seed):
+    """`want` snapshot features at t_snap of trajectories still undecided
+    there, labelled by their verdicts (full runs), over every instance."""
+    feats, labels, got, begin = [], [], 0, 0
+    while got < want:
+        o = ctx.simulate_snapshot('mixed', seed=seed, traj_begin=begin, n_traj=4096, t_snap=t_snap)
+        f = ctx.snapshot_features(o['x_snap'], t_snap, xs, ts)
+        alive = (o['snap'] == 0).reshape(-1)
+        feats.append(f[alive])
+        labels.append(o['verdict'].reshape(-1)[alive].to(torch.float32))
+        got += int(alive.sum().item())
+        begin += 4096
+    return torch.cat(feats)[:want].contiguous(), torch.cat(labels)[:want].contiguous(), begin
+
+
+@pytest.mark.gpu
+def test_control_variate_lotka_volterra_family(env):
+    # The surrogate workload as configured: the Lotka-Volterra family (rates
+    # times log-uniform factors in [0.7, 1.3]), G[0,30](X>0 & Y>0), a network
+    # trained on 2M prefixes at t_c = 5 labelled by their verdicts, 95% Wilson
+    # half-width 0.002.  On held-out instances the control-variate estimate
+    # must agree with a plain estimate of 10^6 trajectories within its own
+    # error (unbiased for any network); the plain iterative estimate to the
+    # same half-width runs beside it and the gain is reported, whatever it is.
+    torch, smc = env
+    fam, p = workloads.lotka_volterra_family(512, seed=1)
+    test, _ = workloads.lotka_volterra_family(2, seed=2)
+    t_c, xs, ts = 5.0, np.array([1000.0, 1000.0], np.float32), 30.0
+    ref = np.log(np.asarray(fam.rates, np.float64)).mean(axis=0)
+    with smc.Context(0) as ctx:
+        ctx.load_model(fam)
+        ctx.load_property(p)
+        ctx.set_features(log_rate_ref=ref)
+        x, y, used = _family_snapshots(ctx, torch, t_c, 2_000_000, xs, ts, seed=11)
+        torch.cuda.synchronize()
+        assert x.shape == (2_000_000, 6) and 0.0 < float(y.mean()) < 1.0
+        net = smc.Mlp(6, seed=7)
+        loss = net.train(x, y, epochs=4, batch=8192, lr=1e-3, seed=3)
+        assert loss[-1] < loss[0], loss
+    for i in range(test.n_inst):
+        with smc.Context(0) as ctx:
+            ctx.load_model(test.instance(i))
+            ctx.load_property(p)
+            ctx.set_features(log_rate_ref=ref)
+            beta, resid, calib = _held_out_beta(ctx, net, t_c, xs, ts, 40 + i)
+            cv = ctx.estimate_cv(net, 0.95, 0.002, seed=50 + i, precision='mixed', t_snap=t_c, x_scale=xs,
+                                 t_scale=ts, beta=beta, pilot=2000)
+            plain = ctx.estimate(0.95, 0.002, seed=60 + i, precision='mixed', sampling='iterative')[0]
+            big = ctx.estimate(0.95, 0.002, seed=70 + i, precision='plain', sampling='fixed', fixed_n=1_000_000)[0]
+        sd_big = math.sqrt(max(big['p_hat'] * (1 - big['p_hat']), 1e-12) / big['n'])
+        assert abs(cv['p_hat'] - big['p_hat']) <= 4 * math.sqrt(cv['var']) + 4 * sd_big, (cv, big)
+        assert cv['hi'] - cv['lo'] <= 2 * 0.002 * 1.01, cv
+        plain_events = plain['events']
+        cv_events = cv['events_full'] + cv['events_prefix']
+        print(f'instance {i}: p(10^6) {big["p_hat"]:.5f}, cv {cv["p_hat"]:.5f} (n_eff {cv["n_eff"]:.0f}, '
+              f'full {cv["n_full"]}, prefix {cv["n_prefix"]}), plain {plain["p_hat"]:.5f} (n {plain["n"]}); '
+              f'residual variance share {resid:.3f}, calibration {calib:.4f}, '
+              f'events cv / plain {cv_events / plain_events:.3f}')

@@ -234,7 +234,8 @@ def test_state_updates_keep_the_cascade_totals(orc):
     """x += v_j on a 22-species, 30-reaction network: the seven totals of
     the cascade (the whole left null space of its stoichiometry, rank 15)
     stay at their initial values and no count goes negative, over
-    trajectories of about 1.9e4 events each."""
+    trajectories of about 2.5e4 events each (the literal formula stops at
+    the first KPP = 500)."""
     m, p = workloads.mapk_cascade(n_inst=2)
     W = np.zeros((len(MAPK_TOTALS), m.n_species), np.int64)
     for i, names in enumerate(MAPK_TOTALS):

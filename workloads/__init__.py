@@ -357,35 +357,44 @@ def mapk_cascade(n_inst: int = 256, seed: int = 5, variant: bool = False,
     Ten enzymatic steps E + S <-> ES -> E + P: tier 1 activates KKK by E1 and
     deactivates it by E2; tier 2 double-phosphorylates KK by KKK* and
     dephosphorylates it by KKPase; tier 3 does the same for K by KK-PP and
-    KPase.  Rate constants are base values times a per-instance log-uniform
-    factor in [0.8, 1.25].  The property is
-    (KPP<500) U[0,200] (KPP>=2000 & F[0,50] KPP<500); ``variant=True``
-    replaces the left operand by KPP<2000.
+    KPase.  Every complex dissociates at 0.1 and converts at kcat (0.8 and
+    0.3 in tier 1, 1.0 below); the binding constants give Michaelis constants
+    (koff + kcat) / kon of 90 and 65 (tier 1), 2000 (tier 2) and 4000
+    (tier 3) molecules.  The initial state is a pulse: all 900 KKK
+    molecules active, a weak activator (E1 = 2) against E2 = 100, KK = 2400,
+    K = 6000 (counts reach about 6000), KKPase = 250, KPase = 800, so that
+    KPP rises to about 2000 near t = 40 and falls back within tens of time
+    units, and a trajectory runs about 1.4e5 events before its verdict is
+    fixed.  Rate constants are these base values times a per-instance
+    log-uniform factor in [0.8, 1.25].  ``scale`` multiplies the KKK, KK and
+    K counts.  The property is (KPP<500) U[0,200] (KPP>=2000 & F[0,50]
+    KPP<500); ``variant=True`` replaces the left operand by KPP<2000.
     """
     sp = MAPK_SPECIES
-    steps = [  # (enzyme, substrate, product, complex, kon, koff, kcat)
-        ('E1', 'KKK', 'KKKs', 'KKK_E1', 0.02, 1.0, 0.8),
-        ('E2', 'KKKs', 'KKK', 'KKKs_E2', 0.02, 1.0, 0.3),
-        ('KKKs', 'KK', 'KKP', 'KK_KKKs', 0.001, 1.0, 1.0),
-        ('KKKs', 'KKP', 'KKPP', 'KKP_KKKs', 0.001, 1.0, 1.0),
-        ('KKPase', 'KKPP', 'KKP', 'KKPP_KKPase', 0.001, 1.0, 1.0),
-        ('KKPase', 'KKP', 'KK', 'KKP_KKPase', 0.001, 1.0, 1.0),
-        ('KKPP', 'K', 'KP', 'K_KKPP', 0.0005, 1.0, 1.0),
-        ('KKPP', 'KP', 'KPP', 'KP_KKPP', 0.0005, 1.0, 1.0),
-        ('KPase', 'KPP', 'KP', 'KPP_KPase', 0.0005, 1.0, 1.0),
-        ('KPase', 'KP', 'K', 'KP_KPase', 0.0005, 1.0, 1.0),
+    koff = 0.1
+    steps = [  # (enzyme, substrate, product, complex, Michaelis constant, kcat)
+        ('E1', 'KKK', 'KKKs', 'KKK_E1', 90.0, 0.8),
+        ('E2', 'KKKs', 'KKK', 'KKKs_E2', 65.0, 0.3),
+        ('KKKs', 'KK', 'KKP', 'KK_KKKs', 2000.0, 1.0),
+        ('KKKs', 'KKP', 'KKPP', 'KKP_KKKs', 2000.0, 1.0),
+        ('KKPase', 'KKPP', 'KKP', 'KKPP_KKPase', 2000.0, 1.0),
+        ('KKPase', 'KKP', 'KK', 'KKP_KKPase', 2000.0, 1.0),
+        ('KKPP', 'K', 'KP', 'K_KKPP', 4000.0, 1.0),
+        ('KKPP', 'KP', 'KPP', 'KP_KKPP', 4000.0, 1.0),
+        ('KPase', 'KPP', 'KP', 'KPP_KPase', 4000.0, 1.0),
+        ('KPase', 'KP', 'K', 'KP_KPase', 4000.0, 1.0),
     ]
     reactions, base = [], []
-    for enz, sub, prod, cplx, kon, koff, kcat in steps:
+    for enz, sub, prod, cplx, km, kcat in steps:
         reactions.append(([enz, sub], [cplx]))
-        base.append(kon)
+        base.append((koff + kcat) / km)
         reactions.append(([cplx], [enz, sub]))
         base.append(koff)
         reactions.append(([cplx], [enz, prod]))
         base.append(kcat)
     reac, st = _net(sp, reactions)
-    init = dict(KKK=300, E1=10, E2=10, KK=1200, KKPase=60, K=3000, KPase=60)
-    x0 = np.array([int(round(init.get(s, 0) * (scale if s in ('KK', 'K', 'KKK') else 1.0)))
+    init = dict(KKKs=900, E1=2, E2=100, KK=2400, KKPase=250, K=6000, KPase=800)
+    x0 = np.array([int(round(init.get(s, 0) * (scale if s in ('KK', 'K', 'KKKs') else 1.0)))
                    for s in sp], np.int32)
     rng = np.random.default_rng(seed)
     fac = np.exp(rng.uniform(math.log(0.8), math.log(1.25), size=(n_inst, len(base))))
