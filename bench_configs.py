@@ -499,6 +499,69 @@ def surrogate_inference(args):
           f'surrogate network 6 -> 128 x 3 -> 1 on {n:,} rows of Lotka-Volterra-family features', extra)
 
 
+def _time_batch(smc, b, precision, selection, n, seed=1):
+    """Host time of one fixed-size smc_estimate over batch b (after a
+    tuning/warm-up estimate) with the given selection mode; events."""
+    import torch
+    with smc.Context(0) as ctx:
+        ctx.set_option('selection', selection)
+        ctx.load_batch(b)
+        ctx.load_property(b.properties)
+        ctx.estimate(0.95, 0.01, seed=99, precision=precision, sampling='fixed', fixed_n=max(1, n // 20))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        res = ctx.estimate(0.95, 0.01, seed=seed, precision=precision, sampling='fixed', fixed_n=n)
+        dt = time.perf_counter() - t0
+    return dt, float(sum(r['events'] for r in res))
+
+
+def large_networks(args):
+    """Reaction selection for large networks (65 to 255 reactions): the
+    batch of random_networks_large timed with the linear scan and with the
+    checkpointed running sums, both precisions; then the crossover, batches
+    of 64 networks with exactly R reactions for R from 24 to 255."""
+    import oracle
+    import paper_0912_2551_gb300 as smc
+    import workloads
+    b = workloads.random_networks_large(256, seed=8)
+    n = args.traj or 2000
+    main = {}
+    for prec in ('mixed', 'plain'):
+        for sel, name in ((1, 'linear'), (2, 'checkpoints')):
+            dt, ev = _time_batch(smc, b, prec, sel, n)
+            main[f'{prec}_{name}'] = dict(s=dt, traj_s=256 * n / dt, events_per_s=ev / dt)
+    sweep = []
+    for R in (24, 48, 96, 160, 255):
+        bb = workloads.random_networks(64, seed=20 + R, s_range=(16, 48), r_range=(R, R), theta_above_start=True)
+        row = dict(R=R)
+        for prec in ('mixed', 'plain'):
+            for sel, name in ((1, 'linear'), (2, 'checkpoints')):
+                dt, ev = _time_batch(smc, bb, prec, sel, 1000)
+                row[f'{prec}_{name}_events_per_s'] = ev / dt
+            row[f'{prec}_speedup'] = row[f'{prec}_checkpoints_events_per_s'] / row[f'{prec}_linear_events_per_s']
+        sweep.append(row)
+    t0 = time.perf_counter()
+    k = 0
+    for i in range(0, 256, 32):
+        oracle.run(b.models[i], b.properties[i], seed=1, instance=i, n_traj=8)
+        k += 8
+    cpu = time.perf_counter() - t0
+    best = main['mixed_checkpoints']
+    R = np.array([mm.n_reactions for mm in b.models])
+    ops = 40 + 4 + 1 + 2 + 2 * (SEL_BLOCK_SCAN + float(np.mean((R + 15) // 16))) + 2.5 + 3 * 8 + 2 + 2
+    _line(best['traj_s'], 'trajectories/s', 1, 1, 1e3 * best['s'], 'mixed (f32 propensities, f64 clock)',
+          f'256 random mass-action networks (S 16..64, R 65..255) x {n:,} trajectories, F[0,50](X_k>=theta), '
+          'selection by running sums checkpointed every 16 reactions vs the linear scan',
+          {'events_per_s': best['events_per_s'], 'arms': main, 'crossover': sweep,
+           'roofline': _issue_roofline(best['events_per_s'], ops, 'ssa_kernel<mixed>'),
+           'cpu_baseline': {'value': k / cpu, 'unit': 'trajectories/s', 'cores': os.cpu_count(),
+                            'kind': 'oracle', 'sample': f'8 trajectories of every 32nd instance, {cpu:.1f} s'}})
+
+
+SEL_BLOCK_SCAN = 8  # expected running sums formed inside the selected block
+
+
 def run(args):
     {'immigration_death': immigration_death, 'random_networks': random_networks, 'surrogate': surrogate,
-     'cascade': cascade, 'surrogate_inference': surrogate_inference}[args.config](args)
+     'cascade': cascade, 'surrogate_inference': surrogate_inference,
+     'large_networks': large_networks}[args.config](args)

@@ -94,6 +94,12 @@ extern "C" {
 #define SMC_OPT_JIT 7             /* 1 = model-specialized kernels when every instance shares one
                                      structure with S, R <= 32 (default 1; compiled at run time
                                      with NVRTC, same results as the generic kernels) */
+#define SMC_OPT_SELECTION 8       /* reaction selection of the generic kernel (Eq. 2b):
+                                     0 = automatic (running sums checkpointed every 16
+                                     reactions for networks of more than 64 reactions,
+                                     else a linear scan), 1 = linear scan, 2 = checkpoints
+                                     for networks of more than 16 reactions; the same
+                                     trajectories in every mode (default 0) */
 
 /* A node of the formula in postfix order: operands precede their operator. */
 typedef struct {

@@ -27,7 +27,7 @@ SMC_ITERATIVE = 1 << 4
 SMC_CONSERVATIVE = 2 << 4
 NODE = dict(true=0, false=1, atom=2, **{'not': 3, 'and': 4, 'or': 5, 'implies': 6}, U=7, F=8, G=9, X=10)
 OP = {'<': 0, '<=': 1, '>=': 2, '>': 3, '==': 4, '!=': 5}
-OPT = dict(event_budget=0, renorm_log2=1, autotune=2, warps_per_block=3, blocks_per_sm=4,
+OPT = dict(event_budget=0, renorm_log2=1, autotune=2, warps_per_block=3, blocks_per_sm=4, selection=8,
            refill=5, record=6, jit=7)
 
 c_i32p = ctypes.POINTER(ctypes.c_int32)

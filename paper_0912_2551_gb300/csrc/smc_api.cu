@@ -141,6 +141,7 @@ struct smc_ctx {
     int refill = 1;
     int record = 0;
     int jit = 1;                  // model-specialized kernels when eligible
+    int selection = 0;            // SMC_OPT_SELECTION
     // specialized kernels of the loaded structure (null: the generic ones run)
     smc::JitKernels jit_k;
     bool jit_ready = false;
@@ -532,10 +533,20 @@ int tc_bytes_of(const MonProg &prog)
     return 0;
 }
 
-// warp slice: x[(s_max + 1)][32] | tc | a[r_max][32] (tables stay in global memory)
-int warp_bytes_of(const SizeClass &c, int plain, int tc_bytes)
+// Whether the generic kernel selects by checkpointed running sums for class c
+// (SMC_OPT_SELECTION).
+bool blocked_selection(const smc_ctx *ctx, const SizeClass &c)
 {
-    const int b = (c.s_max + 1) * 128 + tc_bytes + c.r_max * 32 * (plain ? 8 : 4);
+    return ctx->selection == 2 ? c.r_max > SMC_SEL_BLOCK : ctx->selection == 0 && c.r_max > 64;
+}
+
+// warp slice: x[(s_max + 1)][32] | tc | a[r_max][32] | (blocked selection)
+// running sums at every 16th reaction [SMC_SEL_BLOCKS(r_max)][32]; the
+// tables stay in global memory
+int warp_bytes_of(const SizeClass &c, int plain, int tc_bytes, bool blocked)
+{
+    const int b = (c.s_max + 1) * 128 + tc_bytes +
+                  (c.r_max + (blocked ? SMC_SEL_BLOCKS(c.r_max) : 0)) * 32 * (plain ? 8 : 4);
     return (b + 15) & ~15;
 }
 
@@ -544,6 +555,7 @@ struct Launch {
     const SizeClass *c = nullptr;
     void *kernel = nullptr;  // model-specialized kernel, or null for the generic one
     int grid = 0, block = 0, smem = 0, warp_bytes = 0, tc_bytes = 0, refill = 1;
+    bool blocked = false;    // generic kernel: checkpointed selection
 };
 
 // The instance partition in use for a precision: the size classes, or one
@@ -568,7 +580,9 @@ int plan_class(smc_ctx *ctx, int plain, const SizeClass &c, const Shape &sh, Lau
     // warp slice holds only the nested operators' candidate clocks
     L.kernel = ctx->jit_ready ? (plain ? ctx->jit_k.plain : ctx->jit_k.mixed) : nullptr;
     const int rate_bytes = (ctx->jit_k.rate_count * (plain ? 8 : 4) + 15) / 16 * 16;
-    L.warp_bytes = L.kernel ? L.tc_bytes + rate_bytes + SMC_JIT_COOP_BYTES : warp_bytes_of(c, plain, L.tc_bytes);
+    L.blocked = !L.kernel && blocked_selection(ctx, c);
+    L.warp_bytes = L.kernel ? L.tc_bytes + rate_bytes + SMC_JIT_COOP_BYTES
+                            : warp_bytes_of(c, plain, L.tc_bytes, L.blocked);
     L.block = 32 * sh.warps;
     L.smem = (int)sizeof(MonProg) + (plain ? SMC_LOGTAB_BYTES : 0) + (L.kernel ? ctx->jit_k.delta_bytes : 0) +
              sh.warps * L.warp_bytes;
@@ -599,6 +613,7 @@ int issue_class(smc_ctx *ctx, int plain, const SsaParams &common, const Launch &
     p.r_max = L.c->r_max;
     p.tc_bytes = L.tc_bytes;
     p.warp_bytes = L.warp_bytes;
+    p.sel_block = L.blocked ? 1 : 0;
     p.logtab = ctx->d_logtab;
     p.logtab_bytes = plain ? SMC_LOGTAB_BYTES : 0;
     if (smc_launch_queue_init(p, s))
@@ -1127,6 +1142,11 @@ int smc_set_option(smc_ctx *ctx, int option, double value)
         ctx->jit = value != 0.0;
         ctx->dirty = true;  // re-prepare: kernels and tuned shapes change
         ctx->memo[0].valid = ctx->memo[1].valid = false;
+        return SMC_OK;
+    case SMC_OPT_SELECTION:
+        if (!(value == 0.0 || value == 1.0 || value == 2.0)) return fail(ctx, SMC_E_INVALID_ARG, "selection 0, 1 or 2");
+        ctx->selection = (int)value;
+        ctx->memo[0].valid = ctx->memo[1].valid = false;  // launch shapes change with the warp slice
         return SMC_OK;
     default: return fail(ctx, SMC_E_INVALID_ARG, "unknown option");
     }

@@ -171,7 +171,14 @@ struct SsaParams {
     int32_t *o_xsnap;            // [n_inst][out_stride][x_stride]
     uint32_t *o_esnap;           // [n_inst][out_stride] events up to the snapshot
                                  // (or to the verdict, if fixed before t_snap); may be null
+    // generic kernel, networks of more than 16 reactions: 1 = selection by
+    // the running sums at every 16th reaction (the warp slice then holds
+    // SMC_SEL_BLOCKS(r_max) of them per lane after the propensities), 0 =
+    // linear scan
+    int32_t sel_block;
 };
+#define SMC_SEL_BLOCK 16
+#define SMC_SEL_BLOCKS(r) (((r) + SMC_SEL_BLOCK - 1) / SMC_SEL_BLOCK)
 
 // Monitor replay (tests): runs the compiled monitor over given paths.
 struct ReplayParams {

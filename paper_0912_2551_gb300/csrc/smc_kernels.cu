@@ -93,10 +93,27 @@ __device__ __forceinline__ typename Prec<PLAIN>::T propensity(uint32_t pw, const
 template <bool PLAIN, bool EXT>
 __device__ __forceinline__ void run_instance(const SsaParams &p, const MonProg &P, const uint64_t *ltab,
                                              const int m, const uint32_t *blob, int32_t *xs, double *tc,
-                                             typename Prec<PLAIN>::T *as, const int lane)
+                                             typename Prec<PLAIN>::T *as, typename Prec<PLAIN>::T *bs,
+                                             const int lane)
 {
     typedef typename Prec<PLAIN>::T T;
     const int S = (int)blob[BH_S], R = (int)blob[BH_R], NA = (int)blob[BH_NA];
+    // selection by checkpoints (SsaParams::sel_block): bs[b * 32] holds the
+    // running sum a_0 + ... + a_k at k = 16 b + 15 (or R - 1): the FP64
+    // path's exact left-to-right sums, formed with a_0; the mixed path's
+    // FP32 block sums a_16b + ... + a_(16b+15), kept along the dependency
+    // graph and renormalised with a_0
+    const bool blk = p.sel_block != 0 && R > SMC_SEL_BLOCK;
+    const int nb = SMC_SEL_BLOCKS(R);
+    // mixed path: the block sums from scratch (FP64 sums, rounded once)
+    auto block_sums = [&]() {
+        for (int b = 0; b < nb; ++b) {
+            double s = 0.0;
+            for (int k = SMC_SEL_BLOCK * b; k < R && k < SMC_SEL_BLOCK * (b + 1); ++k)
+                s = __dadd_rn(s, (double)as[k * 32]);
+            bs[b * 32] = (T)s;
+        }
+    };
     const double *rate_d = reinterpret_cast<const double *>(blob + blob[BH_RATE_D]);
     const float *rate_f = reinterpret_cast<const float *>(blob + blob[BH_RATE_F]);
     const uint32_t *reac = blob + blob[BH_REAC];
@@ -182,6 +199,7 @@ __device__ __forceinline__ void run_instance(const SsaParams &p, const MonProg &
                             s = __dadd_rn(s, (double)ak);
                         }
                         a0 = (T)s;
+                        if (!PLAIN && blk) block_sums();
                         uint32_t ab = 0;
                         for (int a = 0; a < NA; ++a) ab |= atom_bit<EXT>(atoms, tptr, terms, ex, xs, a);
                         ml.ab = ab;
@@ -220,12 +238,21 @@ __device__ __forceinline__ void run_instance(const SsaParams &p, const MonProg &
             a0 = acc;
         } else if (PLAIN) {  // step 1: a0 as a fresh left-to-right sum
             double s = 0.0;
-            for (int k = 0; k < R; ++k) s = __dadd_rn(s, (double)as[k * 32]);
+            if (blk) {  // keeping the running sum at the end of every block
+                for (int b = 0; b < nb; ++b) {
+                    for (int k = SMC_SEL_BLOCK * b; k < R && k < SMC_SEL_BLOCK * (b + 1); ++k)
+                        s = __dadd_rn(s, (double)as[k * 32]);
+                    bs[b * 32] = (T)s;
+                }
+            } else {
+                for (int k = 0; k < R; ++k) s = __dadd_rn(s, (double)as[k * 32]);
+            }
             a0 = (T)s;
         } else if (!(a0 > (T)0)) {  // drifted running sum: renormalise in FP64
             double s = 0.0;
             for (int k = 0; k < R; ++k) s = __dadd_rn(s, (double)as[k * 32]);
             a0 = (T)s;
+            if (blk) block_sums();
         }
         if (PLAIN ? __double_as_longlong((double)a0) <= 0 : !(a0 > (T)0)) {
             finish(mon_close(ml, P));  // absorbing state: no further position
@@ -277,6 +304,23 @@ __device__ __forceinline__ void run_instance(const SsaParams &p, const MonProg &
                 if (k < R && j < 0 && hit) j = k;
             }
             last = pos ? 31 - __clz(pos) : -1;
+        } else if (PLAIN && blk) {
+            // the first block whose closing running sum exceeds r holds j;
+            // the sum restarts from the previous checkpoint, so every running
+            // sum is the left-to-right one of the linear scan, bit for bit
+            const long long rb = __double_as_longlong((double)r);
+            int b = 0;
+            while (b < nb && __double_as_longlong((double)bs[b * 32]) <= rb) ++b;
+            if (b < nb) {
+                double cum = b ? (double)bs[(b - 1) * 32] : 0.0;
+                for (int k = SMC_SEL_BLOCK * b; k < R && k < SMC_SEL_BLOCK * (b + 1); ++k) {
+                    cum = __dadd_rn(cum, (double)as[k * 32]);
+                    if (__double_as_longlong(cum) > rb) { j = k; break; }
+                }
+            } else {
+                for (int k = R - 1; k >= 0 && last < 0; --k)
+                    if (__double_as_longlong((double)as[k * 32]) > 0) last = k;
+            }
         } else if (PLAIN) {
             const long long rb = __double_as_longlong((double)r);
             double cum = 0.0;
@@ -286,6 +330,25 @@ __device__ __forceinline__ void run_instance(const SsaParams &p, const MonProg &
                 if (__double_as_longlong(ak) > 0) last = k;
                 if (__double_as_longlong(cum) > rb) { j = k; break; }
             }
+        } else if (blk) {
+            float cum = 0.0f;
+            int b = 0;
+            for (; b < nb; ++b) {
+                const float nc = cum + (float)bs[b * 32];
+                if (nc > (float)r) break;
+                cum = nc;
+            }
+            if (b < nb) {
+                for (int k = SMC_SEL_BLOCK * b; k < R && k < SMC_SEL_BLOCK * (b + 1); ++k) {
+                    const float ak = (float)as[k * 32];
+                    cum += ak;
+                    if (ak > 0.0f) last = k;
+                    if (cum > (float)r) { j = k; break; }
+                }
+            }
+            if (j < 0)
+                for (int k = R - 1; k >= 0 && last < 0; --k)
+                    if ((float)as[k * 32] > 0.0f) last = k;
         } else {
             float cum = 0.0f;
             for (int k = 0; k < R; ++k) {
@@ -321,7 +384,11 @@ __device__ __forceinline__ void run_instance(const SsaParams &p, const MonProg &
                 const uint32_t pw = dp[q];
                 const int k = pw & 255u;
                 const T ak = propensity<PLAIN, EXT>(pw, xs, rate_d, rate_f, blob);
-                if (!PLAIN) a0 = a0 + (ak - as[k * 32]);
+                if (!PLAIN) {
+                    const T d = ak - as[k * 32];
+                    a0 = a0 + d;
+                    if (blk) bs[(k / SMC_SEL_BLOCK) * 32] += d;
+                }
                 as[k * 32] = ak;
             }
             ++e;
@@ -330,6 +397,7 @@ __device__ __forceinline__ void run_instance(const SsaParams &p, const MonProg &
                 double s = 0.0;
                 for (int k = 0; k < R; ++k) s = __dadd_rn(s, (double)as[k * 32]);
                 a0 = (T)s;
+                if (blk) block_sums();
             }
             // monitor at the new state: re-evaluate the atoms that j moves
             uint32_t am = amask[j];
@@ -385,6 +453,7 @@ __global__ void __launch_bounds__(256, PLAIN ? 3 : 4) ssa_kernel(const SsaParams
     double *tc = reinterpret_cast<double *>(lanes) + lane;
     lanes += (size_t)p.tc_bytes;
     T *as = reinterpret_cast<T *>(lanes) + lane;
+    T *bs = as + (size_t)p.r_max * 32;  // checkpoints (blocked selection only)
 
     bool first = true;
     int cur = -1;
@@ -396,7 +465,7 @@ __global__ void __launch_bounds__(256, PLAIN ? 3 : 4) ssa_kernel(const SsaParams
             blob = p.blobs + p.blob_off[m];
             cur = m;
         }
-        run_instance<PLAIN, EXT>(p, P, ltab, m, blob, xs, tc, as, lane);
+        run_instance<PLAIN, EXT>(p, P, ltab, m, blob, xs, tc, as, bs, lane);
         __syncwarp();
     }
 

@@ -130,3 +130,59 @@ def test_launch_shapes_cover_instances_and_survive_reload(smc, batch):
         fixed = ctx.launch_shapes('mixed')
         assert all(s['warps_per_block'] == 2 and s['refill'] == 4 for s in fixed)
         assert sum(s['n_instances'] for s in fixed) == len(sub.models)
+
+
+@pytest.fixture(scope='module')
+def large():
+    return workloads.random_networks_large(96, seed=8)
+
+
+def test_large_networks_selection_modes_and_oracle(smc, orc, large):
+    # networks of 65 to 255 reactions: the FP64 path's selection by running
+    # sums checkpointed every 16 reactions (automatic above 64 reactions, and
+    # forced from 17) gives the linear scan's trajectories bit for bit, and
+    # both match the oracle per trajectory
+    import torch
+    n = 64
+    outs = {}
+    for sel in (1, 0, 2):
+        with smc.Context(0) as ctx:
+            ctx.set_option('selection', sel)
+            ctx.load_batch(large)
+            ctx.load_property(large.properties)
+            out = ctx.simulate('plain', seed=4, traj_begin=0, n_traj=n,
+                               outputs=('verdict', 'status', 'events', 't_final'))
+            torch.cuda.synchronize()
+            outs[sel] = {k: v.cpu().numpy() for k, v in out.items()}
+    for sel in (0, 2):
+        for k in ('verdict', 'status', 'events', 't_final', 'counts'):
+            assert np.array_equal(outs[sel][k], outs[1][k]), (sel, k)
+    g = outs[0]
+    agree = ev_eq = total = 0
+    for row in range(len(large.models)):
+        r = orc.run(large.models[row], large.properties[row], seed=4, instance=row, n_traj=n)
+        agree += int((g['verdict'][row] == r['verdict']).sum())
+        ev_eq += int((g['events'][row].astype(np.uint64) == r['events']).sum())
+        total += n
+    assert agree / total >= 0.9999 and ev_eq / total >= 0.9999, (agree / total, ev_eq / total)
+    assert max(m.n_reactions for m in large.models) > 200 and int(g['counts'][:, 2].sum()) > 10 ** 7
+
+
+def test_large_networks_mixed_selection_modes_agree(smc, large):
+    # the mixed path keeps FP32 block sums along the dependency graph: its
+    # estimates with checkpoints and with the linear scan agree within their
+    # combined intervals, instance by instance
+    from oracle import wilson
+    n = 4000
+    res = {}
+    for sel in (1, 2):
+        with smc.Context(0) as ctx:
+            ctx.set_option('selection', sel)
+            ctx.load_batch(large)
+            ctx.load_property(large.properties)
+            res[sel] = ctx.estimate(0.95, 0.01, seed=6, precision='mixed', sampling='fixed', fixed_n=n)
+    for a, b in zip(res[1], res[2]):
+        assert a['n'] == b['n'] == n
+        _, lo_a, hi_a = wilson.wilson_interval(a['yes'], n, 0.9999)
+        _, lo_b, hi_b = wilson.wilson_interval(b['yes'], n, 0.9999)
+        assert abs(a['yes'] - b['yes']) / n <= (hi_a - lo_a) / 2 + (hi_b - lo_b) / 2, (a, b)

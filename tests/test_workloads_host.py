@@ -81,3 +81,14 @@ def test_lotka_volterra_family_recipe():
     q = (lf - math.log(0.7)) / (math.log(1.3) - math.log(0.7))
     assert abs(q.mean() - 0.5) < 0.02 and abs(q.var() - 1 / 12) < 0.01
     assert np.all(m.x0 == 1000)
+
+
+def test_large_random_networks_recipe():
+    b = workloads.random_networks_large(64, seed=8)
+    S = np.array([m.n_species for m in b.models])
+    R = np.array([m.n_reactions for m in b.models])
+    assert S.min() >= 16 and S.max() <= 64 and R.min() >= 65 and R.max() <= 255
+    for m, p in zip(b.models, b.properties):
+        a = p.atoms[0]
+        k = int(np.nonzero(a.coef)[0][0])
+        assert a.op == '>=' and a.bound > m.x0[0, k]  # not satisfied at t = 0

@@ -304,23 +304,26 @@ def sqrt_race(T: float = 15.0) -> Tuple[Model, Property]:
     return m, p
 
 
-def random_networks(n_inst: int = 4096, seed: int = 3) -> Batch:
+def random_networks(n_inst: int = 4096, seed: int = 3, s_range: Tuple[int, int] = (2, 32),
+                    r_range: Tuple[int, int] = (4, 64), theta_above_start: bool = False) -> Batch:
     """Batched random mass-action networks.
 
-    Per instance: S ~ U{2..32}, R ~ U{4..64}; each reaction has reactant
+    Per instance: S ~ U{2..32}, R ~ U{4..64} (by default; s_range and
+    r_range give other bounds, inclusive); each reaction has reactant
     order uniform in {0,1,2} (species uniform, a repeated species is a
     homodimer) and 0-2 product molecules, but never more product molecules
     than reactant molecules for order >= 1 (so only zeroth-order reactions
     create mass and counts stay bounded by x0 plus the influx); rate
     constants log-uniform in [1e-3, 1]; x0 ~ U{0..200}.  Property
     F[0,50](X_k >= theta) with k uniform over species and
-    theta = max(1, ceil(1.5 * mean(x0))).
+    theta = max(1, ceil(1.5 * mean(x0))), or, with theta_above_start,
+    theta = x0_k + max(1, ceil(0.5 * mean(x0))) (never satisfied at t = 0).
     """
     rng = np.random.default_rng(seed)
     models, props = [], []
     for m in range(n_inst):
-        S = int(rng.integers(2, 33))
-        R = int(rng.integers(4, 65))
+        S = int(rng.integers(s_range[0], s_range[1] + 1))
+        R = int(rng.integers(r_range[0], r_range[1] + 1))
         sp = [f's{i}' for i in range(S)]
         reac = -np.ones((R, 2), np.int32)
         st = np.zeros((R, S), np.int32)
@@ -336,11 +339,22 @@ def random_networks(n_inst: int = 4096, seed: int = 3) -> Batch:
         rates = np.exp(rng.uniform(math.log(1e-3), math.log(1.0), size=R))
         x0 = rng.integers(0, 201, size=S).astype(np.int32)
         k = int(rng.integers(0, S))
-        theta = max(1, int(math.ceil(1.5 * float(x0.mean()))))
+        if theta_above_start:
+            theta = int(x0[k]) + max(1, int(math.ceil(0.5 * float(x0.mean()))))
+        else:
+            theta = max(1, int(math.ceil(1.5 * float(x0.mean()))))
         models.append(Model(f'random{m}', sp, reac, st, rates[None, :], x0[None, :]))
         props.append(Property([atom(sp, sp[k], '>=', theta)], ('F', 0.0, 50.0, ('atom', 0)),
                               f'F[0,50]({sp[k]}>={theta})'))
     return Batch(models, props)
+
+
+def random_networks_large(n_inst: int = 256, seed: int = 8) -> Batch:
+    """Random mass-action networks with many reactions, for the selection
+    step of large networks: S ~ U{16..64}, R ~ U{65..255}, otherwise the
+    recipe of random_networks, with the threshold above the species'
+    starting count."""
+    return random_networks(n_inst, seed, s_range=(16, 64), r_range=(65, 255), theta_above_start=True)
 
 
 MAPK_SPECIES = [
