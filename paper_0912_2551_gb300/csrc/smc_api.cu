@@ -620,7 +620,9 @@ int issue_class(smc_ctx *ctx, int plain, const SsaParams &common, const Launch &
         return fail(ctx, SMC_E_CUDA, std::string("queue init: ") + cudaGetErrorString(cudaGetLastError()));
     const int lrc = L.kernel ? smc_jit_launch(L.kernel, p, L.grid, L.block, L.smem, s)
                              : smc_launch_ssa(plain, ctx->ext, p, L.grid, L.block, L.smem, s);
-    if (lrc) return fail(ctx, SMC_E_CUDA, std::string("ssa launch: ") + cudaGetErrorString(cudaGetLastError()));
+    if (lrc)
+        return fail(ctx, SMC_E_CUDA,
+                    std::string("ssa launch: ") + (L.kernel ? cudaGetErrorString(cudaGetLastError()) : smc_kernel_error()));
     return SMC_OK;
 }
 
@@ -1330,6 +1332,26 @@ int smc_estimate(smc_ctx *ctx, double confidence, double half_width, uint64_t se
         rc = plan_class(ctx, plain, *c, c->shape[plain], L);
         if (rc) return rc;
         plan.push_back(L);
+    }
+    // planning set each kernel's shared-memory limit to its last launch's
+    // need; the launches run together, so each kernel gets the largest
+    {
+        int gen_max = 0;
+        std::vector<std::pair<void *, int>> jit_max;
+        for (const Launch &L : plan) {
+            if (!L.kernel) {
+                gen_max = std::max(gen_max, L.smem);
+                continue;
+            }
+            bool seen = false;
+            for (auto &kv : jit_max)
+                if (kv.first == L.kernel) { kv.second = std::max(kv.second, L.smem); seen = true; }
+            if (!seen) jit_max.emplace_back(L.kernel, L.smem);
+        }
+        if (gen_max && smc_ssa_set_smem_limit(plain, ctx->ext, gen_max))
+            return fail(ctx, SMC_E_CUDA, "cudaFuncSetAttribute failed");
+        for (auto &kv : jit_max)
+            if (smc_jit_set_smem_limit(kv.first, kv.second)) return fail(ctx, SMC_E_CUDA, "cudaFuncSetAttribute failed");
     }
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;

@@ -204,6 +204,7 @@ extern "C++" {
 // ext: the model uses rate-law factors or arithmetic atoms (kernel variant)
 int smc_launch_ssa(int plain, int ext, const SsaParams &p, int grid, int block, int smem_bytes,
                    void *stream);
+const char *smc_kernel_error();  // text of the last failed launch wrapper's error
 int smc_ssa_max_blocks_per_sm(int plain, int ext, int block, int smem_bytes, int *out);
 int smc_ssa_set_smem_limit(int plain, int ext, int smem_bytes);
 int smc_launch_queue_init(const SsaParams &p, void *stream);

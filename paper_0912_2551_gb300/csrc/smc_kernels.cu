@@ -527,7 +527,17 @@ __global__ void replay_kernel(const ReplayParams rp)
 // ---------------------------------------------------------------------------
 // host wrappers
 
-static int to_code(cudaError_t e) { return e == cudaSuccess ? 0 : -3; }
+// The last error of a launch wrapper below (its text for the host's messages:
+// cudaGetLastError, once read, no longer holds it).
+static thread_local cudaError_t g_kernel_err = cudaSuccess;
+
+static int to_code(cudaError_t e)
+{
+    if (e != cudaSuccess) g_kernel_err = e;
+    return e == cudaSuccess ? 0 : -3;
+}
+
+const char *smc_kernel_error() { return cudaGetErrorString(g_kernel_err); }
 
 static const void *ssa_kernel_ptr(int plain, int ext)
 {
