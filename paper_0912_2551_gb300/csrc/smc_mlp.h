@@ -6,8 +6,6 @@
 
 #define MLP_IN 16    // input features, zero-padded
 #define MLP_H 128    // hidden width
-#define MLP_ROWS_FWD 64   // rows per CTA of the row-parallel kernels (4 warps x 16)
-#define MLP_CHUNK 128     // rows per CTA of the weight-gradient kernel
 
 // Flat FP32 parameter vector: W1 [H][IN], b1 [H], W2 [H][H], b2 [H], W3 [H][H],
 // b3 [H], w4 [H], b4 [1].

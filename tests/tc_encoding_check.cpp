@@ -50,6 +50,22 @@ static void check_layout(int R, int K)
     for (size_t i = 0; i < hits.size(); ++i) CHECK(hits[i] == 1);
 }
 
+// The stored R x C tile read MN-major (MN = column c, K = row r): element
+// (r, c) lies in the MN-major core matrix (c / 8, r / 8) at row r % 8 (16
+// bytes each) and position c % 8; core matrices along MN are kTcMnSbo
+// apart, along K tc_mn_lbo(C) apart; an MMA step along K (16 rows) starts
+// 2 * tc_mn_lbo(C) bytes further.
+static void check_mn_view(int R, int C)
+{
+    for (int r = 0; r < R; ++r)
+        for (int c = 0; c < C; ++c) {
+            const int off = tc_elem_offset(r, c, C);
+            const int expect = (c / 8) * (int)kTcMnSbo + (r / 8) * (int)tc_mn_lbo(C) + (r % 8) * 16 + (c % 8) * 2;
+            CHECK(off == expect);
+            if (r % 16 == 0) CHECK(tc_elem_offset(r, c, C) - tc_elem_offset(0, c, C) == (r / 16) * 2 * (int)tc_mn_lbo(C));
+        }
+}
+
 static void check_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo)
 {
     const uint64_t d = tc_desc(saddr, lbo, sbo);
@@ -82,6 +98,11 @@ static void check_idesc(int M, int N)
     CHECK(field(d, 24, 5) == (uint64_t)(M >> 4));
     CHECK(field(d, 29, 3) == 0);
     CHECK(field(d, 32, 32) == 0);
+    for (int t = 0; t < 4; ++t) {  // transpose bits of MN-major operands
+        const uint64_t dt = tc_idesc_bf16_t(M, N, t & 1, t & 2);
+        CHECK(field(dt, 15, 1) == (uint64_t)(t & 1) && field(dt, 16, 1) == (uint64_t)((t >> 1) & 1));
+        CHECK((dt & ~((1ull << 15) | (1ull << 16))) == d);
+    }
 }
 
 int main()
@@ -91,6 +112,7 @@ int main()
     // and its bias tile (16 x 16)
     const int shapes[][2] = {{128, 16}, {128, 128}, {16, 128}, {16, 16}};
     for (const auto &sh : shapes) check_layout(sh[0], sh[1]);
+    for (const auto &sh : shapes) check_mn_view(sh[0], sh[1]);
     for (uint32_t a : {0u, 16u, 0x1230u, 0x11000u, 0x3FFF0u})
         for (int K : {16, 128}) check_desc(a, kTcLbo, tc_sbo(K));
     for (int N : {16, 128, 256}) check_idesc(128, N);
