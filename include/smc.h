@@ -398,11 +398,13 @@ int smc_snapshot_features(smc_ctx *ctx, uint64_t n_traj, const int32_t *x_snap, 
                           const float *x_scale, float t_scale, float *feat, void *stream);
 
 /* The network: n_in (<= 16) -> 128 -> 128 -> 128 -> 1, ReLU, logistic
- * output; BF16 tensor-core kernels with FP32 accumulation, FP32 master
- * weights (SMC_MLP_NPARAM floats: W1[128][16], b1, W2[128][128], b2,
- * W3[128][128], b3, w4[128], b4), Adam. */
+ * output; BF16 tensor-core (tcgen05) kernels with FP32 accumulation, FP32
+ * master weights (SMC_MLP_NPARAM floats: W1[128][16], b1, W2[128][128], b2,
+ * W3[128][128], b3, w4[128], b4), Adam.  Activations and deltas are rounded
+ * to BF16 where they are stored (after the ReLU, after the mask); biases,
+ * w4 and the logit stay FP32. */
 #define SMC_MLP_NPARAM 35329
-#define SMC_MLP_MAX_BATCH 8192
+#define SMC_MLP_MAX_BATCH 4194304
 typedef struct smc_mlp smc_mlp;
 int smc_mlp_create(smc_mlp **out, int device, int n_in, uint64_t seed); /* He-uniform init */
 void smc_mlp_destroy(smc_mlp *mlp);
@@ -410,12 +412,20 @@ const char *smc_mlp_last_error(const smc_mlp *mlp);
 int smc_mlp_get_params(smc_mlp *mlp, float *host_params);       /* [SMC_MLP_NPARAM] */
 int smc_mlp_set_params(smc_mlp *mlp, const float *host_params);
 /* Gradient of the mean binary cross-entropy over n <= SMC_MLP_MAX_BATCH rows
- * (device x [n][n_in], y [n] in {0,1}); host outputs. */
+ * (device x [n][n_in], y [n] in {0,1}); host outputs.  The same kernel as
+ * a training step: one fused launch (forward, backward and weight
+ * gradients of each 128-row tile in shared and tensor memory, one partial
+ * gradient per CTA) and a launch summing the partials. */
 int smc_mlp_gradient(smc_mlp *mlp, const float *x, const float *y, int n, float *grad_host,
                      float *loss_host);
-/* Adam training: epochs x ceil(n / batch) steps, batches drawn with
- * replacement (counter-based hash of seed, step, row). loss_host: [epochs]
- * mean loss per epoch or NULL. */
+/* Adam training: epochs (<= 4096) x ceil(n / batch) steps, batch <=
+ * SMC_MLP_MAX_BATCH, minibatches drawn with replacement (step k of the
+ * call takes row hash(seed, k, i) mod n as its row i; counter-based, so
+ * the steps are replayed as captured CUDA graphs).  Asynchronous on
+ * `stream` (NULL: the network's own stream) unless loss_host is given:
+ * [epochs] mean loss per epoch, after a synchronisation.  A tensor-core
+ * wait that gave up (bounded, about a second) makes this and every later
+ * call on the network return SMC_E_CUDA. */
 int smc_mlp_train(smc_mlp *mlp, const float *x, const float *y, uint64_t n, int epochs, int batch,
                   float lr, uint64_t seed, float *loss_host, void *stream);
 /* g[i] = network output for row i of x (device [n][n_in] -> device [n]):

@@ -84,7 +84,7 @@ class smc_cme_result(ctypes.Structure):
 
 
 SMC_MLP_NPARAM = 35329
-SMC_MLP_MAX_BATCH = 8192
+SMC_MLP_MAX_BATCH = 4194304
 c_f32p = ctypes.POINTER(ctypes.c_float)
 
 _lib = None

@@ -82,8 +82,8 @@ constexpr int kTcSmW4 = kTcSmW3 + H * H * 2;    // [16][128]: w4 high, w4 low, z
 constexpr int kTcSmOnes = kTcSmW4 + 16 * H * 2; // [128][16]: ones in columns 0, 1; 4 KB
 constexpr int kTcSmB1 = kTcSmOnes + kTcRows * 16 * 2;  // bias tiles [128][16], 4 KB each (layers 1-3)
 constexpr int kTcSmB4 = kTcSmB1 + 3 * H * 16 * 2;      // [16][16]: b4 high, low in row 0
-constexpr int kTcSmBar = kTcSmB4 + 16 * 16 * 2;        // one mbarrier per pipeline, then the TMEM address
-constexpr int kTcSmGroup = (kTcSmBar + 8 * kTcGroups + 4 + 1023) / 1024 * 1024;
+constexpr int kTcSmBar = kTcSmB4 + 16 * 16 * 2;        // one mbarrier per pipeline, the weights' mbarrier, the TMEM address
+constexpr int kTcSmGroup = (kTcSmBar + 8 * (kTcGroups + 1) + 4 + 1023) / 1024 * 1024;
 constexpr int kTcGroupBytes = kTcRows * H * 2;  // activations [128][128] (features [128][16] at the start)
 constexpr int kTcSmem = kTcSmGroup + kTcGroups * kTcGroupBytes;
 constexpr uint32_t kTcCols = 128 * kTcGroups;   // TMEM columns per CTA: all 512 of the SM
@@ -205,15 +205,33 @@ __device__ __forceinline__ uint32_t relu_pack2(uint32_t lo, uint32_t hi)
     return d;
 }
 
-// stages an N x K row-major BF16 matrix (global) into the core-matrix layout
-__device__ __forceinline__ void tc_stage_operand(unsigned char *dst, const bf16 *src, int N, int K)
+// The BF16 weights live in global memory already in the K-major
+// core-matrix layout (the update kernel writes them so): W1 [128][16],
+// 4 KB, then W2 and W3 [128][128], 32 KB each.  A kernel stages all three
+// into shared memory (W1, W2, W3 contiguous from byte w_off) with bulk
+// copies completing on one mbarrier; issued by one thread after the
+// mbarrier's initialisation.
+constexpr uint32_t kW1Bytes = H * IN * 2, kWHBytes = H * H * 2, kWBytes = kW1Bytes + 2 * kWHBytes;
+
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar)
 {
-    const int chunks = N * (K / 8);
-    for (int i = threadIdx.x; i < chunks; i += blockDim.x) {
-        const int r = i / (K / 8), kg = i % (K / 8);
-        *reinterpret_cast<uint4 *>(dst + tc_core_offset(r, kg, K)) =
-            *reinterpret_cast<const uint4 *>(src + (size_t)r * K + kg * 8);
-    }
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                 "l"(src), "r"(bytes), "r"(bar)
+                 : "memory");
+}
+
+__device__ __forceinline__ void stage_weights(uint32_t w_off, const bf16 *w1b, const bf16 *w2b, const bf16 *w3b,
+                                              uint32_t bar)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(kWBytes) : "memory");
+    bulk_g2s(w_off, w1b, kW1Bytes, bar);
+    bulk_g2s(w_off + kW1Bytes, w2b, kWHBytes, bar);
+    bulk_g2s(w_off + kW1Bytes + kWHBytes, w3b, kWHBytes, bar);
+}
+
+__device__ __forceinline__ uint32_t pack_bf16x2(bf16 lo, bf16 hi)
+{
+    return (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
 }
 
 // element (r, k) of an operand with K columns in the core-matrix layout
@@ -226,37 +244,22 @@ __device__ __forceinline__ bf16 *tc_elem(unsigned char *base, int r, int k, int 
 __device__ __forceinline__ bf16 bf16_hi(float v) { return __float2bfloat16_rn(v); }
 __device__ __forceinline__ bf16 bf16_lo(float v) { return __float2bfloat16_rn(v - __bfloat162float(__float2bfloat16_rn(v))); }
 
-// The training pass's tiles in global memory: per 128-row tile t, the input
-// (4 KB at x + t * 4096) and each layer's activations and deltas (32 KB at
-// h1 + t * 32768, ...), every one in the K-major core-matrix layout of
-// smc_tc.h with the rows as M, so that the backward and weight-gradient
-// kernels read them into shared memory unchanged; the logits z and the
-// output deltas dz per row.
-struct TrainTiles {
-    unsigned char *x, *h1, *h2, *h3, *d1, *d2, *d3;
-    float *z, *dz;
-};
-constexpr int kTileX = kTcRows * IN * 2, kTileH = kTcRows * H * 2;
-
 // The forward pass over n rows, one persistent launch (one CTA of
 // kTcThreads per SM) over 128-row tiles, weights staged once per CTA.
-// Inference (TRAIN = false): FP32 features x [n][n_in] (n_in <= 16), rounded
-// to BF16 as the training input is; g[r] = 1 / (1 + e^-z); rows with
-// skip[r] != 0 (skip may be null) need no output, and a tile whose rows all
-// skip is not computed.  Training (TRAIN = true): BF16 rows xb [n][16]; the
-// input and activation tiles and the logits go to tt.  A wait that gives up
-// sets *err and leaves NaN in the outputs of the tile it was working on,
-// and that pipeline stops.
-template <bool TRAIN>
-__global__ void __launch_bounds__(kTcThreads) mlp_tc_forward(const float *__restrict__ x,
-                                                             const bf16 *__restrict__ xb, uint64_t n, int n_in,
+// FP32 features x [n][n_in] (n_in <= 16), rounded to BF16 as the training
+// input is; g[r] = 1 / (1 + e^-z); rows with skip[r] != 0 (skip may be
+// null) need no output, and a tile whose rows all skip is not computed.  A
+// wait that gives up sets *err and leaves NaN in the outputs of the tile it
+// was working on, and that pipeline stops.
+__global__ void __launch_bounds__(kTcThreads) mlp_tc_forward(const float *__restrict__ x, uint64_t n, int n_in,
                                                              const uint8_t *__restrict__ skip, const bf16 *w1b,
                                                              const bf16 *w2b, const bf16 *w3b, const float *master,
-                                                             float *g_out, TrainTiles tt, int *err)
+                                                             float *g_out, int *err)
 {
     extern __shared__ __align__(1024) unsigned char sm[];
     uint64_t *bars = reinterpret_cast<uint64_t *>(sm + kTcSmBar);
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(sm + kTcSmBar + 8 * kTcGroups);
+    const uint32_t bar_w = smem_u32(bars + kTcGroups);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(sm + kTcSmBar + 8 * (kTcGroups + 1));
     const int tid = threadIdx.x, warp = tid >> 5, grp = tid >> 7, gt = tid & 127;
     const int bid = 1 + grp;  // the pipeline's named barrier
 
@@ -267,37 +270,40 @@ __global__ void __launch_bounds__(kTcThreads) mlp_tc_forward(const float *__rest
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     if (tid == 0) {
-        for (int i = 0; i < kTcGroups; ++i)
+        for (int i = 0; i <= kTcGroups; ++i)
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bars + i)) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        stage_weights(smem_u32(sm + kTcSmW1), w1b, w2b, w3b, bar_w);
     }
-    tc_stage_operand(sm + kTcSmW1, w1b, H, IN);
-    tc_stage_operand(sm + kTcSmW2, w2b, H, H);
-    tc_stage_operand(sm + kTcSmW3, w3b, H, H);
     const bf16 zero = __float2bfloat16_rn(0.0f), one = __float2bfloat16_rn(1.0f);
-    for (int i = tid; i < H * 16; i += blockDim.x) {  // ones, bias tiles (rows x 16 columns)
-        const int r = i >> 4, k = i & 15;
-        *tc_elem(sm + kTcSmOnes, r, k, 16) = k < 2 ? one : zero;
+    if (tid < H) {  // thread r: row r of the ones and bias tiles, column r of the output unit's tile
+        const int r = tid;
+        const float bl[3] = {master[MLP_OFF_B1 + r], master[MLP_OFF_B2 + r], master[MLP_OFF_B3 + r]};
+        const float w = master[MLP_OFF_W4 + r], b4 = master[MLP_OFF_B4];
+        const uint4 z4 = make_uint4(0u, 0u, 0u, 0u);
+        auto row16 = [&](int off, bf16 v0, bf16 v1) {  // columns 0, 1 = v0, v1; 2-15 zero
+            *reinterpret_cast<uint4 *>(sm + off + tc_core_offset(r, 0, 16)) = make_uint4(pack_bf16x2(v0, v1), 0u, 0u, 0u);
+            *reinterpret_cast<uint4 *>(sm + off + tc_core_offset(r, 1, 16)) = z4;
+        };
+        row16(kTcSmOnes, one, one);
 #pragma unroll
-        for (int l = 0; l < 3; ++l) {
-            const float b = master[MLP_OFF_B1 + l * (H * H + H) + r];
-            *tc_elem(sm + kTcSmB1 + l * H * 16 * 2, r, k, 16) = k == 0 ? bf16_hi(b) : k == 1 ? bf16_lo(b) : zero;
+        for (int l = 0; l < 3; ++l) row16(kTcSmB1 + l * H * 16 * 2, bf16_hi(bl[l]), bf16_lo(bl[l]));
+#pragma unroll
+        for (int j = 0; j < 16; ++j)  // output unit: rows 0, 1 = w4 high, low
+            *tc_elem(sm + kTcSmW4, j, r, H) = j == 0 ? bf16_hi(w) : j == 1 ? bf16_lo(w) : zero;
+        if (r < 16) {  // [16][16]: b4 high, low in row 0
+            const bf16 v0 = r == 0 ? bf16_hi(b4) : zero, v1 = r == 0 ? bf16_lo(b4) : zero;
+            *reinterpret_cast<uint4 *>(sm + kTcSmB4 + tc_core_offset(r, 0, 16)) = make_uint4(pack_bf16x2(v0, v1), 0u, 0u, 0u);
+            *reinterpret_cast<uint4 *>(sm + kTcSmB4 + tc_core_offset(r, 1, 16)) = z4;
         }
-    }
-    for (int i = tid; i < 16 * H; i += blockDim.x) {  // output unit: rows 0, 1 = w4 high, low
-        const int r = i / H, k = i % H;
-        const float w = master[MLP_OFF_W4 + k];
-        *tc_elem(sm + kTcSmW4, r, k, H) = r == 0 ? bf16_hi(w) : r == 1 ? bf16_lo(w) : zero;
-    }
-    for (int i = tid; i < 16 * 16; i += blockDim.x) {
-        const int r = i >> 4, k = i & 15;
-        const float b = master[MLP_OFF_B4];
-        *tc_elem(sm + kTcSmB4, r, k, 16) = (r == 0 && k == 0) ? bf16_hi(b) : (r == 0 && k == 1) ? bf16_lo(b) : zero;
     }
     fence_async_smem();
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
+    // the weights' copies (bounded wait; a CTA that gives up computes nothing)
+    const bool w_failed = __syncthreads_or(!tc_wait(bar_w, 0));
+    bool failed = w_failed;
     const uint32_t tmem = *tmem_slot;
     const uint32_t tacc = tmem + 128u * grp;                              // the pipeline's columns
     const uint32_t t_row = tacc + ((uint32_t)(32 * (warp & 3)) << 16);  // this warp's 32 lanes
@@ -306,30 +312,16 @@ __global__ void __launch_bounds__(kTcThreads) mlp_tc_forward(const float *__rest
     const uint32_t bar = smem_u32(bars + grp);
     const uint32_t aAct = smem_u32(act), aOnes = smem_u32(sm + kTcSmOnes);
     uint32_t phase = 0;
-    bool failed = false;
-    const uint64_t tiles = (n + kTcRows - 1) / kTcRows;
+    const uint64_t tiles = failed ? 0 : (n + kTcRows - 1) / kTcRows;
 
     // a tile's features and mask are loaded one tile ahead, so their
     // latency overlaps the previous tile's layers
     const uint64_t stride = (uint64_t)gridDim.x * kTcGroups;
     auto load_tile = [&](uint64_t t, float (&f)[IN], bool &nd) {
         const uint64_t r = t * kTcRows + gt;
-        if constexpr (TRAIN) {
-            nd = r < n;
-            const uint4 *src = reinterpret_cast<const uint4 *>(xb + r * IN);
-            const uint4 v0 = nd ? src[0] : make_uint4(0, 0, 0, 0), v1 = nd ? src[1] : make_uint4(0, 0, 0, 0);
-            const uint32_t w[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
+        nd = r < n && !(skip && skip[r]);
 #pragma unroll
-            for (int k = 0; k < IN / 2; ++k) {  // exact: the values are BF16 already
-                const float2 p = unpack2(w[k]);
-                f[2 * k] = p.x;
-                f[2 * k + 1] = p.y;
-            }
-        } else {
-            nd = r < n && !(skip && skip[r]);
-#pragma unroll
-            for (int k = 0; k < IN; ++k) f[k] = (r < n && k < n_in) ? x[r * n_in + k] : 0.0f;
-        }
+        for (int k = 0; k < IN; ++k) f[k] = (r < n && k < n_in) ? x[r * n_in + k] : 0.0f;
     };
     float f_next[IN];
     bool need_next = false;
@@ -352,8 +344,6 @@ __global__ void __launch_bounds__(kTcThreads) mlp_tc_forward(const float *__rest
                 v.z = pack2(f[8 * kg + 4], f[8 * kg + 5]);
                 v.w = pack2(f[8 * kg + 6], f[8 * kg + 7]);
                 *reinterpret_cast<uint4 *>(act + tc_core_offset(gt, kg, IN)) = v;
-                if constexpr (TRAIN)
-                    *reinterpret_cast<uint4 *>(tt.x + tile * kTileX + tc_core_offset(gt, kg, IN)) = v;
             }
         }
         uint32_t zc[2] = {0u, 0u};
@@ -395,8 +385,6 @@ __global__ void __launch_bounds__(kTcThreads) mlp_tc_forward(const float *__rest
             }
             {   // 4 chunks of 32 columns; the next chunk loads while this one converts
                 uint32_t va[32], vb[32];
-                unsigned char *hg = nullptr;  // training: this layer's tile in global memory
-                if constexpr (TRAIN) hg = (layer == 0 ? tt.h1 : layer == 1 ? tt.h2 : tt.h3) + tile * kTileH;
                 auto store_chunk = [&](int c, const uint32_t (&v)[32]) {
 #pragma unroll
                     for (int q = 0; q < 4; ++q) {
@@ -404,7 +392,6 @@ __global__ void __launch_bounds__(kTcThreads) mlp_tc_forward(const float *__rest
                             make_uint4(relu_pack2(v[8 * q], v[8 * q + 1]), relu_pack2(v[8 * q + 2], v[8 * q + 3]),
                                        relu_pack2(v[8 * q + 4], v[8 * q + 5]), relu_pack2(v[8 * q + 6], v[8 * q + 7]));
                         *reinterpret_cast<uint4 *>(act + tc_core_offset(gt, 4 * c + q, H)) = w;
-                        if constexpr (TRAIN) *reinterpret_cast<uint4 *>(hg + tc_core_offset(gt, 4 * c + q, H)) = w;
                     }
                 };
                 tc_load32_async(t_row, va);
@@ -422,16 +409,12 @@ __global__ void __launch_bounds__(kTcThreads) mlp_tc_forward(const float *__rest
             }
         }
         if (failed) {
-            if (row < n) (TRAIN ? tt.z : g_out)[row] = __int_as_float(0x7fc00000);
+            if (row < n) g_out[row] = __int_as_float(0x7fc00000);
             if (gt == 0) atomicExch(err, 1);
             break;
         }
         const float z = __uint_as_float(zc[0]) + __uint_as_float(zc[1]);
-        if constexpr (TRAIN) {
-            if (need) tt.z[row] = z;
-        } else {
-            if (need) g_out[row] = 1.0f / (1.0f + expf(-z));
-        }
+        if (need) g_out[row] = 1.0f / (1.0f + expf(-z));
     }
     // Release tensor memory once every MMA and load of this CTA has finished.
     // A pipeline that gave up waits again (bounded) for the completion of its
@@ -439,7 +422,14 @@ __global__ void __launch_bounds__(kTcThreads) mlp_tc_forward(const float *__rest
     // tensor cores never report it does the CTA release the memory without
     // the confirmation (a CTA may not exit holding tensor memory), and it
     // records that case (err = 2) for the host.
-    if (failed && gt == 0) {
+    if (w_failed) {  // no products were issued; the copies must land before the CTA exits
+        if (tid == 0) {
+            atomicExch(err, 1);
+            bool drained = false;
+            for (int k = 0; k < 4 && !drained; ++k) drained = tc_wait(bar_w, 0);
+            if (!drained) atomicExch(err, 2);
+        }
+    } else if (failed && gt == 0) {
         bool drained = false;
         for (int k = 0; k < 4 && !drained; ++k) drained = tc_wait(bar, phase ^ 1);
         if (!drained) atomicExch(err, 2);
@@ -454,21 +444,36 @@ __global__ void __launch_bounds__(kTcThreads) mlp_tc_forward(const float *__rest
 
 #include "smc_mlp_train.cuh"
 
-// Sums the partial gradients (one per weight-gradient CTA), optionally
-// applies Adam (lr > 0) to the FP32 master weights, and refreshes their BF16
-// copies (row-major; the kernels stage them in the operand layout and read
-// them MN-major where they need the transpose).
-__global__ void mlp_update_kernel(int nparts, const float *part, float *master, float *am, float *av, float lr,
-                                  float beta1, float beta2, float eps, float bc1, float bc2, float *grad_out,
-                                  bf16 *w1b, bf16 *w2b, bf16 *w3b)
+// Sums the partial gradients (one per CTA of the training-step kernel,
+// kPartStride floats apart), optionally applies Adam (lr > 0) to the FP32
+// master weights, and refreshes their BF16 copies (in the K-major operand
+// layout, which the kernels copy into shared memory as they are and read
+// MN-major where they need the transpose).  Four threads per parameter:
+// thread j of the four sums the partials j, j + 4, ... in order, and the
+// four sums are added in a fixed order (deterministic).  ctr[0] is the
+// sampling step (advanced here when lr > 0), ctr[1] Adam's step count t
+// (advanced by the training-step kernel before this launch).
+constexpr int kUpdThreads = 256, kUpdParams = kUpdThreads / 4;
+__global__ void __launch_bounds__(kUpdThreads) mlp_update_kernel(int nparts, const float *part, float *master,
+                                                                 float *am, float *av, float lr, float beta1,
+                                                                 float beta2, float eps, unsigned long long *ctr,
+                                                                 float *grad_out, bf16 *w1b, bf16 *w2b, bf16 *w3b)
 {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= MLP_NPARAM) return;
+    const int i = blockIdx.x * kUpdParams + (threadIdx.x >> 2), j = threadIdx.x & 3;
+    if (lr > 0.0f && blockIdx.x == 0 && threadIdx.x == 0) ctr[0] += 1ull;
     float gsum = 0.0f;
-    for (int c = 0; c < nparts; ++c) gsum += part[(size_t)c * MLP_NPARAM + i];
+    if (i < MLP_NPARAM) {
+#pragma unroll 8
+        for (int c = j; c < nparts; c += 4) gsum += part[(size_t)c * kPartStride + i];
+    }
+    gsum += __shfl_down_sync(0xffffffffu, gsum, 1, 4);  // (s0 + s1) + (s2 + s3) in lane j = 0
+    gsum += __shfl_down_sync(0xffffffffu, gsum, 2, 4);
+    if (i >= MLP_NPARAM || j != 0) return;
     if (grad_out) grad_out[i] = gsum;
     float w = master[i];
     if (lr > 0.0f) {
+        const float t = (float)ctr[1];
+        const float bc1 = 1.0f - powf(beta1, t), bc2 = 1.0f - powf(beta2, t);
         const float m = beta1 * am[i] + (1.0f - beta1) * gsum;
         const float v = beta2 * av[i] + (1.0f - beta2) * gsum * gsum;
         am[i] = m;
@@ -476,40 +481,35 @@ __global__ void mlp_update_kernel(int nparts, const float *part, float *master, 
         w -= lr * (m / bc1) / (sqrtf(v / bc2) + eps);
         master[i] = w;
     }
-    const bf16 wb = __float2bfloat16(w);
-    if (i < MLP_OFF_B1) w1b[i - MLP_OFF_W1] = wb;
-    else if (i >= MLP_OFF_W2 && i < MLP_OFF_B2) w2b[i - MLP_OFF_W2] = wb;
-    else if (i >= MLP_OFF_W3 && i < MLP_OFF_B3) w3b[i - MLP_OFF_W3] = wb;
+    const bf16 wb = __float2bfloat16(w);  // BF16 copies in the operand layout (rows = outputs, K = inputs)
+    if (i < MLP_OFF_B1) {
+        const int e = i - MLP_OFF_W1;
+        w1b[tc_elem_offset(e / IN, e % IN, IN) / 2] = wb;
+    } else if (i >= MLP_OFF_W2 && i < MLP_OFF_B2) {
+        const int e = i - MLP_OFF_W2;
+        w2b[tc_elem_offset(e / H, e % H, H) / 2] = wb;
+    } else if (i >= MLP_OFF_W3 && i < MLP_OFF_B3) {
+        const int e = i - MLP_OFF_W3;
+        w3b[tc_elem_offset(e / H, e % H, H) / 2] = wb;
+    }
 }
+constexpr int kUpdBlocks = (MLP_NPARAM + kUpdParams - 1) / kUpdParams;
 
-__device__ __forceinline__ uint64_t splitmix64(uint64_t z)
-{
-    z += 0x9E3779B97F4A7C15ull;
-    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-    return z ^ (z >> 31);
-}
+constexpr int kMaxBatch = SMC_MLP_MAX_BATCH;  // rows per training step or gradient
+constexpr int kMaxParts = 256;       // training-step CTAs (at most one per SM)
+constexpr int kMaxEpochs = 4096;
+constexpr int kGraphSteps = 32;      // training steps per captured graph
 
-// Rows of x (FP32 [n][n_in]) into the BF16 input buffer [B][16] (zero
-// padded): row i of the batch is row i + base (predict), or a row drawn with
-// replacement from a counter-based hash of (seed, step, i) (training).
-__global__ void mlp_gather_kernel(const float *x, const float *y, uint64_t n, int n_in, int B, uint64_t base,
-                                  int sample, uint64_t seed, uint64_t step, bf16 *xb, float *yb)
-{
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= B) return;
-    uint64_t r;
-    if (sample) r = splitmix64(seed ^ splitmix64(step * 0x100000001ull + (uint64_t)i)) % n;
-    else r = base + (uint64_t)i;
-    const bool ok = r < n;
-#pragma unroll
-    for (int k = 0; k < IN; ++k) xb[(size_t)i * IN + k] = __float2bfloat16(ok && k < n_in ? x[r * n_in + k] : 0.0f);
-    if (yb) yb[i] = ok ? y[r] : 0.0f;
-}
-
-constexpr int kMaxBatch = 65536;                             // rows per training step
-constexpr int kMaxTiles = kMaxBatch / kTcRows;
-constexpr int kMaxParts = 256;                               // weight-gradient CTAs (one per SM)
+// The training steps of one smc_mlp_train call as CUDA graphs: `full` runs
+// kGraphSteps steps, `rest` the remainder of an epoch; both read the step
+// counters from device memory, so that one graph serves every launch.
+struct TrainGraphs {
+    cudaGraphExec_t full = nullptr, rest = nullptr;
+    const float *x = nullptr, *y = nullptr;
+    uint64_t n = 0, seed = 0;
+    int batch = 0, n_full = 0, n_rest = 0;
+    float lr = 0.0f;
+};
 
 }  // namespace
 
@@ -521,11 +521,11 @@ struct smc_mlp {
     cudaStream_t stream = nullptr;
     float *master = nullptr, *am = nullptr, *av = nullptr, *part = nullptr, *grad = nullptr;
     bf16 *w1b = nullptr, *w2b = nullptr, *w3b = nullptr;
-    bf16 *xb = nullptr;    // the minibatch's rows, BF16 [kMaxBatch][16]
-    float *yb = nullptr, *loss = nullptr;
-    TrainTiles tt{};       // saved tiles of the training step (kMaxTiles each)
-    int *h_err = nullptr, *d_err = nullptr;  // a tensor-core wait gave up (mapped host memory)
-    uint64_t adam_t = 0;
+    float *loss = nullptr;                  // per-epoch loss sums, then the running sum at [kMaxEpochs]
+    unsigned long long *ctr = nullptr;      // sampling step, Adam's t
+    int *h_err = nullptr, *d_err = nullptr; // a tensor-core wait gave up (mapped host memory)
+    TrainGraphs graphs;
+    cudaEvent_t graphs_done = nullptr;      // after the last launch of the cached graphs
 };
 
 namespace {
@@ -546,30 +546,71 @@ int mfail(smc_mlp *m, int code, const std::string &msg)
 
 int refresh(smc_mlp *m, cudaStream_t s)
 {
-    mlp_update_kernel<<<(MLP_NPARAM + 255) / 256, 256, 0, s>>>(0, m->part, m->master, m->am, m->av, 0.0f, 0.f,
-                                                              0.f, 0.f, 1.f, 1.f, nullptr, m->w1b, m->w2b, m->w3b);
+    mlp_update_kernel<<<kUpdBlocks, kUpdThreads, 0, s>>>(0, m->part, m->master, m->am, m->av, 0.0f, 0.f,
+                                                              0.f, 0.f, m->ctr, nullptr, m->w1b, m->w2b, m->w3b);
     MCK(cudaGetLastError());
     return SMC_OK;
 }
 
-// One forward, backward and weight-gradient pass over the B rows already
-// gathered into xb / yb (the loss sum added to *loss_acc); *nparts = the
-// partial gradients written to part.
-int train_pass(smc_mlp *m, int B, float *loss_acc, cudaStream_t s, int *nparts)
+// One training-step kernel over the rows of rs (loss sum added to
+// *loss_acc; with adam, Adam's step count advanced); *nparts = the partial
+// gradients it writes.  Tiles are spread evenly over at most one CTA per SM.
+int step_launch(smc_mlp *m, const StepRows &rs, float *loss_acc, bool adam, cudaStream_t s, int *nparts)
 {
-    const int tiles = (B + kTcRows - 1) / kTcRows;
-    const int grid_rows = std::max(1, std::min((tiles + kTcGroups - 1) / kTcGroups, m->n_sm));
-    mlp_tc_forward<true><<<grid_rows, kTcThreads, kTcSmem, s>>>(nullptr, m->xb, (uint64_t)B, IN, nullptr, m->w1b,
-                                                               m->w2b, m->w3b, m->master, nullptr, m->tt, m->d_err);
+    const int tiles = (rs.B + kTcRows - 1) / kTcRows;
+    const int cap = std::min(m->n_sm, kMaxParts);
+    const int per = (tiles + cap - 1) / cap;
+    const int grid = (tiles + per - 1) / per;
+    mlp_train_step_kernel<<<grid, kStThreads, kStSmem, s>>>(rs, 1.0f / (float)rs.B, m->w1b, m->w2b, m->w3b,
+                                                             m->master, m->part, loss_acc,
+                                                             adam ? m->ctr + 1 : nullptr, m->d_err);
     MCK(cudaGetLastError());
-    mlp_train_bwd_kernel<<<grid_rows, kTcThreads, kBwSmem, s>>>(m->yb, (uint64_t)B, 1.0f / (float)B, m->w2b, m->w3b,
-                                                               m->master, m->tt, loss_acc, m->d_err);
-    MCK(cudaGetLastError());
-    const int parts = std::max(1, std::min(tiles, std::min(m->n_sm, kMaxParts)));
-    mlp_train_wgrad_kernel<<<parts, 128, kWgSmem, s>>>((uint64_t)tiles, m->tt, m->part, m->d_err);
-    MCK(cudaGetLastError());
-    *nparts = parts;
+    *nparts = grid;
     return SMC_OK;
+}
+
+// k training steps (step kernel + Adam update each) on stream s
+int enqueue_steps(smc_mlp *m, const StepRows &rs, float lr, int k, cudaStream_t s)
+{
+    for (int i = 0; i < k; ++i) {
+        int parts = 0;
+        const int rc = step_launch(m, rs, m->loss + kMaxEpochs, true, s, &parts);
+        if (rc) return rc;
+        mlp_update_kernel<<<kUpdBlocks, kUpdThreads, 0, s>>>(parts, m->part, m->master, m->am, m->av, lr,
+                                                                  0.9f, 0.999f, 1e-8f, m->ctr, nullptr, m->w1b,
+                                                                  m->w2b, m->w3b);
+        MCK(cudaGetLastError());
+    }
+    return SMC_OK;
+}
+
+// captures k training steps into an executable graph (on the library's own
+// stream, so that nothing else is captured)
+int capture_steps(smc_mlp *m, const StepRows &rs, float lr, int k, cudaGraphExec_t *out)
+{
+    *out = nullptr;
+    if (k == 0) return SMC_OK;
+    MCK(cudaStreamBeginCapture(m->stream, cudaStreamCaptureModeThreadLocal));
+    const int rc = enqueue_steps(m, rs, lr, k, m->stream);
+    cudaGraph_t g = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(m->stream, &g);
+    if (rc) {
+        if (g) cudaGraphDestroy(g);
+        return rc;
+    }
+    MCK(e);
+    const cudaError_t ei = cudaGraphInstantiate(out, g, 0);
+    cudaGraphDestroy(g);
+    MCK(ei);
+    return SMC_OK;
+}
+
+void drop_graphs(smc_mlp *m)
+{
+    if (m->graphs_done) cudaEventSynchronize(m->graphs_done);
+    if (m->graphs.full) cudaGraphExecDestroy(m->graphs.full);
+    if (m->graphs.rest) cudaGraphExecDestroy(m->graphs.rest);
+    m->graphs = TrainGraphs{};
 }
 
 int check_waits(smc_mlp *m)
@@ -602,33 +643,26 @@ int smc_mlp_create(smc_mlp **out, int device, int n_in, uint64_t seed)
     };
     if (cudaSetDevice(device) != cudaSuccess) return fin(SMC_E_CUDA);
     if (cudaStreamCreateWithFlags(&m->stream, cudaStreamNonBlocking) != cudaSuccess) return fin(SMC_E_CUDA);
+    if (cudaEventCreateWithFlags(&m->graphs_done, cudaEventDisableTiming) != cudaSuccess) return fin(SMC_E_CUDA);
     const size_t np = MLP_NPARAM;
     void **f32[] = {(void **)&m->master, (void **)&m->am, (void **)&m->av, (void **)&m->grad};
     for (void **p : f32)
         if (cudaMalloc(p, np * 4) != cudaSuccess) return fin(SMC_E_OOM);
-    if (cudaMalloc((void **)&m->part, (size_t)kMaxParts * np * 4) != cudaSuccess) return fin(SMC_E_OOM);
+    if (cudaMalloc((void **)&m->part, (size_t)kMaxParts * kPartStride * 4) != cudaSuccess) return fin(SMC_E_OOM);
     void **wb[] = {(void **)&m->w1b, (void **)&m->w2b, (void **)&m->w3b};
     for (void **p : wb)
         if (cudaMalloc(p, (size_t)H * H * 2) != cudaSuccess) return fin(SMC_E_OOM);
-    if (cudaMalloc((void **)&m->xb, (size_t)kMaxBatch * IN * 2) != cudaSuccess) return fin(SMC_E_OOM);
-    if (cudaMalloc((void **)&m->yb, (size_t)kMaxBatch * 4) != cudaSuccess) return fin(SMC_E_OOM);
-    if (cudaMalloc((void **)&m->tt.x, (size_t)kMaxTiles * kTileX) != cudaSuccess) return fin(SMC_E_OOM);
-    unsigned char **tiles[] = {&m->tt.h1, &m->tt.h2, &m->tt.h3, &m->tt.d1, &m->tt.d2, &m->tt.d3};
-    for (unsigned char **p : tiles)
-        if (cudaMalloc((void **)p, (size_t)kMaxTiles * kTileH) != cudaSuccess) return fin(SMC_E_OOM);
-    if (cudaMalloc((void **)&m->tt.z, (size_t)kMaxBatch * 4) != cudaSuccess) return fin(SMC_E_OOM);
-    if (cudaMalloc((void **)&m->tt.dz, (size_t)kMaxBatch * 4) != cudaSuccess) return fin(SMC_E_OOM);
-    if (cudaMalloc((void **)&m->loss, 4096 * 4) != cudaSuccess) return fin(SMC_E_OOM);
+    if (cudaMalloc((void **)&m->loss, (size_t)(kMaxEpochs + 1) * 4) != cudaSuccess) return fin(SMC_E_OOM);
+    if (cudaMalloc((void **)&m->ctr, 2 * sizeof(unsigned long long)) != cudaSuccess) return fin(SMC_E_OOM);
+    if (cudaMemset(m->ctr, 0, 2 * sizeof(unsigned long long)) != cudaSuccess) return fin(SMC_E_CUDA);
     if (cudaHostAlloc((void **)&m->h_err, sizeof(int), cudaHostAllocMapped) != cudaSuccess) return fin(SMC_E_OOM);
     *m->h_err = 0;
     if (cudaHostGetDevicePointer((void **)&m->d_err, m->h_err, 0) != cudaSuccess) return fin(SMC_E_CUDA);
     if (cudaDeviceGetAttribute(&m->n_sm, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) return fin(SMC_E_CUDA);
-    const void *kern[] = {(const void *)mlp_tc_forward<false>, (const void *)mlp_tc_forward<true>,
-                          (const void *)mlp_train_bwd_kernel, (const void *)mlp_train_wgrad_kernel};
-    const int smem[] = {kTcSmem, kTcSmem, kBwSmem, kWgSmem};
-    for (int k = 0; k < 4; ++k)
-        if (cudaFuncSetAttribute(kern[k], cudaFuncAttributeMaxDynamicSharedMemorySize, smem[k]) != cudaSuccess)
-            return fin(SMC_E_CUDA);
+    if (cudaFuncSetAttribute(mlp_tc_forward, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem) != cudaSuccess ||
+        cudaFuncSetAttribute(mlp_train_step_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kStSmem) !=
+            cudaSuccess)
+        return fin(SMC_E_CUDA);
     // He-uniform initial weights from the seed; zero biases and Adam moments
     std::vector<float> w(np, 0.0f);
     std::mt19937_64 gen(seed);
@@ -654,11 +688,12 @@ void smc_mlp_destroy(smc_mlp *m)
     if (!m) return;
     cudaSetDevice(m->device);
     if (m->stream) cudaStreamSynchronize(m->stream);
-    void *ptrs[] = {m->master, m->am, m->av, m->part, m->grad, m->w1b, m->w2b, m->w3b, m->xb, m->yb, m->loss,
-                    m->tt.x, m->tt.h1, m->tt.h2, m->tt.h3, m->tt.d1, m->tt.d2, m->tt.d3, m->tt.z, m->tt.dz};
+    drop_graphs(m);
+    void *ptrs[] = {m->master, m->am, m->av, m->part, m->grad, m->w1b, m->w2b, m->w3b, m->loss, m->ctr};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (m->h_err) cudaFreeHost(m->h_err);
+    if (m->graphs_done) cudaEventDestroy(m->graphs_done);
     if (m->stream) cudaStreamDestroy(m->stream);
     delete m;
 }
@@ -675,6 +710,7 @@ int smc_mlp_get_params(smc_mlp *m, float *host)
 {
     if (!m || !host) return SMC_E_INVALID_ARG;
     MCK(cudaSetDevice(m->device));
+    if (m->graphs_done) MCK(cudaEventSynchronize(m->graphs_done));
     MCK(cudaStreamSynchronize(m->stream));
     MCK(cudaMemcpy(host, m->master, (size_t)MLP_NPARAM * 4, cudaMemcpyDeviceToHost));
     return SMC_OK;
@@ -684,6 +720,7 @@ int smc_mlp_set_params(smc_mlp *m, const float *host)
 {
     if (!m || !host) return SMC_E_INVALID_ARG;
     MCK(cudaSetDevice(m->device));
+    if (m->graphs_done) MCK(cudaEventSynchronize(m->graphs_done));
     MCK(cudaStreamSynchronize(m->stream));
     MCK(cudaMemcpy(m->master, host, (size_t)MLP_NPARAM * 4, cudaMemcpyHostToDevice));
     int rc = refresh(m, m->stream);
@@ -698,18 +735,19 @@ int smc_mlp_gradient(smc_mlp *m, const float *x, const float *y, int n, float *g
     int rc = check_waits(m);
     if (rc) return rc;
     MCK(cudaSetDevice(m->device));
+    if (m->graphs_done) MCK(cudaEventSynchronize(m->graphs_done));
     cudaStream_t s = m->stream;
-    mlp_gather_kernel<<<(n + 127) / 128, 128, 0, s>>>(x, y, (uint64_t)n, m->n_in, n, 0, 0, 0, 0, m->xb, m->yb);
-    MCK(cudaGetLastError());
-    MCK(cudaMemsetAsync(m->loss, 0, 4, s));
+    float *acc = m->loss + kMaxEpochs;
+    MCK(cudaMemsetAsync(acc, 0, 4, s));
+    StepRows rs{x, y, (uint64_t)n, m->n_in, n, 0, 0, 0, nullptr};
     int parts = 0;
-    rc = train_pass(m, n, m->loss, s, &parts);
+    rc = step_launch(m, rs, acc, false, s, &parts);
     if (rc) return rc;
-    mlp_update_kernel<<<(MLP_NPARAM + 255) / 256, 256, 0, s>>>(parts, m->part, m->master, m->am, m->av, 0.0f, 0.f,
-                                                              0.f, 0.f, 1.f, 1.f, m->grad, m->w1b, m->w2b, m->w3b);
+    mlp_update_kernel<<<kUpdBlocks, kUpdThreads, 0, s>>>(parts, m->part, m->master, m->am, m->av, 0.0f, 0.f,
+                                                              0.f, 0.f, m->ctr, m->grad, m->w1b, m->w2b, m->w3b);
     MCK(cudaGetLastError());
     MCK(cudaMemcpyAsync(grad_host, m->grad, (size_t)MLP_NPARAM * 4, cudaMemcpyDeviceToHost, s));
-    if (loss_host) MCK(cudaMemcpyAsync(loss_host, m->loss, 4, cudaMemcpyDeviceToHost, s));
+    if (loss_host) MCK(cudaMemcpyAsync(loss_host, acc, 4, cudaMemcpyDeviceToHost, s));
     MCK(cudaStreamSynchronize(s));
     if (loss_host) *loss_host /= (float)n;
     return check_waits(m);
@@ -718,32 +756,39 @@ int smc_mlp_gradient(smc_mlp *m, const float *x, const float *y, int n, float *g
 int smc_mlp_train(smc_mlp *m, const float *x, const float *y, uint64_t n, int epochs, int batch, float lr,
                   uint64_t seed, float *loss_host, void *stream)
 {
-    if (!m || !x || !y || n < 1 || epochs < 1 || epochs > 4096 || batch < 1 || batch > kMaxBatch || !(lr > 0.0f))
+    if (!m || !x || !y || n < 1 || epochs < 1 || epochs > kMaxEpochs || batch < 1 || batch > kMaxBatch ||
+        !(lr > 0.0f))
         return SMC_E_INVALID_ARG;
     int rc = check_waits(m);
     if (rc) return rc;
     MCK(cudaSetDevice(m->device));
     cudaStream_t s = stream ? (cudaStream_t)stream : m->stream;
     const uint64_t steps = (n + batch - 1) / (uint64_t)batch;
-    const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
-    MCK(cudaMemsetAsync(m->loss, 0, (size_t)epochs * 4, s));
-    for (int ep = 0; ep < epochs; ++ep) {
-        for (uint64_t st = 0; st < steps; ++st) {
-            const uint64_t step_id = (uint64_t)ep * steps + st;
-            mlp_gather_kernel<<<(batch + 127) / 128, 128, 0, s>>>(x, y, n, m->n_in, batch, 0, 1, seed, step_id,
-                                                                  m->xb, m->yb);
-            MCK(cudaGetLastError());
-            int parts = 0;
-            rc = train_pass(m, batch, m->loss + ep, s, &parts);
-            if (rc) return rc;
-            ++m->adam_t;
-            const float bc1 = 1.0f - std::pow(b1, (float)m->adam_t), bc2 = 1.0f - std::pow(b2, (float)m->adam_t);
-            mlp_update_kernel<<<(MLP_NPARAM + 255) / 256, 256, 0, s>>>(parts, m->part, m->master, m->am, m->av, lr,
-                                                                      b1, b2, eps, bc1, bc2, nullptr, m->w1b,
-                                                                      m->w2b, m->w3b);
-            MCK(cudaGetLastError());
+    const int n_full = (int)std::min<uint64_t>(steps, kGraphSteps);
+    const int n_rest = (int)(steps % (uint64_t)n_full);
+    const StepRows rs{x, y, n, m->n_in, batch, 0, 1, seed, m->ctr};
+    TrainGraphs &g = m->graphs;
+    if (!(g.full && g.x == x && g.y == y && g.n == n && g.seed == seed && g.batch == batch && g.lr == lr &&
+          g.n_full == n_full && g.n_rest == n_rest)) {
+        drop_graphs(m);
+        rc = capture_steps(m, rs, lr, n_full, &g.full);
+        if (!rc) rc = capture_steps(m, rs, lr, n_rest, &g.rest);
+        if (rc) {
+            drop_graphs(m);
+            return rc;
         }
+        g.x = x, g.y = y, g.n = n, g.seed = seed, g.batch = batch, g.lr = lr, g.n_full = n_full, g.n_rest = n_rest;
     }
+    // sampling step 0 (Adam's t carries over); the minibatch of step k of
+    // the call is drawn from (seed, k)
+    MCK(cudaMemsetAsync(m->ctr, 0, sizeof(unsigned long long), s));
+    for (int ep = 0; ep < epochs; ++ep) {
+        MCK(cudaMemsetAsync(m->loss + kMaxEpochs, 0, 4, s));
+        for (uint64_t k = 0; k < steps / (uint64_t)n_full; ++k) MCK(cudaGraphLaunch(g.full, s));
+        if (g.rest) MCK(cudaGraphLaunch(g.rest, s));
+        MCK(cudaMemcpyAsync(m->loss + ep, m->loss + kMaxEpochs, 4, cudaMemcpyDeviceToDevice, s));
+    }
+    MCK(cudaEventRecord(m->graphs_done, s));
     if (loss_host) {
         MCK(cudaMemcpyAsync(loss_host, m->loss, (size_t)epochs * 4, cudaMemcpyDeviceToHost, s));
         MCK(cudaStreamSynchronize(s));
@@ -766,8 +811,8 @@ int smc_mlp_predict_masked(smc_mlp *m, const float *x, uint64_t n, const uint8_t
     const uint64_t tiles = (n + kTcRows - 1) / kTcRows;
     const uint64_t want = (tiles + kTcGroups - 1) / kTcGroups;
     const int grid = (int)std::max<uint64_t>(1, std::min<uint64_t>(want, (uint64_t)m->n_sm));
-    mlp_tc_forward<false><<<grid, kTcThreads, kTcSmem, s>>>(x, nullptr, n, m->n_in, skip, m->w1b, m->w2b, m->w3b,
-                                                            m->master, g, TrainTiles{}, m->d_err);
+    mlp_tc_forward<<<grid, kTcThreads, kTcSmem, s>>>(x, n, m->n_in, skip, m->w1b, m->w2b, m->w3b, m->master, g,
+                                                     m->d_err);
     MCK(cudaGetLastError());
     return SMC_OK;
 }
