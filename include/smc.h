@@ -71,7 +71,7 @@ extern "C" {
 #define SMC_NODE_ALWAYS 9     /* G[lo,hi] psi = not F[lo,hi] not psi       */
 #define SMC_NODE_NEXT 10      /* X[lo,hi] psi: the next state is entered at
                                  a time in [lo, hi] and satisfies psi (Sec.
-                                 3.1); psi a state formula, at the top level */
+                                 3.1)                                       */
 
 /* ---- atom comparison operators ------------------------------------------ */
 #define SMC_OP_LT 0
@@ -100,6 +100,10 @@ extern "C" {
                                      else a linear scan), 1 = linear scan, 2 = checkpoints
                                      for networks of more than 16 reactions; the same
                                      trajectories in every mode (default 0) */
+#define SMC_OPT_TRACE_CAP 9       /* trace monitor (formulas nested beyond the monitor's
+                                     units, see smc_load_property): positions each lane
+                                     records per trajectory, 16..2^24 (default 4096); a
+                                     trajectory that needs more gets status 3 */
 
 /* A node of the formula in postfix order: operands precede their operator. */
 typedef struct {
@@ -127,7 +131,9 @@ typedef struct {
     uint64_t *counts; /* [n_inst][4]: yes, n, events, budget_hits; ADDED to  */
     double *wilson;   /* [n_inst][3]: p_hat, lo, hi of the counts after the call */
     uint8_t *verdict; /* [n_inst][n_traj]: 1 = phi holds                      */
-    uint8_t *status;  /* [n_inst][n_traj]: 0 decided, 1 event budget          */
+    uint8_t *status;  /* [n_inst][n_traj]: 0 decided, 1 event budget, 3 the
+                         trace monitor's recording full (or undecided past
+                         4 t_horizon + 1); 1 and 3 count as budget_hits      */
     uint64_t *events; /* [n_inst][n_traj]: reactions fired                    */
     double *t_final;  /* [n_inst][n_traj]: entry time of the last state       */
     int32_t *x_final; /* [n_inst][n_traj][S_max]: last state                  */
@@ -179,15 +185,29 @@ int smc_load_model_batch(smc_ctx *ctx, int n_instances, const int32_t *n_species
  *  t_max_unbounded: horizon of the pessimistic rule (Sec. 3.2) for
  *      formulas with an infinite interval end: a trajectory still undecided
  *      when its clock passes t_max is counted false.
- * The library compiles the formula into a monitor automaton.  Supported:
+ * The library compiles the formula into a monitor automaton when it can:
  * boolean combinations (<= 4 temporal operators, <= 6 distinct atoms) of
  * U[a,b], F[a,b], G[a,b] whose left operand is a state formula and whose
  * right operand is a state formula, or a state formula AND F[0,d] / G[0,d]
- * of a state formula (after pushing negations inward).  Others:
- * SMC_E_UNSUPPORTED. */
+ * of a state formula (after pushing negations inward), and X[a,b] of a
+ * state formula at the top level.  Any other formula of the grammar (Sec.
+ * 3.1: U, F, G, X nested in either operand, to a tree height of 10 and 32
+ * nodes, <= 6 distinct atoms) runs on the trace monitor: each lane records
+ * its trajectory (entry times, atoms; SMC_OPT_TRACE_CAP positions) and the
+ * formula's verdict, and the first point at which it is fixed, are computed
+ * from the recording (Sec. 3.2's lookahead buffer) on a doubling schedule of
+ * events and at the formula's horizon; the trajectory then reports the
+ * events, clock and state of that point, as if it had stopped there.  The
+ * trace monitor runs on the generic kernels only, and not under
+ * smc_simulate_noalloc, smc_simulate_snapshot or smc_estimate_cv (those
+ * return SMC_E_UNSUPPORTED).  Beyond its limits: SMC_E_UNSUPPORTED. */
 int smc_load_property(smc_ctx *ctx, int n_atoms, const int32_t *atom_coef,
                       const int32_t *atom_op, const double *atom_bound, int per_instance,
                       const smc_node *nodes, int n_nodes, double t_max_unbounded);
+
+/* Which monitor the loaded property runs on: 1 the monitor's units, 2 the
+ * trace monitor (see smc_load_property), 0 no property loaded (or ctx NULL). */
+int smc_monitor_kind(const smc_ctx *ctx);
 
 /* Rate-law factors beyond mass action.  Sec. 2.2 uses mass-action
  * propensities; the cell-cycle model of Sec. 5 needs rational rate laws

@@ -200,6 +200,12 @@ class Context:
     def set_option(self, name: str, value: float):
         self._check(N.smc_set_option(self.h, N.OPT[name], float(value)), f'smc_set_option({name})')
 
+    @property
+    def monitor_kind(self) -> str:
+        """'units' (the monitor automaton), 'trace' (the trace monitor, for
+        formulas nested beyond the units) or 'none' (smc_monitor_kind)."""
+        return {0: 'none', 1: 'units', 2: 'trace'}[N.smc_monitor_kind(self.h)]
+
     def cme_reach(self, instance: int = 0, cap: int = 1000, max_states: int = 2_000_000):
         """Exact P(property) by uniformisation (smc_cme_reach): dict p,
         truncated, poisson_tail, n_states, iterations, lambda_t."""

@@ -28,7 +28,7 @@ SMC_CONSERVATIVE = 2 << 4
 NODE = dict(true=0, false=1, atom=2, **{'not': 3, 'and': 4, 'or': 5, 'implies': 6}, U=7, F=8, G=9, X=10)
 OP = {'<': 0, '<=': 1, '>=': 2, '>': 3, '==': 4, '!=': 5}
 OPT = dict(event_budget=0, renorm_log2=1, autotune=2, warps_per_block=3, blocks_per_sm=4, selection=8,
-           refill=5, record=6, jit=7)
+           refill=5, record=6, jit=7, trace_cap=9)
 
 c_i32p = ctypes.POINTER(ctypes.c_int32)
 c_u8p = ctypes.POINTER(ctypes.c_uint8)
@@ -103,6 +103,7 @@ SIGNATURES = {
                                          ctypes.c_int, ctypes.POINTER(smc_node), ctypes.c_int,
                                          ctypes.c_double]),
     'smc_set_option': (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_double]),
+    'smc_monitor_kind': (ctypes.c_int, [ctypes.c_void_p]),
     'smc_cme_reach': (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int32, ctypes.c_int64,
                                      ctypes.POINTER(smc_cme_result)]),
     'smc_set_atom_expression': (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int,

@@ -12,7 +12,7 @@ CSRC = os.path.join(HERE, 'csrc')
 BUILD = os.path.join(HERE, '_build')
 LIB = os.path.join(BUILD, 'libsmc.so')
 SOURCES = ['smc_kernels.cu', 'smc_api.cu', 'smc_compile.cpp', 'smc_mlp.cu', 'smc_jit.cpp', 'smc_cme.cu']
-HEADERS = ['smc_internal.h', 'smc_compile.h', 'smc_mlp.h', 'smc_mlp_train.cuh', 'smc_tc.h', 'smc_device.cuh', 'smc_jit.h',
+HEADERS = ['smc_internal.h', 'smc_compile.h', 'smc_nest.h', 'smc_mlp.h', 'smc_mlp_train.cuh', 'smc_tc.h', 'smc_device.cuh', 'smc_jit.h',
            'smc_jit_kernel.cuh', 'nvrtc_stdint.h', 'smc_cme.h', 'smc_fp64i.h']
 # sources of the run-time compiled kernels, embedded into the library as
 # (include name, file) pairs

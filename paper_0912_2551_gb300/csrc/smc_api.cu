@@ -61,6 +61,14 @@ struct smc_ctx {
     // property
     bool have_prop = false;
     MonProg prog;
+    // trace monitor (formulas nested beyond the monitor's units, smc_nest.h)
+    bool nest_mode = false;
+    NestProg nest{};
+    NestProg *d_nest = nullptr;
+    uint32_t trace_cap = 4096;          // positions recorded per lane
+    double *d_tr_t = nullptr;           // [trace_cap][lanes] entry times
+    uint32_t *d_tr_w = nullptr;         // [trace_cap][lanes] atom bits | reaction << 24
+    size_t tr_lanes = 0;                // lanes the buffers hold
     std::vector<int> used_atoms;
     int n_atoms = 0;
     bool per_instance_bound = false;
@@ -177,6 +185,10 @@ void free_device(smc_ctx *ctx)
     dfree(ctx->d_blobs);
     dfree(ctx->d_blob_off);
     dfree(ctx->d_prog);
+    dfree(ctx->d_nest);
+    dfree(ctx->d_tr_t);
+    dfree(ctx->d_tr_w);
+    ctx->tr_lanes = 0;
     for (auto &c : ctx->classes) dfree(c.d_list);
     ctx->classes.clear();
     dfree(ctx->single.d_list);
@@ -363,6 +375,7 @@ void try_specialize(smc_ctx *ctx)
     ctx->jit_ready = false;
     ctx->jit_why.clear();
     if (!ctx->jit) { ctx->jit_why = "disabled by option"; return; }
+    if (ctx->nest_mode) { ctx->jit_why = "the formula needs the trace monitor"; return; }
     const int n = ctx->n_inst, S = ctx->S[0], R = ctx->R[0], nu = (int)ctx->used_atoms.size();
     std::vector<int32_t> coef0((size_t)nu * S);
     std::vector<int64_t> lo0(nu), hi0(nu);
@@ -493,6 +506,10 @@ int prepare(smc_ctx *ctx)
     CK(cudaMemcpy(ctx->d_blob_off, off.data(), n * 8, cudaMemcpyHostToDevice));
     CK(cudaMalloc(&ctx->d_prog, sizeof(MonProg)));
     CK(cudaMemcpy(ctx->d_prog, &ctx->prog, sizeof(MonProg), cudaMemcpyHostToDevice));
+    if (ctx->nest_mode) {
+        CK(cudaMalloc(&ctx->d_nest, sizeof(NestProg)));
+        CK(cudaMemcpy(ctx->d_nest, &ctx->nest, sizeof(NestProg), cudaMemcpyHostToDevice));
+    }
     std::vector<SizeClass *> all_classes;
     for (auto &c : ctx->classes) all_classes.push_back(&c);
     all_classes.push_back(&ctx->single);
@@ -522,6 +539,32 @@ int prepare(smc_ctx *ctx)
     }
     try_specialize(ctx);
     ctx->dirty = false;
+    return SMC_OK;
+}
+
+// generic kernel variant: bit 0 rate-law factors / arithmetic atoms, bit 1
+// the trace monitor
+int kvar(const smc_ctx *ctx) { return (ctx->ext ? 1 : 0) | (ctx->nest_mode ? 2 : 0); }
+
+// Trace monitor: recording buffers for `lanes` lanes of trace_cap positions
+// (grown, never shrunk, while the context's device state lives).  Called
+// when a launch is planned, before any stream capture.
+int ensure_trace(smc_ctx *ctx, size_t lanes)
+{
+    if (ctx->tr_lanes >= lanes && ctx->d_tr_t) return SMC_OK;
+    dfree(ctx->d_tr_t);
+    dfree(ctx->d_tr_w);
+    ctx->tr_lanes = 0;
+    const size_t n = lanes * ctx->trace_cap;
+    if (cudaMalloc(&ctx->d_tr_t, n * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&ctx->d_tr_w, n * sizeof(uint32_t)) != cudaSuccess) {
+        cudaGetLastError();
+        dfree(ctx->d_tr_t);
+        dfree(ctx->d_tr_w);
+        return fail(ctx, SMC_E_OOM, "trace monitor buffers (" + std::to_string(n * 12 >> 20) + " MiB): "
+                                    "lower SMC_OPT_TRACE_CAP or the launch shape");
+    }
+    ctx->tr_lanes = lanes;
     return SMC_OK;
 }
 
@@ -590,14 +633,15 @@ int plan_class(smc_ctx *ctx, int plain, const SizeClass &c, const Shape &sh, Lau
     if ((size_t)L.smem > ctx->smem_optin)
         return fail(ctx, SMC_E_UNSUPPORTED, "model tables do not fit in shared memory");
     const int set_rc =
-        L.kernel ? smc_jit_set_smem_limit(L.kernel, L.smem) : smc_ssa_set_smem_limit(plain, ctx->ext, L.smem);
+        L.kernel ? smc_jit_set_smem_limit(L.kernel, L.smem) : smc_ssa_set_smem_limit(plain, kvar(ctx), L.smem);
     if (set_rc) return fail(ctx, SMC_E_CUDA, "cudaFuncSetAttribute failed");
     int per_sm = 0;
     const int occ_rc = L.kernel ? smc_jit_max_blocks_per_sm(L.kernel, L.block, L.smem, &per_sm)
-                                : smc_ssa_max_blocks_per_sm(plain, ctx->ext, L.block, L.smem, &per_sm);
+                                : smc_ssa_max_blocks_per_sm(plain, kvar(ctx), L.block, L.smem, &per_sm);
     if (occ_rc || per_sm < 1) return fail(ctx, SMC_E_UNSUPPORTED, "no block of this shape fits on an SM");
     if (sh.blocks_sm > 0) per_sm = std::min(per_sm, sh.blocks_sm);
     L.grid = ctx->n_sm * per_sm;
+    if (ctx->nest_mode) return ensure_trace(ctx, (size_t)L.grid * L.block);
     return SMC_OK;
 }
 
@@ -616,10 +660,17 @@ int issue_class(smc_ctx *ctx, int plain, const SsaParams &common, const Launch &
     p.sel_block = L.blocked ? 1 : 0;
     p.logtab = ctx->d_logtab;
     p.logtab_bytes = plain ? SMC_LOGTAB_BYTES : 0;
+    if (ctx->nest_mode) {  // buffers as planned (launches on one stream, one after another)
+        p.nest = ctx->d_nest;
+        p.tr_t = ctx->d_tr_t;
+        p.tr_w = ctx->d_tr_w;
+        p.tr_cap = ctx->trace_cap;
+        p.tr_stride = ctx->tr_lanes;
+    }
     if (smc_launch_queue_init(p, s))
         return fail(ctx, SMC_E_CUDA, std::string("queue init: ") + cudaGetErrorString(cudaGetLastError()));
     const int lrc = L.kernel ? smc_jit_launch(L.kernel, p, L.grid, L.block, L.smem, s)
-                             : smc_launch_ssa(plain, ctx->ext, p, L.grid, L.block, L.smem, s);
+                             : smc_launch_ssa(plain, kvar(ctx), p, L.grid, L.block, L.smem, s);
     if (lrc)
         return fail(ctx, SMC_E_CUDA,
                     std::string("ssa launch: ") + (L.kernel ? cudaGetErrorString(cudaGetLastError()) : smc_kernel_error()));
@@ -682,7 +733,9 @@ std::vector<int64_t> tune_signature(const smc_ctx *ctx)
 
 int autotune(smc_ctx *ctx, int plain, cudaStream_t s)
 {
-    if (!ctx->autotune || ctx->explicit_shape || ctx->tuned[plain]) return SMC_OK;
+    // (the trace monitor keeps the default shape: its trials would time the
+    // formula's evaluation, not the launch shape)
+    if (!ctx->autotune || ctx->explicit_shape || ctx->tuned[plain] || ctx->nest_mode) return SMC_OK;
     const std::vector<int64_t> sig = tune_signature(ctx);
     auto &memo = ctx->memo[plain];
     if (memo.valid && memo.sig == sig) {
@@ -1082,8 +1135,17 @@ int smc_load_property(smc_ctx *ctx, int n_atoms, const int32_t *atom_coef, const
     int rc = smc::parse_formula(nodes, n_nodes, n_atoms, tree, root, ctx->err);
     if (rc) return rc;
     MonProg prog;
+    NestProg nest;
     std::vector<int> used;
     rc = smc::compile_formula(tree, root, n_atoms, t_max_unbounded, prog, used, ctx->err);
+    const bool nested = rc == SMC_E_UNSUPPORTED;  // outside the units' shapes: the trace monitor
+    if (nested) {
+        rc = smc::compile_nested(tree, root, n_atoms, t_max_unbounded, nest, used, ctx->err);
+        if (!rc) {
+            std::memset(&prog, 0, sizeof(prog));
+            prog.n_atoms = (int)used.size();
+        }
+    }
     if (rc) return rc;
     const int n = ctx->n_inst;
     std::vector<size_t> coff(n);
@@ -1096,6 +1158,8 @@ int smc_load_property(smc_ctx *ctx, int n_atoms, const int32_t *atom_coef, const
     for (size_t i = 0; i < nb; ++i)
         if (!std::isfinite(atom_bound[i])) return fail(ctx, SMC_E_INVALID_ARG, "atom bounds must be finite");
     ctx->prog = prog;
+    ctx->nest_mode = nested;
+    if (nested) ctx->nest = nest;
     ctx->used_atoms = used;
     ctx->n_atoms = n_atoms;
     ctx->per_instance_bound = per_instance != 0;
@@ -1109,6 +1173,12 @@ int smc_load_property(smc_ctx *ctx, int n_atoms, const int32_t *atom_coef, const
     return SMC_OK;
 }
 
+int smc_monitor_kind(const smc_ctx *ctx)
+{
+    if (!ctx || !ctx->have_prop) return 0;
+    return ctx->nest_mode ? 2 : 1;
+}
+
 int smc_set_option(smc_ctx *ctx, int option, double value)
 {
     if (!ctx) return SMC_E_INVALID_ARG;
@@ -1116,6 +1186,15 @@ int smc_set_option(smc_ctx *ctx, int option, double value)
     case SMC_OPT_EVENT_BUDGET:
         if (!(value >= 1.0) || value > 4294967295.0) return fail(ctx, SMC_E_INVALID_ARG, "budget 1..2^32-1");
         ctx->budget = (uint64_t)value;
+        return SMC_OK;
+    case SMC_OPT_TRACE_CAP:
+        if (!(value >= 16.0 && value <= 16777216.0)) return fail(ctx, SMC_E_INVALID_ARG, "trace capacity 16..2^24");
+        if ((uint32_t)value != ctx->trace_cap) {
+            ctx->trace_cap = (uint32_t)value;
+            dfree(ctx->d_tr_t);
+            dfree(ctx->d_tr_w);
+            ctx->tr_lanes = 0;
+        }
         return SMC_OK;
     case SMC_OPT_RENORM_LOG2:
         if (!(value >= 0.0 && value <= 24.0)) return fail(ctx, SMC_E_INVALID_ARG, "renorm log2 0..24");
@@ -1233,6 +1312,8 @@ int smc_simulate_noalloc(smc_ctx *ctx, int precision, uint64_t seed, uint64_t tr
     if (!ctx->have_model || !ctx->have_prop || ctx->dirty || !ctx->d_blobs)
         return fail(ctx, SMC_E_STATE,
                     "model tables not on the device: call smc_simulate or smc_estimate once first");
+    if (ctx->nest_mode)
+        return fail(ctx, SMC_E_UNSUPPORTED, "smc_simulate_noalloc: the trace monitor's formulas need its buffers");
     if (ctx->n_inst > SMC_NOALLOC_MAX_INSTANCES)
         return fail(ctx, SMC_E_INVALID_ARG,
                     "smc_simulate_noalloc supports at most SMC_NOALLOC_MAX_INSTANCES (4096) instances");
@@ -1348,7 +1429,7 @@ int smc_estimate(smc_ctx *ctx, double confidence, double half_width, uint64_t se
                 if (kv.first == L.kernel) { kv.second = std::max(kv.second, L.smem); seen = true; }
             if (!seen) jit_max.emplace_back(L.kernel, L.smem);
         }
-        if (gen_max && smc_ssa_set_smem_limit(plain, ctx->ext, gen_max))
+        if (gen_max && smc_ssa_set_smem_limit(plain, kvar(ctx), gen_max))
             return fail(ctx, SMC_E_CUDA, "cudaFuncSetAttribute failed");
         for (auto &kv : jit_max)
             if (smc_jit_set_smem_limit(kv.first, kv.second)) return fail(ctx, SMC_E_CUDA, "cudaFuncSetAttribute failed");
@@ -1491,6 +1572,8 @@ int smc_monitor_replay(smc_ctx *ctx, int n_paths, const int32_t *len, const int3
         if (ng) neg |= 1u << b;
     }
     MonProg *d_prog = nullptr;
+    NestProg *d_nest = nullptr;
+    uint32_t *d_w = nullptr;
     int32_t *d_coef = nullptr, *d_len = nullptr, *d_x = nullptr, *d_v = nullptr;
     int64_t *d_thr = nullptr, *d_off = nullptr, *d_q = nullptr;
     double *d_t = nullptr, *d_tmin = nullptr;
@@ -1517,6 +1600,11 @@ int smc_monitor_replay(smc_ctx *ctx, int n_paths, const int32_t *len, const int3
         CK(cudaMemcpy(d_t, t, (size_t)total * 8, cudaMemcpyHostToDevice));
         CK(cudaMemcpy(d_tmin, tmin, n_paths * 8, cudaMemcpyHostToDevice));
         CK(cudaMemcpy(d_closed, closed, n_paths, cudaMemcpyHostToDevice));
+        if (ctx->nest_mode) {
+            CK(cudaMalloc(&d_nest, sizeof(NestProg)));
+            CK(cudaMemcpy(d_nest, &ctx->nest, sizeof(NestProg), cudaMemcpyHostToDevice));
+            CK(cudaMalloc(&d_w, (size_t)total * 4));
+        }
         ReplayParams rp;
         rp.prog = d_prog;
         rp.coef = d_coef;
@@ -1532,6 +1620,8 @@ int smc_monitor_replay(smc_ctx *ctx, int n_paths, const int32_t *len, const int3
         rp.closed = d_closed;
         rp.verdict = d_v;
         rp.decided_at = d_q;
+        rp.nest = d_nest;
+        rp.w = d_w;
         if (smc_launch_replay(rp, nullptr)) return fail(ctx, SMC_E_CUDA, "replay launch failed");
         CK(cudaMemcpy(verdict, d_v, n_paths * 4, cudaMemcpyDeviceToHost));
         CK(cudaMemcpy(decided_at, d_q, n_paths * 8, cudaMemcpyDeviceToHost));
@@ -1539,7 +1629,7 @@ int smc_monitor_replay(smc_ctx *ctx, int n_paths, const int32_t *len, const int3
     };
     rc = run();
     dfree(d_prog); dfree(d_coef); dfree(d_thr); dfree(d_len); dfree(d_off); dfree(d_x);
-    dfree(d_t); dfree(d_tmin); dfree(d_closed); dfree(d_v); dfree(d_q);
+    dfree(d_t); dfree(d_tmin); dfree(d_closed); dfree(d_v); dfree(d_q); dfree(d_nest); dfree(d_w);
     return rc;
 }
 
@@ -1553,6 +1643,8 @@ int smc_simulate_snapshot(smc_ctx *ctx, int precision, uint64_t seed, uint64_t t
     if (precision != SMC_PLAIN_FP64 && precision != SMC_MIXED) return fail(ctx, SMC_E_INVALID_ARG, "bad precision");
     if (traj_begin + n_traj > (1ull << 32)) return fail(ctx, SMC_E_INVALID_ARG, "trajectory index >= 2^32");
     if (!(t_snap >= 0.0) || !std::isfinite(t_snap)) return fail(ctx, SMC_E_INVALID_ARG, "t_snap must be finite, >= 0");
+    if (ctx->nest_mode)
+        return fail(ctx, SMC_E_UNSUPPORTED, "snapshots need the monitor's units (the formula needs the trace monitor)");
     int rc = prepare(ctx);
     if (rc) return rc;
     CK(cudaSetDevice(ctx->device));
@@ -1669,6 +1761,8 @@ int smc_estimate_cv(smc_ctx *ctx, smc_mlp *mlp, double confidence, double half_w
     if (!mlp || !out || !x_scale) return fail(ctx, SMC_E_INVALID_ARG, "null argument");
     if (!ctx->have_model || !ctx->have_prop) return fail(ctx, SMC_E_STATE, "load a model and a property first");
     if (ctx->n_inst != 1 || ctx->batch) return fail(ctx, SMC_E_UNSUPPORTED, "control variate needs one instance");
+    if (ctx->nest_mode)
+        return fail(ctx, SMC_E_UNSUPPORTED, "the control variate needs the monitor's units (the formula needs the trace monitor)");
     if (!(confidence > 0.0 && confidence < 1.0) || !(half_width > 0.0 && half_width < 0.5) || pilot < 2 ||
         !std::isfinite(beta))
         return fail(ctx, SMC_E_INVALID_ARG, "bad confidence, half width, pilot or beta");

@@ -291,6 +291,81 @@ int compile_formula(const std::vector<FNode> &tree, int root, int n_atoms, doubl
     return SMC_OK;
 }
 
+// The trace monitor's program (smc_nest.h): the formula tree renumbered
+// from the root, atoms as bits of the used-atom vector, the static horizon
+// (the latest time a position can matter: temporal operators add their
+// interval end to their operands' horizons) and the stopping time.
+namespace {
+// -1: too large (err says why), -2: a bad interval
+int nest_copy(const std::vector<FNode> &T, int n, const std::vector<int> &bit, NestProg &np, int depth,
+              std::string &err)
+{
+    if (depth > SMC_NEST_MAX_DEPTH) { err = "formula deeper than 10 nodes"; return -1; }
+    if (np.n_nodes >= SMC_NEST_MAX_NODES) { err = "formula of more than 32 nodes"; return -1; }
+    const FNode &f = T[n];
+    const int id = np.n_nodes++;
+    NestNode nd{};
+    nd.kind = f.kind;
+    nd.c0 = nd.c1 = -1;
+    nd.bit = f.kind == SMC_NODE_ATOM ? bit[f.arg] : -1;
+    nd.lo = f.lo;
+    nd.hi = f.hi;
+    const bool temporal = f.kind == SMC_NODE_UNTIL || f.kind == SMC_NODE_EVENTUALLY ||
+                          f.kind == SMC_NODE_ALWAYS || f.kind == SMC_NODE_NEXT;
+    if (temporal && !(f.lo >= 0.0 && std::isfinite(f.lo) && f.hi >= f.lo)) {
+        err = "temporal interval needs 0 <= lo <= hi, lo finite";
+        return -2;
+    }
+    if (f.c0 >= 0 && (nd.c0 = nest_copy(T, f.c0, bit, np, depth + 1, err)) < 0) return nd.c0;
+    if (f.c1 >= 0 && (nd.c1 = nest_copy(T, f.c1, bit, np, depth + 1, err)) < 0) return nd.c1;
+    np.height = std::max(np.height, depth);
+    np.nd[id] = nd;
+    return id;
+}
+
+double nest_horizon(const NestProg &np, int n)
+{
+    const NestNode &f = np.nd[n];
+    switch (f.kind) {
+    case SMC_NODE_TRUE: case SMC_NODE_FALSE: case SMC_NODE_ATOM: return 0.0;
+    case SMC_NODE_NOT: return nest_horizon(np, f.c0);
+    case SMC_NODE_AND: case SMC_NODE_OR: case SMC_NODE_IMPLIES:
+        return std::max(nest_horizon(np, f.c0), nest_horizon(np, f.c1));
+    case SMC_NODE_UNTIL: return f.hi + std::max(nest_horizon(np, f.c0), nest_horizon(np, f.c1));
+    default: return f.hi + nest_horizon(np, f.c0);
+    }
+}
+}  // namespace
+
+int compile_nested(const std::vector<FNode> &tree, int root, int n_atoms, double t_max, NestProg &np,
+                   std::vector<int> &used_atoms, std::string &err)
+{
+    std::memset(&np, 0, sizeof(np));
+    std::vector<int> bit(n_atoms, -1);
+    used_atoms.clear();
+    collect_atoms(tree, root, bit, used_atoms);
+    if ((int)used_atoms.size() > SMC_MAX_ATOMS) {
+        err = "more than 6 distinct atoms";
+        return SMC_E_UNSUPPORTED;
+    }
+    const int rc = nest_copy(tree, root, bit, np, 1, err);
+    if (rc == -2) return SMC_E_INVALID_ARG;
+    if (rc < 0) return SMC_E_UNSUPPORTED;
+    np.root = 0;
+    np.t_static = nest_horizon(np, 0);
+    if (std::isinf(np.t_static)) {
+        if (!(t_max > 0.0) || std::isinf(t_max)) {
+            err = "unbounded formula needs a finite t_max_unbounded > 0";
+            return SMC_E_INVALID_ARG;
+        }
+        np.unbounded = 1;
+        np.t_stop = t_max;
+    } else {
+        np.t_stop = np.t_static;
+    }
+    return SMC_OK;
+}
+
 // ---------------------------------------------------------------------------
 
 namespace {

@@ -7,6 +7,7 @@
 
 #include "../../include/smc.h"
 #include "smc_internal.h"
+#include "smc_nest.h"
 
 namespace smc {
 
@@ -35,6 +36,14 @@ int parse_formula(const smc_node *nodes, int n_nodes, int n_atoms, std::vector<F
 // Compiles the formula tree into `prog`; used_atoms[bit] = original atom index.
 int compile_formula(const std::vector<FNode> &tree, int root, int n_atoms, double t_max,
                     MonProg &prog, std::vector<int> &used_atoms, std::string &err);
+
+// The trace monitor's program for any formula (smc_nest.h): used when
+// compile_formula rejects the shape.  SMC_E_UNSUPPORTED beyond 32 nodes, a
+// tree deeper than 10 or more than 6 atoms; SMC_E_INVALID_ARG for an
+// interval without 0 <= lo <= hi (lo finite) or an unbounded formula
+// without a finite t_max > 0.
+int compile_nested(const std::vector<FNode> &tree, int root, int n_atoms, double t_max, NestProg &np,
+                   std::vector<int> &used_atoms, std::string &err);
 
 // atom  L <op> b  (L an integer)  as  lo <= L <= hi, negated when neg.
 void atom_threshold(int op, double b, int64_t &lo, int64_t &hi, bool &neg);

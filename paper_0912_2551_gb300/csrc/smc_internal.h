@@ -176,6 +176,16 @@ struct SsaParams {
     // SMC_SEL_BLOCKS(r_max) of them per lane after the propensities), 0 =
     // linear scan
     int32_t sel_block;
+    // trace monitor (smc_nest.h; formulas nested beyond the units above):
+    // when nest is set the units are unused, and each lane records its
+    // trajectory's positions (at most tr_cap) in tr_t / tr_w, position m of
+    // lane l = blockIdx.x * blockDim.x + threadIdx.x at m * tr_stride + l
+    // (lanes interleaved): entry times; atom bits | entering reaction << 24
+    const struct NestProg *nest;
+    double *tr_t;
+    uint32_t *tr_w;
+    uint32_t tr_cap;
+    uint64_t tr_stride;
 };
 #define SMC_SEL_BLOCK 16
 #define SMC_SEL_BLOCKS(r) (((r) + SMC_SEL_BLOCK - 1) / SMC_SEL_BLOCK)
@@ -196,12 +206,15 @@ struct ReplayParams {
     const uint8_t *closed;   // [n_paths]
     int32_t *verdict;        // [n_paths] 0 undetermined, 1 false, 2 true
     int64_t *decided_at;     // [n_paths] 2k / 2k+1 decision point or -1
+    const struct NestProg *nest;  // trace monitor instead of the units (or null)
+    uint32_t *w;             // [total] scratch: atom bits per state (trace monitor)
 };
 
 #if defined(__cplusplus) && !defined(__CUDACC_RTC__)  // host code only (not in run-time compilation)
 extern "C++" {
 // host launch wrappers (smc_kernels.cu)
-// ext: the model uses rate-law factors or arithmetic atoms (kernel variant)
+// ext: kernel variant, bit 0 the model uses rate-law factors or arithmetic
+// atoms, bit 1 the trace monitor (SsaParams::nest)
 int smc_launch_ssa(int plain, int ext, const SsaParams &p, int grid, int block, int smem_bytes,
                    void *stream);
 const char *smc_kernel_error();  // text of the last failed launch wrapper's error

@@ -28,6 +28,7 @@
 #include "smc_internal.h"
 
 #include "smc_device.cuh"
+#include "smc_nest.h"
 
 namespace {
 
@@ -90,7 +91,7 @@ __device__ __forceinline__ typename Prec<PLAIN>::T propensity(uint32_t pw, const
     return a;
 }
 
-template <bool PLAIN, bool EXT>
+template <bool PLAIN, bool EXT, bool NEST>
 __device__ __forceinline__ void run_instance(const SsaParams &p, const MonProg &P, const uint64_t *ltab,
                                              const int m, const uint32_t *blob, int32_t *xs, double *tc,
                                              typename Prec<PLAIN>::T *as, typename Prec<PLAIN>::T *bs,
@@ -146,17 +147,28 @@ __device__ __forceinline__ void run_instance(const SsaParams &p, const MonProg &
     unsigned long long c_ev = 0;
     const int snap_mode = p.snap_mode;
     const double t_snap = p.t_snap;
+    // trace monitor: this lane's recording of the trajectory, and the
+    // doubling schedule of its checks (events 0, 1, 2, 4, ...; also at the
+    // horizon, absorption and the budget)
+    const NestProg *NP = NEST ? p.nest : nullptr;  // (NEST: a kernel variant of its own)
+    const uint64_t lane_id = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const uint64_t trs = p.tr_stride;  // position m of this lane at m * trs (lanes interleaved)
+    double *trt = NP ? p.tr_t + lane_id : nullptr;
+    uint32_t *trw = NP ? p.tr_w + lane_id : nullptr;
+    uint64_t nchk = 0;
 
     // verdict codes: 1 false, 2 true, 3 event budget exhausted, 4 stopped at
-    // the snapshot (prefix-only run: no verdict, not counted)
+    // the snapshot (prefix-only run: no verdict, not counted), 5 trace
+    // monitor gave up (its recording full, or still undecided when the
+    // clock passed 4 t_stop + 1): counted with the budget's undecided ones
     auto finish = [&](int v) {
-        if (v == 3) ++c_bud;
+        if (v == 3 || v == 5) ++c_bud;
         else if (v != 4) { ++c_dec; c_yes += (v == 2); }
         c_ev += e;
         const uint64_t idx = (uint64_t)m * p.out_stride + ((uint64_t)traj - p.out_base);
         if (p.o_verdict) {
             p.o_verdict[idx] = (v == 2);
-            if (p.o_status) p.o_status[idx] = (v == 3) ? 1 : (v == 4 ? 2 : 0);
+            if (p.o_status) p.o_status[idx] = (v == 3) ? 1 : (v == 4 ? 2 : (v == 5 ? 3 : 0));
             if (p.o_events) p.o_events[idx] = e;
             if (p.o_tfinal) p.o_tfinal[idx] = t;
             if (p.o_xfinal)
@@ -167,6 +179,28 @@ __device__ __forceinline__ void run_instance(const SsaParams &p, const MonProg &
             if (p.o_esnap) p.o_esnap[idx] = e;
         }
         active = false;
+    };
+    // trace monitor: the formula on the recorded positions 0..e and what
+    // follows them (smc_nest.h)
+    auto nest_at = [&](int end, double tnx) -> NestVal {
+        const NestTrace T{trt, trw, (int64_t)trs, (int64_t)e, end, tnx};
+        return nest_decide(*NP, T);
+    };
+    // stop at the decision point: the trajectory's outputs are those of
+    // position k = d / 2 (the counts rewound by the reactions recorded after it)
+    auto finish_at = [&](NestVal d) {
+        const uint32_t k = (uint32_t)(d.d >> 1);
+        if (p.o_xfinal)
+            for (uint32_t m2 = e; m2 > k; --m2) {
+                const uint32_t jr = trw[m2 * trs] >> 24;
+                for (uint32_t q = stp[jr], qe = stp[jr + 1]; q < qe; ++q) {
+                    const uint32_t w = st[q];
+                    xs[(w & 255u) * 32] -= ((int32_t)w) >> 8;
+                }
+            }
+        e = k;
+        t = trt[k * trs];
+        finish(d.v);
     };
 
     for (;;) {
@@ -202,12 +236,21 @@ __device__ __forceinline__ void run_instance(const SsaParams &p, const MonProg &
                         if (!PLAIN && blk) block_sums();
                         uint32_t ab = 0;
                         for (int a = 0; a < NA; ++a) ab |= atom_bit<EXT>(atoms, tptr, terms, ex, xs, a);
-                        ml.ab = ab;
-                        mon_start(ml, P);
                         active = true;
-                        const int v = mon_state(ml, P, 0.0, tc);
-                        mh.load(ml);
-                        if (v) finish(v);
+                        if constexpr (NEST) {
+                            trt[0] = 0.0;
+                            trw[0] = ab;
+                            mh.ab = ab;
+                            nchk = 1;
+                            const NestVal d = nest_at(0, 0.0);
+                            if (d.v) finish_at(d);
+                        } else {
+                            ml.ab = ab;
+                            mon_start(ml, P);
+                            const int v = mon_state(ml, P, 0.0, tc);
+                            mh.load(ml);
+                            if (v) finish(v);
+                        }
                     }
                 }
                 act = __ballot_sync(FULL_MASK, active);
@@ -254,8 +297,14 @@ __device__ __forceinline__ void run_instance(const SsaParams &p, const MonProg &
             a0 = (T)s;
             if (blk) block_sums();
         }
-        if (PLAIN ? __double_as_longlong((double)a0) <= 0 : !(a0 > (T)0)) {
-            finish(mon_close(ml, P));  // absorbing state: no further position
+        if (PLAIN ? __double_as_longlong((double)a0) <= 0 : !(a0 > (T)0)) {  // absorbing state: no further position
+            if constexpr (NEST) {
+                const NestVal d = nest_at(2, 0.0);
+                if (d.v) finish_at(d);
+                else finish(5);
+            } else {
+                finish(mon_close(ml, P));
+            }
             continue;
         }
         uint32_t w0, w1, w2, w3;
@@ -286,12 +335,21 @@ __device__ __forceinline__ void run_instance(const SsaParams &p, const MonProg &
             if (snap_mode == 2) { finish(4); continue; }
         }
         int v = 0;
-        if (mh.pend || __double_as_longlong(tn) > mh.hb) {
-            v = mon_draw(ml, P, tn, tc);
-            mh.load(ml);
+        if constexpr (NEST) {
+            if (dgt(tn, NP->t_stop)) {  // no later position can matter (or, unbounded: t_max passed)
+                const NestVal d = nest_at(1, tn);
+                if (d.v) { finish_at(d); continue; }
+                if (NP->unbounded) { finish_at(NestVal{1, 2 * (int64_t)e + 1}); continue; }  // pessimistic rule
+                if (dgt(tn, __dadd_rn(__dmul_rn(4.0, NP->t_stop), 1.0))) { finish(5); continue; }
+            }
+        } else {
+            if (mh.pend || __double_as_longlong(tn) > mh.hb) {
+                v = mon_draw(ml, P, tn, tc);
+                mh.load(ml);
+            }
+            if (!v && unbounded && dgt(tn, t_max)) v = 1;  // pessimistic rule (Sec. 3.2)
+            if (v) { finish(v); continue; }
         }
-        if (!v && unbounded && dgt(tn, t_max)) v = 1;  // pessimistic rule (Sec. 3.2)
-        if (v) { finish(v); continue; }
 
         // step 2: selection, first j whose running sum exceeds r
         int j = -1, last = -1;
@@ -360,7 +418,13 @@ __device__ __forceinline__ void run_instance(const SsaParams &p, const MonProg &
         }
         if (j < 0) j = last;  // r reached the full sum (rounding, or a drifted a0)
         if (j < 0) {          // every a_k is 0 (only a drifted FP32 a0 gets here)
-            finish(mon_close(ml, P));
+            if constexpr (NEST) {
+                const NestVal d = nest_at(2, 0.0);
+                if (d.v) finish_at(d);
+                else finish(5);
+            } else {
+                finish(mon_close(ml, P));
+            }
             continue;
         }
 
@@ -407,6 +471,20 @@ __device__ __forceinline__ void run_instance(const SsaParams &p, const MonProg &
                 ab = (ab & ~(1u << a)) | atom_bit<EXT>(atoms, tptr, terms, ex, xs, a);
             }
         }
+        if constexpr (NEST) {  // record the new position; check on the doubling schedule and at the budget
+            if (e >= p.tr_cap) { finish(5); continue; }
+            trt[e * trs] = t;
+            trw[e * trs] = ab | ((uint32_t)j << 24);
+            mh.ab = ab;
+            const bool at_budget = (uint64_t)e >= budget;
+            if ((uint64_t)e == nchk || at_budget) {
+                const NestVal d = nest_at(0, 0.0);
+                if (d.v) { finish_at(d); continue; }
+                if ((uint64_t)e == nchk) nchk *= 2;
+                if (at_budget) finish(3);
+            }
+            continue;
+        }
         if (always_step || ab != mh.ab || mh.pend) {
             ml.ab = ab;
             v = mon_state(ml, P, t, tc);
@@ -431,7 +509,7 @@ __device__ __forceinline__ void run_instance(const SsaParams &p, const MonProg &
 // SM), 80 for the FP64 path (24 warps; its FP64 pipe saturates before issue).
 // EXT: the model uses rate-law factors or arithmetic atoms; without them the
 // kernel carries none of their code (and none of its register pressure).
-template <bool PLAIN, bool EXT>
+template <bool PLAIN, bool EXT, bool NEST>
 __global__ void __launch_bounds__(256, PLAIN ? 3 : 4) ssa_kernel(const SsaParams p)
 {
     typedef typename Prec<PLAIN>::T T;
@@ -465,7 +543,7 @@ __global__ void __launch_bounds__(256, PLAIN ? 3 : 4) ssa_kernel(const SsaParams
             blob = p.blobs + p.blob_off[m];
             cur = m;
         }
-        run_instance<PLAIN, EXT>(p, P, ltab, m, blob, xs, tc, as, bs, lane);
+        run_instance<PLAIN, EXT, NEST>(p, P, ltab, m, blob, xs, tc, as, bs, lane);
         __syncwarp();
     }
 
@@ -491,6 +569,24 @@ __global__ void replay_kernel(const ReplayParams rp)
     const int na = P.n_atoms, S = rp.S, n = rp.len[i];
     const int32_t *x = rp.x + rp.off[i] * S;
     const double *t = rp.t + rp.off[i];
+    if (rp.nest) {  // trace monitor: the path as recorded, then what follows it
+        uint32_t *w = rp.w + rp.off[i];
+        for (int k = 0; k < n; ++k) {
+            uint32_t ab = 0;
+            for (int a = 0; a < na; ++a) {
+                long long L = 0;
+                for (int s2 = 0; s2 < S; ++s2) L += (long long)rp.coef[a * S + s2] * x[k * S + s2];
+                const uint32_t in = (L >= rp.athr[2 * a]) & (L <= rp.athr[2 * a + 1]);
+                ab |= (in ^ ((rp.aneg >> a) & 1u)) << a;
+            }
+            w[k] = ab;
+        }
+        const NestTrace T{t, w, 1, (int64_t)n - 1, rp.closed[i] ? 2 : 3, rp.tmin[i]};
+        const NestVal d = nest_decide(*rp.nest, T);
+        rp.verdict[i] = d.v;
+        rp.decided_at[i] = d.v ? d.d : -1;
+        return;
+    }
     double tc_local[SMC_MAX_UNITS * 32];
     double *tc = tc_local;
     MonLane ml;
@@ -539,10 +635,15 @@ static int to_code(cudaError_t e)
 
 const char *smc_kernel_error() { return cudaGetErrorString(g_kernel_err); }
 
-static const void *ssa_kernel_ptr(int plain, int ext)
+// variant: bit 0 rate-law factors or arithmetic atoms (EXT), bit 1 the
+// trace monitor (NEST)
+static const void *ssa_kernel_ptr(int plain, int variant)
 {
-    if (plain) return ext ? (const void *)ssa_kernel<true, true> : (const void *)ssa_kernel<true, false>;
-    return ext ? (const void *)ssa_kernel<false, true> : (const void *)ssa_kernel<false, false>;
+    const void *k[2][4] = {{(const void *)ssa_kernel<false, false, false>, (const void *)ssa_kernel<false, true, false>,
+                            (const void *)ssa_kernel<false, false, true>, (const void *)ssa_kernel<false, true, true>},
+                           {(const void *)ssa_kernel<true, false, false>, (const void *)ssa_kernel<true, true, false>,
+                            (const void *)ssa_kernel<true, false, true>, (const void *)ssa_kernel<true, true, true>}};
+    return k[plain ? 1 : 0][variant & 3];
 }
 
 int smc_ssa_set_smem_limit(int plain, int ext, int smem_bytes)
@@ -559,14 +660,8 @@ int smc_ssa_max_blocks_per_sm(int plain, int ext, int block, int smem_bytes, int
 int smc_launch_ssa(int plain, int ext, const SsaParams &p, int grid, int block, int smem_bytes, void *stream)
 {
     cudaStream_t s = (cudaStream_t)stream;
-    if (plain) {
-        if (ext) ssa_kernel<true, true><<<grid, block, smem_bytes, s>>>(p);
-        else ssa_kernel<true, false><<<grid, block, smem_bytes, s>>>(p);
-    } else {
-        if (ext) ssa_kernel<false, true><<<grid, block, smem_bytes, s>>>(p);
-        else ssa_kernel<false, false><<<grid, block, smem_bytes, s>>>(p);
-    }
-    return to_code(cudaGetLastError());
+    void *args[] = {(void *)&p};
+    return to_code(cudaLaunchKernel(ssa_kernel_ptr(plain, ext), dim3(grid), dim3(block), args, (size_t)smem_bytes, s));
 }
 
 int smc_launch_queue_init(const SsaParams &p, void *stream)

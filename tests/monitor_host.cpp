@@ -9,7 +9,10 @@
 // Input: S n_atoms n_nodes; per atom op bound coef[S]; per node kind arg lo
 // hi; n_paths; per path len closed tmin, then len x [S] and len t.
 // Output: one line "verdict decided_at" per path (verdict 0 undetermined,
-// 1 false, 2 true).
+// 1 false, 2 true).  As the library does, a formula outside the monitor's
+// fragment goes to the trace monitor (smc_nest.h: the path's states and
+// entry times recorded, the verdict and its decision point computed from
+// them); with the argument "nest" every formula does.
 #include <math.h>
 #include <stdint.h>
 #include <stdio.h>
@@ -22,9 +25,11 @@
 #include "smc.h"
 #include "smc_compile.h"
 #include "smc_device.cuh"
+#include "smc_nest.h"
 
-int main()
+int main(int argc, char **argv)
 {
+    const bool force_nest = argc > 1 && strcmp(argv[1], "nest") == 0;
     int S, NA, NN;
     if (scanf("%d %d %d", &S, &NA, &NN) != 3) return 2;
     std::vector<int32_t> coef((size_t)NA * S), op(NA);
@@ -41,8 +46,12 @@ int main()
     std::string err;
     if (smc::parse_formula(nodes.data(), NN, NA, tree, root, err) != SMC_OK) { printf("parse: %s\n", err.c_str()); return 1; }
     MonProg P;
+    NestProg NP;
     std::vector<int> used;
-    if (smc::compile_formula(tree, root, NA, INFINITY, P, used, err) != SMC_OK) { printf("compile: %s\n", err.c_str()); return 1; }
+    int rc = force_nest ? SMC_E_UNSUPPORTED : smc::compile_formula(tree, root, NA, INFINITY, P, used, err);
+    const bool nest = rc == SMC_E_UNSUPPORTED;
+    if (nest) rc = smc::compile_nested(tree, root, NA, 1.0e300, NP, used, err);
+    if (rc != SMC_OK) { printf("compile: %s\n", err.c_str()); return 1; }
     const int nu = (int)used.size();
     std::vector<int64_t> thr(2 * (size_t)std::max(nu, 1));
     uint32_t aneg = 0;
@@ -61,6 +70,23 @@ int main()
         std::vector<double> t(n);
         for (auto &v : x) if (scanf("%d", &v) != 1) return 2;
         for (auto &v : t) if (scanf("%lf", &v) != 1) return 2;
+        if (nest) {  // the recorded path: atom bits per state, then what follows it
+            std::vector<uint32_t> w(n);
+            for (int k = 0; k < n; ++k) {
+                uint32_t ab = 0;
+                for (int b = 0; b < nu; ++b) {
+                    long long L = 0;
+                    for (int s = 0; s < S; ++s) L += (long long)coef[(size_t)used[b] * S + s] * x[(size_t)k * S + s];
+                    const uint32_t in = (L >= thr[2 * b]) & (L <= thr[2 * b + 1]);
+                    ab |= (in ^ ((aneg >> b) & 1u)) << b;
+                }
+                w[k] = ab;
+            }
+            const NestTrace T{t.data(), w.data(), 1, (int64_t)n - 1, closed ? 2 : 3, tmin};
+            const NestVal d = nest_decide(NP, T);
+            printf("%d %lld\n", d.v, d.v ? (long long)d.d : -1ll);
+            continue;
+        }
         // the replay order of the SSA kernels: draw of state k's entry time
         // (when the monitor asks for it), then state k; after the last state
         // the end of the path (closed) or a lower bound on the next entry time

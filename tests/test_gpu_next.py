@@ -1,7 +1,7 @@
 """The Next operator X[a,b] on the GPU: a closed form, per-trajectory parity
 with the oracle (FP64, both kernels) inside boolean combinations with other
-temporal operators, and rejection where it is not supported (nested in a
-right operand, or over a temporal operand)."""
+temporal operators, and nested in a temporal operand or over one (the trace
+monitor's shapes)."""
 import math
 
 import numpy as np
@@ -64,13 +64,22 @@ def test_fp64_matches_oracle_per_trajectory(smc, orc, name, jit):
     assert (g['events'][0].astype(np.uint64) == r['events']).mean() >= 0.9999
 
 
-def test_unsupported_next_shapes(smc):
-    from paper_0912_2551_gb300 import _native as N
+def test_next_nested_shapes_run_on_the_trace_monitor(smc, orc):
+    # X inside a temporal operand, and a temporal operator under X: beyond
+    # the monitor's units, decided by the trace monitor, per trajectory as
+    # the oracle decides them
+    import torch
     for f in [('F', 0.0, 10.0, ('X', 0.0, 1.0, A(0))),      # X inside a right operand
               ('X', 0.0, 1.0, ('F', 0.0, 1.0, A(0)))]:      # temporal operand
         m, p = _id(f)
+        n = 2000
         with smc.Context(0) as ctx:
             ctx.load_model(m)
-            with pytest.raises(smc.SmcError) as e:
-                ctx.load_property(p)
-            assert e.value.code == N.SMC_E_UNSUPPORTED, f
+            ctx.load_property(p)
+            assert ctx.monitor_kind == 'trace', f
+            g = ctx.simulate('plain', seed=8, n_traj=n, outputs=('verdict', 'status', 'events', 't_final'))
+            torch.cuda.synchronize()
+            g = {k: v.cpu().numpy() for k, v in g.items()}
+        r = orc.run(m, p, seed=8, n_traj=n)
+        assert (g['verdict'][0] == r['verdict']).all(), f
+        assert (g['events'][0].astype(np.uint64) == r['events']).all(), f

@@ -330,12 +330,18 @@ def test_invalid_arguments_are_rejected(ctx, smc):
         ctx.load_model(bad)
     assert e.value.code == -1
     ctx.load_model(m)
-    with pytest.raises(smc.SmcError) as e:  # F nested in the left operand of U
-        ctx.load_property(workloads.Property(p.atoms, ('U', 0, 5, ('F', 0, 1, ('atom', 0)), ('atom', 0))))
+    # F nested in the left operand of U: beyond the units, on the trace monitor
+    ctx.load_property(workloads.Property(p.atoms, ('U', 0, 5, ('F', 0, 1, ('atom', 0)), ('atom', 0))))
+    assert ctx.monitor_kind == 'trace'
+    deep = ('atom', 0)
+    for _ in range(10):  # a formula tree 11 nodes high: beyond the trace monitor too
+        deep = ('F', 0.0, 1.0, deep)
+    with pytest.raises(smc.SmcError) as e:
+        ctx.load_property(workloads.Property(p.atoms, ('U', 0, 5, deep, ('atom', 0))))
     assert e.value.code == -4
     with pytest.raises(smc.SmcError) as e:  # interval with lo > hi
         ctx.load_property(workloads.Property(p.atoms, ('F', 5.0, 1.0, ('atom', 0))))
-    assert e.value.code == -4
+    assert e.value.code == -1
     with pytest.raises(smc.SmcError) as e:  # estimate before the property
         ctx.estimate(0.95, 0.01, sampling='iterative')
     assert e.value.code == -5

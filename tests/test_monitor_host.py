@@ -5,7 +5,9 @@ driven over exhaustive tiny paths (all count sequences of length <= 5 over
 verdict at the same point as the oracle's trace semantics, for every
 formula of the oracle's monitor tests (nested F / G, until with windows,
 boolean combinations, Next).  The GPU test of the replay kernel runs the
-same comparison on the device."""
+same comparison on the device.  The same paths also go through the trace
+monitor (smc_nest.h) for every formula, and it alone serves the formulas
+nested beyond the unit monitor's shapes."""
 import math
 import os
 import random
@@ -32,14 +34,17 @@ def exe(tmp_path_factory):
     if gxx is None or not os.path.exists(os.path.join(CUDA, 'include', 'cuda_runtime.h')):
         pytest.skip('no g++ or CUDA headers')
     out = str(tmp_path_factory.mktemp('mon') / 'monitor_host')
-    subprocess.run([gxx, '-O1', '-std=c++17', '-I', CSRC, '-I', os.path.join(ROOT, 'include'),
+    subprocess.run([gxx, '-O1', '-std=c++17', '-ffp-contract=off', '-I', CSRC, '-I', os.path.join(ROOT, 'include'),
                     '-I', os.path.join(CUDA, 'include'), os.path.join(ROOT, 'tests', 'monitor_host.cpp'),
                     os.path.join(CSRC, 'smc_compile.cpp'), '-o', out], check=True)
     return out
 
 
+@pytest.mark.parametrize('mode', ['library', 'nest'])
 @pytest.mark.parametrize('fi', range(len(FORMULAS)))
-def test_monitor_matches_oracle_on_tiny_paths(exe, orc, fi):
+def test_monitor_matches_oracle_on_tiny_paths(exe, orc, fi, mode):
+    # library: the unit monitor for the formulas of its fragment, the trace
+    # monitor for the rest; nest: the trace monitor for every formula
     prop = workloads.Property(_atoms(), FORMULAS[fi])
     S = 1
     rng = random.Random(1000 + fi)
@@ -58,7 +63,8 @@ def test_monitor_matches_oracle_on_tiny_paths(exe, orc, fi):
         lines.append(f'{len(ts)} {int(closed)} {"inf" if math.isinf(tmin) else repr(float(tmin))}')
         lines.append(' '.join(str(int(v)) for v in xs))
         lines.append(' '.join(repr(float(v)) for v in ts))
-    r = subprocess.run([exe], input='\n'.join(lines) + '\n', capture_output=True, text=True, timeout=120)
+    args = [exe] + (['nest'] if mode == 'nest' else [])
+    r = subprocess.run(args, input='\n'.join(lines) + '\n', capture_output=True, text=True, timeout=120)
     assert r.returncode == 0, r.stdout + r.stderr
     out = [tuple(int(w) for w in ln.split()) for ln in r.stdout.splitlines()]
     assert len(out) == len(paths)

@@ -46,7 +46,19 @@ FORMULAS = [
     ('X', 0.5, 1.5, ('not', A(1))),
     ('and', ('X', 0.0, 2.0, A(2)), ('F', 0.0, 2.0, A(0))),
     ('or', ('X', 0.25, 1.0, A(5)), A(2)),
+    # nesting beyond the unit monitor's shapes (the trace monitor's formulas)
+    ('U', 0.0, 2.0, ('U', 0.0, 1.0, A(4), A(0)), A(2)),
+    ('F', 0.0, 2.0, ('X', 0.0, 0.5, A(0))),
+    ('G', 0.5, 2.0, ('X', 0.0, 1.0, ('not', A(1)))),
+    ('U', 0.0, 2.5, ('X', 0.0, 1.0, A(4)), A(2)),
+    ('F', 0.5, 1.5, ('G', 0.5, 1.0, A(0))),
+    ('G', 0.0, 1.5, ('F', 0.0, 1.0, ('G', 0.0, 0.5, A(0)))),
+    ('X', 0.0, 1.0, ('X', 0.0, 1.0, A(2))),
+    ('U', 0.5, 2.0, ('F', 0.0, 0.5, A(5)), ('G', 0.0, 1.0, A(4))),
+    ('or', ('G', 0.0, 1.0, ('F', 0.5, 1.0, A(0))), ('X', 0.0, 0.25, A(1))),
+    ('implies', ('F', 0.0, 1.0, A(2)), ('U', 0.0, 2.0, ('not', A(1)), ('X', 0.25, 0.75, A(0)))),
 ]
+NESTED = set(range(18, len(FORMULAS)))  # outside the unit monitor's fragment
 SINGLE = {0, 1, 2, 3, 4, 5, 14, 15}  # single-operator formulas: Kleene is complete
 
 
