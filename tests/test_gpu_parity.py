@@ -342,6 +342,8 @@ def test_invalid_arguments_are_rejected(ctx, smc):
     with pytest.raises(smc.SmcError) as e:  # interval with lo > hi
         ctx.load_property(workloads.Property(p.atoms, ('F', 5.0, 1.0, ('atom', 0))))
     assert e.value.code == -1
-    with pytest.raises(smc.SmcError) as e:  # estimate before the property
-        ctx.estimate(0.95, 0.01, sampling='iterative')
-    assert e.value.code == -5
+    with smc.Context(0) as fresh:  # estimate before the property
+        fresh.load_model(m)
+        with pytest.raises(smc.SmcError) as e:
+            fresh.estimate(0.95, 0.01, sampling='iterative')
+        assert e.value.code == -5
