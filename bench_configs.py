@@ -462,7 +462,7 @@ def cascade(args):
 # DRAM bytes (read + write) of one launch of the inference kernel on
 # 6,000,000 rows (ncu: the FP32 features read once, the outputs written
 # once; the weights come from L2)
-TRAFFIC_INFER = 144110336 + 14355712
+TRAFFIC_INFER = 144143872 + 13789952
 
 
 def surrogate_inference(args):
@@ -511,7 +511,7 @@ def surrogate_inference(args):
     z, _ = om.forward(theta, om.bf16_round(x[idx].numpy()))
     err = float(np.max(np.abs(out.cpu().numpy()[idx] - 1.0 / (1.0 + np.exp(-z)))))
     extra = {'tflops': tflops, 'rows': n,
-             'roofline': {'bound': 'tensor', 'kernel': 'mlp_infer_kernel (tcgen05, TMEM accumulators)',
+             'roofline': {'bound': 'tensor', 'kernel': 'mlp_tc_forward (tcgen05, TMEM accumulators)',
                           'achieved': tflops, 'peak': peak, 'unit': 'TFLOP/s', 'frac': tflops / peak,
                           'traffic': TRAFFIC_INFER if n == 6_000_000 else None,
                           'flop_per_row': flop_row,
@@ -526,6 +526,71 @@ def surrogate_inference(args):
                                  'sample': f'first {m} rows, FP64 NumPy (BLAS on all host cores), {dt:.1f} s'}
     _line(n / (ms * 1e-3), 'rows/s', args.steps, args.warmup, ms, 'bf16 (fp32 accumulate)',
           f'surrogate network 6 -> 128 x 3 -> 1 on {n:,} rows of Lotka-Volterra-family features', extra)
+
+
+def surrogate_training(args):
+    """The surrogate's training step alone (fused tcgen05 step kernel + Adam
+    update, replayed as CUDA graphs): one step of this line is one epoch of
+    minibatches of 65,536 rows over 8,388,608 synthetic feature rows (6
+    inputs: two counts / 1000 in [0, 3), the time, three log-rate offsets;
+    logistic targets), 201 MB of inputs (> L2, no flush needed); the other
+    batch sizes are reported beside it."""
+    import torch
+    import paper_0912_2551_gb300 as smc
+    from oracle import mlp as om
+    n, n_in, batch = 8 * 2**20, 6, 65536
+    dev = torch.device('cuda', 0)
+    g = torch.Generator(device=dev).manual_seed(0)
+    x = torch.rand((n, n_in), generator=g, device=dev)
+    x[:, :2] *= 3.0
+    x[:, 3:] = (x[:, 3:] * 2.0 - 1.0) * math.log(1.3)
+    logit = 2.0 * (x[:, 0] - x[:, 1]) + 0.5 * x[:, 2] + x[:, 3]
+    y = (torch.rand(n, generator=g, device=dev) < torch.sigmoid(logit)).float()
+    steps_per_epoch = math.ceil(n / batch)
+    flop = MLP_FLOPS_PER_ROW * batch * steps_per_epoch
+    net = smc.Mlp(n_in, seed=1)
+    stream = torch.cuda.current_stream(dev)
+    for w in range(args.warmup):
+        net.train(x, y, epochs=1, batch=batch, lr=1e-3, seed=100 + w)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clocks = bench.Clocks(0)
+    clocks.start()
+    for k in range(args.steps):
+        ev[k][0].record(stream)
+        net.train(x, y, epochs=1, batch=batch, lr=1e-3, seed=k)
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = sum(a.elapsed_time(b) for a, b in ev) / args.steps
+    loss = float(net.train(x[:batch * 8], y[:batch * 8], epochs=1, batch=batch, lr=1e-3, seed=999)[0])
+    tflops = flop / (ms * 1e-3) / 1e12
+    pk, src = bench.peaks()
+    peak = float(pk.get('bf16_tflops', 1960.8))
+    sus = float(pk.get('bf16_tflops_sustained', 1754.4))
+    others = _train_rate(smc, torch, x[:2**21], y[:2**21])
+    extra = {'batch': batch, 'steps_per_epoch': steps_per_epoch, 'tflops': tflops, 'loss_after': loss,
+             'batch_sizes': others,
+             'roofline': {'bound': 'tensor', 'kernel': 'mlp_train_step_kernel (tcgen05, TMEM) + mlp_update_kernel',
+                          'achieved': tflops, 'peak': peak, 'unit': 'TFLOP/s', 'frac': tflops / peak,
+                          'frac_of_sustained': tflops / sus, 'traffic': None,
+                          'flop_per_row': MLP_FLOPS_PER_ROW,
+                          'peak_source': f'bf16_tflops ({src}: cuBLAS bf16 GEMM, burst); sustained {sus}'},
+             'gpu_launches': 2 * steps_per_epoch * args.steps, 'clocks': clk}
+    if not args.no_cpu_baseline:
+        theta = net.get_params().astype(np.float64)
+        xs, ys = x[:4096].cpu().numpy().astype(np.float64), y[:4096].cpu().numpy().astype(np.float64)
+        t0 = time.perf_counter()
+        reps = 0
+        while time.perf_counter() - t0 < 10.0:
+            om.gradient(theta, xs, ys, bf16=True)
+            reps += 1
+        dt = time.perf_counter() - t0
+        extra['cpu_baseline'] = {'value': reps * 4096 / dt, 'unit': 'training rows/s', 'cores': os.cpu_count(),
+                                 'kind': 'oracle',
+                                 'sample': f'{reps} gradients of 4096 rows (oracle/mlp.py, FP64 NumPy), {dt:.1f} s'}
+    _line(n / (ms * 1e-3), 'training rows/s', args.steps, args.warmup, ms, 'bf16 (fp32 accumulate)',
+          f'surrogate network 6 -> 128 x 3 -> 1, Adam, minibatch {batch:,}, one epoch over {n:,} rows', extra)
 
 
 def _time_batch(smc, b, precision, selection, n, seed=1):
@@ -592,5 +657,5 @@ SEL_BLOCK_SCAN = 8  # expected running sums formed inside the selected block
 
 def run(args):
     {'immigration_death': immigration_death, 'random_networks': random_networks, 'surrogate': surrogate,
-     'cascade': cascade, 'surrogate_inference': surrogate_inference,
+     'cascade': cascade, 'surrogate_inference': surrogate_inference, 'surrogate_training': surrogate_training,
      'large_networks': large_networks}[args.config](args)

@@ -1,7 +1,7 @@
 // smc_nest.h -- the trace monitor: BLTLc formulas of any nesting (Sec. 3.1)
 // decided on the recorded prefix of a trajectory (the paper's lookahead
 // buffer of Sec. 3.2, one per lane).  Host and device code, so that a host
-// program can check it (tests/nest_host_eval.cpp).
+// program can check it (tests/monitor_host.cpp).
 //
 // Knowledge points (the order in which the SSA learns about a path):
 //   q = 2k      positions 0..k are known (entry times and states); the next
