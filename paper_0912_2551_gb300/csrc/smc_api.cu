@@ -102,6 +102,8 @@ struct smc_ctx {
         bool use_single = false;
     } memo[2];
     unsigned long long *d_trial = nullptr;  // autotuner counts
+    float *d_cost = nullptr;                // expected events per trajectory, per instance (from the trials)
+    bool have_cost = false;
     uint64_t *d_tbegin = nullptr, *d_tend = nullptr;
     unsigned long long *d_tnext = nullptr;
     unsigned int *d_sync = nullptr;  // cursor, ticket
@@ -194,6 +196,8 @@ void free_device(smc_ctx *ctx)
     dfree(ctx->single.d_list);
     ctx->single = SizeClass();
     dfree(ctx->d_trial);
+    dfree(ctx->d_cost);
+    ctx->have_cost = false;
     ctx->use_single[0] = ctx->use_single[1] = false;
     ctx->tuned[0] = ctx->tuned[1] = false;
     dfree(ctx->d_tbegin);
@@ -523,6 +527,7 @@ int prepare(smc_ctx *ctx)
         }
     }
     CK(cudaMalloc(&ctx->d_trial, (size_t)n * 4 * 8));
+    CK(cudaMalloc(&ctx->d_cost, (size_t)n * 4));
     CK(cudaMalloc(&ctx->d_tbegin, n * 8));
     CK(cudaMalloc(&ctx->d_tend, n * 8));
     CK(cudaMalloc(&ctx->d_tnext, n * 8));
@@ -693,6 +698,7 @@ void fill_common(smc_ctx *ctx, SsaParams &p, uint64_t seed, double z, const smc_
     p.cursor = ctx->d_sync;
     p.ticket = ctx->d_sync + 1;
     p.prog = ctx->d_prog;
+    p.inst_cost = ctx->have_cost ? ctx->d_cost : nullptr;
     round_keys(seed, p.rk0, p.rk1);
     p.budget = ctx->budget;
     p.renorm_mask = (1u << ctx->renorm_log2) - 1u;
@@ -731,6 +737,39 @@ std::vector<int64_t> tune_signature(const smc_ctx *ctx)
     return sig;
 }
 
+// Longest work first: each instance's expected cost of a trajectory from
+// the autotuner's trial counts (events per trajectory; a trial trajectory
+// that hit the trials' event budget counts 8 budgets), the lists of the size
+// classes sorted by it (costliest first: the cursor hands instances out in
+// list order) and the costs kept for the warps' work stealing.  Results do
+// not depend on the order (random numbers are keyed by trajectory and
+// instance).
+int order_by_cost(smc_ctx *ctx, cudaStream_t s, uint64_t trial_budget)
+{
+    const int n = ctx->n_inst;
+    if (n < 2) return SMC_OK;
+    std::vector<unsigned long long> c((size_t)n * 4);
+    CK(cudaMemcpyAsync(c.data(), ctx->d_trial, c.size() * 8, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    std::vector<float> cost(n);
+    for (int m = 0; m < n; ++m) {
+        const double runs = (double)(c[4 * m + 1] + c[4 * m + 3]);
+        const double ev = (double)c[4 * m + 2] + 8.0 * (double)trial_budget * (double)c[4 * m + 3];
+        cost[m] = (float)std::max(1.0, runs > 0 ? ev / runs : 1.0);
+    }
+    CK(cudaMemcpyAsync(ctx->d_cost, cost.data(), (size_t)n * 4, cudaMemcpyHostToDevice, s));
+    std::vector<SizeClass *> all;
+    for (auto &cl : ctx->classes) all.push_back(&cl);
+    all.push_back(&ctx->single);
+    for (SizeClass *cl : all) {
+        std::stable_sort(cl->inst.begin(), cl->inst.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+        CK(cudaMemcpyAsync(cl->d_list, cl->inst.data(), cl->inst.size() * 4, cudaMemcpyHostToDevice, s));
+    }
+    CK(cudaStreamSynchronize(s));
+    ctx->have_cost = true;
+    return SMC_OK;
+}
+
 int autotune(smc_ctx *ctx, int plain, cudaStream_t s)
 {
     // (the trace monitor keeps the default shape: its trials would time the
@@ -758,6 +797,7 @@ int autotune(smc_ctx *ctx, int plain, cudaStream_t s)
     // trials measure the bulk throughput: a short event budget keeps a rare
     // very long trajectory from dominating every trial
     pc.budget = std::min<uint64_t>(pc.budget, 1u << 13);
+    CK(cudaMemsetAsync(ctx->d_trial, 0, (size_t)n * 4 * 8, s));  // the trials' counts give the costs
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
@@ -813,6 +853,8 @@ int autotune(smc_ctx *ctx, int plain, cudaStream_t s)
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    if (rc) return rc;
+    rc = order_by_cost(ctx, s, pc.budget);
     if (rc) return rc;
     ctx->tuned[plain] = true;
     memo.valid = true;

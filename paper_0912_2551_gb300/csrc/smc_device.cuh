@@ -346,9 +346,12 @@ __device__ __forceinline__ unsigned long long warp_sum(unsigned long long v)
     return v;
 }
 
-// Claims an instance for the warp: first one each from the cursor, then the
-// instance with the most trajectories left (so that warps whose instance ran
-// dry help the slowest ones).  Returns -1 when no work is left.
+// Claims an instance for the warp: first one each from the cursor (in the
+// launch's list order: the host puts the costliest instances first when it
+// knows their costs), then the instance with the most work left --
+// trajectories left, times the expected cost of one when known -- so that
+// warps whose instance ran dry help the slowest ones.  Returns -1 when no
+// work is left.
 // Warp-collective.
 __device__ int acquire_instance(const SsaParams &p, bool &first, int gw, int lane)
 {
@@ -361,7 +364,7 @@ __device__ int acquire_instance(const SsaParams &p, bool &first, int gw, int lan
     }
     const int n = p.n_list;
     const int start = (int)(((unsigned)gw * 2654435761u) % (unsigned)n);
-    unsigned long long best = 0;
+    float best = 0.0f;  // trajectories left, times the instance's expected cost when known
     int best_m = -1;
     for (int k = lane; k < n; k += 32) {
         int idx = start + k;
@@ -370,15 +373,16 @@ __device__ int acquire_instance(const SsaParams &p, bool &first, int gw, int lan
         const unsigned long long nx = *((volatile unsigned long long *)&p.tnext[m]);
         const unsigned long long end = p.uniform ? p.u_end : p.tend[m];
         const unsigned long long left = nx < end ? end - nx : 0;
-        if (left > best) { best = left; best_m = m; }
+        const float wgt = left ? (float)left * (p.inst_cost ? p.inst_cost[m] : 1.0f) : 0.0f;
+        if (wgt > best) { best = wgt; best_m = m; }
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-        const unsigned long long ob = __shfl_xor_sync(FULL_MASK, best, o);
+        const float ob = __shfl_xor_sync(FULL_MASK, best, o);
         const int om = __shfl_xor_sync(FULL_MASK, best_m, o);
         if (ob > best || (ob == best && om > best_m)) { best = ob; best_m = om; }
     }
-    return best ? best_m : -1;
+    return best > 0.0f ? best_m : -1;
 }
 
 template <bool PLAIN>

@@ -181,6 +181,10 @@ struct SsaParams {
     // trajectory's positions (at most tr_cap) in tr_t / tr_w, position m of
     // lane l = blockIdx.x * blockDim.x + threadIdx.x at m * tr_stride + l
     // (lanes interleaved): entry times; atom bits | entering reaction << 24
+    // expected cost of a trajectory per instance (or null): warps that
+    // have run out of fresh instances join the one with the most work left,
+    // trajectories left x cost
+    const float *inst_cost;
     const struct NestProg *nest;
     double *tr_t;
     uint32_t *tr_w;
