@@ -146,3 +146,50 @@ def test_trace_monitor_refuses_the_snapshot_paths(ctx, smc):
     m2, p2 = workloads.immigration_death()
     ctx.load_property(p2)
     assert ctx.monitor_kind == 'units'
+
+
+def _ext_cases():
+    # rate-law factors (Hill repression) and arithmetic atoms: the trace
+    # monitor's kernel variant with the EXT code
+    from tests.test_gpu_expr import _quotient_model
+    m1, p1 = workloads.autorepressor()
+    yield 'autorepressor_next_inside_F', m1, workloads.Property(p1.atoms, ('F', 5.0, 40.0, ('X', 0.0, 0.5, A(0))))
+    m2, p2 = _quotient_model()
+    yield 'quotient_F_inside_U_left', m2, workloads.Property(p2.atoms, ('U', 0.0, 15.0, ('F', 0.0, 1.0, A(0)), A(1)))
+
+
+@pytest.mark.parametrize('name', ['autorepressor_next_inside_F', 'quotient_F_inside_U_left'])
+def test_nested_formula_with_rate_laws_and_expressions(ctx, orc, name):
+    m, prop = next((mm, pp) for nm, mm, pp in _ext_cases() if nm == name)
+    n = 3000
+    g = _run(ctx, m, prop, math.inf, n, 'plain', seed=5)
+    r = orc.run(m, prop, seed=5, n_traj=n)
+    same = (g['verdict'][0] == r['verdict']) & (g['events'][0].astype(np.uint64) == r['events'])
+    print(f'{name}: {int(same.sum())} of {n} equal, p = {g["verdict"][0].mean():.4f}')
+    assert same.mean() >= 0.999
+    assert (g['status'][0] == r['status']).all()
+
+
+def test_nested_formula_on_a_batch(ctx, orc):
+    # per-instance atoms of the random-network batch, one nested formula shape
+    import torch
+    b = workloads.random_networks(4096, seed=3)
+    idx = [i for i, mm in enumerate(b.models) if mm.n_reactions <= 24][:48]
+    sub = workloads.Batch([b.models[i] for i in idx],
+                          [workloads.Property(b.properties[i].atoms, ('F', 0.0, 30.0, ('G', 0.5, 1.5, A(0))))
+                           for i in idx])
+    n = 64
+    ctx.load_batch(sub)
+    ctx.load_property(sub.properties)
+    assert ctx.monitor_kind == 'trace'
+    out = ctx.simulate('plain', seed=9, n_traj=n, outputs=('verdict', 'status', 'events'))
+    torch.cuda.synchronize()
+    g = {k: v.cpu().numpy() for k, v in out.items()}
+    agree = total = 0
+    for row in range(len(idx)):
+        r = orc.run(sub.models[row], sub.properties[row], seed=9, instance=row, n_traj=n)
+        agree += int(((g['verdict'][row] == r['verdict']) &
+                      (g['events'][row].astype(np.uint64) == r['events'])).sum())
+        total += n
+    print(f'batch: {agree} of {total} equal')
+    assert agree / total >= 0.999
