@@ -193,3 +193,41 @@ def test_nested_formula_on_a_batch(ctx, orc):
         total += n
     print(f'batch: {agree} of {total} equal')
     assert agree / total >= 0.999
+
+
+def test_nested_formula_at_the_event_budget(ctx, orc):
+    # a budget below the events a verdict needs: undecided trajectories stop
+    # at the budget with status 1, decided ones keep their decision point
+    import torch
+    _, kind, formula, t_max, _ = CASES[4]  # G with a lower bound inside F[5, 30]
+    m, prop = _model(kind, formula)
+    n, budget = 2000, 300
+    ctx.load_model(m)
+    ctx.load_property(prop, t_max=t_max)
+    ctx.set_option('event_budget', budget)
+    out = ctx.simulate('plain', seed=13, n_traj=n, outputs=('verdict', 'status', 'events', 't_final'))
+    torch.cuda.synchronize()
+    g = {k: v.cpu().numpy() for k, v in out.items()}
+    r = orc.run(m, prop, seed=13, n_traj=n, budget=budget)
+    assert (r['status'] == 1).mean() > 0.2  # the budget binds for many trajectories
+    assert (g['status'][0] == r['status']).all()
+    assert (g['events'][0].astype(np.uint64) == r['events']).all()
+    assert (g['verdict'][0] == r['verdict']).all()
+    assert int(g['counts'][0, 3]) == int((r['status'] == 1).sum())
+
+
+def test_nested_formula_on_absorbing_paths(ctx, orc):
+    # pure decay A -> 0 from A0 = 6: paths absorb at A = 0 (no further
+    # position), which decides a nested formula at the closed end
+    m, _ = workloads.pure_decay(A0=6, k=1.0)
+    sp = ['A']
+    atoms = [workloads.atom(sp, 'A', '>=', 3), workloads.atom(sp, 'A', '<=', 0)]
+    prop = workloads.Property(atoms, ('or', ('F', 0.0, 3.0, ('X', 0.0, 0.3, A(1))),
+                                      ('U', 0.0, 4.0, ('F', 0.0, 0.5, A(0)), A(1))))
+    n = 4000
+    g = _run(ctx, m, prop, math.inf, n, 'plain', seed=2)
+    r = orc.run(m, prop, seed=2, n_traj=n, want_x=True)
+    assert 0.02 < r['verdict'].mean() < 0.98
+    assert (g['verdict'][0] == r['verdict']).all()
+    assert (g['events'][0].astype(np.uint64) == r['events']).all()
+    assert (g['x_final'][0][:, :1] == r['x_final']).all()
