@@ -211,7 +211,7 @@ def make_parser() -> argparse.ArgumentParser:
                     help='trajectories per step (per instance for --config workloads; profiling runs)')
     ap.add_argument('--config', default='lotka_volterra',
                     choices=['lotka_volterra', 'immigration_death', 'random_networks', 'surrogate', 'cascade',
-                             'surrogate_inference', 'surrogate_training', 'large_networks'])
+                             'surrogate_inference', 'surrogate_training', 'large_networks', 'nested'])
     return ap
 
 

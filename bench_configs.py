@@ -165,6 +165,47 @@ def random_networks(args):
                             'kind': 'oracle', 'sample': f'2 trajectories of every 16th instance, {cpu:.1f} s'}})
 
 
+def nested(args):
+    """A formula nested beyond the monitor's units on the trace monitor:
+    immigration-death, G[0,20](A >= 80 -> F[0,3] G[0,1] A >= 75) (depth 4),
+    10^5 trajectories per step, FP64 and mixed paths; the same formula's
+    oracle on a 2,000-trajectory sample."""
+    import oracle
+    import paper_0912_2551_gb300 as smc
+    import workloads
+    m, _ = workloads.immigration_death()
+    sp = ['A']
+    atoms = [workloads.atom(sp, 'A', '>=', 80), workloads.atom(sp, 'A', '>=', 75)]
+    A = lambda k: ('atom', k)  # noqa: E731
+    p = workloads.Property(atoms, ('G', 0.0, 20.0, ('implies', A(0), ('F', 0.0, 3.0, ('G', 0.0, 1.0, A(1))))))
+    n = args.traj or 100000
+    with smc.Context(0) as ctx:
+        ctx.load_model(m)
+        ctx.load_property(p)
+        assert ctx.monitor_kind == 'trace'
+        ms, c, wil, clk = _timed_simulate(ctx, 'plain', n, args.steps, args.warmup, seed=0, label='nested')
+        ms_m, c_m, _, clk_m = _timed_simulate(ctx, 'mixed', n, args.steps, args.warmup, seed=0, label='nested')
+        kname = bench.kernel_name(ctx, 'plain')
+    k = 2000
+    t0 = time.perf_counter()
+    r = oracle.run(m, p, seed=0, n_traj=k)
+    cpu = time.perf_counter() - t0
+    ev = float(c[0, 2])
+    _line(n / (ms / 1e3), 'trajectories/s', args.steps, args.warmup, ms, 'f64',
+          'immigration-death, G[0,20](A>=80 -> F[0,3] G[0,1] A>=75) on the trace monitor, '
+          f'{n:,} trajectories per step',
+          {'events_per_s': ev / (ms / 1e3), 'events_per_trajectory': ev / n, 'clocks': clk,
+           'mixed': {'value': n / (ms_m / 1e3), 'ms_per_step': ms_m, 'events_per_s': float(c_m[0, 2]) / (ms_m / 1e3),
+                     'clocks': clk_m},
+           'result': {'p_hat': wil[0, 0], 'lo': wil[0, 1], 'hi': wil[0, 2],
+                      'oracle_p_hat_2000': float(r['verdict'].mean())},
+           'roofline': _issue_roofline(ev / (ms / 1e3), bench.algorithmic_ops_per_event(m, 2, True), kname),
+           'note': 'the issue roofline counts the SSA\'s work per event only; the trace monitor adds the '
+                   'recording and its checks',
+           'cpu_baseline': {'value': k / cpu, 'unit': 'trajectories/s', 'cores': os.cpu_count(),
+                            'kind': 'oracle', 'sample': f'{k} trajectories, {cpu:.2f} s'}})
+
+
 def _collect_snapshots(ctx, torch, t_c, want, per_call, x_scale, t_scale, seed):
     """Snapshots at t_c of trajectories still undecided there, labelled by
     their verdicts (full runs)."""
@@ -658,4 +699,5 @@ SEL_BLOCK_SCAN = 8  # expected running sums formed inside the selected block
 def run(args):
     {'immigration_death': immigration_death, 'random_networks': random_networks, 'surrogate': surrogate,
      'cascade': cascade, 'surrogate_inference': surrogate_inference, 'surrogate_training': surrogate_training,
+     'nested': nested,
      'large_networks': large_networks}[args.config](args)

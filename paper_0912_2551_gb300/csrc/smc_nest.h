@@ -185,10 +185,12 @@ SMC_NEST_HD SMC_NEST_NOINLINE NestVal nest_eval(const NestProg &P, const NestTra
     case SMC_NODE_OR:
     case SMC_NODE_IMPLIES: {
         NestVal a = nest_eval<DEPTH - 1>(P, T, n.c0, j);
-        const NestVal b = nest_eval<DEPTH - 1>(P, T, n.c1, j);
-        if (n.kind == SMC_NODE_AND) return nest_and(a, b);
         if (n.kind == SMC_NODE_IMPLIES) a.v = nest_not(a.v);
-        return nest_or(a, b);
+        // a first operand that settles the result at 2j (the earliest point a
+        // value at position j can be known) leaves nothing for the second
+        if (a.d == 2 * j && a.v == (n.kind == SMC_NODE_AND ? 1 : 2)) return a;
+        const NestVal b = nest_eval<DEPTH - 1>(P, T, n.c1, j);
+        return n.kind == SMC_NODE_AND ? nest_and(a, b) : nest_or(a, b);
     }
     case SMC_NODE_UNTIL: return nest_until<DEPTH>(P, T, n.c0, n.c1, false, n.lo, n.hi, j);
     case SMC_NODE_EVENTUALLY: return nest_until<DEPTH>(P, T, -1, n.c0, false, n.lo, n.hi, j);
