@@ -68,7 +68,9 @@ struct smc_ctx {
     uint32_t trace_cap = 4096;          // positions recorded per lane
     double *d_tr_t = nullptr;           // [trace_cap][lanes] entry times
     uint32_t *d_tr_w = nullptr;         // [trace_cap][lanes] atom bits | reaction << 24
+    uint32_t *d_tr_m = nullptr;         // [slots][trace_cap][lanes] evaluator memo
     size_t tr_lanes = 0;                // lanes the buffers hold
+    int tr_slots = 0;                   // memo slots they hold
     std::vector<int> used_atoms;
     int n_atoms = 0;
     bool per_instance_bound = false;
@@ -190,7 +192,9 @@ void free_device(smc_ctx *ctx)
     dfree(ctx->d_nest);
     dfree(ctx->d_tr_t);
     dfree(ctx->d_tr_w);
+    dfree(ctx->d_tr_m);
     ctx->tr_lanes = 0;
+    ctx->tr_slots = 0;
     for (auto &c : ctx->classes) dfree(c.d_list);
     ctx->classes.clear();
     dfree(ctx->single.d_list);
@@ -552,24 +556,31 @@ int prepare(smc_ctx *ctx)
 int kvar(const smc_ctx *ctx) { return (ctx->ext ? 1 : 0) | (ctx->nest_mode ? 2 : 0); }
 
 // Trace monitor: recording buffers for `lanes` lanes of trace_cap positions
-// (grown, never shrunk, while the context's device state lives).  Called
-// when a launch is planned, before any stream capture.
+// and the evaluator's memo, 4 bytes per position and slot (grown, never
+// shrunk, while the context's device state lives).  Called when a launch is
+// planned, before any stream capture.
 int ensure_trace(smc_ctx *ctx, size_t lanes)
 {
-    if (ctx->tr_lanes >= lanes && ctx->d_tr_t) return SMC_OK;
+    const int slots = ctx->nest.n_slots;
+    if (ctx->tr_lanes >= lanes && ctx->d_tr_t && ctx->tr_slots >= slots) return SMC_OK;
     dfree(ctx->d_tr_t);
     dfree(ctx->d_tr_w);
+    dfree(ctx->d_tr_m);
     ctx->tr_lanes = 0;
+    ctx->tr_slots = 0;
     const size_t n = lanes * ctx->trace_cap;
     if (cudaMalloc(&ctx->d_tr_t, n * sizeof(double)) != cudaSuccess ||
-        cudaMalloc(&ctx->d_tr_w, n * sizeof(uint32_t)) != cudaSuccess) {
+        cudaMalloc(&ctx->d_tr_w, n * sizeof(uint32_t)) != cudaSuccess ||
+        (slots > 0 && cudaMalloc(&ctx->d_tr_m, n * slots * sizeof(uint32_t)) != cudaSuccess)) {
         cudaGetLastError();
         dfree(ctx->d_tr_t);
         dfree(ctx->d_tr_w);
-        return fail(ctx, SMC_E_OOM, "trace monitor buffers (" + std::to_string(n * 12 >> 20) + " MiB): "
-                                    "lower SMC_OPT_TRACE_CAP or the launch shape");
+        dfree(ctx->d_tr_m);
+        return fail(ctx, SMC_E_OOM, "trace monitor buffers (" + std::to_string(n * (12 + 4 * slots) >> 20) +
+                                    " MiB): lower SMC_OPT_TRACE_CAP or the launch shape");
     }
     ctx->tr_lanes = lanes;
+    ctx->tr_slots = slots;
     return SMC_OK;
 }
 
@@ -669,8 +680,10 @@ int issue_class(smc_ctx *ctx, int plain, const SsaParams &common, const Launch &
         p.nest = ctx->d_nest;
         p.tr_t = ctx->d_tr_t;
         p.tr_w = ctx->d_tr_w;
+        p.tr_m = ctx->nest.n_slots > 0 ? ctx->d_tr_m : nullptr;
         p.tr_cap = ctx->trace_cap;
         p.tr_stride = ctx->tr_lanes;
+        p.tr_mslot = (uint64_t)ctx->trace_cap * ctx->tr_lanes;
     }
     if (smc_launch_queue_init(p, s))
         return fail(ctx, SMC_E_CUDA, std::string("queue init: ") + cudaGetErrorString(cudaGetLastError()));
@@ -1235,7 +1248,9 @@ int smc_set_option(smc_ctx *ctx, int option, double value)
             ctx->trace_cap = (uint32_t)value;
             dfree(ctx->d_tr_t);
             dfree(ctx->d_tr_w);
+            dfree(ctx->d_tr_m);
             ctx->tr_lanes = 0;
+            ctx->tr_slots = 0;
         }
         return SMC_OK;
     case SMC_OPT_RENORM_LOG2:

@@ -294,11 +294,14 @@ int compile_formula(const std::vector<FNode> &tree, int root, int n_atoms, doubl
 // The trace monitor's program (smc_nest.h): the formula tree renumbered
 // from the root, atoms as bits of the used-atom vector, the static horizon
 // (the latest time a position can matter: temporal operators add their
-// interval end to their operands' horizons) and the stopping time.
+// interval end to their operands' horizons), the stopping time, and a memo
+// column for each temporal node below another one (evaluated at many
+// positions per check).
 namespace {
-// -1: too large (err says why), -2: a bad interval
+// -1: too large (err says why), -2: a bad interval; under: a temporal
+// operator is among the node's ancestors
 int nest_copy(const std::vector<FNode> &T, int n, const std::vector<int> &bit, NestProg &np, int depth,
-              std::string &err)
+              bool under, std::string &err)
 {
     if (depth > SMC_NEST_MAX_DEPTH) { err = "formula deeper than 10 nodes"; return -1; }
     if (np.n_nodes >= SMC_NEST_MAX_NODES) { err = "formula of more than 32 nodes"; return -1; }
@@ -316,8 +319,10 @@ int nest_copy(const std::vector<FNode> &T, int n, const std::vector<int> &bit, N
         err = "temporal interval needs 0 <= lo <= hi, lo finite";
         return -2;
     }
-    if (f.c0 >= 0 && (nd.c0 = nest_copy(T, f.c0, bit, np, depth + 1, err)) < 0) return nd.c0;
-    if (f.c1 >= 0 && (nd.c1 = nest_copy(T, f.c1, bit, np, depth + 1, err)) < 0) return nd.c1;
+    nd.slot = (under && temporal && f.kind != SMC_NODE_NEXT) ? np.n_slots++ : -1;
+    under = under || temporal;
+    if (f.c0 >= 0 && (nd.c0 = nest_copy(T, f.c0, bit, np, depth + 1, under, err)) < 0) return nd.c0;
+    if (f.c1 >= 0 && (nd.c1 = nest_copy(T, f.c1, bit, np, depth + 1, under, err)) < 0) return nd.c1;
     np.height = std::max(np.height, depth);
     np.nd[id] = nd;
     return id;
@@ -348,7 +353,7 @@ int compile_nested(const std::vector<FNode> &tree, int root, int n_atoms, double
         err = "more than 6 distinct atoms";
         return SMC_E_UNSUPPORTED;
     }
-    const int rc = nest_copy(tree, root, bit, np, 1, err);
+    const int rc = nest_copy(tree, root, bit, np, 1, false, err);
     if (rc == -2) return SMC_E_INVALID_ARG;
     if (rc < 0) return SMC_E_UNSUPPORTED;
     np.root = 0;

@@ -176,20 +176,24 @@ struct SsaParams {
     // SMC_SEL_BLOCKS(r_max) of them per lane after the propensities), 0 =
     // linear scan
     int32_t sel_block;
-    // trace monitor (smc_nest.h; formulas nested beyond the units above):
-    // when nest is set the units are unused, and each lane records its
-    // trajectory's positions (at most tr_cap) in tr_t / tr_w, position m of
-    // lane l = blockIdx.x * blockDim.x + threadIdx.x at m * tr_stride + l
-    // (lanes interleaved): entry times; atom bits | entering reaction << 24
     // expected cost of a trajectory per instance (or null): warps that
     // have run out of fresh instances join the one with the most work left,
     // trajectories left x cost
     const float *inst_cost;
+    // trace monitor (smc_nest.h; formulas nested beyond the units above):
+    // when nest is set the units are unused, and each lane records its
+    // trajectory's positions (at most tr_cap) in tr_t / tr_w, position m of
+    // lane l = blockIdx.x * blockDim.x + threadIdx.x at m * tr_stride + l
+    // (lanes interleaved): entry times; atom bits | entering reaction << 24.
+    // tr_m: the evaluator's memo, slot k's cell for position m of lane l at
+    // k * tr_mslot + m * tr_stride + l (nest->n_slots slots; null if none)
     const struct NestProg *nest;
     double *tr_t;
     uint32_t *tr_w;
+    uint32_t *tr_m;
     uint32_t tr_cap;
     uint64_t tr_stride;
+    uint64_t tr_mslot;
 };
 #define SMC_SEL_BLOCK 16
 #define SMC_SEL_BLOCKS(r) (((r) + SMC_SEL_BLOCK - 1) / SMC_SEL_BLOCK)

@@ -155,6 +155,12 @@ __device__ __forceinline__ void run_instance(const SsaParams &p, const MonProg &
     const uint64_t trs = p.tr_stride;  // position m of this lane at m * trs (lanes interleaved)
     double *trt = NP ? p.tr_t + lane_id : nullptr;
     uint32_t *trw = NP ? p.tr_w + lane_id : nullptr;
+    uint32_t *trm = NP ? (p.tr_m ? p.tr_m + lane_id : nullptr) : nullptr;
+    const int n_slots = (NP && p.tr_m) ? NP->n_slots : 0;
+    // a recorded position's memo cells start unknown
+    auto clear_memo = [&](uint32_t pos) {
+        for (int k = 0; k < n_slots; ++k) trm[k * p.tr_mslot + pos * trs] = 0u;
+    };
     uint64_t nchk = 0;
 
     // verdict codes: 1 false, 2 true, 3 event budget exhausted, 4 stopped at
@@ -183,7 +189,7 @@ __device__ __forceinline__ void run_instance(const SsaParams &p, const MonProg &
     // trace monitor: the formula on the recorded positions 0..e and what
     // follows them (smc_nest.h)
     auto nest_at = [&](int end, double tnx) -> NestVal {
-        const NestTrace T{trt, trw, (int64_t)trs, (int64_t)e, end, tnx};
+        const NestTrace T{trt, trw, (int64_t)trs, (int64_t)e, end, tnx, trm, (int64_t)p.tr_mslot};
         return nest_decide(*NP, T);
     };
     // stop at the decision point: the trajectory's outputs are those of
@@ -240,6 +246,7 @@ __device__ __forceinline__ void run_instance(const SsaParams &p, const MonProg &
                         if constexpr (NEST) {
                             trt[0] = 0.0;
                             trw[0] = ab;
+                            clear_memo(0);
                             mh.ab = ab;
                             nchk = 1;
                             const NestVal d = nest_at(0, 0.0);
@@ -475,6 +482,7 @@ __device__ __forceinline__ void run_instance(const SsaParams &p, const MonProg &
             if (e >= p.tr_cap) { finish(5); continue; }
             trt[e * trs] = t;
             trw[e * trs] = ab | ((uint32_t)j << 24);
+            clear_memo(e);
             mh.ab = ab;
             const bool at_budget = (uint64_t)e >= budget;
             if ((uint64_t)e == nchk || at_budget) {

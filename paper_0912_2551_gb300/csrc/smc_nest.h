@@ -27,8 +27,13 @@
 // F[a,b] psi = tt U[a,b] psi; G[a,b] psi = not F[a,b] not psi; X[a,b] psi at
 // j: position j + 1 is entered after a sojourn in [a, b] and satisfies psi.
 // The evaluation recurses on the formula tree (depth bounded at compile
-// time: no run-time recursion) and rescans windows, so its cost grows with
-// the product of the nested windows' lengths in positions.
+// time: no run-time recursion).  Without a memo it rescans windows, so its
+// cost grows with the product of the nested windows' lengths in positions.
+// With one (NestTrace::memo), every temporal node below another temporal
+// node keeps, per position, its value once decided -- final, since
+// knowledge only grows -- or the knowledge point at which it was last found
+// undetermined; each such value is then computed once per knowledge point
+// at most, and a decided one once per path.
 #pragma once
 #include <stdint.h>
 
@@ -53,14 +58,19 @@
 // Node kinds are the SMC_NODE_* codes of smc.h; c0, c1 operands (c0 the
 // left one of Until), bit the atom's bit in the state's atom vector, [lo, hi]
 // the interval of a temporal operator.
+// slot: the node's memo column (a temporal node with a temporal ancestor),
+// else -1.
 struct NestNode {
     int32_t kind, c0, c1, bit;
+    int32_t slot, pad_;
     double lo, hi;
 };
 
 struct NestProg {
     int32_t n_nodes, root, height;
     int32_t unbounded;  // the formula's horizon is infinite: pessimistic rule at t_stop
+    int32_t n_slots;    // memo columns (nodes with slot >= 0)
+    int32_t pad_;
     double t_static;    // latest time at which a position can still matter (+inf: unbounded)
     double t_stop;      // t_static, or t_max_unbounded for an unbounded formula
     NestNode nd[SMC_NEST_MAX_NODES];
@@ -73,6 +83,12 @@ struct NestProg {
 //   1  the entry time tnext of position E + 1, drawn (2E + 1);
 //   2  the path absorbed after E, no further position (2E + 1);
 //   3  a lower bound tnext of the next entry time (2E + 1; replay only).
+// memo (optional): slot k's cell for position m at memo[k * mslot + m * s];
+// 0 unknown, else (d << 2) | v for a decided value (v = 1 false, 2 true),
+// (q << 2) | 3 for one undetermined at knowledge point q.  Whoever records
+// position m zeroes its cells first; the knowledge points at which one
+// memo is used must not decrease (the SSA's order: memo values of a
+// trajectory are final or tied to the point that computed them).
 struct NestTrace {
     const double *t;
     const uint32_t *w;
@@ -80,6 +96,8 @@ struct NestTrace {
     int64_t E;
     int32_t end;
     double tnext;
+    uint32_t *memo;
+    int64_t mslot;
 };
 
 // v: 0 undetermined, 1 false, 2 true (the monitor's codes); d: the decision
@@ -192,11 +210,22 @@ SMC_NEST_HD SMC_NEST_NOINLINE NestVal nest_eval(const NestProg &P, const NestTra
         const NestVal b = nest_eval<DEPTH - 1>(P, T, n.c1, j);
         return n.kind == SMC_NODE_AND ? nest_and(a, b) : nest_or(a, b);
     }
-    case SMC_NODE_UNTIL: return nest_until<DEPTH>(P, T, n.c0, n.c1, false, n.lo, n.hi, j);
-    case SMC_NODE_EVENTUALLY: return nest_until<DEPTH>(P, T, -1, n.c0, false, n.lo, n.hi, j);
+    case SMC_NODE_UNTIL:
+    case SMC_NODE_EVENTUALLY:
     case SMC_NODE_ALWAYS: {
-        NestVal g = nest_until<DEPTH>(P, T, -1, n.c0, true, n.lo, n.hi, j);
-        g.v = nest_not(g.v);
+        const uint32_t q = (uint32_t)(2 * T.E + (T.end != 0));  // this knowledge point
+        uint32_t *cell = nullptr;
+        if (T.memo && n.slot >= 0) {
+            cell = T.memo + n.slot * T.mslot + j * T.s;
+            const uint32_t c = *cell;
+            if ((c & 3u) == 1u || (c & 3u) == 2u) return {(int32_t)(c & 3u), (int64_t)(c >> 2)};
+            if (c == ((q << 2) | 3u)) return {0, SMC_NEST_NEVER};
+        }
+        NestVal g = n.kind == SMC_NODE_UNTIL
+                        ? nest_until<DEPTH>(P, T, n.c0, n.c1, false, n.lo, n.hi, j)
+                        : nest_until<DEPTH>(P, T, -1, n.c0, n.kind == SMC_NODE_ALWAYS, n.lo, n.hi, j);
+        if (n.kind == SMC_NODE_ALWAYS) g.v = nest_not(g.v);
+        if (cell) *cell = g.v ? (((uint32_t)g.d << 2) | (uint32_t)g.v) : ((q << 2) | 3u);
         return g;
     }
     case SMC_NODE_NEXT: {

@@ -12,7 +12,11 @@
 // 1 false, 2 true).  As the library does, a formula outside the monitor's
 // fragment goes to the trace monitor (smc_nest.h: the path's states and
 // entry times recorded, the verdict and its decision point computed from
-// them); with the argument "nest" every formula does.
+// them); with the argument "nest" every formula does, and with "memo" every
+// formula goes to the trace monitor with its memo, run as the SSA kernel
+// runs it: positions recorded in order (their memo cells zeroed), the
+// formula evaluated at every knowledge point in turn, each result checked
+// against the evaluation without the memo (exit status 3 on a mismatch).
 #include <math.h>
 #include <stdint.h>
 #include <stdio.h>
@@ -29,7 +33,8 @@
 
 int main(int argc, char **argv)
 {
-    const bool force_nest = argc > 1 && strcmp(argv[1], "nest") == 0;
+    const bool use_memo = argc > 1 && strcmp(argv[1], "memo") == 0;
+    const bool force_nest = use_memo || (argc > 1 && strcmp(argv[1], "nest") == 0);
     int S, NA, NN;
     if (scanf("%d %d %d", &S, &NA, &NN) != 3) return 2;
     std::vector<int32_t> coef((size_t)NA * S), op(NA);
@@ -83,7 +88,32 @@ int main(int argc, char **argv)
                 w[k] = ab;
             }
             const NestTrace T{t.data(), w.data(), 1, (int64_t)n - 1, closed ? 2 : 3, tmin};
-            const NestVal d = nest_decide(NP, T);
+            NestVal d = nest_decide(NP, T);
+            if (use_memo && n > 0) {
+                // garbage in every cell: only zeroing at the record may clear them
+                std::vector<uint32_t> memo((size_t)std::max(NP.n_slots, 1) * n, 0xA5A5A5A5u);
+                for (int k = 0; k < n; ++k) {
+                    for (int sl = 0; sl < NP.n_slots; ++sl) memo[(size_t)sl * n + k] = 0;
+                    const bool last = k == n - 1;
+                    for (int half = 0; half < 2; ++half) {
+                        NestTrace U{t.data(), w.data(), 1, k, 0, 0.0, nullptr, 0};
+                        if (half) {
+                            U.end = last ? (closed ? 2 : 3) : 1;
+                            U.tnext = last ? tmin : t[k + 1];
+                        }
+                        const NestVal a = nest_decide(NP, U);
+                        U.memo = memo.data();
+                        U.mslot = n;
+                        const NestVal b = nest_decide(NP, U);
+                        if (a.v != b.v || (a.v && a.d != b.d)) {
+                            printf("mismatch path %d q %lld: %d %lld vs %d %lld\n", i, 2ll * k + half, a.v,
+                                   (long long)a.d, b.v, (long long)b.d);
+                            return 3;
+                        }
+                        if (last && half) d = b;
+                    }
+                }
+            }
             printf("%d %lld\n", d.v, d.v ? (long long)d.d : -1ll);
             continue;
         }
