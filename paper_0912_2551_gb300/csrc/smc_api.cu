@@ -66,9 +66,9 @@ struct smc_ctx {
     NestProg nest{};
     NestProg *d_nest = nullptr;
     uint32_t trace_cap = 4096;          // positions recorded per lane
-    double *d_tr_t = nullptr;           // [trace_cap][lanes] entry times
-    uint32_t *d_tr_w = nullptr;         // [trace_cap][lanes] atom bits | reaction << 24
-    uint32_t *d_tr_m = nullptr;         // [slots][trace_cap][lanes] evaluator memo
+    double *d_tr_t = nullptr;           // [lanes][trace_cap] entry times
+    uint32_t *d_tr_w = nullptr;         // [lanes][trace_cap] atom bits | reaction << 24
+    uint32_t *d_tr_m = nullptr;         // [lanes][slots][trace_cap] evaluator memo
     size_t tr_lanes = 0;                // lanes the buffers hold
     int tr_slots = 0;                   // memo slots they hold
     std::vector<int> used_atoms;
@@ -682,8 +682,6 @@ int issue_class(smc_ctx *ctx, int plain, const SsaParams &common, const Launch &
         p.tr_w = ctx->d_tr_w;
         p.tr_m = ctx->nest.n_slots > 0 ? ctx->d_tr_m : nullptr;
         p.tr_cap = ctx->trace_cap;
-        p.tr_stride = ctx->tr_lanes;
-        p.tr_mslot = (uint64_t)ctx->trace_cap * ctx->tr_lanes;
     }
     if (smc_launch_queue_init(p, s))
         return fail(ctx, SMC_E_CUDA, std::string("queue init: ") + cudaGetErrorString(cudaGetLastError()));

@@ -183,17 +183,16 @@ struct SsaParams {
     // trace monitor (smc_nest.h; formulas nested beyond the units above):
     // when nest is set the units are unused, and each lane records its
     // trajectory's positions (at most tr_cap) in tr_t / tr_w, position m of
-    // lane l = blockIdx.x * blockDim.x + threadIdx.x at m * tr_stride + l
-    // (lanes interleaved): entry times; atom bits | entering reaction << 24.
-    // tr_m: the evaluator's memo, slot k's cell for position m of lane l at
-    // k * tr_mslot + m * tr_stride + l (nest->n_slots slots; null if none)
+    // lane l = blockIdx.x * blockDim.x + threadIdx.x at l * tr_cap + m (a
+    // lane's positions contiguous: its evaluation scans them in order):
+    // entry times; atom bits | entering reaction << 24.  tr_m: the
+    // evaluator's memo, slot k's cell for position m of lane l at
+    // (l * n_slots + k) * tr_cap + m (nest->n_slots slots; null if none)
     const struct NestProg *nest;
     double *tr_t;
     uint32_t *tr_w;
     uint32_t *tr_m;
     uint32_t tr_cap;
-    uint64_t tr_stride;
-    uint64_t tr_mslot;
 };
 #define SMC_SEL_BLOCK 16
 #define SMC_SEL_BLOCKS(r) (((r) + SMC_SEL_BLOCK - 1) / SMC_SEL_BLOCK)

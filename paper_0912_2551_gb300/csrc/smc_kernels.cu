@@ -152,14 +152,14 @@ __device__ __forceinline__ void run_instance(const SsaParams &p, const MonProg &
     // horizon, absorption and the budget)
     const NestProg *NP = NEST ? p.nest : nullptr;  // (NEST: a kernel variant of its own)
     const uint64_t lane_id = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const uint64_t trs = p.tr_stride;  // position m of this lane at m * trs (lanes interleaved)
-    double *trt = NP ? p.tr_t + lane_id : nullptr;
-    uint32_t *trw = NP ? p.tr_w + lane_id : nullptr;
-    uint32_t *trm = NP ? (p.tr_m ? p.tr_m + lane_id : nullptr) : nullptr;
+    const uint64_t cap = p.tr_cap;  // this lane's positions are contiguous
+    double *trt = NP ? p.tr_t + lane_id * cap : nullptr;
+    uint32_t *trw = NP ? p.tr_w + lane_id * cap : nullptr;
     const int n_slots = (NP && p.tr_m) ? NP->n_slots : 0;
+    uint32_t *trm = n_slots ? p.tr_m + lane_id * n_slots * cap : nullptr;
     // a recorded position's memo cells start unknown
     auto clear_memo = [&](uint32_t pos) {
-        for (int k = 0; k < n_slots; ++k) trm[k * p.tr_mslot + pos * trs] = 0u;
+        for (int k = 0; k < n_slots; ++k) trm[k * cap + pos] = 0u;
     };
     uint64_t nchk = 0;
 
@@ -189,7 +189,7 @@ __device__ __forceinline__ void run_instance(const SsaParams &p, const MonProg &
     // trace monitor: the formula on the recorded positions 0..e and what
     // follows them (smc_nest.h)
     auto nest_at = [&](int end, double tnx) -> NestVal {
-        const NestTrace T{trt, trw, (int64_t)trs, (int64_t)e, end, tnx, trm, (int64_t)p.tr_mslot};
+        const NestTrace T{trt, trw, 1, (int64_t)e, end, tnx, trm, (int64_t)cap};
         return nest_decide(*NP, T);
     };
     // stop at the decision point: the trajectory's outputs are those of
@@ -198,14 +198,14 @@ __device__ __forceinline__ void run_instance(const SsaParams &p, const MonProg &
         const uint32_t k = (uint32_t)(d.d >> 1);
         if (p.o_xfinal)
             for (uint32_t m2 = e; m2 > k; --m2) {
-                const uint32_t jr = trw[m2 * trs] >> 24;
+                const uint32_t jr = trw[m2] >> 24;
                 for (uint32_t q = stp[jr], qe = stp[jr + 1]; q < qe; ++q) {
                     const uint32_t w = st[q];
                     xs[(w & 255u) * 32] -= ((int32_t)w) >> 8;
                 }
             }
         e = k;
-        t = trt[k * trs];
+        t = trt[k];
         finish(d.v);
     };
 
@@ -480,8 +480,8 @@ __device__ __forceinline__ void run_instance(const SsaParams &p, const MonProg &
         }
         if constexpr (NEST) {  // record the new position; check on the doubling schedule and at the budget
             if (e >= p.tr_cap) { finish(5); continue; }
-            trt[e * trs] = t;
-            trw[e * trs] = ab | ((uint32_t)j << 24);
+            trt[e] = t;
+            trw[e] = ab | ((uint32_t)j << 24);
             clear_memo(e);
             mh.ab = ab;
             const bool at_budget = (uint64_t)e >= budget;

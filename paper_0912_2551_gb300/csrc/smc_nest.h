@@ -77,8 +77,8 @@ struct NestProg {
 };
 
 // What is known of a path: positions 0..E (entry times t[m * s], atom bit
-// vectors w[m * s] in bits 0-23; s = 1, or the number of lanes when the
-// lanes' recordings are interleaved) and, after position E, `end`:
+// vectors w[m * s] in bits 0-23; s the stride between positions, 1 for a
+// contiguous recording) and, after position E, `end`:
 //   0  nothing (the last knowledge point is 2E);
 //   1  the entry time tnext of position E + 1, drawn (2E + 1);
 //   2  the path absorbed after E, no further position (2E + 1);
