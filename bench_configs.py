@@ -187,9 +187,11 @@ def nested(args):
         ms_m, c_m, _, clk_m = _timed_simulate(ctx, 'mixed', n, args.steps, args.warmup, seed=0, label='nested')
         kname = bench.kernel_name(ctx, 'plain')
     k = 2000
-    t0 = time.perf_counter()
-    r = oracle.run(m, p, seed=0, n_traj=k)
-    cpu = time.perf_counter() - t0
+    r, cpu = None, None
+    if not args.no_cpu_baseline:
+        t0 = time.perf_counter()
+        r = oracle.run(m, p, seed=0, n_traj=k)
+        cpu = time.perf_counter() - t0
     ev = float(c[0, 2])
     _line(n / (ms / 1e3), 'trajectories/s', args.steps, args.warmup, ms, 'f64',
           'immigration-death, G[0,20](A>=80 -> F[0,3] G[0,1] A>=75) on the trace monitor, '
@@ -198,12 +200,13 @@ def nested(args):
            'mixed': {'value': n / (ms_m / 1e3), 'ms_per_step': ms_m, 'events_per_s': float(c_m[0, 2]) / (ms_m / 1e3),
                      'clocks': clk_m},
            'result': {'p_hat': wil[0, 0], 'lo': wil[0, 1], 'hi': wil[0, 2],
-                      'oracle_p_hat_2000': float(r['verdict'].mean())},
+                      'oracle_p_hat_2000': float(r['verdict'].mean()) if r else None},
            'roofline': _issue_roofline(ev / (ms / 1e3), bench.algorithmic_ops_per_event(m, 2, True), kname),
            'note': 'the issue roofline counts the SSA\'s work per event only; the trace monitor adds the '
                    'recording and its checks',
-           'cpu_baseline': {'value': k / cpu, 'unit': 'trajectories/s', 'cores': os.cpu_count(),
-                            'kind': 'oracle', 'sample': f'{k} trajectories, {cpu:.2f} s'}})
+           'cpu_baseline': None if r is None else
+           {'value': k / cpu, 'unit': 'trajectories/s', 'cores': os.cpu_count(),
+            'kind': 'oracle', 'sample': f'{k} trajectories, {cpu:.2f} s'}})
 
 
 def _collect_snapshots(ctx, torch, t_c, want, per_call, x_scale, t_scale, seed):

@@ -91,6 +91,14 @@ __device__ __forceinline__ typename Prec<PLAIN>::T propensity(uint32_t pw, const
     return a;
 }
 
+// trace monitor: pending checks that make a warp take them together, and
+// the iterations after which it takes them anyway (measured on
+// immigration-death with a depth-4 formula, trajectories/s: group 8 / wait
+// 64 0.76M, 16 / 256 0.88M, 32 / 128 0.96M, 32 / 512 0.99M, 32 / 2048
+// 1.00M; a longer wait only delays the early stop of a decided trajectory)
+#define SMC_NEST_GROUP 32
+#define SMC_NEST_WAIT 512
+
 template <bool PLAIN, bool EXT, bool NEST>
 __device__ __forceinline__ void run_instance(const SsaParams &p, const MonProg &P, const uint64_t *ltab,
                                              const int m, const uint32_t *blob, int32_t *xs, double *tc,
@@ -162,6 +170,20 @@ __device__ __forceinline__ void run_instance(const SsaParams &p, const MonProg &
         for (int k = 0; k < n_slots; ++k) trm[k * cap + pos] = 0u;
     };
     uint64_t nchk = 0;
+    // Checks are taken by the warp's lanes together (the evaluation's loops
+    // then run side by side instead of one lane at a time): a lane whose
+    // check would end its trajectory one way or another waits (hold: 1 the
+    // horizon draw, entry time hold_t; 2 absorbed; 3 at the event budget),
+    // one on the doubling schedule keeps simulating (due); the waiting and
+    // due lanes evaluate when SMC_NEST_GROUP of them are pending, when every
+    // active lane waits, or SMC_NEST_WAIT iterations after the first began
+    // to.  `passed`: the event whose horizon check came back undecided on a
+    // bounded formula (its draw is then taken).
+    int hold = 0;
+    double hold_t = 0.0;
+    bool due = false;
+    uint32_t passed = 0xFFFFFFFFu;
+    int wait_it = 0;
 
     // verdict codes: 1 false, 2 true, 3 event budget exhausted, 4 stopped at
     // the snapshot (prefix-only run: no verdict, not counted), 5 trace
@@ -249,6 +271,9 @@ __device__ __forceinline__ void run_instance(const SsaParams &p, const MonProg &
                             clear_memo(0);
                             mh.ab = ab;
                             nchk = 1;
+                            hold = 0;
+                            due = false;
+                            passed = 0xFFFFFFFFu;
                             const NestVal d = nest_at(0, 0.0);
                             if (d.v) finish_at(d);
                         } else {
@@ -266,6 +291,33 @@ __device__ __forceinline__ void run_instance(const SsaParams &p, const MonProg &
         if (!act) {
             if (exhausted) break;
             continue;
+        }
+        if constexpr (NEST) {  // the pending checks, taken together
+            const unsigned H = __ballot_sync(FULL_MASK, active && hold != 0);
+            const unsigned W = __ballot_sync(FULL_MASK, active && (hold != 0 || due));
+            if (W) ++wait_it;
+            if (H == act || __popc(W) >= SMC_NEST_GROUP || wait_it >= SMC_NEST_WAIT) {
+                wait_it = 0;
+                if (active && (hold != 0 || due)) {
+                    const int h = hold;
+                    hold = 0;
+                    due = false;
+                    const NestVal d = nest_at(h == 1 ? 1 : (h == 2 ? 2 : 0), hold_t);
+                    if (d.v) {
+                        finish_at(d);
+                    } else if (h == 1) {
+                        if (NP->unbounded) finish_at(NestVal{1, 2 * (int64_t)e + 1});  // pessimistic rule
+                        else if (dgt(hold_t, __dadd_rn(__dmul_rn(4.0, NP->t_stop), 1.0))) finish(5);
+                        else passed = e;  // resume: take the draw
+                    } else if (h == 2) {
+                        finish(5);
+                    } else if (h == 3) {
+                        finish(3);
+                    }
+                }
+                continue;
+            }
+            if (hold != 0) continue;
         }
         if (!active) continue;
 
@@ -306,9 +358,7 @@ __device__ __forceinline__ void run_instance(const SsaParams &p, const MonProg &
         }
         if (PLAIN ? __double_as_longlong((double)a0) <= 0 : !(a0 > (T)0)) {  // absorbing state: no further position
             if constexpr (NEST) {
-                const NestVal d = nest_at(2, 0.0);
-                if (d.v) finish_at(d);
-                else finish(5);
+                hold = 2;
             } else {
                 finish(mon_close(ml, P));
             }
@@ -343,11 +393,10 @@ __device__ __forceinline__ void run_instance(const SsaParams &p, const MonProg &
         }
         int v = 0;
         if constexpr (NEST) {
-            if (dgt(tn, NP->t_stop)) {  // no later position can matter (or, unbounded: t_max passed)
-                const NestVal d = nest_at(1, tn);
-                if (d.v) { finish_at(d); continue; }
-                if (NP->unbounded) { finish_at(NestVal{1, 2 * (int64_t)e + 1}); continue; }  // pessimistic rule
-                if (dgt(tn, __dadd_rn(__dmul_rn(4.0, NP->t_stop), 1.0))) { finish(5); continue; }
+            if (dgt(tn, NP->t_stop) && passed != e) {  // no later position can matter (or, unbounded: t_max passed)
+                hold = 1;
+                hold_t = tn;
+                continue;
             }
         } else {
             if (mh.pend || __double_as_longlong(tn) > mh.hb) {
@@ -426,9 +475,7 @@ __device__ __forceinline__ void run_instance(const SsaParams &p, const MonProg &
         if (j < 0) j = last;  // r reached the full sum (rounding, or a drifted a0)
         if (j < 0) {          // every a_k is 0 (only a drifted FP32 a0 gets here)
             if constexpr (NEST) {
-                const NestVal d = nest_at(2, 0.0);
-                if (d.v) finish_at(d);
-                else finish(5);
+                hold = 2;
             } else {
                 finish(mon_close(ml, P));
             }
@@ -484,12 +531,10 @@ __device__ __forceinline__ void run_instance(const SsaParams &p, const MonProg &
             trw[e] = ab | ((uint32_t)j << 24);
             clear_memo(e);
             mh.ab = ab;
-            const bool at_budget = (uint64_t)e >= budget;
-            if ((uint64_t)e == nchk || at_budget) {
-                const NestVal d = nest_at(0, 0.0);
-                if (d.v) { finish_at(d); continue; }
-                if ((uint64_t)e == nchk) nchk *= 2;
-                if (at_budget) finish(3);
+            if ((uint64_t)e >= budget) hold = 3;
+            else if ((uint64_t)e == nchk) {
+                due = true;
+                nchk *= 2;
             }
             continue;
         }
