@@ -206,6 +206,8 @@ def make_parser() -> argparse.ArgumentParser:
     ap.add_argument('--warmup', type=int, default=3)
     ap.add_argument('--impl', default='native', choices=['native', 'reference'])
     ap.add_argument('--no-cpu-baseline', action='store_true')
+    ap.add_argument('--trace-cap', type=int, default=None,
+                    help='nested: positions recorded per lane (SMC_OPT_TRACE_CAP)')
     ap.add_argument('--no-e2e', action='store_true')
     ap.add_argument('--traj', type=int, default=None,
                     help='trajectories per step (per instance for --config workloads; profiling runs)')

@@ -183,6 +183,8 @@ def nested(args):
         ctx.load_model(m)
         ctx.load_property(p)
         assert ctx.monitor_kind == 'trace'
+        if args.trace_cap:
+            ctx.set_option('trace_cap', args.trace_cap)
         ms, c, wil, clk = _timed_simulate(ctx, 'plain', n, args.steps, args.warmup, seed=0, label='nested')
         ms_m, c_m, _, clk_m = _timed_simulate(ctx, 'mixed', n, args.steps, args.warmup, seed=0, label='nested')
         kname = bench.kernel_name(ctx, 'plain')
