@@ -135,6 +135,29 @@ SMC_NEST_HD inline NestVal nest_or(NestVal a, NestVal b)
 template <int DEPTH>
 SMC_NEST_HD SMC_NEST_NOINLINE NestVal nest_eval(const NestProg &P, const NestTrace &T, int node, int64_t j);
 
+// A memo cell's value at knowledge point q: decided (final), undetermined
+// at q, or not known (v = -1: the node must be evaluated).
+SMC_NEST_HD inline NestVal nest_cell(uint32_t c, uint32_t q)
+{
+    if ((c & 3u) == 1u || (c & 3u) == 2u) return {(int32_t)(c & 3u), (int64_t)(c >> 2)};
+    if (c == ((q << 2) | 3u)) return {0, SMC_NEST_NEVER};
+    return {-1, 0};
+}
+
+// A node's value at position j: atoms and memo hits in line, the rest by
+// the (out-of-line) evaluator
+template <int DEPTH>
+SMC_NEST_HD inline NestVal nest_child(const NestProg &P, const NestTrace &T, int node, int64_t j)
+{
+    const NestNode &n = P.nd[node];
+    if (n.kind == SMC_NODE_ATOM) return {((T.w[j * T.s] >> n.bit) & 1u) ? 2 : 1, 2 * j};
+    if (T.memo && n.slot >= 0) {
+        const NestVal c = nest_cell(T.memo[n.slot * T.mslot + j * T.s], (uint32_t)(2 * T.E + (T.end != 0)));
+        if (c.v >= 0) return c;
+    }
+    return nest_eval<DEPTH>(P, T, node, j);
+}
+
 // phi U[a,b] psi at position j (l = -1: phi = tt; neg: psi negated, for G)
 template <int DEPTH>
 SMC_NEST_HD SMC_NEST_NOINLINE NestVal nest_until(const NestProg &P, const NestTrace &T, int l, int r, bool neg,
@@ -152,14 +175,14 @@ SMC_NEST_HD SMC_NEST_NOINLINE NestVal nest_until(const NestProg &P, const NestTr
             break;
         }
         if (dt >= a) {  // candidate witness
-            NestVal rv = nest_eval<DEPTH - 1>(P, T, r, m);
+            NestVal rv = nest_child<DEPTH - 1>(P, T, r, m);
             if (neg) rv.v = nest_not(rv.v);
             if (canT && rv.v == 2) dT = nest_min(dT, nest_max(rv.d, maxDl));
             if (rv.v != 1) canF = false;
             else maxDr = nest_max(maxDr, rv.d);
         }
         if (l >= 0) {
-            const NestVal lv = nest_eval<DEPTH - 1>(P, T, l, m);
+            const NestVal lv = nest_child<DEPTH - 1>(P, T, l, m);
             if (lv.v == 1 && canF) dF = nest_min(dF, nest_max(lv.d, maxDr));  // the scan ends here
             if (lv.v != 2) canT = false;
             else maxDl = nest_max(maxDl, lv.d);
@@ -195,19 +218,19 @@ SMC_NEST_HD SMC_NEST_NOINLINE NestVal nest_eval(const NestProg &P, const NestTra
     case SMC_NODE_FALSE: return {1, 2 * j};
     case SMC_NODE_ATOM: return {((T.w[j * T.s] >> n.bit) & 1u) ? 2 : 1, 2 * j};
     case SMC_NODE_NOT: {
-        NestVal a = nest_eval<DEPTH - 1>(P, T, n.c0, j);
+        NestVal a = nest_child<DEPTH - 1>(P, T, n.c0, j);
         a.v = nest_not(a.v);
         return a;
     }
     case SMC_NODE_AND:
     case SMC_NODE_OR:
     case SMC_NODE_IMPLIES: {
-        NestVal a = nest_eval<DEPTH - 1>(P, T, n.c0, j);
+        NestVal a = nest_child<DEPTH - 1>(P, T, n.c0, j);
         if (n.kind == SMC_NODE_IMPLIES) a.v = nest_not(a.v);
         // a first operand that settles the result at 2j (the earliest point a
         // value at position j can be known) leaves nothing for the second
         if (a.d == 2 * j && a.v == (n.kind == SMC_NODE_AND ? 1 : 2)) return a;
-        const NestVal b = nest_eval<DEPTH - 1>(P, T, n.c1, j);
+        const NestVal b = nest_child<DEPTH - 1>(P, T, n.c1, j);
         return n.kind == SMC_NODE_AND ? nest_and(a, b) : nest_or(a, b);
     }
     case SMC_NODE_UNTIL:
@@ -217,9 +240,8 @@ SMC_NEST_HD SMC_NEST_NOINLINE NestVal nest_eval(const NestProg &P, const NestTra
         uint32_t *cell = nullptr;
         if (T.memo && n.slot >= 0) {
             cell = T.memo + n.slot * T.mslot + j * T.s;
-            const uint32_t c = *cell;
-            if ((c & 3u) == 1u || (c & 3u) == 2u) return {(int32_t)(c & 3u), (int64_t)(c >> 2)};
-            if (c == ((q << 2) | 3u)) return {0, SMC_NEST_NEVER};
+            const NestVal c = nest_cell(*cell, q);
+            if (c.v >= 0) return c;
         }
         NestVal g = n.kind == SMC_NODE_UNTIL
                         ? nest_until<DEPTH>(P, T, n.c0, n.c1, false, n.lo, n.hi, j)
@@ -232,7 +254,7 @@ SMC_NEST_HD SMC_NEST_NOINLINE NestVal nest_eval(const NestProg &P, const NestTra
         if (j < T.E) {  // position j + 1 is known; its entry time was drawn at 2j + 1
             const double d = SMC_NEST_SUB(T.t[(j + 1) * T.s], T.t[j * T.s]);
             if (d < n.lo || d > n.hi) return {1, 2 * j + 1};
-            return nest_eval<DEPTH - 1>(P, T, n.c0, j + 1);
+            return nest_child<DEPTH - 1>(P, T, n.c0, j + 1);
         }
         if (T.end == 2) return {1, 2 * j + 1};  // no next position
         if (T.end == 1 || T.end == 3) {
