@@ -91,11 +91,14 @@ __device__ __forceinline__ typename Prec<PLAIN>::T propensity(uint32_t pw, const
     return a;
 }
 
-// trace monitor: pending checks that make a warp take them together, and
-// the iterations after which it takes them anyway (measured on
-// immigration-death with a depth-4 formula, trajectories/s: group 8 / wait
-// 64 0.76M, 16 / 256 0.88M, 32 / 128 0.96M, 32 / 512 0.99M, 32 / 2048
-// 1.00M; a longer wait only delays the early stop of a decided trajectory)
+// trace monitor: waiting lanes that make a warp take its pending checks
+// together, and the iterations after which it takes them anyway (measured
+// on immigration-death with a depth-4 formula, 10^5 trajectories per
+// launch: counting due checks too, group 8 / wait 64 0.76M trajectories/s,
+// 16 / 256 0.88M, 32 / 128 0.96M, 32 / 512 0.99M, 32 / 2048 1.00M; waiting
+// lanes only, 8 / 512 1.18M, 16 / 512 1.18M, 32 / 512 1.20M (1.54M at 10^6
+// per launch); a longer wait only delays the early stop of a decided
+// trajectory)
 #define SMC_NEST_GROUP 32
 #define SMC_NEST_WAIT 512
 
@@ -175,10 +178,11 @@ __device__ __forceinline__ void run_instance(const SsaParams &p, const MonProg &
     // check would end its trajectory one way or another waits (hold: 1 the
     // horizon draw, entry time hold_t; 2 absorbed; 3 at the event budget),
     // one on the doubling schedule keeps simulating (due); the waiting and
-    // due lanes evaluate when SMC_NEST_GROUP of them are pending, when every
-    // active lane waits, or SMC_NEST_WAIT iterations after the first began
-    // to.  `passed`: the event whose horizon check came back undecided on a
-    // bounded formula (its draw is then taken).
+    // due lanes evaluate when SMC_NEST_GROUP lanes wait, when every active
+    // lane waits, or SMC_NEST_WAIT iterations after a check became pending
+    // (due checks ride along: they stop a decided trajectory early, but
+    // need not be taken at once).  `passed`: the event whose horizon check
+    // came back undecided on a bounded formula (its draw is then taken).
     int hold = 0;
     double hold_t = 0.0;
     bool due = false;
@@ -296,7 +300,7 @@ __device__ __forceinline__ void run_instance(const SsaParams &p, const MonProg &
             const unsigned H = __ballot_sync(FULL_MASK, active && hold != 0);
             const unsigned W = __ballot_sync(FULL_MASK, active && (hold != 0 || due));
             if (W) ++wait_it;
-            if (H == act || __popc(W) >= SMC_NEST_GROUP || wait_it >= SMC_NEST_WAIT) {
+            if (H == act || __popc(H) >= SMC_NEST_GROUP || wait_it >= SMC_NEST_WAIT) {
                 wait_it = 0;
                 if (active && (hold != 0 || due)) {
                     const int h = hold;
