@@ -47,9 +47,12 @@
 #if defined(__CUDA_ARCH__)
 #define SMC_NEST_NOINLINE __noinline__
 #define SMC_NEST_SUB(x, y) __dsub_rn((x), (y))
+#define SMC_NEST_ADD(x, y) __dadd_rn((x), (y))
 #else
+#include <string.h>
 #define SMC_NEST_NOINLINE
 #define SMC_NEST_SUB(x, y) ((x) - (y))
+#define SMC_NEST_ADD(x, y) ((x) + (y))
 #endif
 
 #define SMC_NEST_MAX_NODES 32
@@ -132,6 +135,59 @@ SMC_NEST_HD inline NestVal nest_or(NestVal a, NestVal b)
     return {0, SMC_NEST_NEVER};
 }
 
+SMC_NEST_HD inline int64_t nest_bits(double x)
+{
+#if defined(__CUDA_ARCH__)
+    return __double_as_longlong(x);
+#else
+    int64_t b;
+    memcpy(&b, &x, 8);
+    return b;
+#endif
+}
+
+SMC_NEST_HD inline double nest_from_bits(int64_t b)
+{
+#if defined(__CUDA_ARCH__)
+    return __longlong_as_double(b);
+#else
+    double x;
+    memcpy(&x, &b, 8);
+    return x;
+#endif
+}
+
+// The window tests of the scans (t - t_j > b, t - t_j >= a, rounded as the
+// oracle rounds them) on the integer pipes.  Rounded subtraction is
+// monotone in its first operand, so over times t >= 0 each test holds on an
+// interval of t, and bit patterns of non-negative doubles order like their
+// values: t - t_j <= b iff bits(t) <= nest_last_within(t_j, b), and
+// t - t_j >= a iff bits(t) >= nest_first_reaching(t_j, a).  The boundary
+// lies within an ulp or two of the rounded t_j + b (t_j + a); it is
+// searched for there and confirmed (it passes, its neighbour fails).
+// -1 when the confirmation fails (bounds near the top of the double
+// range): the scan then subtracts.
+SMC_NEST_HD inline int64_t nest_last_within(double tj, double b)
+{
+    const int64_t inf = 0x7FF0000000000000ll;
+    if (!(b < nest_from_bits(inf))) return inf;  // b = +inf: every time lies within
+    int64_t xb = nest_bits(SMC_NEST_ADD(tj, b));
+    auto within = [&](int64_t x) { return SMC_NEST_SUB(nest_from_bits(x), tj) <= b; };
+    for (int k = 0; k < 4 && xb > 0 && !within(xb); ++k) --xb;
+    for (int k = 0; k < 4 && xb < inf && within(xb + 1); ++k) ++xb;
+    return (xb >= 0 && xb < inf && within(xb) && !within(xb + 1)) ? xb : -1;
+}
+
+SMC_NEST_HD inline int64_t nest_first_reaching(double tj, double a)
+{
+    const int64_t inf = 0x7FF0000000000000ll;
+    int64_t xb = nest_bits(SMC_NEST_ADD(tj, a));
+    auto reach = [&](int64_t x) { return SMC_NEST_SUB(nest_from_bits(x), tj) >= a; };
+    for (int k = 0; k < 4 && xb < inf && !reach(xb); ++k) ++xb;
+    for (int k = 0; k < 4 && xb > 0 && reach(xb - 1); ++k) --xb;
+    return (xb >= 0 && xb <= inf && reach(xb) && (xb == 0 || !reach(xb - 1))) ? xb : -1;
+}
+
 template <int DEPTH>
 SMC_NEST_HD SMC_NEST_NOINLINE NestVal nest_eval(const NestProg &P, const NestTrace &T, int node, int64_t j);
 
@@ -167,14 +223,17 @@ SMC_NEST_HD SMC_NEST_NOINLINE NestVal nest_until(const NestProg &P, const NestTr
     bool canT = true, canF = true;  // a later witness / a later end can still decide
     int64_t maxDl = 0, maxDr = 0;   // phi known true on [j, m); psi known false at the candidates so far
     bool stopped = false;
+    const double tj = T.t[j * T.s];
+    const int64_t last_in = nest_last_within(tj, b), first_in = nest_first_reaching(tj, a);
+    auto beyond = [&](double t) { return last_in >= 0 ? nest_bits(t) > last_in : SMC_NEST_SUB(t, tj) > b; };
     for (int64_t m = j; m <= T.E; ++m) {
-        const double dt = SMC_NEST_SUB(T.t[m * T.s], T.t[j * T.s]);
-        if (dt > b) {  // the window is known closed once position m's entry time is drawn
+        const double tm = T.t[m * T.s];
+        if (beyond(tm)) {  // the window is known closed once position m's entry time is drawn
             if (canF) dF = nest_min(dF, nest_max(2 * m - 1, maxDr));
             stopped = true;
             break;
         }
-        if (dt >= a) {  // candidate witness
+        if (first_in >= 0 ? nest_bits(tm) >= first_in : SMC_NEST_SUB(tm, tj) >= a) {  // candidate witness
             NestVal rv = nest_child<DEPTH - 1>(P, T, r, m);
             if (neg) rv.v = nest_not(rv.v);
             if (canT && rv.v == 2) dT = nest_min(dT, nest_max(rv.d, maxDl));
@@ -195,7 +254,7 @@ SMC_NEST_HD SMC_NEST_NOINLINE NestVal nest_until(const NestProg &P, const NestTr
         }
     }
     if (!stopped && canF) {  // every position scanned: the window closes after E, or never here
-        const bool shut = T.end == 2 || ((T.end == 1 || T.end == 3) && SMC_NEST_SUB(T.tnext, T.t[j * T.s]) > b);
+        const bool shut = T.end == 2 || ((T.end == 1 || T.end == 3) && beyond(T.tnext));
         if (shut) dF = nest_min(dF, nest_max(2 * T.E + 1, maxDr));
     }
     if (dT != SMC_NEST_NEVER && dT <= dF) return {2, dT};
