@@ -103,7 +103,12 @@ extern "C" {
 #define SMC_OPT_TRACE_CAP 9       /* trace monitor (formulas nested beyond the monitor's
                                      units, see smc_load_property): positions each lane
                                      records per trajectory, 16..2^24 (default 4096); a
-                                     trajectory that needs more gets status 3 */
+                                     trajectory that needs more gets status 3.  Device
+                                     memory: lanes x cap x (12 + 4 x memo slots) bytes,
+                                     one memo slot per temporal operator nested inside
+                                     another (116,736 lanes, the FP64 path's default
+                                     shape on a GB300: 1.4 GB per 1024 positions, plus
+                                     0.5 GB per slot); SMC_E_OOM when it does not fit */
 
 /* A node of the formula in postfix order: operands precede their operator. */
 typedef struct {
