@@ -10,12 +10,18 @@
 //    left / right / nested truth tables over the atom bit vector) and the
 //    three-valued verdict table of boolean combinations of temporal
 //    operators, checked against Kleene's strong three-valued logic; and
-//    every formula outside the monitorable fragment is rejected.
+//    every formula outside the monitorable fragment is rejected;
+//  * compile_nested (the trace monitor's program): those rejected shapes
+//    compile; horizons (each temporal operator adds its interval end to its
+//    operands'), memo columns exactly on the U / F / G nodes below another
+//    temporal operator, tree height 10 / 32 nodes / 6 atoms accepted and
+//    one more rejected, bad intervals, unbounded formulas and t_max.
 // Prints "ok" and exits 0 when every check holds.
 #include <math.h>
 #include <stdint.h>
 #include <stdio.h>
 
+#include <functional>
 #include <limits>
 #include <string>
 #include <vector>
@@ -274,11 +280,150 @@ static void check_formulas()
     CHECK(compile({nd(SMC_NODE_ATOM, 0), nd(SMC_NODE_EVENTUALLY, 0, 0.0, NAN)}, 1, inf, p, err) != SMC_OK);
 }
 
+// ---------------------------------------------------------------- trace monitor
+static int compile_n(const std::vector<smc_node> &f, int n_atoms, double t_max, NestProg &np, std::string &err)
+{
+    std::vector<FNode> tree;
+    int root = -1;
+    int rc = parse_formula(f.data(), (int)f.size(), n_atoms, tree, root, err);
+    if (rc != SMC_OK) return rc;
+    std::vector<int> used;
+    return compile_nested(tree, root, n_atoms, t_max, np, used, err);
+}
+
+static bool is_temporal(int k)
+{
+    return k == SMC_NODE_UNTIL || k == SMC_NODE_EVENTUALLY || k == SMC_NODE_ALWAYS || k == SMC_NODE_NEXT;
+}
+
+// Memo columns: exactly the U / F / G nodes with a temporal ancestor, numbered
+// 0..n_slots-1 (an ancestor is found by walking down from the root).
+static bool slots_ok(const NestProg &np)
+{
+    std::vector<int> under(np.n_nodes, 0), seen(np.n_slots, 0);
+    std::vector<int> stack{np.root};
+    while (!stack.empty()) {
+        const int k = stack.back();
+        stack.pop_back();
+        const NestNode &n = np.nd[k];
+        const bool want = under[k] && is_temporal(n.kind) && n.kind != SMC_NODE_NEXT;
+        if (want != (n.slot >= 0)) return false;
+        if (n.slot >= 0) {
+            if (n.slot >= np.n_slots || seen[n.slot]) return false;
+            seen[n.slot] = 1;
+        }
+        for (int c : {n.c0, n.c1})
+            if (c >= 0) {
+                under[c] = under[k] || is_temporal(n.kind);
+                stack.push_back(c);
+            }
+    }
+    for (int v : seen)
+        if (!v) return false;
+    return true;
+}
+
+static void check_nested()
+{
+    std::string err;
+    NestProg np;
+    const double inf = std::numeric_limits<double>::infinity();
+    // G[0,20](a0 -> F[0,3] G[0,1] a1): horizon 20 + 3 + 1, memo for F and the inner G
+    const std::vector<smc_node> g = {nd(SMC_NODE_ATOM, 0), nd(SMC_NODE_ATOM, 1), nd(SMC_NODE_ALWAYS, 0, 0.0, 1.0),
+                                     nd(SMC_NODE_EVENTUALLY, 0, 0.0, 3.0), nd(SMC_NODE_IMPLIES),
+                                     nd(SMC_NODE_ALWAYS, 0, 0.0, 20.0)};
+    CHECK(compile_n(g, 2, inf, np, err) == SMC_OK);
+    CHECK(np.n_nodes == 6 && np.root == 0 && np.height == 5 && !np.unbounded);
+    CHECK(np.t_static == 24.0 && np.t_stop == 24.0 && np.n_slots == 2 && slots_ok(np));
+    CHECK(np.nd[np.root].kind == SMC_NODE_ALWAYS && np.nd[np.root].slot < 0);
+
+    // the shapes the unit monitor rejects (above) compile here
+    // X over F: horizon 1 + 1; F below X has a column
+    CHECK(compile_n({nd(SMC_NODE_ATOM, 0), nd(SMC_NODE_EVENTUALLY, 0, 0.0, 1.0), nd(SMC_NODE_NEXT, 0, 0.0, 1.0)}, 1,
+                    inf, np, err) == SMC_OK);
+    CHECK(np.t_static == 2.0 && np.n_slots == 1 && slots_ok(np));
+    // U with a temporal left operand: horizon 2 + max(1, 0)
+    CHECK(compile_n({nd(SMC_NODE_ATOM, 0), nd(SMC_NODE_EVENTUALLY, 0, 0.0, 1.0), nd(SMC_NODE_ATOM, 1),
+                     nd(SMC_NODE_UNTIL, 0, 0.0, 2.0)},
+                    2, inf, np, err) == SMC_OK);
+    CHECK(np.t_static == 3.0 && np.n_slots == 1 && slots_ok(np));
+    // a nested window with a lower bound: horizon 5 + 2
+    CHECK(compile_n({nd(SMC_NODE_ATOM, 0), nd(SMC_NODE_EVENTUALLY, 0, 1.0, 2.0), nd(SMC_NODE_EVENTUALLY, 0, 0.0, 5.0)},
+                    1, inf, np, err) == SMC_OK);
+    CHECK(np.t_static == 7.0 && np.n_slots == 1 && slots_ok(np));
+    // three nested F: horizon 1 + 2 + 3, two columns
+    CHECK(compile_n({nd(SMC_NODE_ATOM, 0), nd(SMC_NODE_EVENTUALLY, 0, 0.0, 1.0), nd(SMC_NODE_EVENTUALLY, 0, 0.0, 2.0),
+                     nd(SMC_NODE_EVENTUALLY, 0, 0.0, 3.0)},
+                    1, inf, np, err) == SMC_OK);
+    CHECK(np.t_static == 6.0 && np.n_slots == 2 && np.height == 4 && slots_ok(np));
+    // X below F: no column for X (one position per evaluation)
+    CHECK(compile_n({nd(SMC_NODE_ATOM, 0), nd(SMC_NODE_NEXT, 0, 0.0, 1.0), nd(SMC_NODE_EVENTUALLY, 0, 0.0, 2.0)}, 1,
+                    inf, np, err) == SMC_OK);
+    CHECK(np.n_slots == 0 && slots_ok(np));
+
+    // height 10 accepted, 11 rejected (a chain of negations over an F)
+    std::vector<smc_node> chain = {nd(SMC_NODE_ATOM, 0), nd(SMC_NODE_EVENTUALLY, 0, 0.0, 1.0)};
+    for (int i = 0; i < 8; ++i) chain.push_back(nd(SMC_NODE_NOT));
+    CHECK(compile_n(chain, 1, inf, np, err) == SMC_OK && np.height == 10);
+    chain.push_back(nd(SMC_NODE_NOT));
+    CHECK(compile_n(chain, 1, inf, np, err) == SMC_E_UNSUPPORTED);
+
+    // 32 nodes accepted, 33 rejected: 11 leaves F[0,1+i] a_(i mod 6) joined by
+    // 10 ORs in a balanced tree (3 x 11 - 1 = 32 nodes, height 6), then a
+    // negation on top
+    std::vector<smc_node> wide;
+    std::function<void(int, int)> build = [&](int lo, int hi) {
+        if (hi - lo == 1) {
+            wide.push_back(nd(SMC_NODE_ATOM, lo % 6));
+            wide.push_back(nd(SMC_NODE_EVENTUALLY, 0, 0.0, 1.0 + lo));
+            return;
+        }
+        const int mid = (lo + hi) / 2;
+        build(lo, mid);
+        build(mid, hi);
+        wide.push_back(nd(SMC_NODE_OR));
+    };
+    build(0, 11);
+    CHECK(wide.size() == 32 && compile_n(wide, 6, inf, np, err) == SMC_OK && np.n_nodes == 32 && np.height == 6);
+    CHECK(np.t_static == 11.0 && np.n_slots == 0 && slots_ok(np));
+    wide.push_back(nd(SMC_NODE_NOT));
+    CHECK(compile_n(wide, 6, inf, np, err) == SMC_E_UNSUPPORTED);
+
+    // atoms: 6 distinct accepted, 7 rejected
+    std::vector<smc_node> six;
+    for (int i = 0; i < 6; ++i) {
+        six.push_back(nd(SMC_NODE_ATOM, i));
+        six.push_back(nd(SMC_NODE_EVENTUALLY, 0, 0.0, 1.0));
+        if (i) six.push_back(nd(SMC_NODE_OR));
+    }
+    CHECK(compile_n(six, 6, inf, np, err) == SMC_OK);
+    std::vector<smc_node> seven = six;
+    seven.push_back(nd(SMC_NODE_ATOM, 6));
+    seven.push_back(nd(SMC_NODE_OR));
+    CHECK(compile_n(seven, 7, inf, np, err) == SMC_E_UNSUPPORTED);
+
+    // intervals: 0 <= lo <= hi, lo finite
+    const auto f_in_g = [&](double lo, double hi) {
+        return std::vector<smc_node>{nd(SMC_NODE_ATOM, 0), nd(SMC_NODE_EVENTUALLY, 0, lo, hi),
+                                     nd(SMC_NODE_ALWAYS, 0, 0.0, 1.0)};
+    };
+    CHECK(compile_n(f_in_g(2.0, 1.0), 1, inf, np, err) == SMC_E_INVALID_ARG);
+    CHECK(compile_n(f_in_g(-1.0, 1.0), 1, inf, np, err) == SMC_E_INVALID_ARG);
+    CHECK(compile_n(f_in_g(0.0, NAN), 1, inf, np, err) != SMC_OK);
+    CHECK(compile_n(f_in_g(inf, inf), 1, inf, np, err) != SMC_OK);
+    // unbounded: needs a finite t_max > 0 (the pessimistic rule stops there)
+    CHECK(compile_n(f_in_g(0.0, inf), 1, inf, np, err) == SMC_E_INVALID_ARG);
+    CHECK(compile_n(f_in_g(0.0, inf), 1, 0.0, np, err) == SMC_E_INVALID_ARG);
+    CHECK(compile_n(f_in_g(0.0, inf), 1, 50.0, np, err) == SMC_OK && np.unbounded && np.t_stop == 50.0 &&
+          std::isinf(np.t_static));
+}
+
 int main()
 {
     check_thresholds();
     check_tokens();
     check_formulas();
+    check_nested();
     if (failures) {
         printf("failures=%d\n", failures);
         return 1;
