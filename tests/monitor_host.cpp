@@ -16,7 +16,9 @@
 // formula goes to the trace monitor with its memo, run as the SSA kernel
 // runs it: positions recorded in order (their memo cells zeroed), the
 // formula evaluated at every knowledge point in turn, each result checked
-// against the evaluation without the memo (exit status 3 on a mismatch).
+// against the evaluation without the memo (exit status 3 on a mismatch);
+// "memo_sparse" the same at a pseudo-random third of the knowledge points
+// (the last one always), as the kernel's checks skip most of them.
 #include <math.h>
 #include <stdint.h>
 #include <stdio.h>
@@ -33,7 +35,11 @@
 
 int main(int argc, char **argv)
 {
-    const bool use_memo = argc > 1 && strcmp(argv[1], "memo") == 0;
+    // memo_sparse: the memo evaluated at a pseudo-random subset of the
+    // knowledge points (as the kernel's deferred, grouped checks take them),
+    // the last one always
+    const bool sparse = argc > 1 && strcmp(argv[1], "memo_sparse") == 0;
+    const bool use_memo = sparse || (argc > 1 && strcmp(argv[1], "memo") == 0);
     const bool force_nest = use_memo || (argc > 1 && strcmp(argv[1], "nest") == 0);
     int S, NA, NN;
     if (scanf("%d %d %d", &S, &NA, &NN) != 3) return 2;
@@ -96,6 +102,8 @@ int main(int argc, char **argv)
                     for (int sl = 0; sl < NP.n_slots; ++sl) memo[(size_t)sl * n + k] = 0;
                     const bool last = k == n - 1;
                     for (int half = 0; half < 2; ++half) {
+                        const uint32_t h = (uint32_t)(i * 2654435761u) ^ (uint32_t)((2 * k + half) * 40503u);
+                        if (sparse && !(last && half) && ((h >> 7) % 3u) != 0u) continue;
                         NestTrace U{t.data(), w.data(), 1, k, 0, 0.0, nullptr, 0};
                         if (half) {
                             U.end = last ? (closed ? 2 : 3) : 1;

@@ -8,9 +8,10 @@ boolean combinations, Next).  The GPU test of the replay kernel runs the
 same comparison on the device.  The same paths also go through the trace
 monitor (smc_nest.h) for every formula, and it alone serves the formulas
 nested beyond the unit monitor's shapes; and through the trace monitor
-with its memo, evaluated at every knowledge point in the SSA's order (the
-memo's results equal to the plain evaluation at each point), on the tiny
-paths and on long ones whose windows hold many positions."""
+with its memo, evaluated at every knowledge point in the SSA's order, or at
+a pseudo-random subset of them as the kernel's deferred checks take them
+(the memo's results equal to the plain evaluation at each point), on the
+tiny paths and on long ones whose windows hold many positions."""
 import math
 import os
 import random
@@ -80,12 +81,13 @@ def test_trace_monitor_memo_on_long_paths(exe, orc, fi):
         tmin = math.inf if closed else ts[-1] + rng.choice([0.0, 0.5, 3.0])
         paths.append((np.asarray(xs), np.asarray(ts, float), tmin, closed))
     out = _run(exe, prop, paths, 'memo')
+    assert _run(exe, prop, paths, 'memo_sparse') == out
     for (v, q), (xs, ts, tmin, closed) in zip(out[:8], paths[:8]):
         ov, oq = _oracle_decision_point(orc, prop, 1, xs, ts, tmin, closed)
         assert (v, q) == ({0: 1, 1: 2, 2: 0}[ov], oq), (FORMULAS[fi], v, q, ov, oq)
 
 
-@pytest.mark.parametrize('mode', ['library', 'nest', 'memo'])
+@pytest.mark.parametrize('mode', ['library', 'nest', 'memo', 'memo_sparse'])
 @pytest.mark.parametrize('fi', range(len(FORMULAS)))
 def test_monitor_matches_oracle_on_tiny_paths(exe, orc, fi, mode):
     # library: the unit monitor for the formulas of its fragment, the trace
